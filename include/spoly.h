@@ -1,0 +1,236 @@
+/* spoly.h -- C ABI of the GB300-native specular-polynomial solver.
+ *
+ * The library finds every admissible specular path between two fixed
+ * endpoints (separators x0 and x_{k+1}) through a candidate chain of k
+ * triangles with barycentrically interpolated vertex normals, following
+ * "Specular Polynomials" (Fan et al. 2024):
+ *   - problem statement: Sec. 3.1 (Eq. eq_xi, eq_ni, eq_ch);
+ *   - bivariate systems: Sec. 3.5 (R: Eq. eq_coplane + eq_pf_result,
+ *     T: Eq. eq_coplane + eq_cpf_result);
+ *   - elimination: Sec. 5.1 (Bezout matrix, Eq. eq_bezout);
+ *   - univariate phase: Sec. 5.2 (Laplace expansion + recursive-derivative
+ *     isolation for one bounce; determinant bisection for k bounces);
+ *   - path phase: Sec. 5.3 (u recovery, path-space check, in-triangle test).
+ *
+ * Conventions for every entry point
+ *   - All inputs are plain pointers plus sizes.  Each input struct says
+ *     whether its pointers are host or device memory (`on_device`).  The
+ *     caller owns every input buffer and keeps it valid until the call
+ *     returns (or, with SPOLY_SOLVE_ASYNC, until the context's stream has
+ *     passed the enqueued work).
+ *   - The library owns its handles (spoly_ctx, spoly_chains,
+ *     spoly_solution_set) and the device memory behind them; free them with
+ *     the matching *_destroy / *_free call.  Handles may be reused across
+ *     calls, which keeps allocation out of steady-state loops.
+ *   - All device work is enqueued on the context's CUDA stream.
+ *   - Every call returns a spoly_status; nothing throws across the ABI.  On
+ *     an error the context keeps a message (spoly_last_error).  Errors:
+ *       SPOLY_EINVAL       bad pointer, shape or value (message names it)
+ *       SPOLY_ENOMEM       device allocation failed
+ *       SPOLY_ECUDA        a CUDA call failed (message has the CUDA error)
+ *       SPOLY_ECAPACITY    the caller's output buffer is too small;
+ *                          *n_total holds the required count and nothing is
+ *                          silently truncated
+ *       SPOLY_ETIMEOUT     a bounded device-side wait gave up
+ *       SPOLY_EUNSUPPORTED bounce count or scattering type not built
+ */
+#ifndef SPOLY_H_
+#define SPOLY_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t spoly_status;
+#define SPOLY_OK 0
+#define SPOLY_EINVAL (-1)
+#define SPOLY_ENOMEM (-2)
+#define SPOLY_ECUDA (-3)
+#define SPOLY_ECAPACITY (-4)
+#define SPOLY_ETIMEOUT (-5)
+#define SPOLY_EUNSUPPORTED (-6)
+
+/* Scattering type per bounce (Sec. 3.5, Heckbert notation). */
+#define SPOLY_R 0 /* reflection */
+#define SPOLY_T 1 /* refraction */
+
+/* Path flags. */
+#define SPOLY_FLAG_ILL_COND 1u      /* |r'(v*)| / sum|r_i| < 1e-8, or a tangent root */
+#define SPOLY_FLAG_EDGE 2u          /* min(u, v, 1-u-v) within 1e-7 of the edge */
+#define SPOLY_FLAG_BACKFACE 4u      /* (x0 - x1) . n < 0 */
+#define SPOLY_FLAG_NEWTON 8u        /* refined by path-space Newton (k = 2) */
+#define SPOLY_FLAG_SQRT_SPLIT 16u   /* rational sqrt piece split (k = 2, T) */
+#define SPOLY_FLAG_TANGENT 32u      /* root found at a critical point of r */
+
+typedef struct spoly_ctx spoly_ctx;
+typedef struct spoly_chains spoly_chains;
+typedef struct spoly_solution_set spoly_solution_set;
+
+/* Triangles (Sec. 3.1, D1): FP64 SoA of shape [18][n_tris], rows
+ * p0x p0y p0z p1x p1y p1z p2x p2y p2z n0x n0y n0z n1x n1y n1z n2x n2y n2z,
+ * row-major, n_tris contiguous doubles per row.  Normals need not be unit
+ * length; they are interpolated unnormalised (Eq. eq_ni). */
+typedef struct {
+  const double* tri;
+  int64_t n_tris;
+  int32_t on_device; /* 1: device pointer, 0: host pointer (copied in) */
+  int32_t reserved;
+} spoly_mesh;
+
+/* Endpoint queries (Sec. 3.1, D2): one row per query q.
+ *   x_first[q][3] = x0, x_last[q][3] = x_{k+1} (FP64)
+ *   eta[q][3]     = eta_0 .. eta_k, IOR of the outgoing side of each vertex
+ *                   (Sec. 3.1); reflection ignores it
+ *   types[q][2]   = SPOLY_R / SPOLY_T per bounce
+ *   k[q]          = bounce count (1 is built; 2 returns SPOLY_EUNSUPPORTED) */
+typedef struct {
+  const double* x_first;
+  const double* x_last;
+  const double* eta;
+  const int32_t* types;
+  const int32_t* k;
+  int64_t n_queries;
+  int32_t on_device;
+  int32_t reserved;
+} spoly_queries;
+
+/* Candidate construction (stands in for the tuple pruning of Sec. 6). */
+#define SPOLY_CHAINS_ALL 0      /* every (query, triangle) pair */
+#define SPOLY_CHAINS_CONE 1     /* pairs passing a conservative direction-box test */
+#define SPOLY_CHAINS_EXPLICIT 2 /* caller's list */
+
+typedef struct {
+  int32_t mode;
+  int32_t reserved;
+  int32_t tri_begin; /* triangle range [tri_begin, tri_end); tri_end <= 0: all */
+  int32_t tri_end;
+  double margin;     /* CONE: slack added to every unit-direction box (>= 0) */
+  const int32_t* explicit_chains; /* EXPLICIT: [n][3] (query, tri0, tri1) */
+  int64_t n_explicit;
+  int32_t explicit_on_device;
+  int32_t reserved2;
+} spoly_chain_opts;
+
+/* Solve options. */
+#define SPOLY_PLAIN_FP64 0 /* every step in FP64 */
+#define SPOLY_MIXED 1      /* FP64 construction of a, b and the Bezout entries;
+                              FP32 Laplace + isolation; FP64 polish and checks */
+#define SPOLY_SOLVE_ASYNC 1  /* do not synchronise or read counters back */
+#define SPOLY_SOLVE_TIMING 2 /* record CUDA events around the solve's phases */
+
+typedef struct {
+  int32_t precision;       /* SPOLY_PLAIN_FP64 or SPOLY_MIXED */
+  int32_t flags;           /* SPOLY_SOLVE_ASYNC */
+  int64_t path_capacity;   /* initial path buffer size (0: automatic) */
+} spoly_solve_opts;
+
+/* One admissible path (104 bytes).  For k = 1, tri[1] = -1 and the second
+ * vertex entries are zero. */
+typedef struct {
+  int32_t query;
+  int32_t tri[2];
+  int32_t reserved;
+  double uv[2][2]; /* (u_i, v_i) of each specular vertex */
+  double x[2][3];  /* world position of each specular vertex */
+  float residual;  /* max_i |h_i x n_i| / (|h_i| |n_i|) */
+  uint32_t flags;  /* SPOLY_FLAG_* */
+} spoly_path;
+
+/* Counters of one solve. */
+typedef struct {
+  int64_t candidates;   /* chains solved */
+  int64_t degenerate;   /* r(v) vanished identically or no u-degree */
+  int64_t v_roots;      /* roots of r(v) isolated on [-1e-6, 1 + 1e-6] */
+  int64_t queued;       /* brackets sent to the FP64 polish */
+  int64_t prefiltered;  /* brackets whose u lies far outside the triangle */
+  int64_t polish_lost;  /* brackets with no FP64 sign change */
+  int64_t u_roots;      /* (u, v) pairs checked in path space */
+  int64_t admissible;   /* paths returned */
+  int64_t flagged;      /* returned paths with SPOLY_FLAG_ILL_COND */
+  int64_t reserved[7];
+} spoly_counters;
+
+/* Creates a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Errors: EINVAL (out NULL), ECUDA (bad device). */
+spoly_status spoly_ctx_create(int device, void* cuda_stream, spoly_ctx** out);
+
+/* Synchronises the stream and frees the context and its scratch.  Handles
+ * created from it must be freed before. */
+spoly_status spoly_ctx_destroy(spoly_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* spoly_last_error(const spoly_ctx* ctx);
+
+/* Builds the candidate chain list (query, tri0, tri1) on the device.
+ * ALL enumerates every (query, triangle) pair with the query index fastest
+ * (consecutive chains share a triangle); CONE keeps the pairs whose conservative box of outgoing unit
+ * directions over the triangle (reflected or refracted per the query,
+ * interval arithmetic over the triangle's bounding box and normal range)
+ * overlaps the box of unit directions from the triangle toward x_{k+1};
+ * EXPLICIT copies the caller's list after a bounds check.  *inout: NULL to
+ * allocate a new handle, or a handle to reuse.  The call synchronises once
+ * to read the chain count.  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED
+ * (CONE with k != 1). */
+spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
+                                const spoly_chain_opts* opts, spoly_chains** inout);
+
+/* Number of chains in a chain list. */
+spoly_status spoly_chains_count(const spoly_chains* chains, int64_t* n);
+
+/* Copies the chain list [n][3] int32 into dst (host or device).  Errors:
+ * ECAPACITY (capacity < count; *n_total = count). */
+spoly_status spoly_chains_copy(spoly_ctx* ctx, const spoly_chains* chains, int32_t* dst, int64_t capacity,
+                               int64_t* n_total, int32_t dst_is_device);
+
+/* Frees a chain list. */
+spoly_status spoly_chains_free(spoly_chains* chains);
+
+/* Solves every chain (Sec. 5.3 pipeline) and keeps the admissible paths in
+ * a library-owned solution set.  mesh and q must be the ones the chains were
+ * built from.  *inout: NULL for a new set or a set to reuse.  Unless
+ * SPOLY_SOLVE_ASYNC is set, the call synchronises, grows the path buffer and
+ * re-runs the path phase if it overflowed, and returns with counters valid.
+ * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (k = 2 chains). */
+spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
+                         const spoly_chains* chains, const spoly_solve_opts* opts,
+                         spoly_solution_set** inout);
+
+/* Copies up to `capacity` paths to dst (host or device) in the device's
+ * completion order; *n_total receives the path count.  Errors: ECAPACITY
+ * when capacity < *n_total (the first `capacity` paths are still copied). */
+spoly_status spoly_paths(spoly_ctx* ctx, const spoly_solution_set* set, spoly_path* dst, int64_t capacity,
+                         int64_t* n_total, int32_t dst_is_device);
+
+/* Counters of the last solve into `set` (synchronises the context stream). */
+spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_counters* out);
+
+/* Device time of the last solve's phases, measured with CUDA events on the
+ * context stream when the solve set SPOLY_SOLVE_TIMING: ms[0] = isolation
+ * (coefficient, elimination and univariate phases, both isolation kernels),
+ * ms[1] = FP64 polish and path phase.  n >= 2.  Synchronises on the last
+ * event.  Errors: EINVAL if the solve was not timed. */
+spoly_status spoly_phase_ms(spoly_ctx* ctx, const spoly_solution_set* set, float* ms, int32_t n);
+
+/* Peak-throughput microbenchmark of a scalar pipe on the context's device:
+ * SPOLY_PEAK_FP32_FMA or SPOLY_PEAK_FP64_FMA.  *tflops receives the best
+ * TFLOP/s (2 flop per FMA) over timed launches of independent FMA chains on
+ * every SM.  Allocates and frees a small device buffer.  The roofline
+ * fractions the project reports use these numbers as denominators. */
+#define SPOLY_PEAK_FP32_FMA 0
+#define SPOLY_PEAK_FP64_FMA 1
+spoly_status spoly_measure_peak(spoly_ctx* ctx, int32_t kind, double* tflops);
+
+/* Frees a solution set. */
+spoly_status spoly_solution_free(spoly_solution_set* set);
+
+/* Library version string. */
+const char* spoly_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPOLY_H_ */

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of libspoly (include/spoly.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA
+library.  Functions keep the C names.  Device arrays are torch CUDA tensors
+(PyTorch supplies device memory and streams); host arrays are numpy arrays.
+There is no fallback: if the compiled library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libspoly.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "spoly.h")
+
+SPOLY_OK = 0
+SPOLY_EINVAL = -1
+SPOLY_ENOMEM = -2
+SPOLY_ECUDA = -3
+SPOLY_ECAPACITY = -4
+SPOLY_ETIMEOUT = -5
+SPOLY_EUNSUPPORTED = -6
+
+SPOLY_R = 0
+SPOLY_T = 1
+
+FLAG_ILL_COND = 1
+FLAG_EDGE = 2
+FLAG_BACKFACE = 4
+FLAG_NEWTON = 8
+FLAG_SQRT_SPLIT = 16
+FLAG_TANGENT = 32
+
+CHAINS_ALL = 0
+CHAINS_CONE = 1
+CHAINS_EXPLICIT = 2
+
+PLAIN_FP64 = 0
+MIXED = 1
+SOLVE_ASYNC = 1
+SOLVE_TIMING = 2
+PEAK_FP32_FMA = 0
+PEAK_FP64_FMA = 1
+
+c_void_p = ctypes.c_void_p
+c_int32 = ctypes.c_int32
+c_int64 = ctypes.c_int64
+
+
+class spoly_mesh(ctypes.Structure):
+    _fields_ = [("tri", c_void_p), ("n_tris", c_int64), ("on_device", c_int32), ("reserved", c_int32)]
+
+
+class spoly_queries(ctypes.Structure):
+    _fields_ = [("x_first", c_void_p), ("x_last", c_void_p), ("eta", c_void_p), ("types", c_void_p),
+                ("k", c_void_p), ("n_queries", c_int64), ("on_device", c_int32), ("reserved", c_int32)]
+
+
+class spoly_chain_opts(ctypes.Structure):
+    _fields_ = [("mode", c_int32), ("reserved", c_int32), ("tri_begin", c_int32), ("tri_end", c_int32),
+                ("margin", ctypes.c_double), ("explicit_chains", c_void_p), ("n_explicit", c_int64),
+                ("explicit_on_device", c_int32), ("reserved2", c_int32)]
+
+
+class spoly_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("flags", c_int32), ("path_capacity", c_int64)]
+
+
+class spoly_path(ctypes.Structure):
+    _fields_ = [("query", c_int32), ("tri", c_int32 * 2), ("reserved", c_int32),
+                ("uv", ctypes.c_double * 4), ("x", ctypes.c_double * 6),
+                ("residual", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class spoly_counters(ctypes.Structure):
+    _fields_ = [(n, c_int64) for n in ("candidates", "degenerate", "v_roots", "queued", "prefiltered",
+                                       "polish_lost", "u_roots", "admissible", "flagged")] + \
+               [("reserved", c_int64 * 7)]
+
+
+PATH_DTYPE = np.dtype([("query", "<i4"), ("tri", "<i4", (2,)), ("reserved", "<i4"), ("uv", "<f8", (4,)),
+                       ("x", "<f8", (6,)), ("residual", "<f4"), ("flags", "<u4")])
+assert PATH_DTYPE.itemsize == ctypes.sizeof(spoly_path) == 104
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the entry points declared in include/spoly.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:spoly_status|const char\*|void)\s+(spoly_\w+)\s*\(", text, re.M)))
+
+
+def load():
+    """Loads libspoly.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (or "
+                           "python paper_2405_13409_gb300/build.py) first; there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    sig = {
+        "spoly_version": ([], ctypes.c_char_p),
+        "spoly_ctx_create": ([ctypes.c_int, P, ctypes.POINTER(P)], c_int32),
+        "spoly_ctx_destroy": ([P], c_int32),
+        "spoly_last_error": ([P], ctypes.c_char_p),
+        "spoly_build_chains": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries),
+                                ctypes.POINTER(spoly_chain_opts), ctypes.POINTER(P)], c_int32),
+        "spoly_chains_count": ([P, ctypes.POINTER(c_int64)], c_int32),
+        "spoly_chains_copy": ([P, P, P, c_int64, ctypes.POINTER(c_int64), c_int32], c_int32),
+        "spoly_chains_free": ([P], c_int32),
+        "spoly_solve": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P,
+                         ctypes.POINTER(spoly_solve_opts), ctypes.POINTER(P)], c_int32),
+        "spoly_paths": ([P, P, P, c_int64, ctypes.POINTER(c_int64), c_int32], c_int32),
+        "spoly_stats": ([P, P, ctypes.POINTER(spoly_counters)], c_int32),
+        "spoly_solution_free": ([P], c_int32),
+        "spoly_phase_ms": ([P, P, ctypes.POINTER(ctypes.c_float), c_int32], c_int32),
+        "spoly_measure_peak": ([P, c_int32, ctypes.POINTER(ctypes.c_double)], c_int32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+class SpolyError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"spoly status {status}: {msg}")
+        self.status = status
+
+
+def _ptr(x) -> int:
+    """Raw address of a numpy array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+def _on_device(x) -> int:
+    return 0 if isinstance(x, np.ndarray) else int(x.is_cuda)
+
+
+class Context:
+    """Owns a spoly_ctx bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        h = c_void_p()
+        st = self.lib.spoly_ctx_create(int(device), c_void_p(stream or 0), ctypes.byref(h))
+        if st != SPOLY_OK:
+            raise SpolyError(st, "spoly_ctx_create failed")
+        self.h = h
+        self._keep = []
+
+    def check(self, st: int, what: str):
+        if st != SPOLY_OK:
+            raise SpolyError(st, f"{what}: {self.lib.spoly_last_error(self.h).decode()}")
+
+    def close(self):
+        if self.h:
+            self.lib.spoly_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def mesh(tri) -> spoly_mesh:
+        return spoly_mesh(_ptr(tri), int(tri.shape[1]), _on_device(tri), 0)
+
+    @staticmethod
+    def queries(x_first, x_last, eta, types, k) -> spoly_queries:
+        return spoly_queries(_ptr(x_first), _ptr(x_last), _ptr(eta), _ptr(types), _ptr(k),
+                             int(x_first.shape[0]), _on_device(x_first), 0)
+
+    def spoly_build_chains(self, mesh: spoly_mesh, q: spoly_queries, mode: int, margin: float = 1e-3,
+                           explicit=None, tri_range=(0, 0), reuse=None):
+        opts = spoly_chain_opts(mode, 0, int(tri_range[0]), int(tri_range[1]), float(margin),
+                                _ptr(explicit) if explicit is not None else 0,
+                                int(explicit.shape[0]) if explicit is not None else 0,
+                                _on_device(explicit) if explicit is not None else 0, 0)
+        h = c_void_p(reuse.value if reuse is not None else None)
+        self.check(self.lib.spoly_build_chains(self.h, ctypes.byref(mesh), ctypes.byref(q), ctypes.byref(opts),
+                                               ctypes.byref(h)), "spoly_build_chains")
+        return h
+
+    def spoly_chains_count(self, chains) -> int:
+        n = c_int64()
+        self.check(self.lib.spoly_chains_count(chains, ctypes.byref(n)), "spoly_chains_count")
+        return int(n.value)
+
+    def spoly_chains_copy(self, chains) -> np.ndarray:
+        n = self.spoly_chains_count(chains)
+        out = np.zeros((n, 3), dtype=np.int32)
+        tot = c_int64()
+        self.check(self.lib.spoly_chains_copy(self.h, chains, c_void_p(out.ctypes.data), n, ctypes.byref(tot), 0),
+                   "spoly_chains_copy")
+        return out
+
+    def spoly_chains_free(self, chains):
+        self.lib.spoly_chains_free(chains)
+
+    def spoly_solve(self, mesh: spoly_mesh, q: spoly_queries, chains, precision: int = MIXED, flags: int = 0,
+                    path_capacity: int = 0, reuse=None):
+        opts = spoly_solve_opts(int(precision), int(flags), int(path_capacity))
+        h = c_void_p(reuse.value if reuse is not None else None)
+        self.check(self.lib.spoly_solve(self.h, ctypes.byref(mesh), ctypes.byref(q), chains, ctypes.byref(opts),
+                                        ctypes.byref(h)), "spoly_solve")
+        return h
+
+    def spoly_paths(self, sol) -> np.ndarray:
+        """All paths of a solution set as a PATH_DTYPE array (host)."""
+        tot = c_int64()
+        st = self.lib.spoly_paths(self.h, sol, None, 0, ctypes.byref(tot), 0)
+        if st not in (SPOLY_OK, SPOLY_ECAPACITY) or (st == SPOLY_ECAPACITY and tot.value == 0):
+            self.check(st, "spoly_paths")
+        out = np.zeros(int(tot.value), dtype=PATH_DTYPE)
+        if tot.value:
+            self.check(self.lib.spoly_paths(self.h, sol, c_void_p(out.ctypes.data), int(tot.value),
+                                            ctypes.byref(tot), 0), "spoly_paths")
+        return out
+
+    def spoly_paths_into(self, sol, dst, capacity: int) -> int:
+        """Copies up to `capacity` paths into a host or device buffer; returns the count."""
+        tot = c_int64()
+        st = self.lib.spoly_paths(self.h, sol, c_void_p(_ptr(dst)), int(capacity), ctypes.byref(tot),
+                                  _on_device(dst))
+        if st != SPOLY_ECAPACITY:
+            self.check(st, "spoly_paths")
+        return int(tot.value)
+
+    def spoly_stats(self, sol) -> dict:
+        c = spoly_counters()
+        self.check(self.lib.spoly_stats(self.h, sol, ctypes.byref(c)), "spoly_stats")
+        return {n: int(getattr(c, n)) for n, _ in spoly_counters._fields_ if n != "reserved"}
+
+    def spoly_solution_free(self, sol):
+        self.lib.spoly_solution_free(sol)
+
+    def spoly_phase_ms(self, sol) -> tuple:
+        ms = (ctypes.c_float * 2)()
+        self.check(self.lib.spoly_phase_ms(self.h, sol, ms, 2), "spoly_phase_ms")
+        return float(ms[0]), float(ms[1])
+
+    def spoly_measure_peak(self, kind: int) -> float:
+        t = ctypes.c_double()
+        self.check(self.lib.spoly_measure_peak(self.h, int(kind), ctypes.byref(t)), "spoly_measure_peak")
+        return float(t.value)

@@ -1,0 +1,518 @@
+// C ABI of the specular-polynomial library (declared in include/spoly.h).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "k1.cuh"
+
+using namespace spoly;
+
+namespace spoly {
+double measure_fma_peak(int kind, int num_sms, cudaStream_t st, cudaError_t* err);
+}
+
+namespace {
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+}  // namespace
+
+struct spoly_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  char err[512] = {0};
+  DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
+  DevBuf boxes, flag;                    // cone cull scratch
+};
+
+struct spoly_chains {
+  DevBuf buf;        // [cap][3] int32
+  int64_t n = 0;
+  DevBuf counter;    // unsigned long long + int32 error flag
+};
+
+struct spoly_solution_set {
+  DevBuf queue;      // RootItem[queue_cap]
+  int64_t queue_cap = 0;
+  DevBuf paths;      // spoly_path[path_cap]
+  int64_t path_cap = 0;
+  DevBuf side;       // int32[side_cap] chains for the generic-size kernel
+  int64_t side_cap = 0;
+  DevBuf counters;   // unsigned long long[C_COUNT]
+  unsigned long long host[C_COUNT] = {0};
+  bool host_valid = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing
+  bool timed = false;
+};
+
+namespace {
+
+spoly_status fail(spoly_ctx* ctx, spoly_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+spoly_status cuda_fail(spoly_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, SPOLY_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(ctx, SPOLY_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+// Device views of mesh / queries, staging host arrays into context buffers.
+spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, MeshView* mv,
+                          QueryView* qv) {
+  if (!mesh || !q) return fail(ctx, SPOLY_EINVAL, "mesh and queries are required");
+  if (!mesh->tri || mesh->n_tris <= 0 || mesh->n_tris > INT32_MAX)
+    return fail(ctx, SPOLY_EINVAL, "mesh: tri must be non-null and 0 < n_tris <= 2^31-1 (got %lld)",
+                (long long)mesh->n_tris);
+  if (!q->x_first || !q->x_last || !q->eta || !q->types || !q->k || q->n_queries <= 0 ||
+      q->n_queries > INT32_MAX)
+    return fail(ctx, SPOLY_EINVAL, "queries: all arrays must be non-null and 0 < n_queries <= 2^31-1");
+  const int64_t T = mesh->n_tris, Q = q->n_queries;
+  if (mesh->on_device) {
+    mv->tri = mesh->tri;
+  } else {
+    for (int64_t i = 0; i < 18 * T; ++i)
+      if (!std::isfinite(mesh->tri[i]))
+        return fail(ctx, SPOLY_EINVAL, "mesh: non-finite value at row %lld, triangle %lld", (long long)(i / T),
+                    (long long)(i % T));
+    CK(ctx->mesh.ensure(size_t(18 * T) * sizeof(double)), "mesh staging");
+    CK(cudaMemcpyAsync(ctx->mesh.p, mesh->tri, size_t(18 * T) * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "mesh copy");
+    mv->tri = static_cast<const double*>(ctx->mesh.p);
+  }
+  mv->n_tris = T;
+  if (q->on_device) {
+    qv->x_first = q->x_first;
+    qv->x_last = q->x_last;
+    qv->eta = q->eta;
+    qv->types = q->types;
+    qv->k = q->k;
+  } else {
+    for (int64_t i = 0; i < 3 * Q; ++i)
+      if (!std::isfinite(q->x_first[i]) || !std::isfinite(q->x_last[i]) || !std::isfinite(q->eta[i]))
+        return fail(ctx, SPOLY_EINVAL, "queries: non-finite value in query %lld", (long long)(i / 3));
+    for (int64_t i = 0; i < Q; ++i) {
+      if (q->k[i] < 1 || q->k[i] > 2) return fail(ctx, SPOLY_EINVAL, "queries: k[%lld] = %d", (long long)i, q->k[i]);
+      if ((q->types[2 * i] != SPOLY_R && q->types[2 * i] != SPOLY_T))
+        return fail(ctx, SPOLY_EINVAL, "queries: types[%lld] = %d", (long long)i, q->types[2 * i]);
+    }
+    struct {
+      DevBuf* b;
+      const void* src;
+      size_t n;
+    } items[] = {{&ctx->xf, q->x_first, size_t(3 * Q) * 8}, {&ctx->xl, q->x_last, size_t(3 * Q) * 8},
+                 {&ctx->eta, q->eta, size_t(3 * Q) * 8},    {&ctx->types, q->types, size_t(2 * Q) * 4},
+                 {&ctx->kk, q->k, size_t(Q) * 4}};
+    for (auto& it : items) {
+      CK(it.b->ensure(it.n), "query staging");
+      CK(cudaMemcpyAsync(it.b->p, it.src, it.n, cudaMemcpyHostToDevice, ctx->stream), "query copy");
+    }
+    qv->x_first = static_cast<const double*>(ctx->xf.p);
+    qv->x_last = static_cast<const double*>(ctx->xl.p);
+    qv->eta = static_cast<const double*>(ctx->eta.p);
+    qv->types = static_cast<const int32_t*>(ctx->types.p);
+    qv->k = static_cast<const int32_t*>(ctx->kk.p);
+  }
+  qv->n = Q;
+  return SPOLY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* spoly_version(void) { return "spoly-gb300 0.1 (sm_103a)"; }
+
+spoly_status spoly_ctx_create(int device, void* cuda_stream, spoly_ctx** out) {
+  if (!out) return SPOLY_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SPOLY_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return SPOLY_ECUDA;
+  spoly_ctx* ctx = new (std::nothrow) spoly_ctx();
+  if (!ctx) return SPOLY_ENOMEM;
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return SPOLY_ECUDA;
+  }
+  *out = ctx;
+  return SPOLY_OK;
+}
+
+spoly_status spoly_ctx_destroy(spoly_ctx* ctx) {
+  if (!ctx) return SPOLY_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (DevBuf* b : {&ctx->mesh, &ctx->xf, &ctx->xl, &ctx->eta, &ctx->types, &ctx->kk, &ctx->boxes, &ctx->flag})
+    b->release();
+  delete ctx;
+  return SPOLY_OK;
+}
+
+const char* spoly_last_error(const spoly_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
+                                const spoly_chain_opts* opts, spoly_chains** inout) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!opts || !inout) return fail(ctx, SPOLY_EINVAL, "opts and inout are required");
+  CK(cudaSetDevice(ctx->device), "set device");
+  MeshView mv;
+  QueryView qv;
+  spoly_status st = stage_inputs(ctx, mesh, q, &mv, &qv);
+  if (st != SPOLY_OK) return st;
+  int32_t tb = opts->tri_begin, te = opts->tri_end <= 0 ? int32_t(mv.n_tris) : opts->tri_end;
+  if (tb < 0 || te > mv.n_tris || tb >= te)
+    return fail(ctx, SPOLY_EINVAL, "triangle range [%d, %d) outside [0, %lld)", tb, te, (long long)mv.n_tris);
+  if (opts->mode == SPOLY_CHAINS_CONE && !(opts->margin >= 0.0))
+    return fail(ctx, SPOLY_EINVAL, "cone margin must be >= 0");
+  spoly_chains* ch = *inout;
+  bool fresh = false;
+  if (!ch) {
+    ch = new (std::nothrow) spoly_chains();
+    if (!ch) return fail(ctx, SPOLY_ENOMEM, "chains handle");
+    fresh = true;
+  }
+  auto bail = [&](spoly_status s) {
+    if (fresh) {
+      ch->buf.release();
+      ch->counter.release();
+      delete ch;
+    }
+    return s;
+  };
+  if (ch->counter.ensure(16) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain counter"));
+  ChainParams P{};
+  P.mesh = mv;
+  P.qv = qv;
+  P.tri_begin = tb;
+  P.tri_count = te - tb;
+  P.margin = opts->margin;
+  P.count = static_cast<unsigned long long*>(ch->counter.p);
+  P.error = reinterpret_cast<int32_t*>(static_cast<char*>(ch->counter.p) + 8);
+  cudaError_t e = cudaMemsetAsync(ch->counter.p, 0, 16, ctx->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
+  const int64_t pairs = qv.n * int64_t(P.tri_count);
+  if (opts->mode == SPOLY_CHAINS_ALL) {
+    if (ch->buf.ensure(size_t(pairs) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+    P.out = static_cast<int32_t*>(ch->buf.p);
+    P.cap = pairs;
+    e = launch_chains_all(P, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_all"));
+    ch->n = pairs;
+  } else if (opts->mode == SPOLY_CHAINS_EXPLICIT) {
+    const int64_t n = opts->n_explicit;
+    if (!opts->explicit_chains || n <= 0) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain list is empty"));
+    if (ch->buf.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+    P.out = static_cast<int32_t*>(ch->buf.p);
+    P.cap = n;
+    const int32_t* src = opts->explicit_chains;
+    DevBuf tmp;
+    if (!opts->explicit_on_device) {
+      if (tmp.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
+      e = cudaMemcpyAsync(tmp.p, src, size_t(n) * 12, cudaMemcpyHostToDevice, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain copy"));
+      src = static_cast<const int32_t*>(tmp.p);
+    }
+    e = launch_chains_explicit(P, src, n, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit"));
+    int32_t herr = 0;
+    e = cudaMemcpyAsync(&herr, P.error, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    tmp.release();
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit sync"));
+    if (herr) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain %d references a missing query or triangle", herr - 1));
+    ch->n = n;
+  } else if (opts->mode == SPOLY_CHAINS_CONE) {
+    if (ctx->boxes.ensure(size_t(P.tri_count) * 12 * sizeof(float)) != cudaSuccess ||
+        ctx->flag.ensure(16) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "cone scratch"));
+    P.boxes = static_cast<float*>(ctx->boxes.p);
+    P.shared_x0 = static_cast<int32_t*>(ctx->flag.p);
+    // Capacity: start from 1/64 of the pairs, grow to the exact count if exceeded.
+    int64_t cap = ch->buf.bytes / 12;
+    const int64_t want = pairs / 64 + 4096;
+    if (cap < want) {
+      if (ch->buf.ensure(size_t(want) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+      cap = want;
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      P.out = static_cast<int32_t*>(ch->buf.p);
+      P.cap = cap;
+      e = launch_chains_cone(P, ctx->num_sms, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_cone"));
+      unsigned long long cnt = 0;
+      e = cudaMemcpyAsync(&cnt, P.count, 8, cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_cone sync"));
+      if (int64_t(cnt) <= cap) {
+        ch->n = int64_t(cnt);
+        break;
+      }
+      cap = int64_t(cnt);
+      if (ch->buf.ensure(size_t(cap) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+      e = cudaMemsetAsync(ch->counter.p, 0, 16, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
+    }
+  } else {
+    return bail(fail(ctx, SPOLY_EINVAL, "unknown chain mode %d", opts->mode));
+  }
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build_chains"));
+  *inout = ch;
+  return SPOLY_OK;
+}
+
+spoly_status spoly_chains_count(const spoly_chains* chains, int64_t* n) {
+  if (!chains || !n) return SPOLY_EINVAL;
+  *n = chains->n;
+  return SPOLY_OK;
+}
+
+spoly_status spoly_chains_copy(spoly_ctx* ctx, const spoly_chains* chains, int32_t* dst, int64_t capacity,
+                               int64_t* n_total, int32_t dst_is_device) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!chains || !n_total || (!dst && capacity > 0)) return fail(ctx, SPOLY_EINVAL, "bad arguments");
+  *n_total = chains->n;
+  const int64_t m = capacity < chains->n ? capacity : chains->n;
+  if (m > 0) {
+    CK(cudaMemcpyAsync(dst, chains->buf.p, size_t(m) * 12,
+                       dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
+       "chains copy");
+    CK(cudaStreamSynchronize(ctx->stream), "chains copy sync");
+  }
+  if (capacity < chains->n) return fail(ctx, SPOLY_ECAPACITY, "chains: capacity %lld < %lld", (long long)capacity,
+                                        (long long)chains->n);
+  return SPOLY_OK;
+}
+
+spoly_status spoly_chains_free(spoly_chains* chains) {
+  if (!chains) return SPOLY_EINVAL;
+  chains->buf.release();
+  chains->counter.release();
+  delete chains;
+  return SPOLY_OK;
+}
+
+spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
+                         const spoly_chains* chains, const spoly_solve_opts* opts, spoly_solution_set** inout) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!chains || !opts || !inout) return fail(ctx, SPOLY_EINVAL, "chains, opts and inout are required");
+  if (opts->precision != SPOLY_PLAIN_FP64 && opts->precision != SPOLY_MIXED)
+    return fail(ctx, SPOLY_EINVAL, "unknown precision %d", opts->precision);
+  CK(cudaSetDevice(ctx->device), "set device");
+  MeshView mv;
+  QueryView qv;
+  spoly_status st = stage_inputs(ctx, mesh, q, &mv, &qv);
+  if (st != SPOLY_OK) return st;
+  if (!q->on_device) {
+    for (int64_t i = 0; i < q->n_queries; ++i)
+      if (q->k[i] != 1) return fail(ctx, SPOLY_EUNSUPPORTED, "query %lld has k = %d; only k = 1 is built", (long long)i, q->k[i]);
+  }
+  spoly_solution_set* set = *inout;
+  bool fresh = false;
+  if (!set) {
+    set = new (std::nothrow) spoly_solution_set();
+    if (!set) return fail(ctx, SPOLY_ENOMEM, "solution set");
+    fresh = true;
+  }
+  auto bail = [&](spoly_status s) {
+    if (fresh) {
+      set->queue.release();
+      set->paths.release();
+      set->side.release();
+      set->counters.release();
+      delete set;
+    }
+    return s;
+  };
+  const int64_t nc = chains->n;
+  int64_t qcap = nc / 4 + 4096;
+  if (int64_t(set->queue.bytes / sizeof(RootItem)) > qcap) qcap = int64_t(set->queue.bytes / sizeof(RootItem));
+  int64_t pcap = opts->path_capacity > 0 ? opts->path_capacity : nc / 16 + 4096;
+  if (int64_t(set->paths.bytes / sizeof(spoly_path)) > pcap) pcap = int64_t(set->paths.bytes / sizeof(spoly_path));
+  int64_t scap = nc / 64 + 1024;
+  if (int64_t(set->side.bytes / sizeof(int32_t)) > scap) scap = int64_t(set->side.bytes / sizeof(int32_t));
+  if (set->side.ensure(size_t(scap) * sizeof(int32_t)) != cudaSuccess ||
+      set->queue.ensure(size_t(qcap) * sizeof(RootItem)) != cudaSuccess ||
+      set->paths.ensure(size_t(pcap) * sizeof(spoly_path)) != cudaSuccess ||
+      set->counters.ensure(C_COUNT * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(fail(ctx, SPOLY_ENOMEM, "solution buffers"));
+  set->queue_cap = qcap;
+  set->path_cap = pcap;
+  set->side_cap = scap;
+  set->host_valid = false;
+  K1Params P{};
+  P.mesh = mv;
+  P.qv = qv;
+  P.chains = static_cast<const int32_t*>(chains->buf.p);
+  P.n_chains = nc;
+  P.counters = static_cast<unsigned long long*>(set->counters.p);
+  cudaError_t e;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    P.queue = static_cast<RootItem*>(set->queue.p);
+    P.queue_cap = set->queue_cap;
+    P.side = static_cast<int32_t*>(set->side.p);
+    P.side_cap = set->side_cap;
+    P.paths = static_cast<spoly_path*>(set->paths.p);
+    P.path_cap = set->path_cap;
+    e = cudaMemsetAsync(set->counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
+    const bool timing = (opts->flags & SPOLY_SOLVE_TIMING) != 0;
+    if (timing && !set->ev[0])
+      for (auto& ev : set->ev)
+        if (cudaEventCreate(&ev) != cudaSuccess) return bail(fail(ctx, SPOLY_ECUDA, "event create"));
+    set->timed = timing;
+    if (timing) cudaEventRecord(set->ev[0], ctx->stream);
+    if (nc > 0) {
+      e = launch_k1_isolate(P, opts->precision, ctx->num_sms, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_isolate"));
+      if (timing) cudaEventRecord(set->ev[1], ctx->stream);
+      e = launch_k1_polish(P, ctx->num_sms, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
+    } else if (timing) {
+      cudaEventRecord(set->ev[1], ctx->stream);
+    }
+    if (timing) cudaEventRecord(set->ev[2], ctx->stream);
+    if (opts->flags & SPOLY_SOLVE_ASYNC) break;
+    e = cudaMemcpyAsync(set->host, set->counters.p, sizeof(set->host), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
+    set->host_valid = true;
+    const int64_t queued = int64_t(set->host[C_QUEUED]);
+    const int64_t paths = int64_t(set->host[C_ADMISSIBLE]);
+    const int64_t side = int64_t(set->host[C_SIDE]);
+    if (queued <= set->queue_cap && paths <= set->path_cap && side <= set->side_cap) break;
+    if (side > set->side_cap) {
+      if (set->side.ensure(size_t(side) * sizeof(int32_t)) != cudaSuccess)
+        return bail(fail(ctx, SPOLY_ENOMEM, "side queue growth"));
+      set->side_cap = side;
+    }
+    if (queued > set->queue_cap) {
+      if (set->queue.ensure(size_t(queued) * sizeof(RootItem)) != cudaSuccess)
+        return bail(fail(ctx, SPOLY_ENOMEM, "queue growth"));
+      set->queue_cap = queued;
+    }
+    if (paths > set->path_cap) {
+      if (set->paths.ensure(size_t(paths) * sizeof(spoly_path)) != cudaSuccess)
+        return bail(fail(ctx, SPOLY_ENOMEM, "path growth"));
+      set->path_cap = paths;
+    }
+    set->host_valid = false;
+  }
+  *inout = set;
+  return SPOLY_OK;
+}
+
+spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_counters* out) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!set || !out) return fail(ctx, SPOLY_EINVAL, "bad arguments");
+  unsigned long long h[C_COUNT];
+  CK(cudaMemcpyAsync(h, set->counters.p, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "stats");
+  CK(cudaStreamSynchronize(ctx->stream), "stats sync");
+  std::memset(out, 0, sizeof(*out));
+  out->candidates = int64_t(h[C_CANDIDATES]);
+  out->degenerate = int64_t(h[C_DEGENERATE]);
+  out->v_roots = int64_t(h[C_VROOTS]);
+  out->queued = int64_t(h[C_QUEUED]);
+  out->prefiltered = int64_t(h[C_PREFILTERED]);
+  out->polish_lost = int64_t(h[C_POLISH_LOST]);
+  out->u_roots = int64_t(h[C_UROOTS]);
+  out->admissible = int64_t(h[C_ADMISSIBLE]);
+  out->flagged = int64_t(h[C_FLAGGED]);
+  return SPOLY_OK;
+}
+
+spoly_status spoly_paths(spoly_ctx* ctx, const spoly_solution_set* set, spoly_path* dst, int64_t capacity,
+                         int64_t* n_total, int32_t dst_is_device) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!set || !n_total || (!dst && capacity > 0)) return fail(ctx, SPOLY_EINVAL, "bad arguments");
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, static_cast<unsigned long long*>(set->counters.p) + C_ADMISSIBLE, 8,
+                     cudaMemcpyDeviceToHost, ctx->stream),
+     "path count");
+  CK(cudaStreamSynchronize(ctx->stream), "path count sync");
+  *n_total = int64_t(cnt);
+  if (int64_t(cnt) > set->path_cap)
+    return fail(ctx, SPOLY_ECAPACITY, "solution set overflowed (%lld paths, buffer %lld); re-run spoly_solve "
+                "without SPOLY_SOLVE_ASYNC", (long long)cnt, (long long)set->path_cap);
+  int64_t m = capacity < int64_t(cnt) ? capacity : int64_t(cnt);
+  if (m > 0) {
+    CK(cudaMemcpyAsync(dst, set->paths.p, size_t(m) * sizeof(spoly_path),
+                       dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
+       "path copy");
+    CK(cudaStreamSynchronize(ctx->stream), "path copy sync");
+  }
+  if (capacity < int64_t(cnt))
+    return fail(ctx, SPOLY_ECAPACITY, "paths: capacity %lld < %lld", (long long)capacity, (long long)cnt);
+  return SPOLY_OK;
+}
+
+spoly_status spoly_phase_ms(spoly_ctx* ctx, const spoly_solution_set* set, float* ms, int32_t n) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!set || !ms || n < 2) return fail(ctx, SPOLY_EINVAL, "bad arguments");
+  if (!set->timed) return fail(ctx, SPOLY_EINVAL, "the last solve did not set SPOLY_SOLVE_TIMING");
+  CK(cudaEventSynchronize(set->ev[2]), "phase timing");
+  CK(cudaEventElapsedTime(&ms[0], set->ev[0], set->ev[1]), "phase timing");
+  CK(cudaEventElapsedTime(&ms[1], set->ev[1], set->ev[2]), "phase timing");
+  return SPOLY_OK;
+}
+
+spoly_status spoly_measure_peak(spoly_ctx* ctx, int32_t kind, double* tflops) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!tflops || (kind != SPOLY_PEAK_FP32_FMA && kind != SPOLY_PEAK_FP64_FMA))
+    return fail(ctx, SPOLY_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->device), "set device");
+  cudaError_t e = cudaSuccess;
+  *tflops = measure_fma_peak(kind, ctx->num_sms, ctx->stream, &e);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "peak microbenchmark");
+  return SPOLY_OK;
+}
+
+spoly_status spoly_solution_free(spoly_solution_set* set) {
+  if (!set) return SPOLY_EINVAL;
+  for (auto& ev : set->ev)
+    if (ev) cudaEventDestroy(ev);
+  set->side.release();
+  set->queue.release();
+  set->paths.release();
+  set->counters.release();
+  delete set;
+  return SPOLY_OK;
+}
+
+}  // extern "C"

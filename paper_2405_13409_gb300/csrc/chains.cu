@@ -1,0 +1,318 @@
+// Candidate chain construction: ALL, EXPLICIT and the conservative CONE cull.
+//
+// The paper takes its triangle tuples from an external pruning step (Sec. 3.1
+// and Sec. 6 cite a path-space hierarchy with interval-arithmetic bounds).
+// CONE stands in for it: a pair (query, triangle) survives only if the box of
+// outgoing unit directions over the triangle (reflected or refracted per the
+// query, by interval arithmetic over the triangle's bounding box and vertex
+// normal range) overlaps the box of unit directions from the triangle's
+// bounding box toward x_{k+1}.  Any solution x1 has its outgoing direction in
+// both boxes, so the test never discards an admissible path (margin absorbs
+// FP rounding).
+#include "k1.cuh"
+
+namespace spoly {
+
+namespace {
+
+struct Iv {
+  double lo, hi;
+};
+SPOLY_D Iv iv(double a, double b) { return {fmin(a, b), fmax(a, b)}; }
+SPOLY_D Iv operator+(Iv a, Iv b) { return {a.lo + b.lo, a.hi + b.hi}; }
+SPOLY_D Iv operator-(Iv a, Iv b) { return {a.lo - b.hi, a.hi - b.lo}; }
+SPOLY_D Iv operator*(Iv a, Iv b) {
+  const double p1 = a.lo * b.lo, p2 = a.lo * b.hi, p3 = a.hi * b.lo, p4 = a.hi * b.hi;
+  return {fmin(fmin(p1, p2), fmin(p3, p4)), fmax(fmax(p1, p2), fmax(p3, p4))};
+}
+SPOLY_D Iv scal(double k, Iv a) { return iv(k * a.lo, k * a.hi); }
+SPOLY_D Iv sqr(Iv a) {
+  if (a.lo >= 0.0) return {a.lo * a.lo, a.hi * a.hi};
+  if (a.hi <= 0.0) return {a.hi * a.hi, a.lo * a.lo};
+  return {0.0, fmax(a.lo * a.lo, a.hi * a.hi)};
+}
+// a / L with L = [llo, lhi], llo > 0.
+SPOLY_D Iv divpos(Iv a, double llo, double lhi) {
+  if (a.lo >= 0.0) return {a.lo / lhi, a.hi / llo};
+  if (a.hi <= 0.0) return {a.lo / llo, a.hi / lhi};
+  return {a.lo / llo, a.hi / llo};
+}
+SPOLY_D Iv widen(Iv a, double m) { return {fmax(-1.0, a.lo - m), fmin(1.0, a.hi + m)}; }
+
+struct Iv3 {
+  Iv x, y, z;
+};
+
+// Unit-vector box of a vector box (false if the box touches the origin).
+SPOLY_D bool normalise(const Iv3& v, Iv3& out) {
+  const Iv l2 = sqr(v.x) + sqr(v.y) + sqr(v.z);
+  if (!(l2.lo > 0.0)) return false;
+  const double llo = sqrt(l2.lo), lhi = sqrt(l2.hi);
+  out = {divpos(v.x, llo, lhi), divpos(v.y, llo, lhi), divpos(v.z, llo, lhi)};
+  return true;
+}
+
+// Outgoing-direction box of one triangle lit from x0; returns false when no
+// bound is available (grazing or degenerate), true with `empty` set when no
+// transmitted direction exists anywhere (total internal reflection).
+SPOLY_D bool out_box(const MeshView& M, int t, d3 x0, int type, double eta0, double eta1, Iv3& o, Iv3& bb,
+                     bool& empty) {
+  empty = false;
+  auto g = [&](int row) { return M.tri[int64_t(row) * M.n_tris + t]; };
+  double p[3][3], n[3][3];
+  for (int v = 0; v < 3; ++v)
+    for (int c = 0; c < 3; ++c) {
+      p[v][c] = g(3 * v + c);
+      n[v][c] = g(9 + 3 * v + c);
+    }
+  Iv P[3], N[3];
+  for (int c = 0; c < 3; ++c) {
+    P[c] = {fmin(p[0][c], fmin(p[1][c], p[2][c])), fmax(p[0][c], fmax(p[1][c], p[2][c]))};
+    N[c] = {fmin(n[0][c], fmin(n[1][c], n[2][c])), fmax(n[0][c], fmax(n[1][c], n[2][c]))};
+  }
+  bb = {P[0], P[1], P[2]};
+  const Iv3 d = {P[0] - Iv{x0.x, x0.x}, P[1] - Iv{x0.y, x0.y}, P[2] - Iv{x0.z, x0.z}};
+  Iv3 dh, nh;
+  if (!normalise(d, dh)) return false;
+  if (!normalise({N[0], N[1], N[2]}, nh)) return false;
+  Iv c = dh.x * nh.x + dh.y * nh.y + dh.z * nh.z;
+  c = {-c.hi, -c.lo};  // c = -d^ . n^
+  if (c.hi < 0.0) {    // normal points away from x0: flip it
+    nh = {{-nh.x.hi, -nh.x.lo}, {-nh.y.hi, -nh.y.lo}, {-nh.z.hi, -nh.z.lo}};
+    c = {-c.hi, -c.lo};
+  } else if (!(c.lo > 0.0)) {
+    return false;  // grazing somewhere on the triangle
+  }
+  c.hi = fmin(c.hi, 1.0);
+  if (type == SPOLY_R) {
+    const Iv c2 = scal(2.0, c);
+    o = {dh.x + c2 * nh.x, dh.y + c2 * nh.y, dh.z + c2 * nh.z};
+  } else {
+    const double eta = eta0 / eta1;
+    const Iv k = {1.0 - eta * eta * (1.0 - c.lo * c.lo), 1.0 - eta * eta * (1.0 - c.hi * c.hi)};
+    if (k.hi < 0.0) {
+      empty = true;
+      return true;
+    }
+    const Iv sk = {sqrt(fmax(k.lo, 0.0)), sqrt(k.hi)};
+    const Iv f = scal(eta, c) - sk;
+    o = {scal(eta, dh.x) + f * nh.x, scal(eta, dh.y) + f * nh.y, scal(eta, dh.z) + f * nh.z};
+  }
+  return true;
+}
+
+__global__ void shared_x0_kernel(QueryView Q, int32_t* flag) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < Q.n; q += stride) {
+    bool same = true;
+    for (int c = 0; c < 3; ++c) same &= Q.x_first[3 * q + c] == Q.x_first[c];
+    same &= Q.eta[3 * q] == Q.eta[0] && Q.eta[3 * q + 1] == Q.eta[1] && Q.types[2 * q] == Q.types[0];
+    same &= Q.k[q] == 1;
+    if (!same) atomicExch(flag, 0);
+  }
+}
+
+// Per-triangle boxes for queries sharing x0, eta and type: [t][12] floats
+// (outgoing lo/hi xyz, bbox lo/hi xyz), rounded outward.  A triangle with no
+// bound gets the full box; one with no transmitted direction an empty box.
+__global__ void tri_boxes_kernel(ChainParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.tri_count) return;
+  const int t = P.tri_begin + i;
+  const d3 x0 = mk(P.qv.x_first[0], P.qv.x_first[1], P.qv.x_first[2]);
+  Iv3 o, bb;
+  bool empty = false;
+  const bool ok = out_box(P.mesh, t, x0, P.qv.types[0], P.qv.eta[0], P.qv.eta[1], o, bb, empty);
+  float* B = P.boxes + int64_t(i) * 12;
+  const Iv comps[3] = {o.x, o.y, o.z};
+  const Iv bcomp[3] = {bb.x, bb.y, bb.z};
+  for (int c = 0; c < 3; ++c) {
+    if (empty) {
+      B[c] = 2.0f;
+      B[3 + c] = -2.0f;
+    } else if (!ok) {
+      B[c] = -1.0f;
+      B[3 + c] = 1.0f;
+    } else {
+      const Iv w = widen(comps[c], P.margin);
+      B[c] = __double2float_rd(w.lo);
+      B[3 + c] = __double2float_ru(w.hi);
+    }
+    B[6 + c] = __double2float_rd(bcomp[c].lo);
+    B[9 + c] = __double2float_ru(bcomp[c].hi);
+  }
+}
+
+// Unit-direction box from a point box toward x2, in FP32 with a relative slack.
+SPOLY_D bool to_box_overlaps(const float* B, float x2, float y2, float z2) {
+  const float xl = x2 - B[9], xh = x2 - B[6];
+  const float yl = y2 - B[10], yh = y2 - B[7];
+  const float zl = z2 - B[11], zh = z2 - B[8];
+  auto s2lo = [](float lo, float hi) { return lo >= 0.f ? lo * lo : (hi <= 0.f ? hi * hi : 0.f); };
+  auto s2hi = [](float lo, float hi) { return fmaxf(lo * lo, hi * hi); };
+  const float l2lo = s2lo(xl, xh) + s2lo(yl, yh) + s2lo(zl, zh);
+  const float l2hi = s2hi(xl, xh) + s2hi(yl, yh) + s2hi(zl, zh);
+  if (!(l2lo > 0.f)) return true;
+  const float ilo = rsqrtf(l2hi) * (1.f - 1e-5f), ihi = rsqrtf(l2lo) * (1.f + 1e-5f);
+  auto dlo = [&](float lo, float hi) { return lo >= 0.f ? lo * ilo : lo * ihi; };
+  auto dhi = [&](float lo, float hi) { return hi >= 0.f ? hi * ihi : hi * ilo; };
+  const float sl = 1e-5f;
+  bool ok = true;
+  ok &= dlo(xl, xh) - sl <= B[3] && B[0] <= dhi(xl, xh) + sl;
+  ok &= dlo(yl, yh) - sl <= B[4] && B[1] <= dhi(yl, yh) + sl;
+  ok &= dlo(zl, zh) - sl <= B[5] && B[2] <= dhi(zl, zh) + sl;
+  return ok;
+}
+
+// Pair test over a tile: each thread owns one query, the block walks a chunk
+// of triangles staged in shared memory.  Survivors are appended with one
+// atomic per warp per triangle.
+constexpr int kConeThreads = 128;
+constexpr int kConeTris = 256;
+
+__global__ void __launch_bounds__(kConeThreads) cone_pairs_kernel(ChainParams P, int tris_per_block) {
+  __shared__ float sbox[kConeTris][12];
+  const int64_t q = int64_t(blockIdx.x) * kConeThreads + threadIdx.x;
+  const bool qok = q < P.qv.n;
+  float x2 = 0.f, y2 = 0.f, z2 = 0.f;
+  if (qok) {
+    x2 = float(P.qv.x_last[3 * q]);
+    y2 = float(P.qv.x_last[3 * q + 1]);
+    z2 = float(P.qv.x_last[3 * q + 2]);
+  }
+  const int lane = threadIdx.x & 31;
+  const int t_begin = blockIdx.y * tris_per_block;
+  const int t_end = min(P.tri_count, t_begin + tris_per_block);
+  for (int t0 = t_begin; t0 < t_end; t0 += kConeTris) {
+    const int nt = min(kConeTris, t_end - t0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nt * 12; k += kConeThreads) sbox[k / 12][k % 12] = P.boxes[int64_t(t0) * 12 + k];
+    __syncthreads();
+    for (int k = 0; k < nt; ++k) {
+      const bool keep = qok && to_box_overlaps(sbox[k], x2, y2, z2);
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (!m) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(P.count, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (keep) {
+        const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+        if (idx < (unsigned long long)P.cap) {
+          P.out[3 * idx] = int32_t(q);
+          P.out[3 * idx + 1] = P.tri_begin + t0 + k;
+          P.out[3 * idx + 2] = -1;
+        }
+      }
+    }
+  }
+}
+
+// General pair test for queries that do not share x0 / eta / type: the
+// outgoing box is recomputed per pair in FP64.
+__global__ void cone_pairs_general_kernel(ChainParams P) {
+  const int64_t n = P.qv.n * int64_t(P.tri_count);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t c = base + lane;
+    bool keep = false;
+    int64_t q = 0;
+    int t = 0;
+    if (c < n) {
+      q = c % P.qv.n;
+      t = P.tri_begin + int(c / P.qv.n);
+      if (P.qv.k[q] == 1) {
+        Iv3 o, bb;
+        bool empty = false;
+        const d3 x0 = mk(P.qv.x_first[3 * q], P.qv.x_first[3 * q + 1], P.qv.x_first[3 * q + 2]);
+        const bool ok = out_box(P.mesh, t, x0, P.qv.types[2 * q], P.qv.eta[3 * q], P.qv.eta[3 * q + 1], o, bb, empty);
+        float B[12];
+        const Iv comps[3] = {o.x, o.y, o.z};
+        const Iv bcomp[3] = {bb.x, bb.y, bb.z};
+        for (int k = 0; k < 3; ++k) {
+          const Iv w = widen(comps[k], P.margin);
+          B[k] = empty ? 2.f : (ok ? __double2float_rd(w.lo) : -1.f);
+          B[3 + k] = empty ? -2.f : (ok ? __double2float_ru(w.hi) : 1.f);
+          B[6 + k] = __double2float_rd(bcomp[k].lo);
+          B[9 + k] = __double2float_ru(bcomp[k].hi);
+        }
+        keep = to_box_overlaps(B, float(P.qv.x_last[3 * q]), float(P.qv.x_last[3 * q + 1]),
+                               float(P.qv.x_last[3 * q + 2]));
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) continue;
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(P.count, (unsigned long long)__popc(m));
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (keep) {
+      const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
+      if (idx < (unsigned long long)P.cap) {
+        P.out[3 * idx] = int32_t(q);
+        P.out[3 * idx + 1] = t;
+        P.out[3 * idx + 2] = -1;
+      }
+    }
+  }
+}
+
+__global__ void chains_all_kernel(ChainParams P) {
+  const int64_t n = P.qv.n * int64_t(P.tri_count);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < n; c += stride) {
+    P.out[3 * c] = int32_t(c % P.qv.n);
+    P.out[3 * c + 1] = P.tri_begin + int32_t(c / P.qv.n);
+    P.out[3 * c + 2] = -1;
+  }
+}
+
+__global__ void chains_explicit_kernel(ChainParams P, const int32_t* src, int64_t n) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < n; c += stride) {
+    const int32_t q = src[3 * c], t0 = src[3 * c + 1], t1 = src[3 * c + 2];
+    const bool ok = q >= 0 && q < P.qv.n && t0 >= 0 && t0 < P.mesh.n_tris && t1 >= -1 && t1 < P.mesh.n_tris;
+    if (!ok) atomicCAS(P.error, 0, int32_t(c < 0x7ffffffe ? c + 1 : 0x7fffffff));
+    P.out[3 * c] = ok ? q : 0;
+    P.out[3 * c + 1] = ok ? t0 : 0;
+    P.out[3 * c + 2] = ok ? t1 : -1;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_chains_all(const ChainParams& P, int num_sms, cudaStream_t st) {
+  chains_all_kernel<<<num_sms * 8, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chains_explicit(const ChainParams& P, const int32_t* src, int64_t n, int num_sms,
+                                   cudaStream_t st) {
+  chains_explicit_kernel<<<num_sms * 8, 256, 0, st>>>(P, src, n);
+  return cudaGetLastError();
+}
+
+__global__ void set_flag_kernel(int32_t* flag, int32_t value) { *flag = value; }
+
+cudaError_t launch_chains_cone(const ChainParams& P, int num_sms, cudaStream_t st) {
+  // flag := 1, then cleared by any query that differs from query 0 in x0,
+  // eta or type; the host reads it once to pick the pair-test variant.
+  set_flag_kernel<<<1, 1, 0, st>>>(P.shared_x0, 1);
+  shared_x0_kernel<<<num_sms * 4, 256, 0, st>>>(P.qv, P.shared_x0);
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, P.shared_x0, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  if (h) {
+    tri_boxes_kernel<<<(P.tri_count + 127) / 128, 128, 0, st>>>(P);
+    const int tris_per_block = 1024;
+    dim3 grid((unsigned)((P.qv.n + kConeThreads - 1) / kConeThreads),
+              (unsigned)((P.tri_count + tris_per_block - 1) / tris_per_block));
+    cone_pairs_kernel<<<grid, kConeThreads, 0, st>>>(P, tris_per_block);
+  } else {
+    cone_pairs_general_kernel<<<num_sms * 8, 256, 0, st>>>(P);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace spoly

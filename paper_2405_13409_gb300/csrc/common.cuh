@@ -1,0 +1,142 @@
+// Shared device/host definitions of the GB300 specular-polynomial library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spoly.h"
+
+#define SPOLY_HD __host__ __device__ __forceinline__
+#define SPOLY_D __device__ __forceinline__
+
+namespace spoly {
+
+// ---------------------------------------------------------------- vectors
+struct d3 {
+  double x, y, z;
+};
+SPOLY_HD d3 mk(double x, double y, double z) { return {x, y, z}; }
+SPOLY_HD d3 operator+(d3 a, d3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+SPOLY_HD d3 operator-(d3 a, d3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+SPOLY_HD d3 operator*(double k, d3 a) { return {k * a.x, k * a.y, k * a.z}; }
+SPOLY_HD double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+SPOLY_HD d3 cross(d3 a, d3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+SPOLY_HD double norm(d3 a) { return sqrt(dot(a, a)); }
+
+// One triangle in the library's FP64 SoA mesh: rows p0xyz, p1xyz, p2xyz,
+// n0xyz, n1xyz, n2xyz, each of length n_tris (Sec. 3.1, P_i and N_i).
+struct TriD {
+  d3 p0, p1, p2, n0, n1, n2;
+};
+
+SPOLY_D TriD load_tri(const double* __restrict__ soa, int64_t n_tris, int t) {
+  auto g = [&](int row) { return __ldg(soa + int64_t(row) * n_tris + t); };
+  TriD r;
+  r.p0 = mk(g(0), g(1), g(2));
+  r.p1 = mk(g(3), g(4), g(5));
+  r.p2 = mk(g(6), g(7), g(8));
+  r.n0 = mk(g(9), g(10), g(11));
+  r.n1 = mk(g(12), g(13), g(14));
+  r.n2 = mk(g(15), g(16), g(17));
+  return r;
+}
+
+struct QueryD {
+  d3 x0, x2;
+  double eta0, eta1;
+  int type;
+};
+
+SPOLY_D QueryD load_query(const double* __restrict__ xf, const double* __restrict__ xl,
+                          const double* __restrict__ eta, const int32_t* __restrict__ types, int q) {
+  QueryD r;
+  r.x0 = mk(__ldg(xf + 3 * q), __ldg(xf + 3 * q + 1), __ldg(xf + 3 * q + 2));
+  r.x2 = mk(__ldg(xl + 3 * q), __ldg(xl + 3 * q + 1), __ldg(xl + 3 * q + 2));
+  r.eta0 = __ldg(eta + 3 * q);
+  r.eta1 = __ldg(eta + 3 * q + 1);
+  r.type = __ldg(types + 2 * q);
+  return r;
+}
+
+// Device views of the caller's (or the library's staged) inputs.
+struct MeshView {
+  const double* tri;
+  int64_t n_tris;
+};
+struct QueryView {
+  const double* x_first;
+  const double* x_last;
+  const double* eta;
+  const int32_t* types;
+  const int32_t* k;
+  int64_t n;
+};
+
+// ------------------------------------------------------------ constants
+// Readings shared with the oracle's (they are restated, not shared: the
+// oracle is a separate program).
+constexpr double kDelta = 1e-6;      // v and u search domain [-kDelta, 1 + kDelta]
+constexpr double kTrim = 1e-13;      // negligible u-power / leading coefficient
+constexpr double kIllCond = 1e-8;    // |r'(v*)| / sum|r_i| below this: ILL_COND
+constexpr double kResidual = 1e-9;   // admissible path-space residual
+constexpr double kEdgeEps = 1e-7;    // EDGE flag band
+constexpr double kSwitch = 0.25;     // projection switch threshold (R: edge, T: b)
+constexpr double kNewtonMove = 1e-5; // accepted Newton move on (a, b)
+constexpr int kNewtonIters = 3;
+constexpr double kPolishTol = 1e-12; // FP64 polish bracket width in v
+constexpr float kIsoTol32 = 1e-6f;   // FP32 isolation bracket width in v
+constexpr double kIsoTol64 = 1e-12;  // FP64 isolation bracket width in v (plain mode)
+constexpr double kPrefilterMargin = 0.1;  // u-range margin of the pre-polish filter
+constexpr float kTangent32 = 1e-5f;  // tangent-root test, FP32 isolation
+constexpr double kTangent64 = 1e-12; // tangent-root test, FP64 isolation
+
+// Root-bracket queue item between the isolation and polish kernels.
+struct RootItem {
+  double zlo, zhi;   // bracket in the scaled hidden variable z = v / t
+  int32_t chain;
+  uint32_t flags;    // SPOLY_FLAG_TANGENT for critical-point roots
+  float rscale;      // sum_i |p_i| t^-i of the isolated polynomial
+  int32_t pad;
+};
+static_assert(sizeof(RootItem) == 32, "RootItem layout");
+
+// Counter slots in the solution set's device counter array.
+enum Counter {
+  C_CANDIDATES = 0,
+  C_DEGENERATE,
+  C_VROOTS,       // roots isolated in [-delta, 1 + delta]
+  C_QUEUED,       // brackets passed to the FP64 polish
+  C_PREFILTERED,  // brackets dropped by the u-range pre-filter
+  C_POLISH_LOST,  // brackets without an FP64 sign change
+  C_UROOTS,
+  C_ADMISSIBLE,
+  C_FLAGGED,
+  C_PATHS_WRITTEN,
+  C_QUEUE_OVERFLOW,
+  C_SIDE,         // chains sent to the generic-size kernel
+  C_COUNT
+};
+
+// --------------------------------------------------------- warp helpers
+// Appends `cnt` items per lane to a global array with one atomic per warp;
+// returns this lane's first slot.  All lanes of the warp must call it.
+SPOLY_D unsigned long long warp_append(unsigned long long* counter, unsigned cnt) {
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= unsigned(o)) incl += y;
+  }
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - cnt;
+}
+
+SPOLY_D void warp_count(unsigned long long* counter, unsigned cnt) {
+  unsigned s = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31u) == 0 && s) atomicAdd(counter, (unsigned long long)s);
+}
+
+}  // namespace spoly

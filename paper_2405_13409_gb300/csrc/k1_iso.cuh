@@ -1,0 +1,167 @@
+// Isolation kernel of the 1-bounce solve for the generic Bezout sizes
+// (R: n = 3 or 4, T: n = 6), templated on the arithmetic type of the
+// univariate phase.  Candidates whose trimmed size differs go to a side queue
+// handled by the generic FP64 kernel.
+#pragma once
+#include "k1_sys.cuh"
+#include "laplace_gen.cuh"
+
+namespace spoly {
+
+// Post-Laplace steps shared by the sized and generic kernels: power-of-two
+// normalisation and trimming of r, recursive-derivative isolation and the
+// u-range pre-filter.  Returns the number of brackets written to `items`, or
+// -1 if r vanishes identically.
+template <typename T, int RD, int DB>
+SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD + 1], int chain,
+                      unsigned& n_vroots, unsigned& n_pref) {
+  // Power-of-two normalisation of r and trimming of negligible leading terms
+  // (their contribution over the domain is below kTrim of the largest term).
+  const T Z = T((1.0 + kDelta) / s.sc.t);
+  T mx = T(0);
+#pragma unroll
+  for (int c = 0; c <= RD; ++c) mx = fmax(mx, fabs(r[c]));
+  if (!(mx > T(0))) return -1;
+  int e2;
+  frexp(double(mx), &e2);
+#pragma unroll
+  for (int c = 0; c <= RD; ++c) r[c] = T(ldexp(double(r[c]), -e2));
+  T zpow[RD + 1];
+  zpow[0] = T(1);
+#pragma unroll
+  for (int c = 1; c <= RD; ++c) zpow[c] = zpow[c - 1] * Z;
+  T mxz = T(0);
+#pragma unroll
+  for (int c = 0; c <= RD; ++c) mxz = fmax(mxz, fabs(r[c]) * zpow[c]);
+  int deg = RD;
+#pragma unroll
+  for (int c = RD; c >= 1; --c)
+    if (c == deg && fabs(r[c]) * zpow[c] <= T(kTrim) * mxz) --deg;
+  if (deg < 1) return 0;
+  // sum_i |p_i| t^-i: the magnitude scale of r over v in [0, 1].
+  T rscale = T(0);
+  {
+    const T it = T(1.0 / s.sc.t);
+    T zz = T(1);
+#pragma unroll
+    for (int c = 0; c <= RD; ++c) {
+      if (c <= deg) rscale += fabs(r[c]) * zz;
+      zz *= it;
+    }
+  }
+  const T lo = T(-kDelta / s.sc.t), hi = Z;
+  constexpr bool fp32 = sizeof(T) == 4;
+  const T tol = fp32 ? T(kIsoTol32 / s.sc.t) : T(kIsoTol64 / s.sc.t);
+  const T tang = fp32 ? T(kTangent32) : T(kTangent64);
+  T blo[RD + 1], bhi[RD + 1];
+  uint32_t bfl[RD + 1];
+  const int nb = isolate<T, RD>(r, deg, lo, hi, tol, tang, rscale, blo, bhi, bfl);
+  n_vroots += nb;
+  // Pre-polish filter: keep a bracket only if a(u, v) = 0 has a real u within
+  // kPrefilterMargin of [0, 1 - v] (or a(., v) is degenerate).  The margin is
+  // far wider than the error of the bracket, so no admissible root is lost.
+  int nq = 0;
+  for (int k = 0; k < nb; ++k) {
+    const T zm = T(0.5) * (blo[k] + bhi[k]);
+    const T v = zm * T(s.sc.t);
+    T am[3];
+    a_at<T>(s.a, s.na, zm, am);
+    T w[2];
+    uint32_t wf[2];
+    const T m = T(kPrefilterMargin);
+    const int nw = quad_roots<T>(am[0], am[1], am[2], T(1e-3), w, wf);
+    bool keep = (s.na == 0) || (nw == 0 && fabs(am[0]) + fabs(am[1]) + fabs(am[2]) == T(0));
+    for (int i = 0; i < nw; ++i) {
+      const T u = w[i] * T(s.sc.s);
+      if (u >= -m && u <= T(1) - v + m) keep = true;
+    }
+    if (!keep) {
+      ++n_pref;
+      continue;
+    }
+    RootItem itm;
+    itm.zlo = double(blo[k]);
+    itm.zhi = double(bhi[k]);
+    itm.chain = chain;
+    itm.flags = bfl[k];
+    itm.rscale = float(rscale);
+    itm.pad = e2;
+    items[nq++] = itm;
+  }
+  return nq;
+}
+
+// Resultant of the generic size N by the unrolled Laplace expansion, then
+// the shared post-processing.
+template <typename T, int N, int DB>
+SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int chain, unsigned& n_vroots,
+                             unsigned& n_pref) {
+  constexpr int ED = 2 + DB - 1;
+  constexpr int RD = N * (ED - N + 1);
+  T r[RD + 1];
+  {
+    T E[sym_size(N, ED)];
+    bezout_sym<T, N, 2, DB>(s.a, s.b, s.na, s.nb, E);
+    if constexpr (N == 3 && DB == 4) laplace_R3<T>(E, r);
+    if constexpr (N == 4 && DB == 4) laplace_R4<T>(E, r);
+    if constexpr (N == 6 && DB == 6) laplace_T6<T>(E, r);
+  }
+  return k1_finish<T, RD, DB>(s, r, items, chain, n_vroots, n_pref);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < P.n_chains; base += stride) {
+    const int64_t c = base + lane;
+    RootItem items[kRD + 1];
+    int nq = 0;
+    unsigned n_v = 0, n_pref = 0, n_deg = 0, n_cand = 0, n_side = 0;
+    if (c < P.n_chains) {
+      const int q = __ldg(P.chains + 3 * c);
+      const int t = __ldg(P.chains + 3 * c + 1);
+      if (__ldg(P.qv.k + q) == 1) {
+        n_cand = 1;
+        const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
+        const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
+        int r = 0;
+        if (qd.type == SPOLY_R) {
+          K1Sys<4> s;
+          if (!k1_system<4>(tr, qd, s))
+            r = -1;
+          else if (s.n == 3)
+            r = k1_isolate_sized<T, 3, 4>(s, items, int(c), n_v, n_pref);
+          else if (s.n == 4)
+            r = k1_isolate_sized<T, 4, 4>(s, items, int(c), n_v, n_pref);
+          else
+            r = -2;
+        } else {
+          K1Sys<6> s;
+          if (!k1_system<6>(tr, qd, s))
+            r = -1;
+          else if (s.n == 6)
+            r = k1_isolate_sized<T, 6, 6>(s, items, int(c), n_v, n_pref);
+          else
+            r = -2;
+        }
+        if (r == -1) n_deg = 1;
+        if (r == -2) n_side = 1;
+        nq = r > 0 ? r : 0;
+      }
+    }
+    warp_count(P.counters + C_CANDIDATES, n_cand);
+    warp_count(P.counters + C_DEGENERATE, n_deg);
+    warp_count(P.counters + C_VROOTS, n_v);
+    warp_count(P.counters + C_PREFILTERED, n_pref);
+    const unsigned long long sslot = warp_append(P.counters + C_SIDE, n_side);
+    if (n_side && sslot < (unsigned long long)P.side_cap) P.side[sslot] = int32_t(c);
+    const unsigned long long slot = warp_append(P.counters + C_QUEUED, unsigned(nq));
+    for (int k = 0; k < nq; ++k) {
+      const unsigned long long idx = slot + k;
+      if (idx < (unsigned long long)P.queue_cap) P.queue[idx] = items[k];
+    }
+  }
+}
+
+}  // namespace spoly

@@ -1,0 +1,12 @@
+// Isolation kernel, mixed precision: FP32 Laplace expansion and isolation on
+// Bezout entries built in FP64.
+#include "k1_iso.cuh"
+
+namespace spoly {
+
+cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, cudaStream_t st) {
+  k1_isolate_kernel<float><<<grid, 128, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace spoly

@@ -1,0 +1,11 @@
+// Isolation kernel, plain FP64: every step of the univariate phase in FP64.
+#include "k1_iso.cuh"
+
+namespace spoly {
+
+cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, cudaStream_t st) {
+  k1_isolate_kernel<double><<<grid, 128, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace spoly

@@ -1,0 +1,59 @@
+// FP64 polish kernel of the 1-bounce solve (path phase, Sec. 5.3), plus the
+// host launchers of the 1-bounce kernels.
+#include "k1_sys.cuh"
+
+namespace spoly {
+
+__global__ void __launch_bounds__(128) k1_polish_kernel(K1Params P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const unsigned long long queued = *(volatile unsigned long long*)(P.counters + C_QUEUED);
+  const int64_t n_items = int64_t(queued < (unsigned long long)P.queue_cap ? queued : P.queue_cap);
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n_items; base += stride) {
+    const int64_t i = base + lane;
+    spoly_path out[6];
+    int np = 0;
+    unsigned n_u = 0, lost = 0, n_flag = 0;
+    if (i < n_items) {
+      const RootItem it = P.queue[i];
+      const int q = __ldg(P.chains + 3 * int64_t(it.chain));
+      const int t = __ldg(P.chains + 3 * int64_t(it.chain) + 1);
+      const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
+      const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
+      if (qd.type == SPOLY_R)
+        np = k1_polish_one<4>(tr, qd, it, q, t, out, n_u, lost);
+      else
+        np = k1_polish_one<6>(tr, qd, it, q, t, out, n_u, lost);
+      for (int k = 0; k < np; ++k) n_flag += (out[k].flags & SPOLY_FLAG_ILL_COND) ? 1u : 0u;
+    }
+    warp_count(P.counters + C_UROOTS, n_u);
+    warp_count(P.counters + C_POLISH_LOST, lost);
+    warp_count(P.counters + C_FLAGGED, n_flag);
+    const unsigned long long slot = warp_append(P.counters + C_ADMISSIBLE, unsigned(np));
+    for (int k = 0; k < np; ++k) {
+      const unsigned long long idx = slot + k;
+      if (idx < (unsigned long long)P.path_cap) P.paths[idx] = out[k];
+    }
+  }
+}
+
+cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, cudaStream_t st);
+cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, cudaStream_t st);
+cudaError_t launch_k1_generic(const K1Params& P, int num_sms, cudaStream_t st);
+
+cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st) {
+  int64_t g = (P.n_chains + 127) / 128;
+  if (g < 1) g = 1;
+  if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
+  cudaError_t e = (precision == SPOLY_PLAIN_FP64) ? launch_k1_isolate_f64(P, int(g), st)
+                                                  : launch_k1_isolate_f32(P, int(g), st);
+  if (e != cudaSuccess) return e;
+  return launch_k1_generic(P, num_sms, st);
+}
+
+cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st) {
+  k1_polish_kernel<<<num_sms * 8, 128, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace spoly

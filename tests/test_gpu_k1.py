@@ -1,0 +1,192 @@
+"""GPU parity of the 1-bounce solve against the FP64 oracle, through the C ABI.
+
+Covers the reflection workload (16x16-cell heightfield, 32x32 receivers,
+524,288 exhaustive candidates) in both precisions, the refraction workload
+(64x64 cells, IOR 1.5, 256x256 receivers, bounding-cone cull) on a receiver
+sample and at full size with sampled outputs, ragged tiny cases, flat
+triangles (generic Bezout sizes), strongly curved planted cases, host vs
+device inputs and the error paths.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_13409_gb300 import binding, scenes
+
+from .parity import assert_parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = binding.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gpu_arrays(s):
+    return [_dev(a) for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
+
+
+def _run(ctx, s, mode, precision, explicit=None, margin=1e-3, host=False):
+    arrs = [np.ascontiguousarray(a) for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)] if host \
+        else _gpu_arrays(s)
+    tri, xf, xl, eta, ty, k = arrs
+    mesh = ctx.mesh(tri)
+    q = ctx.queries(xf, xl, eta, ty, k)
+    ex = None if explicit is None else (np.ascontiguousarray(explicit, dtype=np.int32) if host else _dev(explicit))
+    chains = ctx.spoly_build_chains(mesh, q, mode, margin=margin, explicit=ex)
+    sol = ctx.spoly_solve(mesh, q, chains, precision=precision)
+    paths = ctx.spoly_paths(sol)
+    stats = ctx.spoly_stats(sol)
+    ch = ctx.spoly_chains_copy(chains)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(chains)
+    return paths, stats, ch
+
+
+def _oracle(s, chains):
+    return oracle.solve(s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, chains)
+
+
+def _check_invariants(paths):
+    assert np.all(paths["residual"] < 1e-9)
+    u, v = paths["uv"][:, 0], paths["uv"][:, 1]
+    assert np.all(u >= 0) and np.all(v >= 0) and np.all(u + v <= 1)
+
+
+@pytest.mark.parametrize("precision", [binding.PLAIN_FP64, binding.MIXED])
+def test_reflection_exhaustive_matches_oracle(ctx, precision):
+    s = scenes.reflect_scene()
+    paths, stats, ch = _run(ctx, s, binding.CHAINS_ALL, precision)
+    assert ch.shape[0] == 524288 and stats["candidates"] == 524288
+    ref, rc = _oracle(s, ch)
+    st = assert_parity(paths, ref, ch.shape[0])
+    assert st["matched"] >= 0.999 * ref.size and ref.size > 500
+    _check_invariants(paths)
+
+
+def _refract_sample(n_recv, seed):
+    s = scenes.refract_scene()
+    rng = np.random.default_rng(seed)
+    qs = np.sort(rng.choice(s.n_queries, n_recv, replace=False))
+    s.x_first, s.x_last, s.eta, s.types, s.k = (a[qs].copy() for a in (s.x_first, s.x_last, s.eta, s.types, s.k))
+    return s
+
+
+@pytest.mark.parametrize("precision", [binding.PLAIN_FP64, binding.MIXED])
+def test_refraction_cone_cull_recall_and_parity(ctx, precision):
+    s = _refract_sample(24, seed=3)
+    paths, stats, ch = _run(ctx, s, binding.CHAINS_CONE, precision)
+    every = scenes.all_pairs(s.n_queries, s.n_tris)
+    ref, _ = _oracle(s, every)
+    assert ref.size > 5
+    kept = set(map(tuple, ch[:, :2].tolist()))
+    assert all((int(p["query"]), int(p["tri0"])) in kept for p in ref), "cone cull dropped an admissible path"
+    assert ch.shape[0] < 0.05 * every.shape[0]
+    assert_parity(paths, ref, every.shape[0])
+    _check_invariants(paths)
+
+
+def test_refraction_full_size_sampled(ctx):
+    s = scenes.refract_scene()
+    paths, stats, ch = _run(ctx, s, binding.CHAINS_CONE, binding.MIXED)
+    assert stats["candidates"] == ch.shape[0] > 0
+    _check_invariants(paths)
+    rng = np.random.default_rng(5)
+    qs = rng.choice(s.n_queries, 48, replace=False)
+    sel = ch[np.isin(ch[:, 0], qs)]
+    ref, _ = _oracle(s, sel)
+    mine = paths[np.isin(paths["query"], qs)]
+    assert_parity(mine, ref, sel.shape[0])
+
+
+@pytest.mark.parametrize("precision", [binding.PLAIN_FP64, binding.MIXED])
+@pytest.mark.parametrize("n_cells,n_recv", [(1, 1), (1, 3), (2, 5), (3, 7)])
+def test_ragged_small_cases(ctx, precision, n_cells, n_recv):
+    s = scenes.reflect_scene(seed=1, n_cells=n_cells, n_recv=n_recv)
+    paths, stats, ch = _run(ctx, s, binding.CHAINS_ALL, precision)
+    assert ch.shape[0] == 2 * n_cells * n_cells * n_recv * n_recv
+    ref, _ = _oracle(s, ch)
+    assert_parity(paths, ref, ch.shape[0])
+
+
+def _single_triangle_scene(tri, x0, x2, type_, eta1=1.5):
+    n = tri.shape[1]
+    eta = np.tile([1.0, eta1 if type_ == 1 else 1.0, 1.0], (n, 1))
+    chains = np.stack([np.arange(n), np.arange(n), -np.ones(n)], -1).astype(np.int32)
+    return scenes.Scene("single", np.ascontiguousarray(tri), np.ascontiguousarray(x0), np.ascontiguousarray(x2),
+                        eta, np.full((n, 2), type_, np.int32), np.ones(n, np.int32), chains=chains)
+
+
+@pytest.mark.parametrize("type_", [0, 1])
+@pytest.mark.parametrize("precision", [binding.PLAIN_FP64, binding.MIXED])
+def test_flat_triangles_generic_sizes(ctx, type_, precision):
+    tri, x0, x2 = scenes.random_triangle_cases(22 + type_, 3000, flat_normal=True)
+    if type_ == 1:
+        x2 = x2.copy()
+        x2[:, 2] = -x2[:, 2]
+    s = _single_triangle_scene(tri, x0, x2, type_)
+    paths, stats, ch = _run(ctx, s, binding.CHAINS_EXPLICIT, precision, explicit=s.chains)
+    ref, _ = _oracle(s, s.chains)
+    assert ref.size > 20
+    assert_parity(paths, ref, ch.shape[0])
+
+
+@pytest.mark.parametrize("type_", [0, 1])
+@pytest.mark.parametrize("precision", [binding.PLAIN_FP64, binding.MIXED])
+def test_curved_planted_cases(ctx, type_, precision):
+    from tests.test_oracle_pins import _planted_cases
+    tri, x0, x2 = _planted_cases(70 + type_, 2000, type_)
+    s = _single_triangle_scene(tri, x0, x2, type_)
+    paths, stats, ch = _run(ctx, s, binding.CHAINS_EXPLICIT, precision, explicit=s.chains)
+    ref, _ = _oracle(s, s.chains)
+    assert ref.size > 1500
+    assert_parity(paths, ref, ch.shape[0])
+    _check_invariants(paths)
+
+
+def test_host_and_device_inputs_agree(ctx):
+    s = scenes.reflect_scene(seed=2, n_cells=8, n_recv=12)
+    a, _, _ = _run(ctx, s, binding.CHAINS_ALL, binding.MIXED, host=True)
+    b, _, _ = _run(ctx, s, binding.CHAINS_ALL, binding.MIXED, host=False)
+    ka = sorted(zip(a["query"].tolist(), a["tri"][:, 0].tolist(), a["uv"][:, 0].round(9).tolist()))
+    kb = sorted(zip(b["query"].tolist(), b["tri"][:, 0].tolist(), b["uv"][:, 0].round(9).tolist()))
+    assert ka == kb and len(ka) > 0
+
+
+def test_error_paths(ctx):
+    s = scenes.reflect_scene(seed=0, n_cells=2, n_recv=2)
+    tri, xf, xl, eta, ty, k = _gpu_arrays(s)
+    mesh = ctx.mesh(tri)
+    q = ctx.queries(xf, xl, eta, ty, k)
+    bad = np.array([[0, 0, -1], [5, 0, -1]], dtype=np.int32)
+    with pytest.raises(binding.SpolyError) as e:
+        ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=_dev(bad))
+    assert e.value.status == binding.SPOLY_EINVAL
+    with pytest.raises(binding.SpolyError) as e:
+        ctx.spoly_build_chains(mesh, q, 7)
+    assert e.value.status == binding.SPOLY_EINVAL
+    host_tri = s.tri.copy()
+    host_tri[4, 1] = np.nan
+    with pytest.raises(binding.SpolyError) as e:
+        ctx.spoly_build_chains(ctx.mesh(host_tri), q, binding.CHAINS_ALL)
+    assert e.value.status == binding.SPOLY_EINVAL
+    chains = ctx.spoly_build_chains(mesh, q, binding.CHAINS_ALL)
+    sol = ctx.spoly_solve(mesh, q, chains, precision=binding.MIXED)
+    n = ctx.spoly_stats(sol)["admissible"]
+    if n > 0:
+        buf = np.zeros(1, dtype=binding.PATH_DTYPE)
+        assert ctx.spoly_paths_into(sol, buf, 0) == n
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(chains)
