@@ -378,12 +378,14 @@ SPOLY_D int isolate(const T (&p)[DM + 1], int deg, T lo, T hi, T tol, T tang, T 
     int nn = 0;
     T s = lo;
     T fs = horner_from<T, DM>(w, j, s);
+    // Arrays hold DM + 1 roots; evaluation noise could in principle report
+    // more sign changes than the degree allows, so every write is guarded.
     if (fs == T(0)) {
       nlo[nn] = s;
       nhi[nn] = s;
       ++nn;
     }
-    for (int k = 0; k <= nc; ++k) {
+    for (int k = 0; k <= nc && nn <= DM; ++k) {
       const T e = (k < nc) ? crit[k] : hi;
       if (!(e > s)) continue;
       const T fe = horner_from<T, DM>(w, j, e);
@@ -417,7 +419,7 @@ SPOLY_D int isolate(const T (&p)[DM + 1], int deg, T lo, T hi, T tol, T tang, T 
       fs = fe;
     }
     if (j == 0) {
-      for (int k = 0; k < nn; ++k) {
+      for (int k = 0; k < nn && nout <= DM; ++k) {
         blo[nout] = nlo[k];
         bhi[nout] = nhi[k];
         bfl[nout] = 0u;
@@ -441,8 +443,8 @@ SPOLY_D int isolate(const T (&p)[DM + 1], int deg, T lo, T hi, T tol, T tang, T 
         }
       }
     } else {
-      for (int k = 0; k < nn; ++k) crit[k] = T(0.5) * (nlo[k] + nhi[k]);
-      nc = nn;
+      nc = nn < DM ? nn : DM;
+      for (int k = 0; k < nc; ++k) crit[k] = T(0.5) * (nlo[k] + nhi[k]);
     }
   }
   return nout;
