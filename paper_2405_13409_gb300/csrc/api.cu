@@ -383,40 +383,46 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   P.n_chains = nc;
   P.counters = static_cast<unsigned long long*>(set->counters.p);
   cudaError_t e;
-  for (int attempt = 0; attempt < 3; ++attempt) {
+  const bool async = (opts->flags & SPOLY_SOLVE_ASYNC) != 0;
+  const bool timing = (opts->flags & SPOLY_SOLVE_TIMING) != 0;
+  if (timing && !set->ev[0])
+    for (auto& ev : set->ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) return bail(fail(ctx, SPOLY_ECUDA, "event create"));
+  set->timed = timing;
+  auto bind = [&]() {
     P.queue = static_cast<RootItem*>(set->queue.p);
     P.queue_cap = set->queue_cap;
     P.side = static_cast<int32_t*>(set->side.p);
     P.side_cap = set->side_cap;
     P.paths = static_cast<spoly_path*>(set->paths.p);
     P.path_cap = set->path_cap;
+  };
+  auto read_counters = [&]() -> cudaError_t {
+    cudaError_t r = cudaMemcpyAsync(set->host, set->counters.p, sizeof(set->host), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(ctx->stream);
+    return r;
+  };
+  // Stage 1: isolation.  Re-run (only in synchronous mode) until the bracket
+  // queue and the side queue hold every item; each re-run grows them to the
+  // exact counts, so two passes suffice.
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    bind();
     e = cudaMemsetAsync(set->counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
-    const bool timing = (opts->flags & SPOLY_SOLVE_TIMING) != 0;
-    if (timing && !set->ev[0])
-      for (auto& ev : set->ev)
-        if (cudaEventCreate(&ev) != cudaSuccess) return bail(fail(ctx, SPOLY_ECUDA, "event create"));
-    set->timed = timing;
     if (timing) cudaEventRecord(set->ev[0], ctx->stream);
     if (nc > 0) {
       e = launch_k1_isolate(P, opts->precision, ctx->num_sms, ctx->stream);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_isolate"));
-      if (timing) cudaEventRecord(set->ev[1], ctx->stream);
-      e = launch_k1_polish(P, ctx->num_sms, ctx->stream);
-      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
-    } else if (timing) {
-      cudaEventRecord(set->ev[1], ctx->stream);
     }
-    if (timing) cudaEventRecord(set->ev[2], ctx->stream);
-    if (opts->flags & SPOLY_SOLVE_ASYNC) break;
-    e = cudaMemcpyAsync(set->host, set->counters.p, sizeof(set->host), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
-    set->host_valid = true;
+    if (timing) cudaEventRecord(set->ev[1], ctx->stream);
+    if (async) break;
+    e = read_counters();
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "isolation"));
     const int64_t queued = int64_t(set->host[C_QUEUED]);
-    const int64_t paths = int64_t(set->host[C_ADMISSIBLE]);
     const int64_t side = int64_t(set->host[C_SIDE]);
-    if (queued <= set->queue_cap && paths <= set->path_cap && side <= set->side_cap) break;
+    if (queued <= set->queue_cap && side <= set->side_cap) break;
+    if (attempt == 2) return bail(fail(ctx, SPOLY_ECAPACITY, "bracket queue did not converge"));
     if (side > set->side_cap) {
       if (set->side.ensure(size_t(side) * sizeof(int32_t)) != cudaSuccess)
         return bail(fail(ctx, SPOLY_ENOMEM, "side queue growth"));
@@ -427,12 +433,39 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
         return bail(fail(ctx, SPOLY_ENOMEM, "queue growth"));
       set->queue_cap = queued;
     }
+  }
+  // Stage 2: FP64 v-polish (in place, once) and the path phase.  Only the
+  // path phase is re-run if the path buffer overflowed: it reads the polished
+  // queue and is idempotent once its counters are reset.
+  if (nc > 0) {
+    e = launch_k1_polish(P, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
+    e = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_paths"));
+  }
+  if (timing) cudaEventRecord(set->ev[2], ctx->stream);
+  if (!async) {
+    e = read_counters();
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
+    const int64_t paths = int64_t(set->host[C_ADMISSIBLE]);
     if (paths > set->path_cap) {
       if (set->paths.ensure(size_t(paths) * sizeof(spoly_path)) != cudaSuccess)
         return bail(fail(ctx, SPOLY_ENOMEM, "path growth"));
       set->path_cap = paths;
+      bind();
+      for (int c : {int(C_UROOTS), int(C_FLAGGED), int(C_ADMISSIBLE)}) {
+        e = cudaMemsetAsync(static_cast<unsigned long long*>(set->counters.p) + c, 0, sizeof(unsigned long long),
+                            ctx->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
+      }
+      e = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_paths"));
+      e = read_counters();
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
+      if (int64_t(set->host[C_ADMISSIBLE]) > set->path_cap)
+        return bail(fail(ctx, SPOLY_ECAPACITY, "path buffer did not converge"));
     }
-    set->host_valid = false;
+    set->host_valid = true;
   }
   *inout = set;
   return SPOLY_OK;

@@ -86,7 +86,7 @@ constexpr double kPolishTol = 1e-12; // FP64 polish bracket width in v
 constexpr float kIsoTol32 = 1e-6f;   // FP32 isolation bracket width in v
 constexpr double kIsoTol64 = 1e-12;  // FP64 isolation bracket width in v (plain mode)
 constexpr double kPrefilterMargin = 0.1;  // u-range margin of the pre-polish filter
-constexpr float kTangent32 = 1e-5f;  // tangent-root test, FP32 isolation
+constexpr float kTangent32 = 1e-4f;  // tangent-root test, FP32 isolation
 constexpr double kTangent64 = 1e-12; // tangent-root test, FP64 isolation
 
 // Root-bracket queue item between the isolation and polish kernels.

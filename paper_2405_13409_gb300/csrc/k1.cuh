@@ -20,6 +20,7 @@ struct K1Params {
 
 cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st);
+cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st);
 
 // Candidate construction.
 struct ChainParams {

@@ -4,30 +4,59 @@
 
 namespace spoly {
 
-__global__ void __launch_bounds__(128) k1_polish_kernel(K1Params P) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+SPOLY_D int64_t queue_items(const K1Params& P) {
   const unsigned long long queued = *(volatile unsigned long long*)(P.counters + C_QUEUED);
-  const int64_t n_items = int64_t(queued < (unsigned long long)P.queue_cap ? queued : P.queue_cap);
+  return int64_t(queued < (unsigned long long)P.queue_cap ? queued : P.queue_cap);
+}
+
+// FP64 v-polish of every queued bracket, in place.
+__global__ void __launch_bounds__(128) k1_polish_kernel(K1Params P) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t n_items = queue_items(P);
+  const int lane = threadIdx.x & 31;
   for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n_items; base += stride) {
     const int64_t i = base + lane;
-    spoly_path out[6];
-    int np = 0;
-    unsigned n_u = 0, lost = 0, n_flag = 0;
+    unsigned lost = 0;
     if (i < n_items) {
-      const RootItem it = P.queue[i];
+      RootItem it = P.queue[i];
       const int q = __ldg(P.chains + 3 * int64_t(it.chain));
       const int t = __ldg(P.chains + 3 * int64_t(it.chain) + 1);
       const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
       const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
       if (qd.type == SPOLY_R)
-        np = k1_polish_one<4>(tr, qd, it, q, t, out, n_u, lost);
+        k1_polish_v<4>(tr, qd, it, lost);
       else
-        np = k1_polish_one<6>(tr, qd, it, q, t, out, n_u, lost);
+        k1_polish_v<6>(tr, qd, it, lost);
+      P.queue[i] = it;
+    }
+    warp_count(P.counters + C_POLISH_LOST, lost);
+  }
+}
+
+// Path phase of every polished bracket; admissible paths appended with one
+// atomic per warp.
+__global__ void __launch_bounds__(128) k1_path_kernel(K1Params P) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t n_items = queue_items(P);
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n_items; base += stride) {
+    const int64_t i = base + lane;
+    spoly_path out[6];
+    int np = 0;
+    unsigned n_u = 0, n_flag = 0;
+    if (i < n_items) {
+      const int chain = P.queue[i].chain;
+      const int q = __ldg(P.chains + 3 * int64_t(chain));
+      const int t = __ldg(P.chains + 3 * int64_t(chain) + 1);
+      const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
+      const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
+      if (qd.type == SPOLY_R)
+        np = k1_path_item<4>(tr, qd, P.queue, i, q, t, out, n_u);
+      else
+        np = k1_path_item<6>(tr, qd, P.queue, i, q, t, out, n_u);
       for (int k = 0; k < np; ++k) n_flag += (out[k].flags & SPOLY_FLAG_ILL_COND) ? 1u : 0u;
     }
     warp_count(P.counters + C_UROOTS, n_u);
-    warp_count(P.counters + C_POLISH_LOST, lost);
     warp_count(P.counters + C_FLAGGED, n_flag);
     const unsigned long long slot = warp_append(P.counters + C_ADMISSIBLE, unsigned(np));
     for (int k = 0; k < np; ++k) {
@@ -53,6 +82,11 @@ cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cud
 
 cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st) {
   k1_polish_kernel<<<num_sms * 8, 128, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st) {
+  k1_path_kernel<<<num_sms * 8, 128, 0, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -180,18 +180,98 @@ SPOLY_D void newton_ab(const K1Sys<DB>& s, double& w, double& z) {
   }
 }
 
+// Bits of RootItem::flags after the v-polish: root 1 in zlo with public flags
+// in bits 0-7, root 2 in zhi with public flags in bits 8-15.
+constexpr uint32_t kRoot1Valid = 1u << 30;
+constexpr uint32_t kRoot2Valid = 1u << 31;
+
+// FP64 bisection of the numeric determinant on [zl, zh] (signs differ).
 template <int DB>
-SPOLY_D int k1_polish_one(const TriD& tr, const QueryD& qd, const RootItem& it, int q, int t,
-                          spoly_path (&out)[6], unsigned& n_u, unsigned& lost) {
+SPOLY_D double bisect_det(const K1Sys<DB>& s, double zl, double zh, double fl) {
+  const double tol = kPolishTol / s.sc.t;
+  while (zh - zl > tol) {
+    const double zm = 0.5 * (zl + zh);
+    if (!(zm > zl && zm < zh)) break;
+    const double fm = det_at<DB>(s, zm);
+    if (fm == 0.0) return zm;
+    if ((fm < 0.0) == (fl < 0.0)) {
+      zl = zm;
+      fl = fm;
+    } else {
+      zh = zm;
+    }
+  }
+  return 0.5 * (zl + zh);
+}
+
+// Ill-conditioning of a polished root: |r'(v*)| / sum|r_i| from a central
+// difference of the FP64 determinant (h = 1e-6 in v).
+template <int DB>
+SPOLY_D uint32_t ill_flag(const K1Sys<DB>& s, double z, const RootItem& it) {
+  const double h = 1e-6 / s.sc.t;
+  const double slope = (det_at<DB>(s, z + h) - det_at<DB>(s, z - h)) / (2.0 * h);
+  const double scale = ldexp(double(it.rscale), it.pad);
+  return (fabs(slope) / s.sc.t < kIllCond * scale) ? SPOLY_FLAG_ILL_COND : 0u;
+}
+
+// Root next to a critical point c on one side (dir = -1 or +1): step out from
+// c by doubling until the FP64 determinant changes sign (within 1e-3 in v),
+// then bisect.  Returns false when no sign change is found.
+template <int DB>
+SPOLY_D bool side_root(const K1Sys<DB>& s, double c, double fc, int dir, double zmin, double zmax, double* root) {
+  double p = c;
+  double w = 1e-8 / s.sc.t;
+  const double wmax = 1e-3 / s.sc.t;
+  while (w <= wmax) {
+    double x = c + dir * w;
+    if (x < zmin || x > zmax) return false;
+    const double fx = det_at<DB>(s, x);
+    if (fx == 0.0) {
+      *root = x;
+      return true;
+    }
+    if ((fx < 0.0) != (fc < 0.0)) {
+      *root = (dir < 0) ? bisect_det<DB>(s, x, p, fx) : bisect_det<DB>(s, p, x, fc);
+      return true;
+    }
+    p = x;
+    w *= 2.0;
+  }
+  return false;
+}
+
+// v-polish of one bracket in FP64 (north star (1): "root polishing by
+// bisection near the final interval").  A sign-change bracket from the
+// isolation is bisected on the numeric determinant to width 1e-12 in v, after
+// widening by doubling if the FP64 signs agree; a tangent bracket (critical
+// point of the isolated polynomial) is resolved into the roots on either side
+// of it, if the FP64 determinant has them.  Writes the roots back into `it`.
+template <int DB>
+SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigned& lost) {
   K1Sys<DB> s;
-  if (!k1_system<DB>(tr, qd, s)) return 0;
+  const uint32_t in_flags = it.flags & 0xffu;
+  it.flags = 0u;
+  if (!k1_system<DB>(tr, qd, s)) {
+    ++lost;
+    return;
+  }
   const double zmin = -kDelta / s.sc.t, zmax = (1.0 + kDelta) / s.sc.t;
-  double zlo = it.zlo, zhi = it.zhi;
-  uint32_t vflags = it.flags;
-  double zs;
-  if (vflags & SPOLY_FLAG_TANGENT) {
-    zs = 0.5 * (zlo + zhi);
+  double r1 = 0.0, r2 = 0.0;
+  bool v1 = false, v2 = false;
+  uint32_t f1 = 0u, f2 = 0u;
+  if (in_flags & SPOLY_FLAG_TANGENT) {
+    const double c = 0.5 * (it.zlo + it.zhi);
+    const double fc = det_at<DB>(s, c);
+    if (fc == 0.0) {
+      r1 = c;
+      v1 = true;
+      f1 = SPOLY_FLAG_TANGENT | SPOLY_FLAG_ILL_COND;
+    } else {
+      v1 = side_root<DB>(s, c, fc, -1, zmin, zmax, &r1);
+      v2 = side_root<DB>(s, c, fc, +1, zmin, zmax, &r2);
+    }
   } else {
+    double zlo = it.zlo, zhi = it.zhi;
     double flo = det_at<DB>(s, zlo), fhi = det_at<DB>(s, zhi);
     double wdt = fmax(zhi - zlo, 1e-15 / s.sc.t);
     int grow = 0;
@@ -204,41 +284,33 @@ SPOLY_D int k1_polish_one(const TriD& tr, const QueryD& qd, const RootItem& it, 
       ++grow;
     }
     if (flo == 0.0) {
-      zs = zlo;
+      r1 = zlo;
+      v1 = true;
     } else if (fhi == 0.0) {
-      zs = zhi;
+      r1 = zhi;
+      v1 = true;
     } else if ((flo < 0.0) != (fhi < 0.0)) {
-      const double tol = kPolishTol / s.sc.t;
-      while (zhi - zlo > tol) {
-        const double zm = 0.5 * (zlo + zhi);
-        if (!(zm > zlo && zm < zhi)) break;
-        const double fm = det_at<DB>(s, zm);
-        if (fm == 0.0) {
-          zlo = zhi = zm;
-          break;
-        }
-        if ((fm < 0.0) == (flo < 0.0)) {
-          zlo = zm;
-          flo = fm;
-        } else {
-          zhi = zm;
-        }
-      }
-      zs = 0.5 * (zlo + zhi);
-    } else {
-      ++lost;
-      return 0;
+      r1 = bisect_det<DB>(s, zlo, zhi, flo);
+      v1 = true;
     }
-    // Ill-conditioning: |r'(v*)| / sum|r_i| from a central difference of the
-    // FP64 determinant (h = 1e-6 in v).
-    const double h = 1e-6 / s.sc.t;
-    const double slope = (det_at<DB>(s, zs + h) - det_at<DB>(s, zs - h)) / (2.0 * h);
-    const double scale = ldexp(double(it.rscale), it.pad);
-    if (fabs(slope) / s.sc.t < kIllCond * scale) vflags |= SPOLY_FLAG_ILL_COND;
   }
-  if (zs < zmin || zs > zmax) return 0;
+  if (v1 && !(f1 & SPOLY_FLAG_TANGENT)) f1 |= ill_flag<DB>(s, r1, it);
+  if (v2) f2 |= ill_flag<DB>(s, r2, it);
+  v1 = v1 && r1 >= zmin && r1 <= zmax;
+  v2 = v2 && r2 >= zmin && r2 <= zmax;
+  if (!v1 && !v2) ++lost;
+  it.zlo = r1;
+  it.zhi = r2;
+  it.flags = (v1 ? kRoot1Valid : 0u) | (v2 ? kRoot2Valid : 0u) | (f1 & 0xffu) | ((f2 & 0xffu) << 8);
+}
+
+// Path phase (Sec. 5.3) for one polished root z*: u from a(u, v*) = 0 (b if
+// a(., v*) vanishes), Newton on (a, b), path-space check of Eq. eq_ch,
+// sidedness and the in-triangle test.  Appends up to 6 paths to `out`.
+template <int DB>
+SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, double zs, uint32_t vflags, int q,
+                         int t, spoly_path (&out)[6], int np, unsigned& n_u) {
   const double v0 = zs * s.sc.t;
-  // u from a(u, v*) = 0 (Sec. 5.3); fall back to b if a(., v*) vanishes.
   double am[3];
   a_at<double>(s.a, s.na, zs, am);
   double amag = 0.0;
@@ -278,7 +350,6 @@ SPOLY_D int k1_polish_one(const TriD& tr, const QueryD& qd, const RootItem& it, 
       ++nw;
     }
   }
-  int np = 0;
   for (int i = 0; i < nw; ++i) {
     ++n_u;
     double w = wr[i], z = zs;
@@ -315,6 +386,35 @@ SPOLY_D int k1_polish_one(const TriD& tr, const QueryD& qd, const RootItem& it, 
     p.x[1][0] = p.x[1][1] = p.x[1][2] = 0.0;
     p.residual = float(res);
     p.flags = flags;
+  }
+  return np;
+}
+
+// Path phase of queue item i.  Roots already produced by an earlier bracket
+// of the same candidate (items of one candidate are contiguous in the queue)
+// or equal to the item's other root within 1e-9 in v are skipped.
+template <int DB>
+SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue, int64_t i, int q, int t,
+                         spoly_path (&out)[6], unsigned& n_u) {
+  const RootItem it = queue[i];
+  K1Sys<DB> s;
+  if (!k1_system<DB>(tr, qd, s)) return 0;
+  const double dtol = 1e-9 / s.sc.t;
+  int np = 0;
+  for (int r = 0; r < 2; ++r) {
+    const uint32_t valid = r == 0 ? kRoot1Valid : kRoot2Valid;
+    if (!(it.flags & valid)) continue;
+    const double z = r == 0 ? it.zlo : it.zhi;
+    bool dup = (r == 1 && (it.flags & kRoot1Valid) && fabs(it.zlo - z) <= dtol);
+    for (int64_t j = i - 1; j >= 0 && !dup; --j) {
+      const RootItem o = queue[j];
+      if (o.chain != it.chain) break;
+      if (((o.flags & kRoot1Valid) && fabs(o.zlo - z) <= dtol) || ((o.flags & kRoot2Valid) && fabs(o.zhi - z) <= dtol))
+        dup = true;
+    }
+    if (dup) continue;
+    const uint32_t vflags = r == 0 ? (it.flags & 0xffu) : ((it.flags >> 8) & 0xffu);
+    np = k1_path_root<DB>(s, tr, qd, z, vflags, q, t, out, np, n_u);
   }
   return np;
 }
