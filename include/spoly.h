@@ -149,7 +149,9 @@ typedef struct {
   int64_t u_roots;      /* (u, v) pairs checked in path space */
   int64_t admissible;   /* paths returned */
   int64_t flagged;      /* returned paths with SPOLY_FLAG_ILL_COND */
-  int64_t reserved[7];
+  int64_t fallback;     /* chains re-isolated in FP64: FP32 signs not certified,
+                           or a Bezout size without an unrolled kernel */
+  int64_t reserved[6];
 } spoly_counters;
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`

@@ -78,8 +78,8 @@ class spoly_path(ctypes.Structure):
 
 class spoly_counters(ctypes.Structure):
     _fields_ = [(n, c_int64) for n in ("candidates", "degenerate", "v_roots", "queued", "prefiltered",
-                                       "polish_lost", "u_roots", "admissible", "flagged")] + \
-               [("reserved", c_int64 * 7)]
+                                       "polish_lost", "u_roots", "admissible", "flagged", "fallback")] + \
+               [("reserved", c_int64 * 6)]
 
 
 PATH_DTYPE = np.dtype([("query", "<i4"), ("tri", "<i4", (2,)), ("reserved", "<i4"), ("uv", "<f8", (4,)),

@@ -487,6 +487,7 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
   out->u_roots = int64_t(h[C_UROOTS]);
   out->admissible = int64_t(h[C_ADMISSIBLE]);
   out->flagged = int64_t(h[C_FLAGGED]);
+  out->fallback = int64_t(h[C_SIDE]);
   return SPOLY_OK;
 }
 

@@ -1,12 +1,37 @@
 // Shared device/host definitions of the GB300 specular-polynomial library.
 #pragma once
-#include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/spoly.h"
+#include "spoly.h"
 
+#ifdef SPOLY_HOST_BUILD
+// Host build of the per-candidate numerics (used by tests to run the kernels'
+// arithmetic on the CPU); kernels and warp primitives are excluded.
+#include <algorithm>
+#include <cmath>
+#define SPOLY_HD inline
+#define SPOLY_D inline
+#define __constant__
+using std::fabs;
+using std::fma;
+using std::fmax;
+using std::fmin;
+using std::frexp;
+using std::isfinite;
+using std::ldexp;
+using std::log2;
+using std::max;
+using std::min;
+using std::sqrt;
+template <typename T>
+inline T __ldg(const T* p) { return *p; }
+inline int __double2int_rn(double x) { return int(std::nearbyint(x)); }
+inline int __popc(unsigned x) { return __builtin_popcount(x); }
+#else
+#include <cuda_runtime.h>
 #define SPOLY_HD __host__ __device__ __forceinline__
 #define SPOLY_D __device__ __forceinline__
+#endif
 
 namespace spoly {
 
@@ -86,6 +111,7 @@ constexpr double kPolishTol = 1e-12; // FP64 polish bracket width in v
 constexpr float kIsoTol32 = 1e-6f;   // FP32 isolation bracket width in v
 constexpr double kIsoTol64 = 1e-12;  // FP64 isolation bracket width in v (plain mode)
 constexpr double kPrefilterMargin = 0.1;  // u-range margin of the pre-polish filter
+constexpr double kSideReach = 0.25;       // side search reach (in v) of a displaced FP32 root
 constexpr float kTangent32 = 1e-4f;  // tangent-root test, FP32 isolation
 constexpr double kTangent64 = 1e-12; // tangent-root test, FP64 isolation
 
@@ -116,6 +142,7 @@ enum Counter {
   C_COUNT
 };
 
+#ifndef SPOLY_HOST_BUILD
 // --------------------------------------------------------- warp helpers
 // Appends `cnt` items per lane to a global array with one atomic per warp;
 // returns this lane's first slot.  All lanes of the warp must call it.
@@ -138,5 +165,6 @@ SPOLY_D void warp_count(unsigned long long* counter, unsigned cnt) {
   unsigned s = __reduce_add_sync(0xffffffffu, cnt);
   if ((threadIdx.x & 31u) == 0 && s) atomicAdd(counter, (unsigned long long)s);
 }
+#endif
 
 }  // namespace spoly

@@ -18,7 +18,10 @@ from functools import lru_cache
 CONFIGS = [("R3", 3, 5), ("R4", 4, 5), ("T6", 6, 7)]
 
 
-def generate(name: str, N: int, ED: int) -> str:
+def generate(name: str, N: int, ED: int, absolute: bool = False) -> str:
+    """absolute=True emits the same memoised expansion over |E| with every
+    term added: a bound on the sum of absolute values of all products that
+    make each coefficient of the determinant (its rounding-error scale)."""
     def edeg(i, j):
         return ED - i - j
 
@@ -45,9 +48,11 @@ def generate(name: str, N: int, ED: int) -> str:
         a, b = min(i, j), max(i, j)
         return f"E[{offs[(a, b)] + c}]"
 
-    lines = [f"// {name}: N = {N}, entry degree <= {ED} - i - j, result degree <= {RD}.",
+    fname = f"laplace_abs_{name}" if absolute else f"laplace_{name}"
+    what = "sum of |products| of the expansion" if absolute else "determinant"
+    lines = [f"// {name}: N = {N}, entry degree <= {ED} - i - j, result degree <= {RD}; {what}.",
              "template <typename T>",
-             f"SPOLY_D void laplace_{name}(const T (&E)[{sym}], T (&r)[{RD + 1}]) {{"]
+             f"SPOLY_D void {fname}(const T (&E)[{sym}], T (&r)[{RD + 1}]) {{"]
     row = N - 1
     for j in range(N):
         mask = 1 << j
@@ -67,7 +72,7 @@ def generate(name: str, N: int, ED: int) -> str:
                 sub = mask & ~(1 << j)
                 de, ds = edeg(row, j), mdeg(row + 1, sub)
                 if de >= 0 and ds >= 0 and nonzero(row + 1, sub):
-                    neg = pos & 1
+                    neg = (pos & 1) and not absolute
                     for x in range(de + 1):
                         for y in range(ds + 1):
                             terms.setdefault(x + y, []).append((neg, E(row, j, x), f"m{sub}_{y}"))

@@ -18,6 +18,7 @@ struct K1Params {
   int64_t path_cap;
 };
 
+#ifndef SPOLY_HOST_BUILD
 cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st);
@@ -40,5 +41,6 @@ cudaError_t launch_chains_all(const ChainParams& P, int num_sms, cudaStream_t st
 cudaError_t launch_chains_explicit(const ChainParams& P, const int32_t* src, int64_t n, int num_sms,
                                    cudaStream_t st);
 cudaError_t launch_chains_cone(const ChainParams& P, int num_sms, cudaStream_t st);
+#endif
 
 }  // namespace spoly

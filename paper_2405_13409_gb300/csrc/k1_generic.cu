@@ -1,73 +1,15 @@
-// Generic-size isolation kernel of the 1-bounce solve, FP64 throughout.
+// Side kernel of the 1-bounce solve, FP64 throughout.
 //
-// Handles the candidates whose trimmed Bezout size n is not one of the sizes
-// the unrolled kernels are instantiated for (flat or degenerate triangles,
-// index-matched refraction).  Same algorithm, with runtime loops.
-#include "k1_iso.cuh"
+// Handles the side queue: candidates whose trimmed Bezout size n is not one
+// of the sizes the unrolled kernels are instantiated for (flat or degenerate
+// triangles, index-matched refraction), which run the same algorithm with
+// runtime loops, and candidates whose FP32 isolation was not certified, which
+// re-run the unrolled expansion and the isolation in FP64.
+#include "k1_generic.cuh"
 
 namespace spoly {
 
-// Bezout entry (i, j) for a runtime size n (Eq. eq_bezout).
-template <int DB>
-SPOLY_D void bezout_entry_rt(const BPd<2>& a, const BPd<DB>& b, int na, int nb, int n, int i, int j,
-                             double (&out)[DB + 2]) {
-  constexpr int ED = DB + 1;
-  for (int c = 0; c <= ED; ++c) out[c] = 0.0;
-  const int kmax = min(i, n - 1 - j);
-  for (int k = 0; k <= kmax; ++k) {
-    const int p = i - k, q = j + 1 + k;
-    if (p <= 2 && p <= na && q <= DB && q <= nb)
-      for (int x = 0; x <= 2 - p; ++x)
-        for (int y = 0; y <= DB - q; ++y) out[x + y] += a.c[bidx(2, p, x)] * b.c[bidx(DB, q, y)];
-    if (q <= 2 && q <= na && p <= DB && p <= nb)
-      for (int x = 0; x <= DB - p; ++x)
-        for (int y = 0; y <= 2 - q; ++y) out[x + y] -= b.c[bidx(DB, p, x)] * a.c[bidx(2, q, y)];
-  }
-}
-
-// Memoised Laplace expansion with a runtime size n <= 6 (Sec. 5.2).
-template <int DB>
-SPOLY_D void laplace_rt(const double (&E)[6][6][DB + 2], int n, double (&r)[kRD + 1]) {
-  constexpr int ED = DB + 1;
-  double M[64][kRD + 1];
-  for (int j = 0; j < n; ++j)
-    for (int c = 0; c <= kRD; ++c) M[1 << j][c] = (c <= ED - (n - 1) - j) ? E[n - 1][j][c] : 0.0;
-  for (int row = n - 2; row >= 0; --row) {
-    for (unsigned mask = 1; mask < (1u << n); ++mask) {
-      if (__popc(mask) != n - row) continue;
-      double acc[kRD + 1];
-      for (int c = 0; c <= kRD; ++c) acc[c] = 0.0;
-      int pos = 0;
-      for (int j = 0; j < n; ++j) {
-        if (!(mask & (1u << j))) continue;
-        const unsigned sub = mask & ~(1u << j);
-        const int de = ED - row - j;
-        const int ds = minor_deg(n, ED, row + 1, sub);
-        if (de >= 0 && ds >= 0)
-          for (int x = 0; x <= de; ++x) {
-            const double ex = (pos & 1) ? -E[row][j][x] : E[row][j][x];
-            for (int y = 0; y <= ds && x + y <= kRD; ++y) acc[x + y] = fma(ex, M[sub][y], acc[x + y]);
-          }
-        ++pos;
-      }
-      for (int c = 0; c <= kRD; ++c) M[mask][c] = acc[c];
-    }
-  }
-  for (int c = 0; c <= kRD; ++c) r[c] = M[(1u << n) - 1u][c];
-}
-
-template <int DB>
-SPOLY_D int k1_generic_one(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int chain, unsigned& n_v,
-                           unsigned& n_pref) {
-  double E[6][6][DB + 2];
-  for (int i = 0; i < s.n; ++i)
-    for (int j = 0; j < s.n; ++j) bezout_entry_rt<DB>(s.a, s.b, s.na, s.nb, s.n, i, j, E[i][j]);
-  double r[kRD + 1];
-  laplace_rt<DB>(E, s.n, r);
-  return k1_finish<double, kRD, DB>(s, r, items, chain, n_v, n_pref);
-}
-
-__global__ void __launch_bounds__(64) k1_generic_kernel(K1Params P) {
+__global__ void __launch_bounds__(64) k1_side_kernel(K1Params P) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const unsigned long long ns = *(volatile unsigned long long*)(P.counters + C_SIDE);
@@ -86,10 +28,22 @@ __global__ void __launch_bounds__(64) k1_generic_kernel(K1Params P) {
       int r = 0;
       if (qd.type == SPOLY_R) {
         K1Sys<4> s;
-        r = k1_system<4>(tr, qd, s) ? k1_generic_one<4>(s, items, c, n_v, n_pref) : -1;
+        if (!k1_system<4>(tr, qd, s))
+          r = -1;
+        else if (s.n == 3)
+          r = k1_isolate_sized<double, 3, 4>(s, items, c, n_v, n_pref);
+        else if (s.n == 4)
+          r = k1_isolate_sized<double, 4, 4>(s, items, c, n_v, n_pref);
+        else
+          r = k1_generic_one<4>(s, items, c, n_v, n_pref);
       } else {
         K1Sys<6> s;
-        r = k1_system<6>(tr, qd, s) ? k1_generic_one<6>(s, items, c, n_v, n_pref) : -1;
+        if (!k1_system<6>(tr, qd, s))
+          r = -1;
+        else if (s.n == 6)
+          r = k1_isolate_sized<double, 6, 6>(s, items, c, n_v, n_pref);
+        else
+          r = k1_generic_one<6>(s, items, c, n_v, n_pref);
       }
       n_deg = (r < 0) ? 1u : 0u;
       nq = r > 0 ? r : 0;
@@ -106,7 +60,7 @@ __global__ void __launch_bounds__(64) k1_generic_kernel(K1Params P) {
 }
 
 cudaError_t launch_k1_generic(const K1Params& P, int num_sms, cudaStream_t st) {
-  k1_generic_kernel<<<num_sms, 64, 0, st>>>(P);
+  k1_side_kernel<<<num_sms * 4, 64, 0, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,7 @@
 // Isolation kernel of the 1-bounce solve for the generic Bezout sizes
 // (R: n = 3 or 4, T: n = 6), templated on the arithmetic type of the
-// univariate phase.  Candidates whose trimmed size differs go to a side queue
-// handled by the generic FP64 kernel.
+// univariate phase.  Candidates whose trimmed size differs go to a side
+// queue handled in FP64 by the side kernel.
 #pragma once
 #include "k1_sys.cuh"
 #include "laplace_gen.cuh"
@@ -109,6 +109,7 @@ SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int
   return k1_finish<T, RD, DB>(s, r, items, chain, n_vroots, n_pref);
 }
 
+#ifndef SPOLY_HOST_BUILD
 template <typename T>
 __global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
   const int lane = threadIdx.x & 31;
@@ -163,5 +164,6 @@ __global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
     }
   }
 }
+#endif
 
 }  // namespace spoly

@@ -214,14 +214,15 @@ SPOLY_D uint32_t ill_flag(const K1Sys<DB>& s, double z, const RootItem& it) {
   return (fabs(slope) / s.sc.t < kIllCond * scale) ? SPOLY_FLAG_ILL_COND : 0u;
 }
 
-// Root next to a critical point c on one side (dir = -1 or +1): step out from
-// c by doubling until the FP64 determinant changes sign (within 1e-3 in v),
+// Root next to a point c on one side (dir = -1 or +1): step out from c by
+// doubling until the FP64 determinant changes sign (within `reach` in v),
 // then bisect.  Returns false when no sign change is found.
 template <int DB>
-SPOLY_D bool side_root(const K1Sys<DB>& s, double c, double fc, int dir, double zmin, double zmax, double* root) {
+SPOLY_D bool side_root(const K1Sys<DB>& s, double c, double fc, int dir, double zmin, double zmax, double* root,
+                       double reach = 1e-3) {
   double p = c;
   double w = 1e-8 / s.sc.t;
-  const double wmax = 1e-3 / s.sc.t;
+  const double wmax = reach / s.sc.t;
   while (w <= wmax) {
     double x = c + dir * w;
     if (x < zmin || x > zmax) return false;
@@ -240,12 +241,12 @@ SPOLY_D bool side_root(const K1Sys<DB>& s, double c, double fc, int dir, double 
   return false;
 }
 
-// v-polish of one bracket in FP64 (north star (1): "root polishing by
-// bisection near the final interval").  A sign-change bracket from the
-// isolation is bisected on the numeric determinant to width 1e-12 in v, after
-// widening by doubling if the FP64 signs agree; a tangent bracket (critical
-// point of the isolated polynomial) is resolved into the roots on either side
-// of it, if the FP64 determinant has them.  Writes the roots back into `it`.
+// v-polish of one bracket in FP64 (root polishing by bisection near the
+// final interval).  A sign-change bracket from the isolation is bisected on
+// the numeric determinant to width 1e-12 in v.  A bracket whose FP64 signs
+// agree (the FP32 root is displaced) and a tangent bracket (critical point of
+// the isolated polynomial) are resolved into the nearest FP64 roots on either
+// side.  Writes the roots back into `it`.
 template <int DB>
 SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigned& lost) {
   K1Sys<DB> s;
@@ -267,22 +268,12 @@ SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigne
       v1 = true;
       f1 = SPOLY_FLAG_TANGENT | SPOLY_FLAG_ILL_COND;
     } else {
-      v1 = side_root<DB>(s, c, fc, -1, zmin, zmax, &r1);
-      v2 = side_root<DB>(s, c, fc, +1, zmin, zmax, &r2);
+      v1 = side_root<DB>(s, c, fc, -1, zmin, zmax, &r1, kSideReach);
+      v2 = side_root<DB>(s, c, fc, +1, zmin, zmax, &r2, kSideReach);
     }
   } else {
-    double zlo = it.zlo, zhi = it.zhi;
-    double flo = det_at<DB>(s, zlo), fhi = det_at<DB>(s, zhi);
-    double wdt = fmax(zhi - zlo, 1e-15 / s.sc.t);
-    int grow = 0;
-    while (!((flo < 0.0) != (fhi < 0.0)) && flo != 0.0 && fhi != 0.0 && grow < 20) {
-      zlo = fmax(zmin - wdt, zlo - wdt);
-      zhi = fmin(zmax + wdt, zhi + wdt);
-      wdt *= 2.0;
-      flo = det_at<DB>(s, zlo);
-      fhi = det_at<DB>(s, zhi);
-      ++grow;
-    }
+    const double zlo = it.zlo, zhi = it.zhi;
+    const double flo = det_at<DB>(s, zlo), fhi = det_at<DB>(s, zhi);
     if (flo == 0.0) {
       r1 = zlo;
       v1 = true;
@@ -292,6 +283,11 @@ SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigne
     } else if ((flo < 0.0) != (fhi < 0.0)) {
       r1 = bisect_det<DB>(s, zlo, zhi, flo);
       v1 = true;
+    } else {
+      // The FP32 bracket has no FP64 sign change: the FP32 root is displaced.
+      // Search outward on both sides for the nearest FP64 roots.
+      v1 = side_root<DB>(s, zlo, flo, -1, zmin, zmax, &r1, kSideReach);
+      v2 = side_root<DB>(s, zhi, fhi, +1, zmin, zmax, &r2, kSideReach);
     }
   }
   if (v1 && !(f1 & SPOLY_FLAG_TANGENT)) f1 |= ill_flag<DB>(s, r1, it);

@@ -365,6 +365,7 @@ SPOLY_D T horner_from(const T (&w)[DM + 1], int j, T x) {
 // |p(c)| <= tang * rscale are reported as tangent roots.  Derivatives are
 // taken as p^(j) / j! (binomial weights), which has the same roots.
 // Returns the number of brackets written to (blo, bhi, bfl).
+
 template <typename T, int DM>
 SPOLY_D int isolate(const T (&p)[DM + 1], int deg, T lo, T hi, T tol, T tang, T rscale, T (&blo)[DM + 1],
                     T (&bhi)[DM + 1], uint32_t (&bfl)[DM + 1]) {
