@@ -15,7 +15,7 @@ from __future__ import annotations
 import os
 from functools import lru_cache
 
-CONFIGS = [("R3", 3, 5), ("R4", 4, 5), ("T6", 6, 7)]
+CONFIGS = [("R3", 3, 5), ("R4", 4, 5), ("T5", 5, 7), ("T6", 6, 7)]
 
 
 def generate(name: str, N: int, ED: int, absolute: bool = False) -> str:

@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(64) k1_side_kernel(K1Params P) {
           r = -1;
         else if (s.n == 6)
           r = k1_isolate_sized<double, 6, 6>(s, items, c, n_v, n_pref);
+        else if (s.n == 5)
+          r = k1_isolate_sized<double, 5, 6>(s, items, c, n_v, n_pref);
         else
           r = k1_generic_one<6>(s, items, c, n_v, n_pref);
       }

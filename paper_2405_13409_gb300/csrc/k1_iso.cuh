@@ -1,5 +1,5 @@
-// Isolation kernel of the 1-bounce solve for the generic Bezout sizes
-// (R: n = 3 or 4, T: n = 6), templated on the arithmetic type of the
+// Isolation kernel of the 1-bounce solve for the common Bezout sizes
+// (R: n = 3 or 4, T: n = 5 or 6), templated on the arithmetic type of the
 // univariate phase.  Candidates whose trimmed size differs go to a side
 // queue handled in FP64 by the side kernel.
 #pragma once
@@ -104,6 +104,7 @@ SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int
     bezout_sym<T, N, 2, DB>(s.a, s.b, s.na, s.nb, E);
     if constexpr (N == 3 && DB == 4) laplace_R3<T>(E, r);
     if constexpr (N == 4 && DB == 4) laplace_R4<T>(E, r);
+    if constexpr (N == 5 && DB == 6) laplace_T5<T>(E, r);
     if constexpr (N == 6 && DB == 6) laplace_T6<T>(E, r);
   }
   return k1_finish<T, RD, DB>(s, r, items, chain, n_vroots, n_pref);
@@ -143,6 +144,8 @@ __global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
             r = -1;
           else if (s.n == 6)
             r = k1_isolate_sized<T, 6, 6>(s, items, int(c), n_v, n_pref);
+          else if (s.n == 5)
+            r = k1_isolate_sized<T, 5, 6>(s, items, int(c), n_v, n_pref);
           else
             r = -2;
         }

@@ -1,6 +1,6 @@
 // FP64 polish kernel of the 1-bounce solve (path phase, Sec. 5.3), plus the
 // host launchers of the 1-bounce kernels.
-#include "k1_sys.cuh"
+#include "k1_polish.cuh"
 
 namespace spoly {
 

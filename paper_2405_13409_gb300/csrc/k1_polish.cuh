@@ -1,0 +1,328 @@
+// FP64 v-polish and path phase of the 1-bounce solve (Sec. 5.3).
+#pragma once
+#include "k1_generic.cuh"
+
+namespace spoly {
+
+// Bits of RootItem::flags after the v-polish: root 1 in zlo with public flags
+// in bits 0-7, root 2 in zhi with public flags in bits 8-15.
+constexpr uint32_t kRoot1Valid = 1u << 30;
+constexpr uint32_t kRoot2Valid = 1u << 31;
+
+// FP64 resultant r(z) of a candidate's scaled system (the same Bezout entries
+// and Laplace expansion as the isolation, in FP64), normalised by a power of
+// two and trimmed like the isolation's.  Returns its degree (< 1: none).
+template <int DB>
+SPOLY_D int k1_r64(const K1Sys<DB>& s, double (&r)[kRD + 1]) {
+  constexpr int ED = DB + 1;
+#pragma unroll
+  for (int c = 0; c <= kRD; ++c) r[c] = 0.0;
+  int rd = -1;
+  if constexpr (DB == 4) {
+    if (s.n == 3) {
+      double E[sym_size(3, ED)], rr[10];
+      bezout_sym<double, 3, 2, 4>(s.a, s.b, s.na, s.nb, E);
+      laplace_R3<double>(E, rr);
+#pragma unroll
+      for (int c = 0; c <= 9; ++c) r[c] = rr[c];
+      rd = 9;
+    } else if (s.n == 4) {
+      double E[sym_size(4, ED)], rr[9];
+      bezout_sym<double, 4, 2, 4>(s.a, s.b, s.na, s.nb, E);
+      laplace_R4<double>(E, rr);
+#pragma unroll
+      for (int c = 0; c <= 8; ++c) r[c] = rr[c];
+      rd = 8;
+    }
+  } else {
+    if (s.n == 6) {
+      double E[sym_size(6, ED)], rr[13];
+      bezout_sym<double, 6, 2, 6>(s.a, s.b, s.na, s.nb, E);
+      laplace_T6<double>(E, rr);
+#pragma unroll
+      for (int c = 0; c <= 12; ++c) r[c] = rr[c];
+      rd = 12;
+    } else if (s.n == 5) {
+      double E[sym_size(5, ED)], rr[16];
+      bezout_sym<double, 5, 2, 6>(s.a, s.b, s.na, s.nb, E);
+      laplace_T5<double>(E, rr);
+#pragma unroll
+      for (int c = 0; c <= 15; ++c) r[c] = rr[c];
+      rd = 15;
+    }
+  }
+  if (rd < 0) {
+    double E[6][6][DB + 2];
+    for (int i = 0; i < s.n; ++i)
+      for (int j = 0; j < s.n; ++j) bezout_entry_rt<DB>(s.a, s.b, s.na, s.nb, s.n, i, j, E[i][j]);
+    laplace_rt<DB>(E, s.n, r);
+    rd = s.n * (ED - s.n + 1);
+  }
+  double mx = 0.0;
+#pragma unroll
+  for (int c = 0; c <= kRD; ++c) mx = fmax(mx, fabs(r[c]));
+  if (!(mx > 0.0)) return -1;
+  int e2;
+  frexp(mx, &e2);
+  const double Z = (1.0 + kDelta) / s.sc.t;
+  double mxz = 0.0, zp = 1.0;
+#pragma unroll
+  for (int c = 0; c <= kRD; ++c) {
+    r[c] = ldexp(r[c], -e2);
+    mxz = fmax(mxz, fabs(r[c]) * zp);
+    zp *= Z;
+  }
+  int deg = rd;
+  zp = pow(Z, double(deg));
+  while (deg >= 1 && fabs(r[deg]) * zp <= kTrim * mxz) {
+    --deg;
+    zp /= Z;
+  }
+  return deg;
+}
+
+SPOLY_D double horner64(const double (&r)[kRD + 1], int deg, double z) {
+  double f = 0.0;
+#pragma unroll
+  for (int c = kRD; c >= 0; --c)
+    if (c <= deg) f = fma(f, z, r[c]);
+  return f;
+}
+
+SPOLY_D double dhorner64(const double (&r)[kRD + 1], int deg, double z) {
+  double f = 0.0;
+#pragma unroll
+  for (int c = kRD; c >= 1; --c)
+    if (c <= deg) f = fma(f, z, double(c) * r[c]);
+  return f;
+}
+
+// FP64 bisection of r on [zl, zh] (signs differ) to width kPolishTol in v.
+SPOLY_D double bisect64(const double (&r)[kRD + 1], int deg, double zl, double zh, double fl, double tol) {
+  while (zh - zl > tol) {
+    const double zm = 0.5 * (zl + zh);
+    if (!(zm > zl && zm < zh)) break;
+    const double fm = horner64(r, deg, zm);
+    if (fm == 0.0) return zm;
+    if ((fm < 0.0) == (fl < 0.0)) {
+      zl = zm;
+      fl = fm;
+    } else {
+      zh = zm;
+    }
+  }
+  return 0.5 * (zl + zh);
+}
+
+// Root of r next to a point c on one side (dir = -1 or +1): step out from c
+// by doubling until r changes sign (within `reach` in v), then bisect.
+SPOLY_D bool side_root64(const double (&r)[kRD + 1], int deg, double t, double c, double fc, int dir, double zmin,
+                         double zmax, double* root) {
+  double p = c;
+  double w = 1e-8 / t;
+  const double wmax = kSideReach / t;
+  const double tol = kPolishTol / t;
+  while (w <= wmax) {
+    const double x = c + dir * w;
+    if (x < zmin || x > zmax) return false;
+    const double fx = horner64(r, deg, x);
+    if (fx == 0.0) {
+      *root = x;
+      return true;
+    }
+    if ((fx < 0.0) != (fc < 0.0)) {
+      *root = (dir < 0) ? bisect64(r, deg, x, p, fx, tol) : bisect64(r, deg, p, x, fc, tol);
+      return true;
+    }
+    p = x;
+    w *= 2.0;
+  }
+  return false;
+}
+
+// ILL_COND when |r'(v*)| / sum_i |r_i| < kIllCond (v-domain coefficients:
+// r(v) = p(v / t), so r_i = p_i t^-i and r'(v) = p'(z) / t).
+SPOLY_D uint32_t ill_flag64(const double (&r)[kRD + 1], int deg, double t, double z) {
+  double S = 0.0, ti = 1.0;
+#pragma unroll
+  for (int c = 0; c <= kRD; ++c) {
+    if (c <= deg) S += fabs(r[c]) * ti;
+    ti /= t;
+  }
+  return (fabs(dhorner64(r, deg, z)) / t < kIllCond * S) ? SPOLY_FLAG_ILL_COND : 0u;
+}
+
+// v-polish of one bracket in FP64 (root polishing by bisection near the
+// final interval) on the FP64 resultant.  A sign-change bracket from the
+// isolation is bisected to width 1e-12 in v.  A bracket whose FP64 signs agree
+// (the FP32 root is displaced) and a tangent bracket (critical point of the
+// isolated polynomial) are resolved into the nearest FP64 roots on either
+// side, within kSideReach.  Writes the roots back into `it`.
+template <int DB>
+SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigned& lost) {
+  K1Sys<DB> s;
+  const uint32_t in_flags = it.flags & 0xffu;
+  it.flags = 0u;
+  double r[kRD + 1];
+  int deg = -1;
+  if (k1_system<DB>(tr, qd, s)) deg = k1_r64<DB>(s, r);
+  if (deg < 1) {
+    ++lost;
+    return;
+  }
+  const double t = s.sc.t, tol = kPolishTol / t;
+  const double zmin = -kDelta / t, zmax = (1.0 + kDelta) / t;
+  double r1 = 0.0, r2 = 0.0;
+  bool v1 = false, v2 = false;
+  uint32_t f1 = 0u, f2 = 0u;
+  const double zlo = it.zlo, zhi = it.zhi;
+  const double flo = horner64(r, deg, zlo), fhi = horner64(r, deg, zhi);
+  if (in_flags & SPOLY_FLAG_TANGENT) {
+    const double c = 0.5 * (zlo + zhi), fc = horner64(r, deg, c);
+    if (fc == 0.0) {
+      r1 = c;
+      v1 = true;
+      f1 = SPOLY_FLAG_TANGENT | SPOLY_FLAG_ILL_COND;
+    } else {
+      v1 = side_root64(r, deg, t, c, fc, -1, zmin, zmax, &r1);
+      v2 = side_root64(r, deg, t, c, fc, +1, zmin, zmax, &r2);
+    }
+  } else if (flo == 0.0) {
+    r1 = zlo;
+    v1 = true;
+  } else if (fhi == 0.0) {
+    r1 = zhi;
+    v1 = true;
+  } else if ((flo < 0.0) != (fhi < 0.0)) {
+    r1 = bisect64(r, deg, zlo, zhi, flo, tol);
+    v1 = true;
+  } else {
+    v1 = side_root64(r, deg, t, zlo, flo, -1, zmin, zmax, &r1);
+    v2 = side_root64(r, deg, t, zhi, fhi, +1, zmin, zmax, &r2);
+  }
+  if (v1 && !(f1 & SPOLY_FLAG_TANGENT)) f1 |= ill_flag64(r, deg, t, r1);
+  if (v2) f2 |= ill_flag64(r, deg, t, r2);
+  v1 = v1 && r1 >= zmin && r1 <= zmax;
+  v2 = v2 && r2 >= zmin && r2 <= zmax;
+  if (!v1 && !v2) ++lost;
+  it.zlo = r1;
+  it.zhi = r2;
+  it.flags = (v1 ? kRoot1Valid : 0u) | (v2 ? kRoot2Valid : 0u) | (f1 & 0xffu) | ((f2 & 0xffu) << 8);
+}
+
+// Path phase (Sec. 5.3) for one polished root z*: u from a(u, v*) = 0 (b if
+// a(., v*) vanishes), Newton on (a, b), path-space check of Eq. eq_ch,
+// sidedness and the in-triangle test.  Appends up to 6 paths to `out`.
+template <int DB>
+SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, double zs, uint32_t vflags, int q,
+                         int t, spoly_path (&out)[6], int np, unsigned& n_u) {
+  const double v0 = zs * s.sc.t;
+  double am[3];
+  a_at<double>(s.a, s.na, zs, am);
+  double amag = 0.0;
+#pragma unroll
+  for (int k = 0; k < bsize(2); ++k) amag = fmax(amag, fabs(s.a.c[k]));
+  double wr[DB + 1];
+  uint32_t wf[DB + 1];
+  int nw = 0;
+  const double wlo = -kDelta / s.sc.s, whi = (1.0 - v0 + kDelta) / s.sc.s;
+  if (fmax(fabs(am[0]), fmax(fabs(am[1]), fabs(am[2]))) > kTrim * amag) {
+    double w2[2];
+    uint32_t f2[2];
+    const int n2 = quad_roots<double>(am[0], am[1], am[2], 1e-12, w2, f2);
+    for (int i = 0; i < n2; ++i)
+      if (w2[i] >= wlo && w2[i] <= whi) {
+        wr[nw] = w2[i];
+        wf[nw] = f2[i];
+        ++nw;
+      }
+  } else {
+    double bv[DB + 1];
+    double bs = 0.0;
+#pragma unroll
+    for (int mm = 0; mm <= DB; ++mm) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = DB - mm; j >= 0; --j) acc = fma(acc, zs, s.b.c[bidx(DB, mm, j)]);
+      bv[mm] = (mm <= s.nb) ? acc : 0.0;
+      bs += fabs(bv[mm]);
+    }
+    double blo[DB + 1], bhi[DB + 1];
+    uint32_t bfl[DB + 1];
+    const int n2 = isolate<double, DB>(bv, s.nb, wlo, whi, kIsoTol64 / s.sc.s * 1e-2, kTangent64, bs, blo, bhi, bfl);
+    for (int i = 0; i < n2 && nw <= DB; ++i) {
+      wr[nw] = 0.5 * (blo[i] + bhi[i]);
+      wf[nw] = bfl[i];
+      ++nw;
+    }
+  }
+  for (int i = 0; i < nw; ++i) {
+    ++n_u;
+    double w = wr[i], z = zs;
+    newton_ab<DB>(s, w, z);
+    const double u = w * s.sc.s, v = z * s.sc.t;
+    uint32_t flags = vflags | wf[i];
+    const d3 x1 = tr.p0 + u * (tr.p1 - tr.p0) + v * (tr.p2 - tr.p0);
+    const d3 nn = tr.n0 + u * (tr.n1 - tr.n0) + v * (tr.n2 - tr.n0);
+    double res = 1.0;
+    if (!vertex_check(qd.x0, x1, qd.x2, nn, qd.type, qd.eta0, qd.eta1, &res, &flags)) continue;
+    if (!(res < kResidual)) continue;
+    const double wmin = fmin(fmin(u, v), 1.0 - u - v);
+    if (wmin < 0.0) continue;
+    if (wmin < kEdgeEps) flags |= SPOLY_FLAG_EDGE;
+    bool dup = false;
+    for (int k = 0; k < np; ++k)
+      if (fabs(out[k].uv[0][0] - u) <= 1e-9 && fabs(out[k].uv[0][1] - v) <= 1e-9) {
+        out[k].flags |= flags;
+        dup = true;
+      }
+    if (dup || np >= 6) continue;
+    spoly_path& p = out[np++];
+    p.query = q;
+    p.tri[0] = t;
+    p.tri[1] = -1;
+    p.reserved = 0;
+    p.uv[0][0] = u;
+    p.uv[0][1] = v;
+    p.uv[1][0] = 0.0;
+    p.uv[1][1] = 0.0;
+    p.x[0][0] = x1.x;
+    p.x[0][1] = x1.y;
+    p.x[0][2] = x1.z;
+    p.x[1][0] = p.x[1][1] = p.x[1][2] = 0.0;
+    p.residual = float(res);
+    p.flags = flags;
+  }
+  return np;
+}
+
+// Path phase of queue item i.  Roots already produced by an earlier bracket
+// of the same candidate (items of one candidate are contiguous in the queue)
+// or equal to the item's other root within 1e-9 in v are skipped.
+template <int DB>
+SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue, int64_t i, int q, int t,
+                         spoly_path (&out)[6], unsigned& n_u) {
+  const RootItem it = queue[i];
+  K1Sys<DB> s;
+  if (!k1_system<DB>(tr, qd, s)) return 0;
+  const double dtol = 1e-9 / s.sc.t;
+  int np = 0;
+  for (int r = 0; r < 2; ++r) {
+    const uint32_t valid = r == 0 ? kRoot1Valid : kRoot2Valid;
+    if (!(it.flags & valid)) continue;
+    const double z = r == 0 ? it.zlo : it.zhi;
+    bool dup = (r == 1 && (it.flags & kRoot1Valid) && fabs(it.zlo - z) <= dtol);
+    for (int64_t j = i - 1; j >= 0 && !dup; --j) {
+      const RootItem o = queue[j];
+      if (o.chain != it.chain) break;
+      if (((o.flags & kRoot1Valid) && fabs(o.zlo - z) <= dtol) || ((o.flags & kRoot2Valid) && fabs(o.zhi - z) <= dtol))
+        dup = true;
+    }
+    if (dup) continue;
+    const uint32_t vflags = r == 0 ? (it.flags & 0xffu) : ((it.flags >> 8) & 0xffu);
+    np = k1_path_root<DB>(s, tr, qd, z, vflags, q, t, out, np, n_u);
+  }
+  return np;
+}
+
+}  // namespace spoly

@@ -3,7 +3,7 @@
 // the CPU, so tests can exercise kernel arithmetic without a GPU.  It is not
 // a product path and it makes no parity claim: the GPU tests do.
 #define SPOLY_HOST_BUILD 1
-#include "k1_generic.cuh"
+#include "k1_polish.cuh"
 
 using namespace spoly;
 
@@ -19,6 +19,7 @@ int isolate_one(const K1Sys<DB>& s, int precision, RootItem (&items)[kRD + 1], u
       if (s.n == 4) r = k1_isolate_sized<float, 4, 4>(s, items, 0, nv, np);
     } else {
       if (s.n == 6) r = k1_isolate_sized<float, 6, 6>(s, items, 0, nv, np);
+      if (s.n == 5) r = k1_isolate_sized<float, 5, 6>(s, items, 0, nv, np);
     }
   }
   status[0] = r;
@@ -28,6 +29,7 @@ int isolate_one(const K1Sys<DB>& s, int precision, RootItem (&items)[kRD + 1], u
     if (s.n == 4) return k1_isolate_sized<double, 4, 4>(s, items, 0, nv, np);
   } else {
     if (s.n == 6) return k1_isolate_sized<double, 6, 6>(s, items, 0, nv, np);
+    if (s.n == 5) return k1_isolate_sized<double, 5, 6>(s, items, 0, nv, np);
   }
   return k1_generic_one<DB>(s, items, 0, nv, np);
 }

@@ -153,8 +153,12 @@ def test_curved_planted_cases(ctx, type_, precision):
     ref, _ = _oracle(s, s.chains)
     assert ref.size > 1500
     # Strongly curved normals (about 15 degrees across a triangle) push FP32
-    # isolation past its accuracy; mixed precision must keep recall >= 99.8%.
-    assert_parity(paths, ref, ch.shape[0], min_recall=1.0 if precision == binding.PLAIN_FP64 else 0.998)
+    # isolation past its accuracy; mixed precision must keep recall >= 99.8%
+    # and flagged disagreements <= 0.5% of candidates.
+    if precision == binding.PLAIN_FP64:
+        assert_parity(paths, ref, ch.shape[0])
+    else:
+        assert_parity(paths, ref, ch.shape[0], min_recall=0.998, max_flagged_frac=5e-3)
     _check_invariants(paths)
 
 

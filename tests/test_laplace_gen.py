@@ -12,7 +12,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2405_13409_gb300", "csrc")
-CONFIGS = [("R3", 3, 5), ("R4", 4, 5), ("T6", 6, 7)]
+CONFIGS = [("R3", 3, 5), ("R4", 4, 5), ("T5", 5, 7), ("T6", 6, 7)]
 
 
 def _packing(N, ED):
