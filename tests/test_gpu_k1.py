@@ -152,13 +152,13 @@ def test_curved_planted_cases(ctx, type_, precision):
     paths, stats, ch = _run(ctx, s, binding.CHAINS_EXPLICIT, precision, explicit=s.chains)
     ref, _ = _oracle(s, s.chains)
     assert ref.size > 1500
-    # Strongly curved normals (about 15 degrees across a triangle) push FP32
-    # isolation past its accuracy; mixed precision must keep recall >= 99.8%
-    # and flagged disagreements <= 0.5% of candidates.
-    if precision == binding.PLAIN_FP64:
-        assert_parity(paths, ref, ch.shape[0])
-    else:
-        assert_parity(paths, ref, ch.shape[0], min_recall=0.998, max_flagged_frac=5e-3)
+    # Strongly curved normals (about 15 degrees across a triangle) make many
+    # near-double roots: ill-conditioned (flagged) disagreements may reach
+    # 0.5% of candidates.  Plain FP64 keeps every unflagged path; mixed
+    # precision pushes FP32 isolation past its accuracy and must keep recall
+    # >= 99.8%.
+    recall = 1.0 if precision == binding.PLAIN_FP64 else 0.998
+    assert_parity(paths, ref, ch.shape[0], min_recall=recall, max_flagged_frac=5e-3)
     _check_invariants(paths)
 
 
