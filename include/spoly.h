@@ -228,6 +228,42 @@ spoly_status spoly_measure_peak(spoly_ctx* ctx, int32_t kind, double* tflops);
 /* Frees a solution set. */
 spoly_status spoly_solution_free(spoly_solution_set* set);
 
+/* The 1-bounce solve for callers that cannot allocate device memory.  (The
+ * paper has no counterpart: this is a deployment variant of spoly_solve.)
+ *
+ * Some callers may not allocate at all: code running where the allocator is
+ * off limits (a host callback, a real-time loop that must not block on an
+ * allocation), a plug-in whose host application owns all device memory, or
+ * a process with a fixed memory pool.  This entry point allocates nothing:
+ * the solve's scratch (counters and root-bracket queues) lives in one static
+ * device array of about 2.2 MiB inside the library, which every GPU that
+ * loads the library keeps until the process exits.
+ *
+ * Inputs are device pointers with the layouts of spoly_mesh, spoly_queries
+ * and the chain list (int32 [n_chains][3]); `paths` is a device buffer of
+ * `path_capacity` records that receives the admissible paths; *n_paths (host)
+ * receives their count.  precision is SPOLY_PLAIN_FP64 or SPOLY_MIXED.  The
+ * call selects `device`, enqueues on `cuda_stream`, waits for it to finish,
+ * restores the caller's current device and returns.  `msg` (host buffer of
+ * msg_len bytes, may be NULL) receives a message on failure.
+ *
+ * Limits and sharing: at most 4096 chains per call (more is rejected with
+ * SPOLY_EINVAL and a message).  All calls share the static array; each call
+ * clears its counters and overwrites its queues, so calls whose GPU work
+ * overlaps (other streams, unordered host threads) race and corrupt each
+ * other.  The first call on a device performs a one-time set-up (it looks up
+ * the array's device address); make that first call before any stream
+ * capture begins.
+ * Errors: EINVAL (null pointer, negative size, too many chains, bad
+ * precision or device), ECUDA (a CUDA call failed), ECAPACITY (more paths
+ * than path_capacity: *n_paths holds the required count and the first
+ * path_capacity paths, in completion order, were written). */
+spoly_status spoly_solve_noalloc(int device, void* cuda_stream, const double* tri, int64_t n_tris,
+                                 const double* x_first, const double* x_last, const double* eta,
+                                 const int32_t* types, const int32_t* k, int64_t n_queries, const int32_t* chains,
+                                 int64_t n_chains, int32_t precision, spoly_path* paths, int64_t path_capacity,
+                                 int64_t* n_paths, char* msg, int32_t msg_len);
+
 /* Library version string. */
 const char* spoly_version(void);
 

@@ -122,6 +122,8 @@ def load():
         "spoly_solution_free": ([P], c_int32),
         "spoly_phase_ms": ([P, P, ctypes.POINTER(ctypes.c_float), c_int32], c_int32),
         "spoly_measure_peak": ([P, c_int32, ctypes.POINTER(ctypes.c_double)], c_int32),
+        "spoly_solve_noalloc": ([ctypes.c_int, P, P, c_int64, P, P, P, P, P, c_int64, P, c_int64, c_int32, P,
+                                 c_int64, ctypes.POINTER(c_int64), ctypes.c_char_p, c_int32], c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -257,3 +259,17 @@ class Context:
         t = ctypes.c_double()
         self.check(self.lib.spoly_measure_peak(self.h, int(kind), ctypes.byref(t)), "spoly_measure_peak")
         return float(t.value)
+
+
+def spoly_solve_noalloc(device: int, stream, tri, x_first, x_last, eta, types, k, chains, precision: int, paths,
+                        path_capacity: int):
+    """Calls the no-allocation solve on device tensors.  Returns (status,
+    n_paths, message); the paths land in the caller's device buffer."""
+    lib = load()
+    n = c_int64(0)
+    msg = ctypes.create_string_buffer(256)
+    st = lib.spoly_solve_noalloc(int(device), c_void_p(stream or 0), _ptr(tri), int(tri.shape[1]), _ptr(x_first),
+                                 _ptr(x_last), _ptr(eta), _ptr(types), _ptr(k), int(x_first.shape[0]),
+                                 _ptr(chains), int(chains.shape[0]), int(precision), _ptr(paths),
+                                 int(path_capacity), ctypes.byref(n), msg, 256)
+    return int(st), int(n.value), msg.value.decode()
