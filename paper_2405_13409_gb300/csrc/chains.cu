@@ -143,11 +143,13 @@ __global__ void tri_boxes_kernel(ChainParams P) {
   }
 }
 
-// Unit-direction box from a point box toward x2, in FP32 with a relative slack.
-SPOLY_D bool to_box_overlaps(const float* B, float x2, float y2, float z2) {
-  const float xl = x2 - B[9], xh = x2 - B[6];
-  const float yl = y2 - B[10], yh = y2 - B[7];
-  const float zl = z2 - B[11], zh = z2 - B[8];
+// Unit-direction box from the triangle's bounding box toward a box of
+// endpoints [x2l, x2h] x [y2l, y2h] x [z2l, z2h] (a point when l = h), in
+// FP32 with a relative slack, tested against the outgoing-direction box.
+SPOLY_D bool box_overlaps(const float* B, float x2l, float x2h, float y2l, float y2h, float z2l, float z2h) {
+  const float xl = x2l - B[9], xh = x2h - B[6];
+  const float yl = y2l - B[10], yh = y2h - B[7];
+  const float zl = z2l - B[11], zh = z2h - B[8];
   auto s2lo = [](float lo, float hi) { return lo >= 0.f ? lo * lo : (hi <= 0.f ? hi * hi : 0.f); };
   auto s2hi = [](float lo, float hi) { return fmaxf(lo * lo, hi * hi); };
   const float l2lo = s2lo(xl, xh) + s2lo(yl, yh) + s2lo(zl, zh);
@@ -164,14 +166,23 @@ SPOLY_D bool to_box_overlaps(const float* B, float x2, float y2, float z2) {
   return ok;
 }
 
+SPOLY_D bool to_box_overlaps(const float* B, float x2, float y2, float z2) {
+  return box_overlaps(B, x2, x2, y2, y2, z2, z2);
+}
+
 // Pair test over a tile: each thread owns one query, the block walks a chunk
-// of triangles staged in shared memory.  Survivors are appended with one
-// atomic per warp per triangle.
+// of triangles staged in shared memory.  A triangle is first tested once
+// against the bounding box of the block's endpoints (a conservative superset
+// of its pair tests); only triangles that pass are tested pair by pair.
+// Survivors are appended with one atomic per warp per triangle.
 constexpr int kConeThreads = 128;
 constexpr int kConeTris = 256;
 
 __global__ void __launch_bounds__(kConeThreads) cone_pairs_kernel(ChainParams P, int tris_per_block) {
   __shared__ float sbox[kConeTris][12];
+  __shared__ int slist[kConeTris];
+  __shared__ int scount;
+  __shared__ float sred[6][kConeThreads / 32];
   const int64_t q = int64_t(blockIdx.x) * kConeThreads + threadIdx.x;
   const bool qok = q < P.qv.n;
   float x2 = 0.f, y2 = 0.f, z2 = 0.f;
@@ -180,15 +191,39 @@ __global__ void __launch_bounds__(kConeThreads) cone_pairs_kernel(ChainParams P,
     y2 = float(P.qv.x_last[3 * q + 1]);
     z2 = float(P.qv.x_last[3 * q + 2]);
   }
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // bounding box of the block's endpoints
+  float v[6] = {qok ? x2 : 3e38f, qok ? -x2 : 3e38f, qok ? y2 : 3e38f, qok ? -y2 : 3e38f,
+                qok ? z2 : 3e38f, qok ? -z2 : 3e38f};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[c] = fminf(v[c], __shfl_xor_sync(0xffffffffu, v[c], o));
+    if (lane == 0) sred[c][warp] = v[c];
+  }
+  __syncthreads();
+  float tb[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float m = sred[c][0];
+#pragma unroll
+    for (int w = 1; w < kConeThreads / 32; ++w) m = fminf(m, sred[c][w]);
+    tb[c] = m;
+  }
   const int t_begin = blockIdx.y * tris_per_block;
   const int t_end = min(P.tri_count, t_begin + tris_per_block);
   for (int t0 = t_begin; t0 < t_end; t0 += kConeTris) {
     const int nt = min(kConeTris, t_end - t0);
     __syncthreads();
     for (int k = threadIdx.x; k < nt * 12; k += kConeThreads) sbox[k / 12][k % 12] = P.boxes[int64_t(t0) * 12 + k];
+    if (threadIdx.x == 0) scount = 0;
     __syncthreads();
-    for (int k = 0; k < nt; ++k) {
+    for (int k = threadIdx.x; k < nt; k += kConeThreads)
+      if (box_overlaps(sbox[k], tb[0], -tb[1], tb[2], -tb[3], tb[4], -tb[5])) slist[atomicAdd(&scount, 1)] = k;
+    __syncthreads();
+    const int ns = scount;
+    for (int idx = 0; idx < ns; ++idx) {
+      const int k = slist[idx];
       const bool keep = qok && to_box_overlaps(sbox[k], x2, y2, z2);
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       if (!m) continue;
@@ -196,11 +231,11 @@ __global__ void __launch_bounds__(kConeThreads) cone_pairs_kernel(ChainParams P,
       if (lane == 0) base = atomicAdd(P.count, (unsigned long long)__popc(m));
       base = __shfl_sync(0xffffffffu, base, 0);
       if (keep) {
-        const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
-        if (idx < (unsigned long long)P.cap) {
-          P.out[3 * idx] = int32_t(q);
-          P.out[3 * idx + 1] = P.tri_begin + t0 + k;
-          P.out[3 * idx + 2] = -1;
+        const unsigned long long idx2 = base + __popc(m & ((1u << lane) - 1u));
+        if (idx2 < (unsigned long long)P.cap) {
+          P.out[3 * idx2] = int32_t(q);
+          P.out[3 * idx2 + 1] = P.tri_begin + t0 + k;
+          P.out[3 * idx2 + 2] = -1;
         }
       }
     }

@@ -27,6 +27,18 @@ template <typename T>
 inline T __ldg(const T* p) { return *p; }
 inline int __double2int_rn(double x) { return int(std::nearbyint(x)); }
 inline int __popc(unsigned x) { return __builtin_popcount(x); }
+#include <cstring>
+inline long long __double_as_longlong(double x) {
+  long long b;
+  std::memcpy(&b, &x, 8);
+  return b;
+}
+inline double __longlong_as_double(long long b) {
+  double x;
+  std::memcpy(&x, &b, 8);
+  return x;
+}
+inline int __float2int_rn(float x) { return int(std::nearbyint(x)); }
 #else
 #include <cuda_runtime.h>
 #define SPOLY_HD __host__ __device__ __forceinline__
@@ -95,6 +107,21 @@ struct QueryView {
   const int32_t* k;
   int64_t n;
 };
+
+// ------------------------------------------- FP64 magnitude bookkeeping
+// |x| as an integer that orders like |x| (non-NaN doubles), its binary
+// exponent, and exact scaling by 2^k: integer-pipe replacements for
+// fabs/fmax/frexp/ldexp, which would otherwise occupy the scarce FP64 pipe.
+SPOLY_D long long absbits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+SPOLY_D int expo_bits(long long ab) { return int(ab >> 52) - 1023; }
+SPOLY_D double scale2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const long long ab = b & 0x7fffffffffffffffLL;
+  if (ab == 0) return x;
+  const int e = int(ab >> 52) + k;
+  if (e <= 0) return 0.0;  // would be subnormal: negligible at these scales
+  return __longlong_as_double(b + ((long long)k << 52));
+}
 
 // ------------------------------------------------------------ constants
 // Readings shared with the oracle's (they are restated, not shared: the

@@ -17,15 +17,16 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
                       unsigned& n_vroots, unsigned& n_pref) {
   // Power-of-two normalisation of r and trimming of negligible leading terms
   // (their contribution over the domain is below kTrim of the largest term).
-  const T Z = T((1.0 + kDelta) / s.sc.t);
+  const double inv_t = scale2(1.0, -s.sc.kt);  // 1 / t, exact
+  const T Z = T((1.0 + kDelta) * inv_t);
   T mx = T(0);
 #pragma unroll
   for (int c = 0; c <= RD; ++c) mx = fmax(mx, fabs(r[c]));
   if (!(mx > T(0))) return -1;
   int e2;
-  frexp(double(mx), &e2);
+  frexp(mx, &e2);
 #pragma unroll
-  for (int c = 0; c <= RD; ++c) r[c] = T(ldexp(double(r[c]), -e2));
+  for (int c = 0; c <= RD; ++c) r[c] = ldexp(r[c], -e2);
   T zpow[RD + 1];
   zpow[0] = T(1);
 #pragma unroll
@@ -41,7 +42,7 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
   // sum_i |p_i| t^-i: the magnitude scale of r over v in [0, 1].
   T rscale = T(0);
   {
-    const T it = T(1.0 / s.sc.t);
+    const T it = T(inv_t);
     T zz = T(1);
 #pragma unroll
     for (int c = 0; c <= RD; ++c) {
@@ -49,9 +50,9 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
       zz *= it;
     }
   }
-  const T lo = T(-kDelta / s.sc.t), hi = Z;
+  const T lo = T(-kDelta * inv_t), hi = Z;
   constexpr bool fp32 = sizeof(T) == 4;
-  const T tol = fp32 ? T(kIsoTol32 / s.sc.t) : T(kIsoTol64 / s.sc.t);
+  const T tol = fp32 ? T(kIsoTol32 * inv_t) : T(kIsoTol64 * inv_t);
   const T tang = fp32 ? T(kTangent32) : T(kTangent64);
   T blo[RD + 1], bhi[RD + 1];
   uint32_t bfl[RD + 1];

@@ -10,7 +10,7 @@ SPOLY_D int64_t queue_items(const K1Params& P) {
 }
 
 // FP64 v-polish of every queued bracket, in place.
-__global__ void __launch_bounds__(128) k1_polish_kernel(K1Params P) {
+__global__ void __launch_bounds__(128, 1) k1_polish_kernel(K1Params P) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t n_items = queue_items(P);
   const int lane = threadIdx.x & 31;

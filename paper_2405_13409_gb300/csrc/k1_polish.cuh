@@ -9,6 +9,21 @@ namespace spoly {
 constexpr uint32_t kRoot1Valid = 1u << 30;
 constexpr uint32_t kRoot2Valid = 1u << 31;
 
+// Generic-size FP64 resultant (runtime n), kept out of line so its large
+// local arrays do not shape the register allocation of the common path.
+#ifdef SPOLY_HOST_BUILD
+#define SPOLY_NOINLINE
+#else
+#define SPOLY_NOINLINE __device__ __noinline__
+#endif
+template <int DB>
+SPOLY_NOINLINE void k1_r64_generic(const K1Sys<DB>& s, double (&r)[kRD + 1]) {
+  double E[6][6][DB + 2];
+  for (int i = 0; i < s.n; ++i)
+    for (int j = 0; j < s.n; ++j) bezout_entry_rt<DB>(s.a, s.b, s.na, s.nb, s.n, i, j, E[i][j]);
+  laplace_rt<DB>(E, s.n, r);
+}
+
 // FP64 resultant r(z) of a candidate's scaled system (the same Bezout entries
 // and Laplace expansion as the isolation, in FP64), normalised by a power of
 // two and trimmed like the isolation's.  Returns its degree (< 1: none).
@@ -52,32 +67,28 @@ SPOLY_D int k1_r64(const K1Sys<DB>& s, double (&r)[kRD + 1]) {
     }
   }
   if (rd < 0) {
-    double E[6][6][DB + 2];
-    for (int i = 0; i < s.n; ++i)
-      for (int j = 0; j < s.n; ++j) bezout_entry_rt<DB>(s.a, s.b, s.na, s.nb, s.n, i, j, E[i][j]);
-    laplace_rt<DB>(E, s.n, r);
+    k1_r64_generic<DB>(s, r);
     rd = s.n * (ED - s.n + 1);
   }
-  double mx = 0.0;
+  long long mb = 0;
 #pragma unroll
-  for (int c = 0; c <= kRD; ++c) mx = fmax(mx, fabs(r[c]));
-  if (!(mx > 0.0)) return -1;
-  int e2;
-  frexp(mx, &e2);
-  const double Z = (1.0 + kDelta) / s.sc.t;
+  for (int c = 0; c <= kRD; ++c) mb = max(mb, absbits(r[c]));
+  if (mb == 0) return -1;
+  const int e2 = expo_bits(mb) + 1;
+  const double Z = (1.0 + kDelta) * scale2(1.0, -s.sc.kt);
   double mxz = 0.0, zp = 1.0;
+  double zpow[kRD + 1];
 #pragma unroll
   for (int c = 0; c <= kRD; ++c) {
-    r[c] = ldexp(r[c], -e2);
+    r[c] = scale2(r[c], -e2);
+    zpow[c] = zp;
     mxz = fmax(mxz, fabs(r[c]) * zp);
     zp *= Z;
   }
   int deg = rd;
-  zp = pow(Z, double(deg));
-  while (deg >= 1 && fabs(r[deg]) * zp <= kTrim * mxz) {
-    --deg;
-    zp /= Z;
-  }
+#pragma unroll
+  for (int c = kRD; c >= 1; --c)
+    if (c == deg && fabs(r[c]) * zpow[c] <= kTrim * mxz) --deg;
   return deg;
 }
 

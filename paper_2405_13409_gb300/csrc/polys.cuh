@@ -72,28 +72,41 @@ SPOLY_D BPd<D> blin(double x, const BPd<D>& a, double y, const BPd<D>& b) {
 // m = (x2 - x0) x n_c (n_c the centroid normal), the square form uses the
 // first of (1,0,0), (0,0,1), (0,1,0) with |m^ . b| >= kSwitch; the product
 // form uses t = n x e1 unless |m^ . e1^| < kSwitch and |m^ . e2^| > |m^ . e1^|.
+// The choice is a threshold heuristic (it moves spurious roots, never true
+// ones), so it runs in FP32 off the FP64 pipe.
+SPOLY_D void plane_normal32(const TriD& tr, const QueryD& q, float& mx, float& my, float& mz) {
+  const float wx = float(q.x2.x - q.x0.x), wy = float(q.x2.y - q.x0.y), wz = float(q.x2.z - q.x0.z);
+  const float nx = float(tr.n0.x) + float(tr.n1.x) + float(tr.n2.x);
+  const float ny = float(tr.n0.y) + float(tr.n1.y) + float(tr.n2.y);
+  const float nz = float(tr.n0.z) + float(tr.n1.z) + float(tr.n2.z);
+  mx = wy * nz - wz * ny;
+  my = wz * nx - wx * nz;
+  mz = wx * ny - wy * nx;
+}
+
 SPOLY_D d3 choose_b(const TriD& tr, const QueryD& q) {
-  d3 nc = (1.0 / 3.0) * (tr.n0 + tr.n1 + tr.n2);
-  d3 m = cross(q.x2 - q.x0, nc);
-  const double mn = norm(m);
-  if (!(mn > 0.0)) return mk(1, 0, 0);
-  m = (1.0 / mn) * m;
-  if (fabs(m.x) >= kSwitch) return mk(1, 0, 0);
-  if (fabs(m.z) >= kSwitch) return mk(0, 0, 1);
-  if (fabs(m.y) >= kSwitch) return mk(0, 1, 0);
+  float mx, my, mz;
+  plane_normal32(tr, q, mx, my, mz);
+  const float m2 = mx * mx + my * my + mz * mz;
+  if (!(m2 > 0.f)) return mk(1, 0, 0);
+  const float t2 = float(kSwitch * kSwitch) * m2;  // |m^ . b| >= kSwitch  <=>  (m . b)^2 >= kSwitch^2 |m|^2
+  if (mx * mx >= t2) return mk(1, 0, 0);
+  if (mz * mz >= t2) return mk(0, 0, 1);
+  if (my * my >= t2) return mk(0, 1, 0);
   return mk(1, 0, 0);
 }
 
 SPOLY_D int choose_edge(const TriD& tr, const QueryD& q) {
-  d3 nc = (1.0 / 3.0) * (tr.n0 + tr.n1 + tr.n2);
-  d3 m = cross(q.x2 - q.x0, nc);
-  const double mn = norm(m);
-  if (!(mn > 0.0)) return 1;
-  m = (1.0 / mn) * m;
-  const d3 e1 = tr.p1 - tr.p0, e2 = tr.p2 - tr.p0;
-  const double c1 = fabs(dot(m, e1)) / norm(e1);
-  const double c2 = fabs(dot(m, e2)) / norm(e2);
-  return (c1 < kSwitch && c2 > c1) ? 2 : 1;
+  float mx, my, mz;
+  plane_normal32(tr, q, mx, my, mz);
+  const float m2 = mx * mx + my * my + mz * mz;
+  if (!(m2 > 0.f)) return 1;
+  const float e1x = float(tr.p1.x - tr.p0.x), e1y = float(tr.p1.y - tr.p0.y), e1z = float(tr.p1.z - tr.p0.z);
+  const float e2x = float(tr.p2.x - tr.p0.x), e2y = float(tr.p2.y - tr.p0.y), e2z = float(tr.p2.z - tr.p0.z);
+  const float d1 = mx * e1x + my * e1y + mz * e1z, d2 = mx * e2x + my * e2y + mz * e2z;
+  const float c1 = d1 * d1 / (e1x * e1x + e1y * e1y + e1z * e1z);  // (m . e^)^2, times |m|^2
+  const float c2 = d2 * d2 / (e2x * e2x + e2y * e2y + e2z * e2z);
+  return (c1 < float(kSwitch * kSwitch) * m2 && c2 > c1) ? 2 : 1;
 }
 
 // ------------------------------------------------------ coefficient phase
@@ -141,34 +154,19 @@ SPOLY_D BPd<6> build_b_T(const Frame& f, d3 bvec, double eta0, double eta1) {
 // Highest u-power with a non-negligible coefficient polynomial (Bezout size
 // rule "n is the degree", Sec. 5.1; negligible = max-abs <= kTrim * max-abs).
 template <int D>
-SPOLY_D int deg_u(const BPd<D>& p, double* maxabs_out = nullptr) {
-  double m = 0.0;
+SPOLY_D int deg_u(const BPd<D>& p) {
+  long long m = 0;
 #pragma unroll
-  for (int k = 0; k < bsize(D); ++k) m = fmax(m, fabs(p.c[k]));
-  if (maxabs_out) *maxabs_out = m;
+  for (int k = 0; k < bsize(D); ++k) m = max(m, absbits(p.c[k]));
+  if (m == 0) return -1;
+  const long long thr = absbits(kTrim * __longlong_as_double(m));
   int d = -1;
 #pragma unroll
   for (int i = 0; i <= D; ++i) {
-    double mi = 0.0;
+    long long mi = 0;
 #pragma unroll
-    for (int j = 0; i + j <= D; ++j) mi = fmax(mi, fabs(p.c[bidx(D, i, j)]));
-    if (mi > kTrim * m) d = i;
-  }
-  return d;
-}
-
-template <int D>
-SPOLY_D int deg_v(const BPd<D>& p) {
-  double m = 0.0;
-#pragma unroll
-  for (int k = 0; k < bsize(D); ++k) m = fmax(m, fabs(p.c[k]));
-  int d = -1;
-#pragma unroll
-  for (int j = 0; j <= D; ++j) {
-    double mj = 0.0;
-#pragma unroll
-    for (int i = 0; i + j <= D; ++i) mj = fmax(mj, fabs(p.c[bidx(D, i, j)]));
-    if (mj > kTrim * m) d = j;
+    for (int j = 0; i + j <= D; ++j) mi = max(mi, absbits(p.c[bidx(D, i, j)]));
+    if (mi > thr) d = i;
   }
   return d;
 }
@@ -176,7 +174,8 @@ SPOLY_D int deg_v(const BPd<D>& p) {
 // Exact power-of-two change of variables u = 2^ks w, v = 2^kt z that
 // balances b's coefficient magnitudes across u- and v-powers, followed by a
 // power-of-two normalisation of a and b.  Roots are unchanged (z = v / 2^kt);
-// the FP32 Laplace expansion then stays inside FP32's exponent range.
+// the FP32 Laplace expansion then stays inside FP32's exponent range.  The
+// magnitudes are compared by their binary exponents (integer arithmetic).
 struct Scaling {
   int ks, kt;   // u = 2^ks w, v = 2^kt z
   double s, t;  // 2^ks, 2^kt
@@ -184,45 +183,56 @@ struct Scaling {
 
 template <int D>
 SPOLY_D Scaling choose_scaling(const BPd<D>& b, int nu) {
-  const int nv = deg_v(b);
-  double m0u = 0.0, mnu = 0.0, m0v = 0.0, mnv = 0.0;
+  long long mall = 0;
+  long long mu[D + 1], mv[D + 1];
+#pragma unroll
+  for (int i = 0; i <= D; ++i) mu[i] = mv[i] = 0;
 #pragma unroll
   for (int i = 0; i <= D; ++i)
 #pragma unroll
     for (int j = 0; i + j <= D; ++j) {
-      const double a = fabs(b.c[bidx(D, i, j)]);
-      if (i == 0) m0u = fmax(m0u, a);
-      if (i == nu) mnu = fmax(mnu, a);
-      if (j == 0) m0v = fmax(m0v, a);
-      if (j == nv) mnv = fmax(mnv, a);
+      const long long a = absbits(b.c[bidx(D, i, j)]);
+      mu[i] = max(mu[i], a);
+      mv[j] = max(mv[j], a);
+      mall = max(mall, a);
     }
+  const long long thr = absbits(kTrim * __longlong_as_double(mall));
+  int nv = -1;
+#pragma unroll
+  for (int j = 0; j <= D; ++j)
+    if (mv[j] > thr) nv = j;
+  long long m0u = mu[0], mnu = 0, m0v = mv[0], mnv = 0;
+#pragma unroll
+  for (int i = 0; i <= D; ++i) {
+    if (i == nu) mnu = mu[i];
+    if (i == nv) mnv = mv[i];
+  }
   Scaling sc{0, 0, 1.0, 1.0};
-  if (nu > 0 && m0u > 0.0 && mnu > 0.0) sc.ks = __double2int_rn(log2(m0u / mnu) / nu);
-  if (nv > 0 && m0v > 0.0 && mnv > 0.0) sc.kt = __double2int_rn(log2(m0v / mnv) / nv);
+  if (nu > 0 && m0u > 0 && mnu > 0) sc.ks = __float2int_rn(float(expo_bits(m0u) - expo_bits(mnu)) / float(nu));
+  if (nv > 0 && m0v > 0 && mnv > 0) sc.kt = __float2int_rn(float(expo_bits(m0v) - expo_bits(mnv)) / float(nv));
   sc.ks = max(-30, min(60, sc.ks));
   sc.kt = max(-30, min(60, sc.kt));
-  sc.s = ldexp(1.0, sc.ks);
-  sc.t = ldexp(1.0, sc.kt);
+  sc.s = scale2(1.0, sc.ks);
+  sc.t = scale2(1.0, sc.kt);
   return sc;
 }
 
 template <int D>
 SPOLY_D void apply_scaling(BPd<D>& p, const Scaling& sc) {
-  double m = 0.0;
+  int emax = -100000;
 #pragma unroll
   for (int i = 0; i <= D; ++i)
 #pragma unroll
     for (int j = 0; i + j <= D; ++j) {
-      double& c = p.c[bidx(D, i, j)];
-      c = ldexp(c, sc.ks * i + sc.kt * j);
-      m = fmax(m, fabs(c));
+      const long long a = absbits(p.c[bidx(D, i, j)]);
+      if (a) emax = max(emax, expo_bits(a) + sc.ks * i + sc.kt * j);
     }
-  if (m > 0.0) {
-    int e;
-    frexp(m, &e);
+  if (emax == -100000) return;
+  const int shift0 = -(emax + 1);  // largest coefficient lands in [0.5, 1)
 #pragma unroll
-    for (int k = 0; k < bsize(D); ++k) p.c[k] = ldexp(p.c[k], -e);
-  }
+  for (int i = 0; i <= D; ++i)
+#pragma unroll
+    for (int j = 0; i + j <= D; ++j) p.c[bidx(D, i, j)] = scale2(p.c[bidx(D, i, j)], shift0 + sc.ks * i + sc.kt * j);
 }
 
 // ------------------------------------------------------ elimination phase
