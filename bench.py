@@ -44,6 +44,19 @@ FP32_LAPLACE_FLOPS = {"T": 2744, "R": 400}
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 NOMINAL_FP64_TFLOPS = 1.25
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) per launch of the isolation kernel from the last
+# ncu capture (profiles/kernels_refract_64x64_r256_mixed.md).  Reported only
+# while the kernel's sources hash to the value the capture was taken on.
+KERNEL_SOURCES = ["common.cuh", "polys.cuh", "laplace_gen.cuh", "k1_sys.cuh", "k1_iso.cuh", "k1_iso_f32.cu"]
+TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2405_13409_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def parse():
@@ -288,7 +301,9 @@ def main():
                      "chains": total_ms / args.steps - iso - statistics.mean(pol_ms)},
         "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "k1_isolate_kernel<float>",
                      "achieved": achieved64, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved64 / NOMINAL_FP64_TFLOPS, "traffic": None,
+                     "frac": achieved64 / NOMINAL_FP64_TFLOPS,
+                     "traffic": TRAFFIC["bytes_per_launch"]
+                     if TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None,
                      "peak_measured_fp64": peak64, "peak_measured_fp32": peak32,
                      "frac_of_measured": achieved64 / peak64 if peak64 else None,
                      "fp32_laplace_tflops": FP32_LAPLACE_FLOPS[kind] * n_chains / (iso * 1e-3) / 1e12},

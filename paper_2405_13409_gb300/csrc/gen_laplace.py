@@ -15,7 +15,8 @@ from __future__ import annotations
 import os
 from functools import lru_cache
 
-CONFIGS = [("R3", 3, 5), ("R4", 4, 5), ("T5", 5, 7), ("T6", 6, 7)]
+CONFIGS = [("R2", 2, 5), ("R3", 3, 5), ("R4", 4, 5), ("T2", 2, 7), ("T3", 3, 7), ("T4", 4, 7), ("T5", 5, 7),
+           ("T6", 6, 7)]
 
 
 def generate(name: str, N: int, ED: int, absolute: bool = False) -> str:

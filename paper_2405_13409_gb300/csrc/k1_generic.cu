@@ -28,24 +28,20 @@ __global__ void __launch_bounds__(64) k1_side_kernel(K1Params P) {
       int r = 0;
       if (qd.type == SPOLY_R) {
         K1Sys<4> s;
-        if (!k1_system<4>(tr, qd, s))
+        if (!k1_system<4>(tr, qd, s)) {
           r = -1;
-        else if (s.n == 3)
-          r = k1_isolate_sized<double, 3, 4>(s, items, c, n_v, n_pref);
-        else if (s.n == 4)
-          r = k1_isolate_sized<double, 4, 4>(s, items, c, n_v, n_pref);
-        else
-          r = k1_generic_one<4>(s, items, c, n_v, n_pref);
+        } else {
+          r = k1_isolate_dispatch<double, 4>(s, items, c, n_v, n_pref);
+          if (r == -2) r = k1_generic_one<4>(s, items, c, n_v, n_pref);
+        }
       } else {
         K1Sys<6> s;
-        if (!k1_system<6>(tr, qd, s))
+        if (!k1_system<6>(tr, qd, s)) {
           r = -1;
-        else if (s.n == 6)
-          r = k1_isolate_sized<double, 6, 6>(s, items, c, n_v, n_pref);
-        else if (s.n == 5)
-          r = k1_isolate_sized<double, 5, 6>(s, items, c, n_v, n_pref);
-        else
-          r = k1_generic_one<6>(s, items, c, n_v, n_pref);
+        } else {
+          r = k1_isolate_dispatch<double, 6>(s, items, c, n_v, n_pref);
+          if (r == -2) r = k1_generic_one<6>(s, items, c, n_v, n_pref);
+        }
       }
       n_deg = (r < 0) ? 1u : 0u;
       nq = r > 0 ? r : 0;

@@ -103,12 +103,35 @@ SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int
   {
     T E[sym_size(N, ED)];
     bezout_sym<T, N, 2, DB>(s.a, s.b, s.na, s.nb, E);
+    if constexpr (N == 2 && DB == 4) laplace_R2<T>(E, r);
     if constexpr (N == 3 && DB == 4) laplace_R3<T>(E, r);
     if constexpr (N == 4 && DB == 4) laplace_R4<T>(E, r);
+    if constexpr (N == 2 && DB == 6) laplace_T2<T>(E, r);
+    if constexpr (N == 3 && DB == 6) laplace_T3<T>(E, r);
+    if constexpr (N == 4 && DB == 6) laplace_T4<T>(E, r);
     if constexpr (N == 5 && DB == 6) laplace_T5<T>(E, r);
     if constexpr (N == 6 && DB == 6) laplace_T6<T>(E, r);
   }
   return k1_finish<T, RD, DB>(s, r, items, chain, n_vroots, n_pref);
+}
+
+// Isolation with the unrolled expansion of the candidate's Bezout size;
+// -2 when the size has none (handled by the generic runtime-size path).
+template <typename T, int DB>
+SPOLY_D int k1_isolate_dispatch(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int chain, unsigned& n_v,
+                                unsigned& n_pref) {
+  if constexpr (DB == 4) {
+    if (s.n == 3) return k1_isolate_sized<T, 3, 4>(s, items, chain, n_v, n_pref);
+    if (s.n == 4) return k1_isolate_sized<T, 4, 4>(s, items, chain, n_v, n_pref);
+    if (s.n == 2) return k1_isolate_sized<T, 2, 4>(s, items, chain, n_v, n_pref);
+  } else {
+    if (s.n == 6) return k1_isolate_sized<T, 6, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 5) return k1_isolate_sized<T, 5, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 4) return k1_isolate_sized<T, 4, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 3) return k1_isolate_sized<T, 3, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 2) return k1_isolate_sized<T, 2, 6>(s, items, chain, n_v, n_pref);
+  }
+  return -2;
 }
 
 #ifndef SPOLY_HOST_BUILD
@@ -131,24 +154,10 @@ __global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
         int r = 0;
         if (qd.type == SPOLY_R) {
           K1Sys<4> s;
-          if (!k1_system<4>(tr, qd, s))
-            r = -1;
-          else if (s.n == 3)
-            r = k1_isolate_sized<T, 3, 4>(s, items, int(c), n_v, n_pref);
-          else if (s.n == 4)
-            r = k1_isolate_sized<T, 4, 4>(s, items, int(c), n_v, n_pref);
-          else
-            r = -2;
+          r = k1_system<4>(tr, qd, s) ? k1_isolate_dispatch<T, 4>(s, items, int(c), n_v, n_pref) : -1;
         } else {
           K1Sys<6> s;
-          if (!k1_system<6>(tr, qd, s))
-            r = -1;
-          else if (s.n == 6)
-            r = k1_isolate_sized<T, 6, 6>(s, items, int(c), n_v, n_pref);
-          else if (s.n == 5)
-            r = k1_isolate_sized<T, 5, 6>(s, items, int(c), n_v, n_pref);
-          else
-            r = -2;
+          r = k1_system<6>(tr, qd, s) ? k1_isolate_dispatch<T, 6>(s, items, int(c), n_v, n_pref) : -1;
         }
         if (r == -1) n_deg = 1;
         if (r == -2) n_side = 1;

@@ -1,5 +1,7 @@
 // FP64 v-polish and path phase of the 1-bounce solve (Sec. 5.3).
 #pragma once
+#include <type_traits>
+
 #include "k1_generic.cuh"
 
 namespace spoly {
@@ -33,38 +35,31 @@ SPOLY_D int k1_r64(const K1Sys<DB>& s, double (&r)[kRD + 1]) {
 #pragma unroll
   for (int c = 0; c <= kRD; ++c) r[c] = 0.0;
   int rd = -1;
+  auto sized = [&](auto nc, auto lap) {
+    constexpr int N = decltype(nc)::value;
+    constexpr int RDn = N * (ED - N + 1);
+    double E[sym_size(N, ED)], rr[RDn + 1];
+    bezout_sym<double, N, 2, DB>(s.a, s.b, s.na, s.nb, E);
+    lap(E, rr);
+#pragma unroll
+    for (int c = 0; c <= RDn; ++c) r[c] = rr[c];
+    rd = RDn;
+  };
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using I4 = std::integral_constant<int, 4>;
+  using I5 = std::integral_constant<int, 5>;
+  using I6 = std::integral_constant<int, 6>;
   if constexpr (DB == 4) {
-    if (s.n == 3) {
-      double E[sym_size(3, ED)], rr[10];
-      bezout_sym<double, 3, 2, 4>(s.a, s.b, s.na, s.nb, E);
-      laplace_R3<double>(E, rr);
-#pragma unroll
-      for (int c = 0; c <= 9; ++c) r[c] = rr[c];
-      rd = 9;
-    } else if (s.n == 4) {
-      double E[sym_size(4, ED)], rr[9];
-      bezout_sym<double, 4, 2, 4>(s.a, s.b, s.na, s.nb, E);
-      laplace_R4<double>(E, rr);
-#pragma unroll
-      for (int c = 0; c <= 8; ++c) r[c] = rr[c];
-      rd = 8;
-    }
+    if (s.n == 3) sized(I3{}, [](auto& E, auto& rr) { laplace_R3<double>(E, rr); });
+    else if (s.n == 4) sized(I4{}, [](auto& E, auto& rr) { laplace_R4<double>(E, rr); });
+    else if (s.n == 2) sized(I2{}, [](auto& E, auto& rr) { laplace_R2<double>(E, rr); });
   } else {
-    if (s.n == 6) {
-      double E[sym_size(6, ED)], rr[13];
-      bezout_sym<double, 6, 2, 6>(s.a, s.b, s.na, s.nb, E);
-      laplace_T6<double>(E, rr);
-#pragma unroll
-      for (int c = 0; c <= 12; ++c) r[c] = rr[c];
-      rd = 12;
-    } else if (s.n == 5) {
-      double E[sym_size(5, ED)], rr[16];
-      bezout_sym<double, 5, 2, 6>(s.a, s.b, s.na, s.nb, E);
-      laplace_T5<double>(E, rr);
-#pragma unroll
-      for (int c = 0; c <= 15; ++c) r[c] = rr[c];
-      rd = 15;
-    }
+    if (s.n == 6) sized(I6{}, [](auto& E, auto& rr) { laplace_T6<double>(E, rr); });
+    else if (s.n == 5) sized(I5{}, [](auto& E, auto& rr) { laplace_T5<double>(E, rr); });
+    else if (s.n == 4) sized(I4{}, [](auto& E, auto& rr) { laplace_T4<double>(E, rr); });
+    else if (s.n == 3) sized(I3{}, [](auto& E, auto& rr) { laplace_T3<double>(E, rr); });
+    else if (s.n == 2) sized(I2{}, [](auto& E, auto& rr) { laplace_T2<double>(E, rr); });
   }
   if (rd < 0) {
     k1_r64_generic<DB>(s, r);

@@ -13,24 +13,11 @@ template <int DB>
 int isolate_one(const K1Sys<DB>& s, int precision, RootItem (&items)[kRD + 1], unsigned& nv, unsigned& np,
                 int* status) {
   int r = -2;
-  if (precision == 1) {
-    if constexpr (DB == 4) {
-      if (s.n == 3) r = k1_isolate_sized<float, 3, 4>(s, items, 0, nv, np);
-      if (s.n == 4) r = k1_isolate_sized<float, 4, 4>(s, items, 0, nv, np);
-    } else {
-      if (s.n == 6) r = k1_isolate_sized<float, 6, 6>(s, items, 0, nv, np);
-      if (s.n == 5) r = k1_isolate_sized<float, 5, 6>(s, items, 0, nv, np);
-    }
-  }
+  if (precision == 1) r = k1_isolate_dispatch<float, DB>(s, items, 0, nv, np);
   status[0] = r;
   if (r != -2) return r;
-  if constexpr (DB == 4) {
-    if (s.n == 3) return k1_isolate_sized<double, 3, 4>(s, items, 0, nv, np);
-    if (s.n == 4) return k1_isolate_sized<double, 4, 4>(s, items, 0, nv, np);
-  } else {
-    if (s.n == 6) return k1_isolate_sized<double, 6, 6>(s, items, 0, nv, np);
-    if (s.n == 5) return k1_isolate_sized<double, 5, 6>(s, items, 0, nv, np);
-  }
+  r = k1_isolate_dispatch<double, DB>(s, items, 0, nv, np);
+  if (r != -2) return r;
   return k1_generic_one<DB>(s, items, 0, nv, np);
 }
 

@@ -12,7 +12,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2405_13409_gb300", "csrc")
-CONFIGS = [("R3", 3, 5), ("R4", 4, 5), ("T5", 5, 7), ("T6", 6, 7)]
+CONFIGS = [("R2", 2, 5), ("R3", 3, 5), ("R4", 4, 5), ("T2", 2, 7), ("T3", 3, 7), ("T4", 4, 7), ("T5", 5, 7),
+           ("T6", 6, 7)]
 
 
 def _packing(N, ED):
