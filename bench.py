@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    p.add_argument("--workload", choices=["refract", "reflect"], default="refract")
+    p.add_argument("--workload", choices=["refract", "reflect", "glints"], default="refract")
     p.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -74,16 +74,23 @@ def parse():
 
 
 def workload(name):
+    """(scene, chain mode, scattering kind, description, camera or None)."""
     from paper_2405_13409_gb300 import binding, scenes
+    if name == "glints":
+        s = scenes.glint_scene()
+        return s, binding.CHAINS_FOOTPRINT, "R", (
+            "glints: 1024x1024-cell heightfield (2,097,152 triangles, 64 sinusoids of wavelength 2-20 cells), "
+            "pinhole 512x512 at (0,-2,1.5), light (1,1,2), reflection, pixel-footprint candidates"), \
+            s.meta["camera"].as_array()
     if name == "refract":
         s = scenes.refract_scene()
         return s, binding.CHAINS_CONE, "T", (
             "refraction caustics: 64x64-cell sinusoid heightfield (8,192 triangles, amplitude 0.08), "
-            "eta 1 -> 1.5, light (0,0,2), 256x256 receivers on z=-1, bounding-cone cull")
+            "eta 1 -> 1.5, light (0,0,2), 256x256 receivers on z=-1, bounding-cone cull"), None
     s = scenes.reflect_scene()
     return s, binding.CHAINS_ALL, "R", (
         "reflection: 16x16-cell sinusoid heightfield (512 triangles, amplitude 0.05), light (0.3,-0.2,2), "
-        "32x32 receivers on z=1, exhaustive")
+        "32x32 receivers on z=1, exhaustive"), None
 
 
 class ClockSampler:
@@ -151,7 +158,7 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    s, _, kind, desc = workload(args.workload)
+    s, _, kind, desc, _cam = workload(args.workload)
     cores = os.cpu_count()
     for i in range(args.warmup):
         run_oracle_sample(s, args.ref_receivers, 1000 + i)
@@ -194,7 +201,7 @@ def main():
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
     ctx = binding.Context(local, stream.cuda_stream)
-    s, mode, kind, desc = workload(args.workload)
+    s, mode, kind, desc, camera = workload(args.workload)
     precision = binding.MIXED if args.precision == "mixed" else binding.PLAIN_FP64
     host = [np.ascontiguousarray(a) for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
     d = [torch.from_numpy(a).to(dev) for a in host]
@@ -208,15 +215,17 @@ def main():
     state = {"chains": None, "sol": None}
 
     def step(m, qq):
-        state["chains"] = ctx.spoly_build_chains(m, qq, mode, margin=1e-3, reuse=state["chains"])
+        state["chains"] = ctx.spoly_build_chains(m, qq, mode, margin=1e-3, reuse=state["chains"], camera=camera)
         state["sol"] = ctx.spoly_solve(m, qq, state["chains"], precision=precision,
-                                       flags=binding.SOLVE_TIMING, reuse=state["sol"])
+                                       flags=binding.SOLVE_TIMING, reuse=state["sol"], camera=camera)
 
     for _ in range(args.warmup):
         step(mesh, q)
     torch.cuda.synchronize()
     n_chains = ctx.spoly_chains_count(state["chains"])
     stats = ctx.spoly_stats(state["sol"])
+    if mode == binding.CHAINS_FOOTPRINT:
+        pairs = n_chains  # the footprint defines the candidate set of this workload
 
     # timed region: device-resident inputs, L2 flushed between steps
     clocks = ClockSampler(local)

@@ -100,6 +100,7 @@ typedef struct {
 #define SPOLY_CHAINS_ALL 0      /* every (query, triangle) pair */
 #define SPOLY_CHAINS_CONE 1     /* pairs passing a conservative direction-box test */
 #define SPOLY_CHAINS_EXPLICIT 2 /* caller's list */
+#define SPOLY_CHAINS_FOOTPRINT 3 /* pixel footprints of a pinhole camera (query q = pixel q) */
 
 typedef struct {
   int32_t mode;
@@ -111,6 +112,14 @@ typedef struct {
   int64_t n_explicit;
   int32_t explicit_on_device;
   int32_t reserved2;
+  /* FOOTPRINT: host array of 16 doubles: camera origin xyz, forward xyz,
+   * right xyz, up xyz (unit, orthogonal), tan(vertical fov / 2), aspect
+   * (width / height), width, height.  Pixel (ix, iy) = query iy * width + ix
+   * covers screen x in [-1 + 2 ix / w, -1 + 2 (ix + 1) / w] and screen y in
+   * [1 - 2 (iy + 1) / h, 1 - 2 iy / h]; its ray through screen (sx, sy) is
+   * forward + sx tan aspect right + sy tan up. */
+  const double* camera;
+  double cell; /* FOOTPRINT: grid cell size; <= 0 picks one cell per ~2 triangles */
 } spoly_chain_opts;
 
 /* Solve options. */
@@ -122,8 +131,13 @@ typedef struct {
 
 typedef struct {
   int32_t precision;       /* SPOLY_PLAIN_FP64 or SPOLY_MIXED */
-  int32_t flags;           /* SPOLY_SOLVE_ASYNC */
+  int32_t flags;           /* SPOLY_SOLVE_ASYNC, SPOLY_SOLVE_TIMING */
   int64_t path_capacity;   /* initial path buffer size (0: automatic) */
+  /* Optional pixel filter (host array of 16 doubles, camera layout of
+   * spoly_chain_opts): a path of query q is kept only if its first vertex
+   * projects into pixel q, so each path of a footprint workload is counted
+   * once.  NULL: no filter. */
+  const double* camera;
 } spoly_solve_opts;
 
 /* One admissible path (104 bytes).  For k = 1, tri[1] = -1 and the second

@@ -38,6 +38,7 @@ FLAG_TANGENT = 32
 CHAINS_ALL = 0
 CHAINS_CONE = 1
 CHAINS_EXPLICIT = 2
+CHAINS_FOOTPRINT = 3
 
 PLAIN_FP64 = 0
 MIXED = 1
@@ -63,11 +64,12 @@ class spoly_queries(ctypes.Structure):
 class spoly_chain_opts(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("reserved", c_int32), ("tri_begin", c_int32), ("tri_end", c_int32),
                 ("margin", ctypes.c_double), ("explicit_chains", c_void_p), ("n_explicit", c_int64),
-                ("explicit_on_device", c_int32), ("reserved2", c_int32)]
+                ("explicit_on_device", c_int32), ("reserved2", c_int32), ("camera", c_void_p),
+                ("cell", ctypes.c_double)]
 
 
 class spoly_solve_opts(ctypes.Structure):
-    _fields_ = [("precision", c_int32), ("flags", c_int32), ("path_capacity", c_int64)]
+    _fields_ = [("precision", c_int32), ("flags", c_int32), ("path_capacity", c_int64), ("camera", c_void_p)]
 
 
 class spoly_path(ctypes.Structure):
@@ -187,11 +189,13 @@ class Context:
                              int(x_first.shape[0]), _on_device(x_first), 0)
 
     def spoly_build_chains(self, mesh: spoly_mesh, q: spoly_queries, mode: int, margin: float = 1e-3,
-                           explicit=None, tri_range=(0, 0), reuse=None):
+                           explicit=None, tri_range=(0, 0), reuse=None, camera=None, cell: float = 0.0):
+        cam = None if camera is None else np.ascontiguousarray(camera, dtype=np.float64)
         opts = spoly_chain_opts(mode, 0, int(tri_range[0]), int(tri_range[1]), float(margin),
                                 _ptr(explicit) if explicit is not None else 0,
                                 int(explicit.shape[0]) if explicit is not None else 0,
-                                _on_device(explicit) if explicit is not None else 0, 0)
+                                _on_device(explicit) if explicit is not None else 0, 0,
+                                cam.ctypes.data if cam is not None else None, float(cell))
         h = c_void_p(reuse.value if reuse is not None else None)
         self.check(self.lib.spoly_build_chains(self.h, ctypes.byref(mesh), ctypes.byref(q), ctypes.byref(opts),
                                                ctypes.byref(h)), "spoly_build_chains")
@@ -214,8 +218,9 @@ class Context:
         self.lib.spoly_chains_free(chains)
 
     def spoly_solve(self, mesh: spoly_mesh, q: spoly_queries, chains, precision: int = MIXED, flags: int = 0,
-                    path_capacity: int = 0, reuse=None):
-        opts = spoly_solve_opts(int(precision), int(flags), int(path_capacity))
+                    path_capacity: int = 0, reuse=None, camera=None):
+        cam = None if camera is None else np.ascontiguousarray(camera, dtype=np.float64)
+        opts = spoly_solve_opts(int(precision), int(flags), int(path_capacity), cam.ctypes.data if cam is not None else None)
         h = c_void_p(reuse.value if reuse is not None else None)
         self.check(self.lib.spoly_solve(self.h, ctypes.byref(mesh), ctypes.byref(q), chains, ctypes.byref(opts),
                                         ctypes.byref(h)), "spoly_solve")

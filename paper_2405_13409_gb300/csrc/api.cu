@@ -1,4 +1,5 @@
 // C ABI of the specular-polynomial library (declared in include/spoly.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -44,6 +45,7 @@ struct spoly_ctx {
   char err[512] = {0};
   DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
   DevBuf boxes, flag;                    // cone cull scratch
+  DevBuf cam, bounds, fp_scratch, fp_entries;  // footprint builder
 };
 
 struct spoly_chains {
@@ -178,7 +180,8 @@ spoly_status spoly_ctx_destroy(spoly_ctx* ctx) {
   if (!ctx) return SPOLY_EINVAL;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  for (DevBuf* b : {&ctx->mesh, &ctx->xf, &ctx->xl, &ctx->eta, &ctx->types, &ctx->kk, &ctx->boxes, &ctx->flag})
+  for (DevBuf* b : {&ctx->mesh, &ctx->xf, &ctx->xl, &ctx->eta, &ctx->types, &ctx->kk, &ctx->boxes, &ctx->flag,
+                    &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries})
     b->release();
   delete ctx;
   return SPOLY_OK;
@@ -288,6 +291,47 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
       e = cudaMemsetAsync(ch->counter.p, 0, 16, ctx->stream);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
     }
+  } else if (opts->mode == SPOLY_CHAINS_FOOTPRINT) {
+    if (!opts->camera) return bail(fail(ctx, SPOLY_EINVAL, "footprint mode needs a camera"));
+    const double* cam = opts->camera;
+    if (int64_t(cam[14]) * int64_t(cam[15]) != qv.n || cam[14] < 1 || cam[15] < 1)
+      return bail(fail(ctx, SPOLY_EINVAL, "footprint: width x height (%g x %g) must equal n_queries (%lld)", cam[14],
+                       cam[15], (long long)qv.n));
+    if (ctx->cam.ensure(16 * sizeof(double)) != cudaSuccess || ctx->bounds.ensure(64) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
+    e = cudaMemcpyAsync(ctx->cam.p, cam, 16 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "camera copy"));
+    float bh[6];
+    e = compute_mesh_bounds(mv, static_cast<int*>(ctx->bounds.p), bh, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "mesh bounds"));
+    const double wx = double(bh[3]) - bh[0], wy = double(bh[4]) - bh[1];
+    double cell = opts->cell;
+    if (!(cell > 0.0)) cell = std::sqrt(std::max(wx * wy, 1e-30) / std::max<double>(1.0, double(mv.n_tris) / 2.0));
+    FpGrid g;
+    g.cell = cell;
+    g.x0 = bh[0];
+    g.y0 = bh[1];
+    g.gx = int(std::min(8192.0, std::max(1.0, std::ceil(wx / cell) + 1.0)));
+    g.gy = int(std::min(8192.0, std::max(1.0, std::ceil(wy / cell) + 1.0)));
+    const int64_t n_cells = int64_t(g.gx) * g.gy;
+    if (ctx->fp_scratch.ensure(footprint_scratch_bytes(n_cells, qv.n)) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
+    int64_t n_entries = 0, total = 0;
+    e = fp_grid_count(mv, g, ctx->fp_scratch.p, qv.n, &n_entries, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint grid"));
+    if (ctx->fp_entries.ensure(size_t(std::max<int64_t>(n_entries, 1)) * 4) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "footprint grid entries"));
+    const double* cam_dev = static_cast<const double*>(ctx->cam.p);
+    const int* bounds_dev = static_cast<const int*>(ctx->bounds.p);
+    e = fp_grid_fill_and_count(mv, g, ctx->fp_scratch.p, static_cast<int32_t*>(ctx->fp_entries.p), cam_dev,
+                               bounds_dev, qv.n, &total, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint count"));
+    if (ch->buf.ensure(size_t(std::max<int64_t>(total, 1)) * 12) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+    e = fp_fill(mv, g, ctx->fp_scratch.p, static_cast<const int32_t*>(ctx->fp_entries.p), cam_dev, bounds_dev, qv.n,
+                static_cast<int32_t*>(ch->buf.p), ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint fill"));
+    ch->n = total;
   } else {
     return bail(fail(ctx, SPOLY_EINVAL, "unknown chain mode %d", opts->mode));
   }
@@ -379,6 +423,22 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   K1Params P{};
   P.mesh = mv;
   P.qv = qv;
+  if (opts->camera) {
+    const double* c = opts->camera;
+    P.pix.on = 1;
+    for (int i = 0; i < 3; ++i) {
+      P.pix.o[i] = c[i];
+      P.pix.f[i] = c[3 + i];
+      P.pix.r[i] = c[6 + i];
+      P.pix.u[i] = c[9 + i];
+    }
+    P.pix.th = c[12];
+    P.pix.aspect = c[13];
+    P.pix.w = int(c[14]);
+    P.pix.h = int(c[15]);
+    if (P.pix.w < 1 || P.pix.h < 1 || int64_t(P.pix.w) * P.pix.h != qv.n)
+      return bail(fail(ctx, SPOLY_EINVAL, "pixel filter: width x height must equal n_queries"));
+  }
   P.chains = static_cast<const int32_t*>(chains->buf.p);
   P.n_chains = nc;
   P.counters = static_cast<unsigned long long*>(set->counters.p);

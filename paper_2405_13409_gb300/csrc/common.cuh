@@ -142,6 +142,27 @@ constexpr double kSideReach = 0.25;       // side search reach (in v) of a displ
 constexpr float kTangent32 = 1e-4f;  // tangent-root test, FP32 isolation
 constexpr double kTangent64 = 1e-12; // tangent-root test, FP64 isolation
 
+// Pinhole camera of a footprint workload, for the pixel filter of the path
+// phase (layout of spoly_chain_opts::camera).
+struct PixelFilter {
+  int on;
+  int w, h;
+  double o[3], f[3], r[3], u[3], th, aspect;
+};
+
+// Pixel of a point seen by the camera; false if behind it.
+SPOLY_HD bool project_pixel(const PixelFilter& C, double x, double y, double z, int64_t* pix) {
+  const double dx = x - C.o[0], dy = y - C.o[1], dz = z - C.o[2];
+  const double fz = dx * C.f[0] + dy * C.f[1] + dz * C.f[2];
+  if (!(fz > 0.0)) return false;
+  const double sx = (dx * C.r[0] + dy * C.r[1] + dz * C.r[2]) / (fz * C.th * C.aspect);
+  const double sy = (dx * C.u[0] + dy * C.u[1] + dz * C.u[2]) / (fz * C.th);
+  const double fx = (sx + 1.0) * 0.5 * C.w, fy = (1.0 - sy) * 0.5 * C.h;
+  if (!(fx >= 0.0 && fx < C.w && fy >= 0.0 && fy < C.h)) return false;
+  *pix = int64_t(floor(fy)) * C.w + int64_t(floor(fx));
+  return true;
+}
+
 // Root-bracket queue item between the isolation and polish kernels.
 struct RootItem {
   double zlo, zhi;   // bracket in the scaled hidden variable z = v / t

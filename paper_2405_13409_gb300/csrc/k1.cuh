@@ -16,6 +16,7 @@ struct K1Params {
   unsigned long long* counters;  // [C_COUNT]
   spoly_path* paths;
   int64_t path_cap;
+  PixelFilter pix;  // optional: keep a path of query q only if x1 projects into pixel q
 };
 
 #ifndef SPOLY_HOST_BUILD
@@ -41,6 +42,21 @@ cudaError_t launch_chains_all(const ChainParams& P, int num_sms, cudaStream_t st
 cudaError_t launch_chains_explicit(const ChainParams& P, const int32_t* src, int64_t n, int num_sms,
                                    cudaStream_t st);
 cudaError_t launch_chains_cone(const ChainParams& P, int num_sms, cudaStream_t st);
+
+// Pixel-footprint builder (footprint.cu).
+struct FpGrid {
+  double x0, y0, cell;
+  int gx, gy;
+};
+size_t footprint_scratch_bytes(int64_t n_cells, int64_t n_pixels);
+cudaError_t compute_mesh_bounds(const MeshView& M, int* bounds_dev, float* bounds_host, int num_sms, cudaStream_t st);
+cudaError_t fp_grid_count(const MeshView& M, const FpGrid& g, void* scratch, int64_t n_pixels, int64_t* n_entries,
+                          int num_sms, cudaStream_t st);
+cudaError_t fp_grid_fill_and_count(const MeshView& M, const FpGrid& g, void* scratch, int32_t* entries,
+                                   const double* cam_dev, const int* bounds_dev, int64_t n_pixels, int64_t* total,
+                                   int num_sms, cudaStream_t st);
+cudaError_t fp_fill(const MeshView& M, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_dev,
+                    const int* bounds_dev, int64_t n_pixels, int32_t* out, int num_sms, cudaStream_t st);
 #endif
 
 }  // namespace spoly

@@ -51,9 +51,9 @@ __global__ void __launch_bounds__(128) k1_path_kernel(K1Params P) {
       const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
       const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
       if (qd.type == SPOLY_R)
-        np = k1_path_item<4>(tr, qd, P.queue, i, q, t, out, n_u);
+        np = k1_path_item<4>(tr, qd, P.queue, i, q, t, out, n_u, P.pix);
       else
-        np = k1_path_item<6>(tr, qd, P.queue, i, q, t, out, n_u);
+        np = k1_path_item<6>(tr, qd, P.queue, i, q, t, out, n_u, P.pix);
       for (int k = 0; k < np; ++k) n_flag += (out[k].flags & SPOLY_FLAG_ILL_COND) ? 1u : 0u;
     }
     warp_count(P.counters + C_UROOTS, n_u);

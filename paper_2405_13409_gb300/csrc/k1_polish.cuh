@@ -221,7 +221,7 @@ SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigne
 // sidedness and the in-triangle test.  Appends up to 6 paths to `out`.
 template <int DB>
 SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, double zs, uint32_t vflags, int q,
-                         int t, spoly_path (&out)[6], int np, unsigned& n_u) {
+                         int t, spoly_path (&out)[6], int np, unsigned& n_u, const PixelFilter& pix) {
   const double v0 = zs * s.sc.t;
   double am[3];
   a_at<double>(s.a, s.na, zs, am);
@@ -276,6 +276,10 @@ SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, d
     const double wmin = fmin(fmin(u, v), 1.0 - u - v);
     if (wmin < 0.0) continue;
     if (wmin < kEdgeEps) flags |= SPOLY_FLAG_EDGE;
+    if (pix.on) {
+      int64_t pq;
+      if (!project_pixel(pix, x1.x, x1.y, x1.z, &pq) || pq != q) continue;
+    }
     bool dup = false;
     for (int k = 0; k < np; ++k)
       if (fabs(out[k].uv[0][0] - u) <= 1e-9 && fabs(out[k].uv[0][1] - v) <= 1e-9) {
@@ -307,7 +311,7 @@ SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, d
 // or equal to the item's other root within 1e-9 in v are skipped.
 template <int DB>
 SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue, int64_t i, int q, int t,
-                         spoly_path (&out)[6], unsigned& n_u) {
+                         spoly_path (&out)[6], unsigned& n_u, const PixelFilter& pix) {
   const RootItem it = queue[i];
   K1Sys<DB> s;
   if (!k1_system<DB>(tr, qd, s)) return 0;
@@ -326,7 +330,7 @@ SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue
     }
     if (dup) continue;
     const uint32_t vflags = r == 0 ? (it.flags & 0xffu) : ((it.flags >> 8) & 0xffu);
-    np = k1_path_root<DB>(s, tr, qd, z, vflags, q, t, out, np, n_u);
+    np = k1_path_root<DB>(s, tr, qd, z, vflags, q, t, out, np, n_u, pix);
   }
   return np;
 }

@@ -41,7 +41,8 @@ int run(const TriD& tr, const QueryD& qd, int precision, double* out, int cap, i
   status[3] = int(lost);
   for (int i = 0; i < nq; ++i) {
     spoly_path paths[6];
-    const int np = k1_path_item<DB>(tr, qd, items, i, 0, 0, paths, nu);
+    PixelFilter nofilter{};
+    const int np = k1_path_item<DB>(tr, qd, items, i, 0, 0, paths, nu, nofilter);
     for (int k = 0; k < np && total < cap; ++k, ++total) {
       out[3 * total] = paths[k].uv[0][0];
       out[3 * total + 1] = paths[k].uv[0][1];
