@@ -1,21 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the exhaustive specular-polynomial solve on one GB300.
 
-One step is one pass of the whole hot path over the refraction-caustics
-workload: the bounding-cone cull over every (receiver, triangle) pair of a
-64x64-cell heightfield (8,192 triangles, IOR 1.5) under a point light at
-(0, 0, 2) seen by a 256x256 receiver grid on z = -1 (536,870,912 pairs),
-then the mixed-precision solve of every surviving pair (FP64 construction,
-FP32 Laplace expansion and isolation, FP64 polish and path checks), then
-the read-back of the path count.  Inputs are synthetic and seeded.
+Default workload (glints): a 1024x1024-cell heightfield (2,097,152
+triangles, height = sum of 64 random-phase sinusoids of wavelength 2-20
+cells) seen by a 512x512 pinhole camera at (0, -2, 1.5) under a point light
+at (1, 1, 2).  One step is one pass of the whole hot path: the pixel-
+footprint candidate build over a uniform grid, the learned gate (features +
+BF16 tensor-core MLP + compaction), the mixed-precision solve of the
+surviving (pixel, triangle) candidates (FP64 construction, FP32 Laplace
+expansion and isolation, FP64 polish and path checks) with the pixel
+filter, and the read-back of the path count.  The same run times the plain
+FP64 path (no gate, every step in FP64) on the same candidates and reports
+the recall of the gated solve against it.  The gate is trained before the
+timed region on the glint generator's training seeds (its own kernels) and
+calibrated on a validation seed.  Inputs are synthetic and seeded.
 
-metric: candidate solves/s -- (receiver, triangle) tuples whose complete
-admissible path set is produced per second (all pairs of the workload; the
-cull proves most of them empty).  Also reported: survivors solved per
-second and admissible paths per second.
+metric: candidate solves/s -- (pixel, triangle) candidates of the footprint
+whose complete admissible path set is produced per second (the gate proves
+most of them empty).  Also reported: admissible paths per second.
 
---impl reference times the FP64 CPU oracle on the same metric: each step
-solves every pair of a seeded sample of receivers on all host cores.
+--workload refract / reflect time the 1-bounce caustic and reflection
+workloads (bounding-cone cull / exhaustive, no gate).
+--impl reference times the FP64 CPU oracle on the same metric.
 """
 from __future__ import annotations
 
@@ -44,6 +50,14 @@ FP32_LAPLACE_FLOPS = {"T": 2744, "R": 400}
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 NOMINAL_FP64_TFLOPS = 1.25
 L2_FLUSH_BYTES = 512 << 20
+# Gate: algorithmic flops per candidate (24x64 + 64x64 + 64x64 + 64 MACs)
+# and the measured dense BF16 peak of this GPU type (MEASURED_PEAKS.json).
+GATE_FLOPS = 2 * (24 * 64 + 64 * 64 + 64 * 64 + 64)
+BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+# Kernel launches per step, counted from the ncu launch list of each
+# workload (profiles/).
+LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 18, ("glints", True): 19}
 # DRAM bytes (read + write) per launch of the isolation kernel from the last
 # ncu capture (profiles/kernels_refract_64x64_r256_mixed.md).  Reported only
 # while the kernel's sources hash to the value the capture was taken on.
@@ -65,11 +79,21 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    p.add_argument("--workload", choices=["refract", "reflect", "glints"], default="refract")
+    p.add_argument("--workload", choices=["glints", "refract", "reflect"], default="glints")
     p.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
+    p.add_argument("--no-gate", action="store_true", help="glints: solve every candidate (no learned gate)")
+    p.add_argument("--no-plain", action="store_true", help="glints: skip the plain FP64 comparison")
+    p.add_argument("--plain-steps", type=int, default=5)
+    p.add_argument("--train-seeds", type=int, default=2)
+    p.add_argument("--train-steps", type=int, default=3000)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--gate-file", default="",
+                   help="glints: load the trained gate (and its threshold, PATH.json) from PATH if it exists, "
+                        "else train it and save it there")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--ref-receivers", type=int, default=16)
+    p.add_argument("--ref-units", type=int, default=0,
+                   help="reference arm sample per step: receivers (refract/reflect) or pixels (glints)")
     return p.parse_args()
 
 
@@ -94,62 +118,146 @@ def workload(name):
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clock and throttle-reason samples taken DURING the timed region by a
+    thread reading NVML every 5 ms (through ctypes; read-only queries), with
+    nvidia-smi at 100 ms as the fallback when NVML cannot be loaded."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
+        self.rows = []
+        self.thread = None
         self.proc = None
-        self.path = os.path.join("/tmp", f"spoly_clocks_{os.getpid()}.csv")
+        self.stop_flag = False
+        self.nvml = None
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(h)) == 0:
+                    self.nvml, self.h, self.ct = lib, h, ctypes
+        except OSError:
+            self.nvml = None
+
+    def _sample_nvml(self):
+        ct, lib = self.ct, self.nvml
+        clk, mx, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_flag:
+            if (lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx)) == 0 and
+                    get_reasons(self.h, ct.byref(rs)) == 0):
+                self.rows.append((float(clk.value), float(mx.value), int(rs.value)))
+            time.sleep(0.005)
 
     def start(self):
+        import threading
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._sample_nvml, daemon=True)
+            self.thread.start()
+            return
+        self.path = os.path.join("/tmp", f"spoly_clocks_{os.getpid()}.csv")
+        fields = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={fields}", "--format=csv,noheader,nounits",
                                           "-lms", "100", "-i", str(self.gpu)], stdout=open(self.path, "w"),
                                          stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join()
+            rows = self.rows
+            src = "nvml 5 ms"
+        elif self.proc is not None:
+            self.proc.terminate()
             try:
-                rows.append((float(f[1]), float(f[2]), f[5:9]))
-            except ValueError:
-                continue
-        os.remove(self.path)
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            rows = []
+            bits = [0x8, 0x40, 0x20, 0x4]
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                try:
+                    r = sum(b for b, v in zip(bits, f[3:7]) if v.lower() == "active")
+                    rows.append((float(f[1]), float(f[2]), r))
+                except (ValueError, IndexError):
+                    continue
+            os.remove(self.path)
+            src = "nvidia-smi 100 ms"
+        else:
+            return None
         if not rows:
             return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        reasons = sorted({n for _, _, r in rows for b, n in self.REASONS.items() if r & b})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": src}
 
 
-def run_oracle_sample(s, n_recv, seed):
-    import oracle
-    from paper_2405_13409_gb300 import scenes
+def footprint_sample(s, camera, n_pixels, seed):
+    """Host (numpy) footprint candidates of seeded 16x16-pixel blocks (about
+    n_pixels pixels in all), for the CPU legs: the triangles whose xy
+    bounding box meets the pixel's footprint box (its four corner rays
+    between the mesh's z bounds)."""
+    w, h = int(camera[14]), int(camera[15])
+    side = 16
+    n_blocks = max(1, n_pixels // (side * side))
     rng = np.random.default_rng(seed)
-    qs = np.sort(rng.choice(s.n_queries, n_recv, replace=False)).astype(np.int32)
-    chains = np.stack([np.repeat(qs, s.n_tris), np.tile(np.arange(s.n_tris, dtype=np.int32), n_recv),
-                       -np.ones(n_recv * s.n_tris, np.int32)], -1).astype(np.int32)
-    del scenes
+    T = s.tri
+    xs, ys, zs = T[[0, 3, 6]], T[[1, 4, 7]], T[[2, 5, 8]]
+    txl, txh, tyl, tyh = xs.min(0), xs.max(0), ys.min(0), ys.max(0)
+    zlo, zhi = zs.min(), zs.max()
+    o, f, r, u = camera[0:3], camera[3:6], camera[6:9], camera[9:12]
+    th, asp = camera[12], camera[13]
+
+    def box(ixa, ixb, iya, iyb):
+        pts = []
+        for ix in (ixa, ixb):
+            for iy in (iya, iyb):
+                d = f + (-1 + 2 * ix / w) * th * asp * r + (1 - 2 * iy / h) * th * u
+                for z in (zlo, zhi):
+                    pts.append(o + (z - o[2]) / d[2] * d)
+        pts = np.array(pts)
+        return pts[:, 0].min(), pts[:, 0].max(), pts[:, 1].min(), pts[:, 1].max()
+
+    rows = []
+    for _ in range(n_blocks):
+        x0, y0 = int(rng.integers(0, w - side + 1)), int(rng.integers(0, h - side + 1))
+        bx = box(x0, x0 + side, y0, y0 + side)
+        near = np.where(~((txh < bx[0]) | (txl > bx[1]) | (tyh < bx[2]) | (tyl > bx[3])))[0]
+        for iy in range(y0, y0 + side):
+            for ix in range(x0, x0 + side):
+                b = box(ix, ix + 1, iy, iy + 1)
+                t = near[~((txh[near] < b[0]) | (txl[near] > b[1]) | (tyh[near] < b[2]) | (tyl[near] > b[3]))]
+                rows.append(np.stack([np.full(t.size, iy * w + ix), t, -np.ones(t.size, np.int64)], -1))
+    return np.concatenate(rows).astype(np.int32), n_blocks
+
+
+def run_oracle_sample(s, camera, n_units, seed):
+    """One CPU-oracle step: all triangles x n_units seeded receivers, or the
+    footprint candidates of a block of about n_units pixels (glints)."""
+    import oracle
+    if camera is not None:
+        chains, nb = footprint_sample(s, camera, n_units, seed)
+        desc = f"footprint candidates of {nb} 16x16-pixel blocks at seeded positions"
+    else:
+        rng = np.random.default_rng(seed)
+        qs = np.sort(rng.choice(s.n_queries, n_units, replace=False)).astype(np.int32)
+        chains = np.stack([np.repeat(qs, s.n_tris), np.tile(np.arange(s.n_tris, dtype=np.int32), n_units),
+                           -np.ones(n_units * s.n_tris, np.int32)], -1).astype(np.int32)
+        desc = f"all {s.n_tris} triangles x {n_units} seeded receivers"
     t0 = time.perf_counter()
     paths, cnt = oracle.solve(s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, chains)
-    return chains.shape[0], time.perf_counter() - t0, paths.size
+    return chains.shape[0], time.perf_counter() - t0, paths.size, desc
 
 
 def reference_arm(args):
@@ -158,27 +266,106 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    s, _, kind, desc, _cam = workload(args.workload)
+    s, _, kind, desc, cam = workload(args.workload)
+    units = args.ref_units or (16384 if cam is not None else 16)
     cores = os.cpu_count()
     for i in range(args.warmup):
-        run_oracle_sample(s, args.ref_receivers, 1000 + i)
-    tot_c, tot_t, tot_p = 0, 0.0, 0
+        run_oracle_sample(s, cam, units, 1000 + i)
+    tot_c, tot_t, tot_p, sample = 0, 0.0, 0, ""
     for i in range(args.steps):
-        c, t, p = run_oracle_sample(s, args.ref_receivers, 2000 + i)
+        c, t, p, sample = run_oracle_sample(s, cam, units, 2000 + i)
         tot_c += c
         tot_t += t
         tot_p += p
     value = tot_c / tot_t
-    sample = f"all {s.n_tris} triangles x {args.ref_receivers} seeded receivers per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "precision": "plain FP64 CPU oracle"},
+            "config": {"workload": desc, "precision": "plain FP64 CPU oracle, no gate"},
             "paths_per_s": tot_p / tot_t,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def match_paths(got, ref, tol=1e-5):
+    """Paths of `ref` with a path of `got` on the same (pixel, triangle)
+    within tol in (u, v); returns (matched, max |delta(u, v)| over matches)."""
+    from collections import defaultdict
+    g = defaultdict(list)
+    for qq, t, uv in zip(got["query"].tolist(), got["tri"][:, 0].tolist(), got["uv"][:, :2]):
+        g[(qq, t)].append(uv)
+    matched, worst = 0, 0.0
+    for qq, t, uv in zip(ref["query"].tolist(), ref["tri"][:, 0].tolist(), ref["uv"][:, :2]):
+        ds = [float(np.max(np.abs(uv - x))) for x in g.get((qq, t), [])]
+        if ds and min(ds) <= tol:
+            matched += 1
+            worst = max(worst, min(ds))
+    return matched, worst
+
+
+class Pipeline:
+    """One step of the hot path through the C ABI: candidate build, optional
+    gate, solve.  Handles are reused across steps (grow-only buffers)."""
+
+    def __init__(self, ctx, mode, precision, camera, mlp=None, tau=0.0):
+        self.ctx, self.mode, self.precision, self.camera = ctx, mode, precision, camera
+        self.mlp, self.tau = mlp, tau
+        self.chains = self.gated = self.sol = None
+        self.ev = None
+
+    def step(self, mesh, q, stream=None, torch=None):
+        from paper_2405_13409_gb300 import binding
+        ev = None
+        if torch is not None:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+        self.chains = self.ctx.spoly_build_chains(mesh, q, self.mode, margin=1e-3, reuse=self.chains,
+                                                  camera=self.camera)
+        if ev:
+            ev[1].record(stream)
+        solve_on = self.chains
+        if self.mlp is not None:
+            self.gated = self.ctx.spoly_gate(self.mlp, mesh, q, self.chains, self.tau, reuse=self.gated)
+            solve_on = self.gated
+        if ev:
+            ev[2].record(stream)
+        self.sol = self.ctx.spoly_solve(mesh, q, solve_on, precision=self.precision, flags=binding.SOLVE_TIMING,
+                                        reuse=self.sol, camera=self.camera)
+        self.ev = ev
+
+    def phase_ms(self):
+        """(candidate build, gate) milliseconds of the last timed step."""
+        self.ev[2].synchronize()
+        return self.ev[0].elapsed_time(self.ev[1]), self.ev[1].elapsed_time(self.ev[2])
+
+    def free(self):
+        for h in (self.sol,):
+            if h is not None:
+                self.ctx.spoly_solution_free(h)
+        for h in (self.chains, self.gated):
+            if h is not None:
+                self.ctx.spoly_chains_free(h)
+
+
+def timed_steps(pipe, mesh, q, steps, flush, stream, torch):
+    """steps timed with CUDA events on the launching stream, L2 flushed
+    before each; returns per-step dicts."""
+    out = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pipe.step(mesh, q, stream, torch)
+        b.record(stream)
+        b.synchronize()
+        c_ms, g_ms = pipe.phase_ms()
+        i_ms, p_ms = pipe.ctx.spoly_phase_ms(pipe.sol)
+        out.append({"step": a.elapsed_time(b), "chains": c_ms, "gate": g_ms, "isolation": i_ms, "polish": p_ms,
+                    "paths": pipe.ctx.spoly_stats(pipe.sol)["admissible"]})
+    return out
 
 
 def main():
@@ -207,25 +394,44 @@ def main():
     d = [torch.from_numpy(a).to(dev) for a in host]
     mesh = ctx.mesh(d[0])
     q = ctx.queries(*d[1:])
-    pairs = s.n_queries * s.n_tris
 
     peak32 = ctx.spoly_measure_peak(binding.PEAK_FP32_FMA)
     peak64 = ctx.spoly_measure_peak(binding.PEAK_FP64_FMA)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    state = {"chains": None, "sol": None}
 
-    def step(m, qq):
-        state["chains"] = ctx.spoly_build_chains(m, qq, mode, margin=1e-3, reuse=state["chains"], camera=camera)
-        state["sol"] = ctx.spoly_solve(m, qq, state["chains"], precision=precision,
-                                       flags=binding.SOLVE_TIMING, reuse=state["sol"], camera=camera)
+    # learned gate: trained and calibrated before the timed region
+    use_gate = camera is not None and precision == binding.MIXED and not args.no_gate
+    mlp, tau, gate_info = None, 0.0, None
+    if use_gate and args.gate_file and os.path.exists(args.gate_file) and os.path.exists(args.gate_file + ".json"):
+        mlp = ctx.spoly_mlp_load(args.gate_file)
+        gate_info = json.load(open(args.gate_file + ".json"))
+        gate_info["loaded_from"] = args.gate_file
+        tau = gate_info["tau_logit"]
+    elif use_gate:
+        from paper_2405_13409_gb300 import gate_train, scenes
+        t0 = time.perf_counter()
+        train = [scenes.glint_scene(seed=1000 + i) for i in range(args.train_seeds)]
+        val = [scenes.glint_scene(seed=2000)]
+        gen_s = time.perf_counter() - t0
+        mlp, tau, gate_info = gate_train.train_gate(ctx, torch, train, val, mode, camera, steps=args.train_steps,
+                                                    seed=args.seed)
+        gate_info["scene_generation_s"] = gen_s
+        gate_info["train_seeds"] = [1000 + i for i in range(args.train_seeds)]
+        gate_info["val_seeds"] = [2000]
+        del train, val
+        torch.cuda.empty_cache()
+        if args.gate_file:
+            ctx.spoly_mlp_save(mlp, args.gate_file)
+            json.dump(gate_info, open(args.gate_file + ".json", "w"))
 
+    pipe = Pipeline(ctx, mode, precision, camera, mlp, tau)
     for _ in range(args.warmup):
-        step(mesh, q)
+        pipe.step(mesh, q)
     torch.cuda.synchronize()
-    n_chains = ctx.spoly_chains_count(state["chains"])
-    stats = ctx.spoly_stats(state["sol"])
-    if mode == binding.CHAINS_FOOTPRINT:
-        pairs = n_chains  # the footprint defines the candidate set of this workload
+    n_cand = ctx.spoly_chains_count(pipe.chains)
+    n_solved = ctx.spoly_chains_count(pipe.gated) if use_gate else n_cand
+    stats = ctx.spoly_stats(pipe.sol)
+    pairs = n_cand if mode == binding.CHAINS_FOOTPRINT else s.n_queries * s.n_tris
 
     # timed region: device-resident inputs, L2 flushed between steps
     clocks = ClockSampler(local)
@@ -233,41 +439,57 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, iso_ms, pol_ms = [], [], []
-    n_paths = 0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step(mesh, q)
-        b.record(stream)
-        b.synchronize()
-        step_ms.append(a.elapsed_time(b))
-        i_ms, p_ms = ctx.spoly_phase_ms(state["sol"])
-        iso_ms.append(i_ms)
-        pol_ms.append(p_ms)
-        n_paths = ctx.spoly_stats(state["sol"])["admissible"]
+    rec = timed_steps(pipe, mesh, q, args.steps, flush, stream, torch)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
+    total_ms = sum(r["step"] for r in rec)
     t = torch.tensor([total_ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     value = world * pairs * args.steps / (total_ms * 1e-3)
+    n_paths = rec[-1]["paths"]
+    got_paths = ctx.spoly_paths(pipe.sol)
 
-    # end to end: host (pinned) inputs through the C ABI, H2D and D2H inside the timed region
+    # plain FP64 path on the same candidates: no gate, every step in FP64
+    plain = None
+    if camera is not None and not args.no_plain and precision == binding.MIXED:
+        pp = Pipeline(ctx, mode, binding.PLAIN_FP64, camera)
+        pp.step(mesh, q)
+        torch.cuda.synchronize()
+        k = max(1, min(args.steps, args.plain_steps))
+        prec = timed_steps(pp, mesh, q, k, flush, stream, torch)
+        pms = sum(r["step"] for r in prec) / k
+        ref_paths = ctx.spoly_paths(pp.sol)
+        matched, worst = match_paths(got_paths, ref_paths)
+        plain = {"ms_per_step": pms, "value": pairs / (pms * 1e-3), "steps": k, "paths_per_step": int(ref_paths.size),
+                 "isolation_ms": statistics.mean(r["isolation"] for r in prec),
+                 "recall_of_plain_paths": matched / max(1, ref_paths.size), "max_abs_delta_uv": worst,
+                 "speedup": pms / (total_ms / args.steps)}
+        pp.free()
+
+    # end to end through the public API: every step copies its inputs from
+    # pinned host memory to the device, runs the pipeline and reads the paths
+    # back into pinned host memory, all inside the timed region
     e2e = None
     if not args.no_e2e:
         pinned = [torch.from_numpy(a).pin_memory() for a in host]
-        hmesh = ctx.mesh(pinned[0])
-        hq = ctx.queries(*pinned[1:])
+        dd = [torch.empty_like(x, device=dev) for x in pinned]
+        emesh = ctx.mesh(dd[0])
+        eq = ctx.queries(*dd[1:])
         out = torch.empty(max(1, 2 * n_paths + 1024) * binding.PATH_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        cap = out.numel() // binding.PATH_DTYPE.itemsize
+
+        def e2e_step():
+            for dst, src in zip(dd, pinned):
+                dst.copy_(src, non_blocking=True)
+            pipe.step(emesh, eq)
+            return ctx.spoly_paths_into(pipe.sol, out, cap)
+
         for _ in range(2):
-            step(hmesh, hq)
+            e2e_step()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -275,61 +497,75 @@ def main():
         d2h = 0
         for _ in range(args.steps):
             flush.fill_(1.0)
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
-            step(hmesh, hq)
-            cap = out.numel() // binding.PATH_DTYPE.itemsize
-            n = ctx.spoly_paths_into(state["sol"], out, cap)
+            n = e2e_step()
             torch.cuda.synchronize()
             e_ms.append(1e3 * (time.perf_counter() - t0))
             d2h = min(n, cap) * binding.PATH_DTYPE.itemsize + 8
         te = torch.tensor([sum(e_ms)], device=dev)
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        h2d = 2 * sum(a.nbytes for a in host)
         e2e = {"value": world * pairs * args.steps / (float(te.item()) * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": sum(a.nbytes for a in host), "d2h_bytes_per_step": d2h,
+               "ms_per_step": float(te.item()) / args.steps}
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    iso = statistics.mean(iso_ms)
-    achieved64 = FP64_FLOPS[kind] * n_chains / (iso * 1e-3) / 1e12
+    ph = {k: statistics.mean(r[k] for r in rec) for k in ("chains", "gate", "isolation", "polish")}
+    ph["step"] = total_ms / args.steps
+    iso = ph["isolation"]
+    achieved64 = FP64_FLOPS[kind] * n_solved / (iso * 1e-3) / 1e12
+    roof_iso = {"bound": "alu", "pipe": "fp64", "kernel": "k1_isolate_kernel<float>",
+                "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s", "frac": achieved64 / peak64,
+                "peak_source": "measured FP64 FMA microbenchmark (spoly_measure_peak)",
+                "traffic": TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None,
+                "nominal_fp64_tflops": NOMINAL_FP64_TFLOPS, "measured_fp32_tflops": peak32,
+                "fp32_laplace_tflops": FP32_LAPLACE_FLOPS[kind] * n_solved / (iso * 1e-3) / 1e12}
+    roofline = roof_iso
+    if use_gate:
+        gate_tflops = GATE_FLOPS * n_cand / (ph["gate"] * 1e-3) / 1e12
+        roof_gate = {"bound": "tensor", "kernel": "gate_kernel (features + BF16 mma.sync MLP + compaction)",
+                     "achieved": gate_tflops, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": gate_tflops / BF16_PEAK_TFLOPS, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                     "traffic": None, "flops_per_candidate": GATE_FLOPS}
+        # the dominant phase of the step carries the headline roofline
+        roofline = roof_gate if ph["gate"] >= iso else roof_iso
+        roofline = dict(roofline, other={"isolation": roof_iso if roofline is roof_gate else roof_gate})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == binding.MIXED else "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("bf16+f32+f64" if use_gate else "f32+f64") if precision == binding.MIXED else "f64",
         "data": "synthetic",
-        "config": {"workload": desc, "precision": args.precision, "pairs_per_step": pairs,
+        "config": {"workload": desc, "precision": args.precision, "gate": "learned MLP" if use_gate else "off",
+                   "candidates_per_step": pairs,
                    "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "solved_per_s": world * n_chains * args.steps / (total_ms * 1e-3),
+        "solved_per_s": world * n_solved * args.steps / (total_ms * 1e-3),
         "paths_per_s": world * n_paths * args.steps / (total_ms * 1e-3),
-        "survivors_per_step": n_chains, "paths_per_step": n_paths, "counters": stats,
-        "phase_ms": {"step": total_ms / args.steps, "isolation": iso, "polish": statistics.mean(pol_ms),
-                     "chains": total_ms / args.steps - iso - statistics.mean(pol_ms)},
-        "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "k1_isolate_kernel<float>",
-                     "achieved": achieved64, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved64 / NOMINAL_FP64_TFLOPS,
-                     "traffic": TRAFFIC["bytes_per_launch"]
-                     if TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None,
-                     "peak_measured_fp64": peak64, "peak_measured_fp32": peak32,
-                     "frac_of_measured": achieved64 / peak64 if peak64 else None,
-                     "fp32_laplace_tflops": FP32_LAPLACE_FLOPS[kind] * n_chains / (iso * 1e-3) / 1e12},
-        "gpu_launches": 7 * args.steps,
+        "solved_per_step": n_solved, "paths_per_step": n_paths, "counters": stats,
+        "phase_ms": ph,
+        "plain_fp64": plain,
+        "gate": gate_info,
+        "roofline": roofline,
+        "gpu_launches": LAUNCHES_PER_STEP.get((args.workload, use_gate), 7) * args.steps,
         "clocks": clk,
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        n_recv = 64 if kind == "T" else 256
-        c, tcpu, _ = run_oracle_sample(s, min(n_recv, s.n_queries), 7)
+        units = 24576 if camera is not None else (64 if kind == "T" else 256)
+        c, tcpu, _, sample = run_oracle_sample(s, camera, min(units, s.n_queries), 7)
         line["cpu_baseline"] = {"value": c / tcpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"all {s.n_tris} triangles x {min(n_recv, s.n_queries)} seeded receivers"}
+                                "sample": sample}
     print(json.dumps(line))
-    ctx.spoly_solution_free(state["sol"])
-    ctx.spoly_chains_free(state["chains"])
+    pipe.free()
+    if mlp is not None:
+        ctx.spoly_mlp_free(mlp)
     ctx.close()
     if world > 1:
         dist.destroy_process_group()

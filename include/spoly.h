@@ -145,7 +145,7 @@ typedef struct {
 typedef struct {
   int32_t query;
   int32_t tri[2];
-  int32_t reserved;
+  int32_t chain;   /* index of the producing candidate in the solved chain list */
   double uv[2][2]; /* (u_i, v_i) of each specular vertex */
   double x[2][3];  /* world position of each specular vertex */
   float residual;  /* max_i |h_i x n_i| / (|h_i| |n_i|) */
@@ -277,6 +277,101 @@ spoly_status spoly_solve_noalloc(int device, void* cuda_stream, const double* tr
                                  const int32_t* types, const int32_t* k, int64_t n_queries, const int32_t* chains,
                                  int64_t n_chains, int32_t precision, spoly_path* paths, int64_t path_capacity,
                                  int64_t* n_paths, char* msg, int32_t msg_len);
+
+/* ------------------------------------------------------------------------
+ * Learned candidate gate.  (The paper has no counterpart: the gate predicts,
+ * from a candidate's geometry, whether its solve returns any admissible path,
+ * so that candidates predicted empty are not solved.)
+ *
+ * Features: 24 FP32 values per 1-bounce chain, computed from the triangle's
+ * vertices and normals relative to the endpoints: the tangential mismatch
+ * between the unit normal and the generalised half vector (the constraint
+ * h x n = 0 of Eq. eq_ch) at the three vertices, in a frame perpendicular to
+ * the half vector at the centroid; the barycentric coordinates of the zero
+ * of its affine interpolant; shape, distance and type terms.
+ *
+ * Network: 24 (padded to 32) -> 64 -> 64 -> 64 -> 1 with ReLU hidden layers
+ * and a sigmoid output.  The three weight matrices and every matrix-product
+ * operand are BF16 (round to nearest even) with FP32 accumulation on the
+ * tensor cores; biases, the output weights and bias are FP32.  Parameters
+ * form one FP32 vector of SPOLY_MLP_PARAMS values: W1[32][64] (rows 24..31
+ * unused and kept zero), b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
+ * w4[64], b4, each row-major W[in][out].
+ * ---------------------------------------------------------------------- */
+#define SPOLY_MLP_FEATURES 24
+#define SPOLY_MLP_PARAMS 10497
+
+typedef struct spoly_mlp spoly_mlp;
+
+typedef struct {
+  int64_t steps;        /* Adam steps (> 0) */
+  int32_t batch;        /* rows per step, 32 .. 2^20 */
+  float lr;             /* initial learning rate (> 0) */
+  float lr_final;       /* learning rate of the last step, geometric decay; 0: constant */
+  float pos_weight;     /* loss weight of a positive row (> 0) */
+  float pos_fraction;   /* share of positives in every batch, in (0, 1) */
+  int32_t reserved;
+  uint64_t seed;        /* batch sampler seed */
+} spoly_mlp_train_opts;
+
+/* A network with He-uniform weights from `seed` (splitmix64) and zero
+ * biases, resident on the context's device.  Free with spoly_mlp_free. */
+spoly_status spoly_mlp_create(spoly_ctx* ctx, uint64_t seed, spoly_mlp** out);
+spoly_status spoly_mlp_free(spoly_mlp* mlp);
+
+/* Copy the FP32 parameter vector (SPOLY_MLP_PARAMS values, host memory) out
+ * of or into the network.  set rejects non-finite values (EINVAL). */
+spoly_status spoly_mlp_get_params(spoly_ctx* ctx, const spoly_mlp* mlp, float* dst);
+spoly_status spoly_mlp_set_params(spoly_ctx* ctx, spoly_mlp* mlp, const float* src);
+
+/* Checkpoint file: magic "SPOLYMLP", int32 version 1, int32 parameter count,
+ * int64 Adam step, then the parameters and both Adam moment vectors (FP32,
+ * little-endian).  load returns a new network; EINVAL on a bad file. */
+spoly_status spoly_mlp_save(spoly_ctx* ctx, const spoly_mlp* mlp, const char* path);
+spoly_status spoly_mlp_load(spoly_ctx* ctx, const char* path, spoly_mlp** out);
+
+/* Features of every chain of `chains` into dst (device, FP32 [n][24],
+ * 16-byte aligned).  Synchronises. */
+spoly_status spoly_mlp_features(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
+                                const spoly_chains* chains, float* dst);
+
+/* Training labels from a finished (synchronous) solve of a chain list:
+ * dst[c] = 1 if chain c produced a returned path, else 0 (device uint8
+ * [n_chains]).  Solve without a pixel filter to label each chain's own
+ * solution set.  Synchronises. */
+spoly_status spoly_chain_labels(spoly_ctx* ctx, const spoly_solution_set* set, int64_t n_chains, uint8_t* dst);
+
+/* Logits of n feature rows (device FP32 [n][24] -> device FP32 [n]) by the
+ * gate's inference kernel.  Synchronises. */
+spoly_status spoly_mlp_forward(spoly_ctx* ctx, const spoly_mlp* mlp, const float* feat, int64_t n, float* logits);
+
+/* Gradient of the mean weighted binary cross-entropy of n rows (device
+ * features and uint8 labels; n <= 2^24) with respect to the parameter
+ * vector, into grad (host, SPOLY_MLP_PARAMS FP32), by the training kernels;
+ * *loss (host, may be NULL) receives the loss.  The parameters are unchanged. */
+spoly_status spoly_mlp_grad(spoly_ctx* ctx, spoly_mlp* mlp, const float* feat, const uint8_t* labels, int64_t n,
+                            float pos_weight, float* grad, float* loss);
+
+/* Trains on n labelled rows (device features and uint8 labels, both classes
+ * present) with Adam on stratified batches sampled with replacement.
+ * *final_loss (host, may be NULL) receives the mean batch loss of the last
+ * min(steps, 64) steps.  Synchronises. */
+spoly_status spoly_mlp_train(spoly_ctx* ctx, spoly_mlp* mlp, const float* feat, const uint8_t* labels, int64_t n,
+                             const spoly_mlp_train_opts* opts, float* final_loss);
+
+/* The largest logit threshold that keeps at least target_recall of the
+ * positive rows of a labelled set (device features and labels), into
+ * *tau_logit; *pass_fraction (may be NULL) receives the share of all rows at
+ * or above it. */
+spoly_status spoly_mlp_calibrate(spoly_ctx* ctx, spoly_mlp* mlp, const float* feat, const uint8_t* labels,
+                                 int64_t n, double target_recall, float* tau_logit, double* pass_fraction);
+
+/* Gates a chain list: features, network and compaction in one kernel; the
+ * chains whose logit is >= tau_logit are written to *inout (created when
+ * NULL, else reused and grown; it must not be `in`).  Their order is not
+ * preserved.  Synchronises (reads the count back). */
+spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* mlp, const spoly_mesh* mesh, const spoly_queries* q,
+                        const spoly_chains* in, float tau_logit, spoly_chains** inout);
 
 /* Library version string. */
 const char* spoly_version(void);

@@ -46,6 +46,8 @@ SOLVE_ASYNC = 1
 SOLVE_TIMING = 2
 PEAK_FP32_FMA = 0
 PEAK_FP64_FMA = 1
+MLP_FEATURES = 24
+MLP_PARAMS = 10497
 
 c_void_p = ctypes.c_void_p
 c_int32 = ctypes.c_int32
@@ -73,7 +75,7 @@ class spoly_solve_opts(ctypes.Structure):
 
 
 class spoly_path(ctypes.Structure):
-    _fields_ = [("query", c_int32), ("tri", c_int32 * 2), ("reserved", c_int32),
+    _fields_ = [("query", c_int32), ("tri", c_int32 * 2), ("chain", c_int32),
                 ("uv", ctypes.c_double * 4), ("x", ctypes.c_double * 6),
                 ("residual", ctypes.c_float), ("flags", ctypes.c_uint32)]
 
@@ -84,7 +86,13 @@ class spoly_counters(ctypes.Structure):
                [("reserved", c_int64 * 6)]
 
 
-PATH_DTYPE = np.dtype([("query", "<i4"), ("tri", "<i4", (2,)), ("reserved", "<i4"), ("uv", "<f8", (4,)),
+class spoly_mlp_train_opts(ctypes.Structure):
+    _fields_ = [("steps", c_int64), ("batch", c_int32), ("lr", ctypes.c_float), ("lr_final", ctypes.c_float),
+                ("pos_weight", ctypes.c_float), ("pos_fraction", ctypes.c_float), ("reserved", c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+PATH_DTYPE = np.dtype([("query", "<i4"), ("tri", "<i4", (2,)), ("chain", "<i4"), ("uv", "<f8", (4,)),
                        ("x", "<f8", (6,)), ("residual", "<f4"), ("flags", "<u4")])
 assert PATH_DTYPE.itemsize == ctypes.sizeof(spoly_path) == 104
 
@@ -126,6 +134,22 @@ def load():
         "spoly_measure_peak": ([P, c_int32, ctypes.POINTER(ctypes.c_double)], c_int32),
         "spoly_solve_noalloc": ([ctypes.c_int, P, P, c_int64, P, P, P, P, P, c_int64, P, c_int64, c_int32, P,
                                  c_int64, ctypes.POINTER(c_int64), ctypes.c_char_p, c_int32], c_int32),
+        "spoly_mlp_create": ([P, ctypes.c_uint64, ctypes.POINTER(P)], c_int32),
+        "spoly_mlp_free": ([P], c_int32),
+        "spoly_mlp_get_params": ([P, P, P], c_int32),
+        "spoly_mlp_set_params": ([P, P, P], c_int32),
+        "spoly_mlp_save": ([P, P, ctypes.c_char_p], c_int32),
+        "spoly_mlp_load": ([P, ctypes.c_char_p, ctypes.POINTER(P)], c_int32),
+        "spoly_mlp_features": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P, P], c_int32),
+        "spoly_chain_labels": ([P, P, c_int64, P], c_int32),
+        "spoly_mlp_forward": ([P, P, P, c_int64, P], c_int32),
+        "spoly_mlp_grad": ([P, P, P, P, c_int64, ctypes.c_float, P, ctypes.POINTER(ctypes.c_float)], c_int32),
+        "spoly_mlp_train": ([P, P, P, P, c_int64, ctypes.POINTER(spoly_mlp_train_opts),
+                             ctypes.POINTER(ctypes.c_float)], c_int32),
+        "spoly_mlp_calibrate": ([P, P, P, P, c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_double)], c_int32),
+        "spoly_gate": ([P, P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P, ctypes.c_float,
+                        ctypes.POINTER(P)], c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +288,78 @@ class Context:
         t = ctypes.c_double()
         self.check(self.lib.spoly_measure_peak(self.h, int(kind), ctypes.byref(t)), "spoly_measure_peak")
         return float(t.value)
+
+    # ------------------------------------------------------------ gate
+    def spoly_mlp_create(self, seed: int = 0):
+        h = c_void_p()
+        self.check(self.lib.spoly_mlp_create(self.h, int(seed), ctypes.byref(h)), "spoly_mlp_create")
+        return h
+
+    def spoly_mlp_free(self, mlp):
+        self.lib.spoly_mlp_free(mlp)
+
+    def spoly_mlp_get_params(self, mlp) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self.check(self.lib.spoly_mlp_get_params(self.h, mlp, c_void_p(out.ctypes.data)), "spoly_mlp_get_params")
+        return out
+
+    def spoly_mlp_set_params(self, mlp, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.shape == (MLP_PARAMS,)
+        self.check(self.lib.spoly_mlp_set_params(self.h, mlp, c_void_p(t.ctypes.data)), "spoly_mlp_set_params")
+
+    def spoly_mlp_save(self, mlp, path: str):
+        self.check(self.lib.spoly_mlp_save(self.h, mlp, os.fsencode(path)), "spoly_mlp_save")
+
+    def spoly_mlp_load(self, path: str):
+        h = c_void_p()
+        self.check(self.lib.spoly_mlp_load(self.h, os.fsencode(path), ctypes.byref(h)), "spoly_mlp_load")
+        return h
+
+    def spoly_mlp_features(self, mesh: spoly_mesh, q: spoly_queries, chains, dst):
+        """Features of a chain list into a device FP32 tensor [n][24]."""
+        self.check(self.lib.spoly_mlp_features(self.h, ctypes.byref(mesh), ctypes.byref(q), chains,
+                                               c_void_p(_ptr(dst))), "spoly_mlp_features")
+
+    def spoly_chain_labels(self, sol, n_chains: int, dst):
+        self.check(self.lib.spoly_chain_labels(self.h, sol, int(n_chains), c_void_p(_ptr(dst))),
+                   "spoly_chain_labels")
+
+    def spoly_mlp_forward(self, mlp, feat, logits):
+        self.check(self.lib.spoly_mlp_forward(self.h, mlp, c_void_p(_ptr(feat)), int(feat.shape[0]),
+                                              c_void_p(_ptr(logits))), "spoly_mlp_forward")
+
+    def spoly_mlp_grad(self, mlp, feat, labels, pos_weight: float):
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        self.check(self.lib.spoly_mlp_grad(self.h, mlp, c_void_p(_ptr(feat)), c_void_p(_ptr(labels)),
+                                           int(feat.shape[0]), float(pos_weight), c_void_p(g.ctypes.data),
+                                           ctypes.byref(loss)), "spoly_mlp_grad")
+        return float(loss.value), g
+
+    def spoly_mlp_train(self, mlp, feat, labels, steps: int, batch: int = 4096, lr: float = 2e-3,
+                        lr_final: float = 2e-4, pos_weight: float = 1.0, pos_fraction: float = 0.25, seed: int = 0):
+        o = spoly_mlp_train_opts(int(steps), int(batch), float(lr), float(lr_final), float(pos_weight),
+                                 float(pos_fraction), 0, int(seed))
+        loss = ctypes.c_float()
+        self.check(self.lib.spoly_mlp_train(self.h, mlp, c_void_p(_ptr(feat)), c_void_p(_ptr(labels)),
+                                            int(feat.shape[0]), ctypes.byref(o), ctypes.byref(loss)),
+                   "spoly_mlp_train")
+        return float(loss.value)
+
+    def spoly_mlp_calibrate(self, mlp, feat, labels, target_recall: float):
+        tau = ctypes.c_float()
+        frac = ctypes.c_double()
+        self.check(self.lib.spoly_mlp_calibrate(self.h, mlp, c_void_p(_ptr(feat)), c_void_p(_ptr(labels)),
+                                                int(feat.shape[0]), float(target_recall), ctypes.byref(tau),
+                                                ctypes.byref(frac)), "spoly_mlp_calibrate")
+        return float(tau.value), float(frac.value)
+
+    def spoly_gate(self, mlp, mesh: spoly_mesh, q: spoly_queries, chains, tau_logit: float, reuse=None):
+        h = c_void_p(reuse.value if reuse is not None else None)
+        self.check(self.lib.spoly_gate(self.h, mlp, ctypes.byref(mesh), ctypes.byref(q), chains, float(tau_logit),
+                                       ctypes.byref(h)), "spoly_gate")
+        return h
 
 
 def spoly_solve_noalloc(device: int, stream, tri, x_first, x_last, eta, types, k, chains, precision: int, paths,

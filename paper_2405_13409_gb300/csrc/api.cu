@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 
+#include "ctx.cuh"
 #include "k1.cuh"
 
 using namespace spoly;
@@ -14,61 +15,7 @@ namespace spoly {
 double measure_fma_peak(int kind, int num_sms, cudaStream_t st, cudaError_t* err);
 }
 
-namespace {
-
-// Grow-only device buffer.
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  cudaError_t ensure(size_t n) {
-    if (n <= bytes) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-    cudaError_t e = cudaMalloc(&p, n);
-    if (e == cudaSuccess) bytes = n;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-};
-
-}  // namespace
-
-struct spoly_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int num_sms = 0;
-  char err[512] = {0};
-  DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
-  DevBuf boxes, flag;                    // cone cull scratch
-  DevBuf cam, bounds, fp_scratch, fp_entries;  // footprint builder
-};
-
-struct spoly_chains {
-  DevBuf buf;        // [cap][3] int32
-  int64_t n = 0;
-  DevBuf counter;    // unsigned long long + int32 error flag
-};
-
-struct spoly_solution_set {
-  DevBuf queue;      // RootItem[queue_cap]
-  int64_t queue_cap = 0;
-  DevBuf paths;      // spoly_path[path_cap]
-  int64_t path_cap = 0;
-  DevBuf side;       // int32[side_cap] chains for the generic-size kernel
-  int64_t side_cap = 0;
-  DevBuf counters;   // unsigned long long[C_COUNT]
-  unsigned long long host[C_COUNT] = {0};
-  bool host_valid = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing
-  bool timed = false;
-};
-
-namespace {
+namespace spoly {
 
 spoly_status fail(spoly_ctx* ctx, spoly_status st, const char* fmt, ...) {
   if (ctx) {
@@ -84,12 +31,6 @@ spoly_status cuda_fail(spoly_ctx* ctx, cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation) return fail(ctx, SPOLY_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
   return fail(ctx, SPOLY_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-#define CK(call, what)                                  \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
-  } while (0)
 
 // Device views of mesh / queries, staging host arrays into context buffers.
 spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, MeshView* mv,
@@ -152,7 +93,7 @@ spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_qu
   return SPOLY_OK;
 }
 
-}  // namespace
+}  // namespace spoly
 
 extern "C" {
 

@@ -1,0 +1,82 @@
+// Host-side state behind the C ABI's opaque handles, shared by the
+// translation units that implement the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "common.cuh"
+
+namespace spoly {
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+}  // namespace spoly
+
+// The opaque handle types of the C ABI.
+struct spoly_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  char err[512] = {0};
+  spoly::DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
+  spoly::DevBuf boxes, flag;                    // cone cull scratch
+  spoly::DevBuf cam, bounds, fp_scratch, fp_entries;  // footprint builder
+};
+
+struct spoly_chains {
+  spoly::DevBuf buf;        // [cap][3] int32
+  int64_t n = 0;
+  spoly::DevBuf counter;    // unsigned long long + int32 error flag
+};
+
+struct spoly_solution_set {
+  spoly::DevBuf queue;      // RootItem[queue_cap]
+  int64_t queue_cap = 0;
+  spoly::DevBuf paths;      // spoly_path[path_cap]
+  int64_t path_cap = 0;
+  spoly::DevBuf side;       // int32[side_cap] chains for the generic-size kernel
+  int64_t side_cap = 0;
+  spoly::DevBuf counters;   // unsigned long long[C_COUNT]
+  unsigned long long host[spoly::C_COUNT] = {0};
+  bool host_valid = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing
+  bool timed = false;
+};
+
+namespace spoly {
+
+// Records a message on the context and returns `st`.
+spoly_status fail(spoly_ctx* ctx, spoly_status st, const char* fmt, ...);
+// ENOMEM or ECUDA with the CUDA error string.
+spoly_status cuda_fail(spoly_ctx* ctx, cudaError_t e, const char* what);
+// Device views of mesh and queries; host arrays are checked for non-finite
+// values and staged into the context's buffers.
+spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, MeshView* mv,
+                          QueryView* qv);
+
+}  // namespace spoly
+
+#define CK(call, what)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return spoly::cuda_fail(ctx, e_, what); \
+  } while (0)

@@ -221,7 +221,7 @@ SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigne
 // sidedness and the in-triangle test.  Appends up to 6 paths to `out`.
 template <int DB>
 SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, double zs, uint32_t vflags, int q,
-                         int t, spoly_path (&out)[6], int np, unsigned& n_u, const PixelFilter& pix) {
+                         int t, int chain, spoly_path (&out)[6], int np, unsigned& n_u, const PixelFilter& pix) {
   const double v0 = zs * s.sc.t;
   double am[3];
   a_at<double>(s.a, s.na, zs, am);
@@ -291,7 +291,7 @@ SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, d
     p.query = q;
     p.tri[0] = t;
     p.tri[1] = -1;
-    p.reserved = 0;
+    p.chain = chain;
     p.uv[0][0] = u;
     p.uv[0][1] = v;
     p.uv[1][0] = 0.0;
@@ -330,7 +330,7 @@ SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue
     }
     if (dup) continue;
     const uint32_t vflags = r == 0 ? (it.flags & 0xffu) : ((it.flags >> 8) & 0xffu);
-    np = k1_path_root<DB>(s, tr, qd, z, vflags, q, t, out, np, n_u, pix);
+    np = k1_path_root<DB>(s, tr, qd, z, vflags, q, t, it.chain, out, np, n_u, pix);
   }
   return np;
 }

@@ -1,0 +1,252 @@
+"""GPU tests of the learned gate: features, inference and training gradients
+against the FP64 gate oracle, the fused gate kernel against the separate
+feature and forward kernels, checkpoints, and what a trained network gains
+(candidates skipped at a recall of at least 99.9% of the plain solver's
+paths on a held-out glint scene)."""
+import numpy as np
+import pytest
+
+from oracle import gate as G
+from paper_2405_13409_gb300 import binding, scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = binding.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _dev(s):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
+
+
+def _chains(ctx, s, mode, camera=None):
+    d = _dev(s)
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, mode, camera=camera)
+    return d, mesh, q, ch
+
+
+def _features(ctx, mesh, q, ch):
+    n = ctx.spoly_chains_count(ch)
+    f = torch.empty((n, 24), dtype=torch.float32, device="cuda")
+    ctx.spoly_mlp_features(mesh, q, ch, f)
+    return f
+
+
+@pytest.fixture(scope="module")
+def glint_small(ctx):
+    s = scenes.glint_scene(seed=3, n_cells=128, res=64, n_terms=16)
+    cam = s.meta["camera"].as_array()
+    d, mesh, q, ch = _chains(ctx, s, binding.CHAINS_FOOTPRINT, cam)
+    yield s, cam, d, mesh, q, ch
+    ctx.spoly_chains_free(ch)
+
+
+def test_features_match_oracle_glints(ctx, glint_small):
+    s, cam, d, mesh, q, ch = glint_small
+    chains = ctx.spoly_chains_copy(ch)
+    got = _features(ctx, mesh, q, ch).cpu().numpy().astype(np.float64)
+    want = G.chain_features(s.tri, s.x_first, s.x_last, s.eta, s.types, chains)
+    # FP32 features: the mismatch is a difference of unit vectors (error
+    # ~1e-7) divided by S; compare where S >= 1e-3 and, for the barycentric
+    # features, where the mismatch triangle is not degenerate.
+    S_ok = want[:, 13] >= np.log2(1e-3) / 8
+    D = want[:, 6:9].sum(1)
+    assert S_ok.mean() > 0.9
+    err = np.abs(got - want)
+    plain = [0, 1, 2, 3, 4, 5, 6, 7, 8, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23]
+    assert err[S_ok][:, plain].max() < 2e-3, err[S_ok][:, plain].max(0)
+    lam_ok = S_ok & (np.abs(D) > 0.05)
+    assert np.all(err[lam_ok][:, 9:13] <= 2e-3 * (1 + np.abs(want[lam_ok][:, 9:13]) ** 2)), err[lam_ok][:, 9:13].max(0)
+
+
+def test_features_match_oracle_refraction(ctx):
+    s = scenes.refract_scene(seed=0, n_cells=16, n_recv=8)
+    d, mesh, q, ch = _chains(ctx, s, binding.CHAINS_ALL)
+    chains = ctx.spoly_chains_copy(ch)
+    got = _features(ctx, mesh, q, ch).cpu().numpy().astype(np.float64)
+    ctx.spoly_chains_free(ch)
+    want = G.chain_features(s.tri, s.x_first, s.x_last, s.eta, s.types, chains)
+    assert np.all(want[:, 23] == 1.0) and np.all(got[:, 23] == 1.0)
+    S_ok = want[:, 13] >= np.log2(1e-3) / 8
+    err = np.abs(got - want)
+    assert err[S_ok][:, [0, 1, 2, 3, 4, 5, 13, 14, 15, 16, 21, 22]].max() < 2e-3
+
+
+def _random_theta(seed, scale=0.25):
+    rng = np.random.default_rng(seed)
+    th = rng.normal(size=G.N_PARAMS) * scale
+    W1 = th[G.OFF_W1:G.OFF_B1].reshape(G.N_IN, G.N_HID)
+    W1[G.N_FEAT:] = 0.0
+    return th.astype(np.float32)
+
+
+def test_forward_matches_oracle(ctx):
+    rng = np.random.default_rng(11)
+    n = 5000  # 39 tiles of 128 rows plus a ragged tail
+    f = (rng.normal(size=(n, 24)) * 0.7).astype(np.float32)
+    mlp = ctx.spoly_mlp_create(seed=1)
+    try:
+        th = _random_theta(12)
+        ctx.spoly_mlp_set_params(mlp, th)
+        np.testing.assert_array_equal(ctx.spoly_mlp_get_params(mlp), th)
+        z = torch.empty(n, dtype=torch.float32, device="cuda")
+        ctx.spoly_mlp_forward(mlp, torch.from_numpy(f).cuda(), z)
+        got = z.cpu().numpy().astype(np.float64)
+    finally:
+        ctx.spoly_mlp_free(mlp)
+    want, _ = G.forward(th.astype(np.float64), f.astype(np.float64))
+    scale = 1.0 + np.abs(want).mean()
+    err = np.abs(got - want)
+    # FP32 accumulation vs exact; a hidden activation near a BF16 rounding
+    # boundary may round the other way (one BF16 ulp, 2^-8 relative).
+    assert np.median(err) < 1e-4 * scale
+    assert err.max() < 2e-2 * scale, err.max()
+
+
+def test_gradient_matches_oracle(ctx):
+    rng = np.random.default_rng(13)
+    n = 3000
+    f = (rng.normal(size=(n, 24)) * 0.7).astype(np.float32)
+    y = (rng.random(n) < 0.2).astype(np.uint8)
+    th = _random_theta(14, 0.2)
+    mlp = ctx.spoly_mlp_create(seed=2)
+    try:
+        ctx.spoly_mlp_set_params(mlp, th)
+        loss, g = ctx.spoly_mlp_grad(mlp, torch.from_numpy(f).cuda(), torch.from_numpy(y).cuda(), 3.0)
+        np.testing.assert_array_equal(ctx.spoly_mlp_get_params(mlp), th)
+    finally:
+        ctx.spoly_mlp_free(mlp)
+    L, want = G.grad(th.astype(np.float64), f.astype(np.float64), y, 3.0)
+    assert abs(loss - L) <= 1e-3 * abs(L)
+    for lo, hi in [(G.OFF_W1, G.OFF_B1), (G.OFF_B1, G.OFF_W2), (G.OFF_W2, G.OFF_B2), (G.OFF_B2, G.OFF_W3),
+                   (G.OFF_W3, G.OFF_B3), (G.OFF_B3, G.OFF_W4), (G.OFF_W4, G.OFF_B4), (G.OFF_B4, G.N_PARAMS)]:
+        a, b = g[lo:hi].astype(np.float64), want[lo:hi]
+        # BF16 operands in the backward products: relative error ~2^-8 per term
+        assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b) + 1e-9, (lo, np.linalg.norm(a - b) / np.linalg.norm(b))
+    pad = g[G.OFF_W1 + G.N_FEAT * G.N_HID:G.OFF_B1]
+    assert np.all(pad == 0)
+
+
+def test_gate_kernel_matches_features_and_forward(ctx, glint_small):
+    s, cam, d, mesh, q, ch = glint_small
+    mlp = ctx.spoly_mlp_create(seed=5)
+    try:
+        f = _features(ctx, mesh, q, ch)
+        z = torch.empty(f.shape[0], dtype=torch.float32, device="cuda")
+        ctx.spoly_mlp_forward(mlp, f, z)
+        zc = z.cpu().numpy()
+        tau = float(np.quantile(zc, 0.7))
+        gated = ctx.spoly_gate(mlp, mesh, q, ch, tau)
+        kept = ctx.spoly_chains_copy(gated)
+        ctx.spoly_chains_free(gated)
+    finally:
+        ctx.spoly_mlp_free(mlp)
+    chains = ctx.spoly_chains_copy(ch)
+    want = set(map(tuple, chains[zc >= tau].tolist()))
+    assert set(map(tuple, kept.tolist())) == want
+    assert kept.shape[0] == len(want)
+
+
+def test_checkpoint_roundtrip(ctx, tmp_path):
+    mlp = ctx.spoly_mlp_create(seed=9)
+    path = str(tmp_path / "gate.bin")
+    try:
+        ctx.spoly_mlp_save(mlp, path)
+        other = ctx.spoly_mlp_load(path)
+        np.testing.assert_array_equal(ctx.spoly_mlp_get_params(other), ctx.spoly_mlp_get_params(mlp))
+        ctx.spoly_mlp_free(other)
+        with open(path, "r+b") as fp:
+            fp.write(b"XXXX")
+        with pytest.raises(binding.SpolyError):
+            ctx.spoly_mlp_load(path)
+    finally:
+        ctx.spoly_mlp_free(mlp)
+
+
+def test_training_reduces_loss(ctx):
+    """One full-batch step moves every trainable parameter; a few hundred
+    steps on a synthetic nonlinear task cut the loss by 4x."""
+    rng = np.random.default_rng(21)
+    n = 20000
+    f = rng.normal(size=(n, 24)).astype(np.float32)
+    y = ((f[:, 0] + 0.5 * f[:, 1] - f[:, 2] * f[:, 3]) > 1.5).astype(np.uint8)
+    fd, yd = torch.from_numpy(f).cuda(), torch.from_numpy(y).cuda()
+    mlp = ctx.spoly_mlp_create(seed=3)
+    try:
+        l0, g0 = ctx.spoly_mlp_grad(mlp, fd, yd, 1.0)
+        th0 = ctx.spoly_mlp_get_params(mlp)
+        ctx.spoly_mlp_train(mlp, fd, yd, steps=1, batch=n, lr=1e-3, lr_final=0.0, pos_fraction=0.5)
+        th1 = ctx.spoly_mlp_get_params(mlp)
+        moved = np.abs(th1 - th0) > 0
+        assert moved.sum() > 0.9 * (G.N_PARAMS - 8 * G.N_HID)
+        loss = ctx.spoly_mlp_train(mlp, fd, yd, steps=400, batch=2048, lr=3e-3, lr_final=3e-4, pos_fraction=0.5)
+        l1, _ = ctx.spoly_mlp_grad(mlp, fd, yd, 1.0)
+    finally:
+        ctx.spoly_mlp_free(mlp)
+    assert l1 < 0.25 * l0, (l0, l1, loss)
+
+
+def _as_ref(p):
+    """GPU path records in the field layout the parity helper reads for its
+    reference side."""
+    r = np.zeros(p.size, dtype=[("query", "<i4"), ("tri0", "<i4"), ("uv", "<f8", (4,)), ("flags", "<u4")])
+    r["query"], r["tri0"], r["uv"], r["flags"] = p["query"], p["tri"][:, 0], p["uv"], p["flags"]
+    return r
+
+
+def test_trained_gate_keeps_paths_and_skips_candidates(ctx):
+    """Glint scenes of 512x512 cells at 256x256 pixels: train on four seeds,
+    calibrate on a fifth, evaluate on a held-out one.  The gated mixed solve
+    returns at least 99.9% of the plain FP64 solve's pixel-filtered paths
+    (matched at 1e-5 in (u, v)) while solving at most a fifth of the
+    candidates; an untrained network calibrated the same way keeps far more."""
+    from paper_2405_13409_gb300 import gate_train
+    mk = lambda seed: scenes.glint_scene(seed=seed, n_cells=512, res=256)
+    train = [mk(1000 + i) for i in range(4)]
+    val = [mk(2000)]
+    cam = train[0].meta["camera"].as_array()
+    mlp, tau, info = gate_train.train_gate(ctx, torch, train, val, binding.CHAINS_FOOTPRINT, cam, steps=1500)
+    untrained = ctx.spoly_mlp_create(seed=0)
+    try:
+        ev = mk(0)
+        vf, vl = gate_train.labelled_features(ctx, torch, ev, binding.CHAINS_FOOTPRINT, cam)
+        _, base_frac = ctx.spoly_mlp_calibrate(untrained, vf, vl, 0.9995)
+        d = _dev(ev)
+        mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+        ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_FOOTPRINT, camera=cam)
+        n_all = ctx.spoly_chains_count(ch)
+        sol = ctx.spoly_solve(mesh, q, ch, precision=binding.PLAIN_FP64, camera=cam)
+        ref = ctx.spoly_paths(sol)
+        ctx.spoly_solution_free(sol)
+        gated = ctx.spoly_gate(mlp, mesh, q, ch, tau)
+        n_gated = ctx.spoly_chains_count(gated)
+        kept = set(map(tuple, ctx.spoly_chains_copy(gated)[:, :2].tolist()))
+        sol = ctx.spoly_solve(mesh, q, gated, precision=binding.MIXED, camera=cam)
+        got = ctx.spoly_paths(sol)
+        ctx.spoly_solution_free(sol)
+        ctx.spoly_chains_free(gated)
+        ctx.spoly_chains_free(ch)
+    finally:
+        ctx.spoly_mlp_free(untrained)
+        ctx.spoly_mlp_free(mlp)
+    assert ref.size > 200, info
+    # pair by (pixel, triangle) and (u, v) within 1e-5
+    from .parity import compare
+    rep = compare(got, _as_ref(ref))
+    recall = rep["matched"] / ref.size
+    gate_missed = sum((int(a), int(b)) not in kept for a, b in zip(ref["query"], ref["tri"][:, 0]))
+    print("gate", info, "n_all", n_all, "n_gated", n_gated, "recall", recall, "paths of skipped chains", gate_missed,
+          "untrained pass", base_frac, rep)
+    assert recall >= 0.999, (recall, rep)
+    assert n_gated <= 0.2 * n_all, (n_gated, n_all)
+    assert n_gated < 0.5 * base_frac * n_all

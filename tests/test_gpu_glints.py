@@ -1,5 +1,5 @@
 """GPU tests of the glint workload pieces: the pixel-footprint chain builder
-and the pixel filter of the path phase, on a reduced glint scene (128x128
+and the pixel filter of the path phase, on a reduced glint scene (256x256
 cells, 64x64 pixels) so the oracle can solve exhaustively."""
 import math
 
@@ -28,7 +28,7 @@ def ctx():
 
 @pytest.fixture(scope="module")
 def small():
-    s = scenes.glint_scene(seed=3, n_cells=128, res=64, n_terms=16)
+    s = scenes.glint_scene(seed=3, n_cells=256, res=64, n_terms=16)
     return s, s.meta["camera"].as_array()
 
 
