@@ -122,7 +122,7 @@ spoly_status spoly_ctx_destroy(spoly_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf* b : {&ctx->mesh, &ctx->xf, &ctx->xl, &ctx->eta, &ctx->types, &ctx->kk, &ctx->boxes, &ctx->flag,
-                    &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries})
+                    &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries, &ctx->fp_boxes})
     b->release();
   delete ctx;
   return SPOLY_OK;
@@ -238,12 +238,12 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (int64_t(cam[14]) * int64_t(cam[15]) != qv.n || cam[14] < 1 || cam[15] < 1)
       return bail(fail(ctx, SPOLY_EINVAL, "footprint: width x height (%g x %g) must equal n_queries (%lld)", cam[14],
                        cam[15], (long long)qv.n));
-    if (ctx->cam.ensure(16 * sizeof(double)) != cudaSuccess || ctx->bounds.ensure(64) != cudaSuccess)
-      return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
-    e = cudaMemcpyAsync(ctx->cam.p, cam, 16 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "camera copy"));
+    if (ctx->bounds.ensure(64) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
+    if (ctx->fp_boxes.ensure(size_t(mv.n_tris) * sizeof(float4)) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "footprint triangle boxes"));
+    float4* boxes = static_cast<float4*>(ctx->fp_boxes.p);
     float bh[6];
-    e = compute_mesh_bounds(mv, static_cast<int*>(ctx->bounds.p), bh, ctx->num_sms, ctx->stream);
+    e = compute_mesh_bounds(mv, static_cast<int*>(ctx->bounds.p), bh, boxes, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "mesh bounds"));
     const double wx = double(bh[3]) - bh[0], wy = double(bh[4]) - bh[1];
     double cell = opts->cell;
@@ -258,18 +258,17 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (ctx->fp_scratch.ensure(footprint_scratch_bytes(n_cells, qv.n)) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
     int64_t n_entries = 0, total = 0;
-    e = fp_grid_count(mv, g, ctx->fp_scratch.p, qv.n, &n_entries, ctx->num_sms, ctx->stream);
+    e = fp_grid_count(mv, boxes, g, ctx->fp_scratch.p, qv.n, &n_entries, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint grid"));
     if (ctx->fp_entries.ensure(size_t(std::max<int64_t>(n_entries, 1)) * 4) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "footprint grid entries"));
-    const double* cam_dev = static_cast<const double*>(ctx->cam.p);
     const int* bounds_dev = static_cast<const int*>(ctx->bounds.p);
-    e = fp_grid_fill_and_count(mv, g, ctx->fp_scratch.p, static_cast<int32_t*>(ctx->fp_entries.p), cam_dev,
+    e = fp_grid_fill_and_count(mv, boxes, g, ctx->fp_scratch.p, static_cast<int32_t*>(ctx->fp_entries.p), cam,
                                bounds_dev, qv.n, &total, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint count"));
     if (ch->buf.ensure(size_t(std::max<int64_t>(total, 1)) * 12) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
-    e = fp_fill(mv, g, ctx->fp_scratch.p, static_cast<const int32_t*>(ctx->fp_entries.p), cam_dev, bounds_dev, qv.n,
+    e = fp_fill(boxes, g, ctx->fp_scratch.p, static_cast<const int32_t*>(ctx->fp_entries.p), cam, bounds_dev, qv.n,
                 static_cast<int32_t*>(ch->buf.p), ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint fill"));
     ch->n = total;

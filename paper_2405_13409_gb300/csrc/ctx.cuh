@@ -39,7 +39,7 @@ struct spoly_ctx {
   char err[512] = {0};
   spoly::DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
   spoly::DevBuf boxes, flag;                    // cone cull scratch
-  spoly::DevBuf cam, bounds, fp_scratch, fp_entries;  // footprint builder
+  spoly::DevBuf cam, bounds, fp_scratch, fp_entries, fp_boxes;  // footprint builder
 };
 
 struct spoly_chains {

@@ -32,17 +32,26 @@ float o2f_host(int i) {
   return f;
 }
 
-// mesh bounds: [0..2] min xyz, [3..5] max xyz as ordered ints (slack added by the caller)
-__global__ void mesh_bounds_kernel(MeshView M, int* bounds) {
+// Mesh bounds ([0..2] min xyz, [3..5] max xyz as ordered ints; slack added
+// by the caller) and every triangle's FP32 xy box (xl, xh, yl, yh), which the
+// grid and footprint passes read instead of the six FP64 coordinates.
+__global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
   float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < M.n_tris; t += stride)
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < M.n_tris; t += stride) {
+    float tl[3] = {3e38f, 3e38f, 3e38f}, th[3] = {-3e38f, -3e38f, -3e38f};
     for (int v = 0; v < 3; ++v)
       for (int c = 0; c < 3; ++c) {
         const float x = float(M.tri[int64_t(3 * v + c) * M.n_tris + t]);
-        lo[c] = fminf(lo[c], x);
-        hi[c] = fmaxf(hi[c], x);
+        tl[c] = fminf(tl[c], x);
+        th[c] = fmaxf(th[c], x);
       }
+    boxes[t] = make_float4(tl[0], th[0], tl[1], th[1]);
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = fminf(lo[c], tl[c]);
+      hi[c] = fmaxf(hi[c], th[c]);
+    }
+  }
   for (int c = 0; c < 3; ++c) {
     for (int o = 16; o > 0; o >>= 1) {
       lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
@@ -73,22 +82,21 @@ SPOLY_D void cell_range(const GridGeom& G, float xl, float xh, float yl, float y
   cy1 = max(0, min(G.gy - 1, int(floorf((yh - G.y0) * G.inv))));
 }
 
-SPOLY_D void tri_bbox(const MeshView& M, int64_t t, float& xl, float& xh, float& yl, float& yh) {
-  const float a = float(M.tri[0 * M.n_tris + t]), b = float(M.tri[3 * M.n_tris + t]), c = float(M.tri[6 * M.n_tris + t]);
-  const float d = float(M.tri[1 * M.n_tris + t]), e = float(M.tri[4 * M.n_tris + t]), f = float(M.tri[7 * M.n_tris + t]);
-  xl = fminf(a, fminf(b, c));
-  xh = fmaxf(a, fmaxf(b, c));
-  yl = fminf(d, fminf(e, f));
-  yh = fmaxf(d, fmaxf(e, f));
+SPOLY_D void tri_bbox(const float4* __restrict__ boxes, int64_t t, float& xl, float& xh, float& yl, float& yh) {
+  const float4 b = __ldg(boxes + t);
+  xl = b.x;
+  xh = b.y;
+  yl = b.z;
+  yh = b.w;
 }
 
 // pass 0: count entries per cell; pass 1: fill (cursor = count copy)
-__global__ void grid_insert_kernel(MeshView M, GridGeom G, int* cell_count, const int64_t* cell_off,
-                                   int32_t* entries, int pass) {
+__global__ void grid_insert_kernel(MeshView M, const float4* boxes, GridGeom G, int* cell_count,
+                                   const int64_t* cell_off, int32_t* entries, int pass) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < M.n_tris; t += stride) {
     float xl, xh, yl, yh;
-    tri_bbox(M, t, xl, xh, yl, yh);
+    tri_bbox(boxes, t, xl, xh, yl, yh);
     int cx0, cx1, cy0, cy1;
     cell_range(G, xl, xh, yl, yh, cx0, cx1, cy0, cy1);
     for (int cy = cy0; cy <= cy1; ++cy)
@@ -100,47 +108,62 @@ __global__ void grid_insert_kernel(MeshView M, GridGeom G, int* cell_count, cons
   }
 }
 
-struct CamD {
-  d3 o, f, r, u;
-  double th, aspect;
+struct CamF {
+  float ox, oy, oz, fx, fy, fz, rx, ry, rz, ux, uy, uz;
+  float sx_scale, sy_scale;  // 2 tan aspect / w, 2 tan / h
+  float tha, th;             // tan aspect, tan
   int w, h;
 };
 
-SPOLY_D CamD load_cam(const double* c) {
-  CamD k;
-  k.o = mk(c[0], c[1], c[2]);
-  k.f = mk(c[3], c[4], c[5]);
-  k.r = mk(c[6], c[7], c[8]);
-  k.u = mk(c[9], c[10], c[11]);
-  k.th = c[12];
-  k.aspect = c[13];
+CamF make_cam(const double* c) {  // host: c is the caller's 16-double camera
+  CamF k;
+  k.ox = float(c[0]);
+  k.oy = float(c[1]);
+  k.oz = float(c[2]);
+  k.fx = float(c[3]);
+  k.fy = float(c[4]);
+  k.fz = float(c[5]);
+  k.rx = float(c[6]);
+  k.ry = float(c[7]);
+  k.rz = float(c[8]);
+  k.ux = float(c[9]);
+  k.uy = float(c[10]);
+  k.uz = float(c[11]);
   k.w = int(c[14]);
   k.h = int(c[15]);
+  k.tha = float(c[12] * c[13]);
+  k.th = float(c[12]);
+  k.sx_scale = float(2.0 * c[12] * c[13] / c[14]);
+  k.sy_scale = float(2.0 * c[12] / c[15]);
   return k;
 }
 
-// Footprint of a pixel: xy box of its corner rays between z = zlo and z = zhi.
-SPOLY_D bool pixel_footprint(const CamD& C, int64_t q, float zlo, float zhi, float& xl, float& xh, float& yl,
+// Footprint of a pixel: xy box of its corner rays between z = zlo and z = zhi,
+// in FP32 (coordinates are O(1); the 1e-5 relative margin covers rounding).
+SPOLY_D bool pixel_footprint(const CamF& C, int64_t q, float zlo, float zhi, float& xl, float& xh, float& yl,
                              float& yh) {
-  const int ix = int(q % C.w), iy = int(q / C.w);
+  const int qi = int(q);  // n_pixels < 2^31
+  const int iy = qi / C.w, ix = qi - iy * C.w;
   xl = yl = 3e38f;
   xh = yh = -3e38f;
+#pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const double sx = -1.0 + 2.0 * (ix + (k & 1)) / C.w;
-    const double sy = 1.0 - 2.0 * (iy + (k >> 1)) / C.h;
-    const d3 d = C.f + (sx * C.th * C.aspect) * C.r + (sy * C.th) * C.u;
-    if (!(d.z < 0.0)) return false;  // a corner ray never reaches the surface slab
+    const float a = float(ix + (k & 1)) * C.sx_scale - C.tha;  // sx tan aspect
+    const float b = C.th - float(iy + (k >> 1)) * C.sy_scale;  // sy tan
+    const float dx = C.fx + a * C.rx + b * C.ux, dy = C.fy + a * C.ry + b * C.uy, dz = C.fz + a * C.rz + b * C.uz;
+    if (!(dz < 0.0f)) return false;  // a corner ray never reaches the surface slab
+    const float rdz = 1.0f / dz;
+#pragma unroll
     for (int p = 0; p < 2; ++p) {
-      const double z = p ? zhi : zlo;
-      const double tt = (z - C.o.z) / d.z;
-      const float x = float(C.o.x + tt * d.x), y = float(C.o.y + tt * d.y);
+      const float tt = ((p ? zhi : zlo) - C.oz) * rdz;
+      const float x = C.ox + tt * dx, y = C.oy + tt * dy;
       xl = fminf(xl, x);
       xh = fmaxf(xh, x);
       yl = fminf(yl, y);
       yh = fmaxf(yh, y);
     }
   }
-  const float m = 1e-5f * (1.f + fmaxf(fabsf(xl), fabsf(yh)));
+  const float m = 1e-5f * (1.f + fmaxf(fmaxf(fabsf(xl), fabsf(xh)), fmaxf(fabsf(yl), fabsf(yh))));
   xl -= m;
   yl -= m;
   xh += m;
@@ -149,10 +172,9 @@ SPOLY_D bool pixel_footprint(const CamD& C, int64_t q, float zlo, float zhi, flo
 }
 
 // pass 0: count candidates per pixel; pass 1: write them at out_off[q]
-__global__ void footprint_kernel(MeshView M, GridGeom G, const int* bounds, const double* cam, int64_t n_pixels,
+__global__ void footprint_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
                                  const int* cell_count, const int64_t* cell_off, const int32_t* entries,
                                  int64_t* pix_count, const int64_t* pix_off, int32_t* out, int pass) {
-  const CamD C = load_cam(cam);
   const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pixels; q += stride) {
@@ -168,7 +190,7 @@ __global__ void footprint_kernel(MeshView M, GridGeom G, const int* bounds, cons
           for (int64_t k = b; k < e; ++k) {
             const int32_t t = entries[k];
             float txl, txh, tyl, tyh;
-            tri_bbox(M, t, txl, txh, tyl, tyh);
+            tri_bbox(boxes, t, txl, txh, tyl, tyh);
             if (txh < xl || txl > xh || tyh < yl || tyl > yh) continue;
             int tx0, tx1, ty0, ty1;
             cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
@@ -292,48 +314,49 @@ static cudaError_t read_total(const int64_t* off, const void* count, bool count6
 }
 
 // Stage 1: grid cell counts and offsets; returns the number of cell entries.
-cudaError_t fp_grid_count(const MeshView& M, const FpGrid& g, void* scratch, int64_t n_pixels, int64_t* n_entries,
-                          int num_sms, cudaStream_t st) {
+cudaError_t fp_grid_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch, int64_t n_pixels,
+                          int64_t* n_entries, int num_sms, cudaStream_t st) {
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
   cudaError_t e = cudaMemsetAsync(L.cell_count, 0, size_t(n_cells) * 4, st);
   if (e != cudaSuccess) return e;
-  grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, G, L.cell_count, L.cell_off, nullptr, 0);
+  grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, G, L.cell_count, L.cell_off, nullptr, 0);
   if ((e = exclusive_scan<int>(L.cell_count, L.cell_off, n_cells, L, st)) != cudaSuccess) return e;
   return read_total(L.cell_off, L.cell_count, false, n_cells, n_entries, st);
 }
 
 // Stage 2: fills the grid and counts candidates per pixel; returns the total.
-cudaError_t fp_grid_fill_and_count(const MeshView& M, const FpGrid& g, void* scratch, int32_t* entries,
-                                   const double* cam_dev, const int* bounds_dev, int64_t n_pixels, int64_t* total,
-                                   int num_sms, cudaStream_t st) {
+cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch,
+                                   int32_t* entries, const double* cam_host, const int* bounds_dev, int64_t n_pixels,
+                                   int64_t* total, int num_sms, cudaStream_t st) {
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
   cudaError_t e = cudaMemsetAsync(L.cell_count, 0, size_t(n_cells) * 4, st);
   if (e != cudaSuccess) return e;
-  grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, G, L.cell_count, L.cell_off, entries, 1);
-  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(M, G, bounds_dev, cam_dev, n_pixels, L.cell_count, L.cell_off, entries,
-                                                L.pix_count, nullptr, nullptr, 0);
+  grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, G, L.cell_count, L.cell_off, entries, 1);
+  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
+                                                L.cell_off, entries, L.pix_count, nullptr, nullptr, 0);
   if ((e = exclusive_scan<int64_t>(L.pix_count, L.pix_off, n_pixels, L, st)) != cudaSuccess) return e;
   return read_total(L.pix_off, L.pix_count, true, n_pixels, total, st);
 }
 
 // Stage 3: writes the candidates ([total][3] int32, ordered by pixel).
-cudaError_t fp_fill(const MeshView& M, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_dev,
+cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_host,
                     const int* bounds_dev, int64_t n_pixels, int32_t* out, int num_sms, cudaStream_t st) {
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
-  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(M, G, bounds_dev, cam_dev, n_pixels, L.cell_count, L.cell_off, entries,
-                                                nullptr, L.pix_off, out, 1);
+  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
+                                                L.cell_off, entries, nullptr, L.pix_off, out, 1);
   return cudaGetLastError();
 }
 
-cudaError_t compute_mesh_bounds(const MeshView& M, int* bounds_dev, float* bounds_host, int num_sms, cudaStream_t st) {
+cudaError_t compute_mesh_bounds(const MeshView& M, int* bounds_dev, float* bounds_host, float4* boxes, int num_sms,
+                                cudaStream_t st) {
   init_bounds_kernel<<<1, 32, 0, st>>>(bounds_dev);
-  mesh_bounds_kernel<<<num_sms * 4, 256, 0, st>>>(M, bounds_dev);
+  mesh_bounds_kernel<<<num_sms * 4, 256, 0, st>>>(M, bounds_dev, boxes);
   int b[6];
   cudaError_t e = cudaMemcpyAsync(b, bounds_dev, sizeof(b), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

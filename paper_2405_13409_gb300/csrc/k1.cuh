@@ -49,13 +49,16 @@ struct FpGrid {
   int gx, gy;
 };
 size_t footprint_scratch_bytes(int64_t n_cells, int64_t n_pixels);
-cudaError_t compute_mesh_bounds(const MeshView& M, int* bounds_dev, float* bounds_host, int num_sms, cudaStream_t st);
-cudaError_t fp_grid_count(const MeshView& M, const FpGrid& g, void* scratch, int64_t n_pixels, int64_t* n_entries,
-                          int num_sms, cudaStream_t st);
-cudaError_t fp_grid_fill_and_count(const MeshView& M, const FpGrid& g, void* scratch, int32_t* entries,
-                                   const double* cam_dev, const int* bounds_dev, int64_t n_pixels, int64_t* total,
-                                   int num_sms, cudaStream_t st);
-cudaError_t fp_fill(const MeshView& M, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_dev,
+// `boxes` ([n_tris] float4: xl, xh, yl, yh) is written by compute_mesh_bounds
+// and read by the later stages.
+cudaError_t compute_mesh_bounds(const MeshView& M, int* bounds_dev, float* bounds_host, float4* boxes, int num_sms,
+                                cudaStream_t st);
+cudaError_t fp_grid_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch, int64_t n_pixels,
+                          int64_t* n_entries, int num_sms, cudaStream_t st);
+cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch,
+                                   int32_t* entries, const double* cam_host, const int* bounds_dev, int64_t n_pixels,
+                                   int64_t* total, int num_sms, cudaStream_t st);
+cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_host,
                     const int* bounds_dev, int64_t n_pixels, int32_t* out, int num_sms, cudaStream_t st);
 #endif
 

@@ -41,10 +41,13 @@ def labelled_features(ctx, torch, scene, mode, camera=None):
     return feat, labels
 
 
-def train_gate(ctx, torch, train_scenes, val_scenes, mode, camera=None, target_recall=1.0, steps=3000,
+def train_gate(ctx, torch, train_scenes, val_scenes, mode, camera=None, target_recall=1.0, margin=1.0, steps=3000,
                batch=8192, lr=3e-3, lr_final=1e-4, pos_fraction=0.25, seed=0):
     """Trains a gate network on `train_scenes` and calibrates its threshold
-    on `val_scenes`.  Returns (mlp handle, tau_logit, info dict)."""
+    on `val_scenes`: the largest logit that keeps target_recall of the
+    validation positives, lowered by `margin` (logit units) against the
+    spread of the calibration statistic.  Returns (mlp handle, tau_logit,
+    info dict)."""
     t0 = time.perf_counter()
     parts = [labelled_features(ctx, torch, s, mode, camera) for s in train_scenes]
     feat = torch.cat([p[0] for p in parts])
@@ -61,8 +64,13 @@ def train_gate(ctx, torch, train_scenes, val_scenes, mode, camera=None, target_r
     vparts = [labelled_features(ctx, torch, s, mode, camera) for s in val_scenes]
     vf = torch.cat([p[0] for p in vparts])
     vl = torch.cat([p[1] for p in vparts])
-    tau, pass_frac = ctx.spoly_mlp_calibrate(mlp, vf, vl, target_recall)
+    tau_cal, _ = ctx.spoly_mlp_calibrate(mlp, vf, vl, target_recall)
+    tau = tau_cal - margin
+    z = torch.empty(vf.shape[0], dtype=torch.float32, device="cuda")
+    ctx.spoly_mlp_forward(mlp, vf, z)
+    pass_frac = float((z >= tau).float().mean().item())
     info = {"train_rows": n_train, "train_positive": n_pos, "final_loss": loss, "val_rows": int(vl.numel()),
             "val_positive": int(vl.sum().item()), "val_pass_fraction": pass_frac, "tau_logit": tau,
+            "tau_calibrated": tau_cal, "margin": margin, "target_recall": target_recall,
             "label_s": t1 - t0, "train_s": t2 - t1, "steps": steps, "batch": batch}
     return mlp, tau, info

@@ -205,22 +205,24 @@ def _as_ref(p):
 
 
 def test_trained_gate_keeps_paths_and_skips_candidates(ctx):
-    """Glint scenes of 512x512 cells at 256x256 pixels: train on four seeds,
-    calibrate on a fifth, evaluate on a held-out one.  The gated mixed solve
-    returns at least 99.9% of the plain FP64 solve's pixel-filtered paths
-    (matched at 1e-5 in (u, v)) while solving at most a fifth of the
-    candidates; an untrained network calibrated the same way keeps far more."""
+    """The full glint workload (1024x1024 cells, 512x512 pixels): train on
+    two seeds, calibrate on a third, evaluate on a held-out one.  The gated
+    mixed solve returns at least 99.9% of the plain FP64 solve's
+    pixel-filtered paths (matched at 1e-5 in (u, v)) while solving at most
+    2% of the candidates; an untrained network calibrated the same way
+    keeps far more."""
     from paper_2405_13409_gb300 import gate_train
-    mk = lambda seed: scenes.glint_scene(seed=seed, n_cells=512, res=256)
-    train = [mk(1000 + i) for i in range(4)]
-    val = [mk(2000)]
+    train = [scenes.glint_scene(seed=1000 + i) for i in range(2)]
+    val = [scenes.glint_scene(seed=2000)]
     cam = train[0].meta["camera"].as_array()
-    mlp, tau, info = gate_train.train_gate(ctx, torch, train, val, binding.CHAINS_FOOTPRINT, cam, steps=1500)
+    mlp, tau, info = gate_train.train_gate(ctx, torch, train, val, binding.CHAINS_FOOTPRINT, cam)
+    del train, val
     untrained = ctx.spoly_mlp_create(seed=0)
     try:
-        ev = mk(0)
+        ev = scenes.glint_scene(seed=0)
         vf, vl = gate_train.labelled_features(ctx, torch, ev, binding.CHAINS_FOOTPRINT, cam)
-        _, base_frac = ctx.spoly_mlp_calibrate(untrained, vf, vl, 0.9995)
+        _, base_frac = ctx.spoly_mlp_calibrate(untrained, vf, vl, 1.0)
+        del vf, vl
         d = _dev(ev)
         mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
         ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_FOOTPRINT, camera=cam)
@@ -239,8 +241,7 @@ def test_trained_gate_keeps_paths_and_skips_candidates(ctx):
     finally:
         ctx.spoly_mlp_free(untrained)
         ctx.spoly_mlp_free(mlp)
-    assert ref.size > 200, info
-    # pair by (pixel, triangle) and (u, v) within 1e-5
+    assert ref.size > 1000, info
     from .parity import compare
     rep = compare(got, _as_ref(ref))
     recall = rep["matched"] / ref.size
@@ -248,5 +249,5 @@ def test_trained_gate_keeps_paths_and_skips_candidates(ctx):
     print("gate", info, "n_all", n_all, "n_gated", n_gated, "recall", recall, "paths of skipped chains", gate_missed,
           "untrained pass", base_frac, rep)
     assert recall >= 0.999, (recall, rep)
-    assert n_gated <= 0.2 * n_all, (n_gated, n_all)
-    assert n_gated < 0.5 * base_frac * n_all
+    assert n_gated <= 0.02 * n_all, (n_gated, n_all)
+    assert n_gated < 0.05 * base_frac * n_all
