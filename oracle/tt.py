@@ -14,8 +14,9 @@ refractions (IORs eta_0, eta_1, eta_2), in plain numpy FP64:
    ``fit_sqrt_pieces``), then the Moller-Trumbore intersection with T2 as
    u2 = (u~, v~) / kappa.
 2. Bivariate system in (u1, v1) (Sec. 4.5; Table tab_sum): the endpoint
-   coplanarity form at x2 times kappa^2 (total degree 17) and the square form
-   at x2 times kappa^6 (degree 48).
+   coplanarity form and the square form at x2, with x2 - x1 replaced by the
+   mapped direction D and the kappa denominators of x2 and n2 cleared
+   (total degrees 16 and 46; the table's 18 and 48 are upper bounds).
 3. The Bezout matrix in u1 with hidden v1 by the explicit sum of
    Eq. eq_bezout, evaluated at 2^12 + 1 uniform v1 in [0, 1]; its
    determinant's sign from an LU factorisation with partial pivoting
@@ -231,7 +232,7 @@ def constant_normal(N):
 
 
 def build_tt(x0, x3, etas, P1, N1, P2, N2, piece, table):
-    """a (degree 17) and b (degree 48) of the TT system, and the mapping."""
+    """a (degree 16) and b (degree 46) of the TT system, and the mapping."""
     x0 = np.asarray(x0, float)
     x3 = np.asarray(x3, float)
     P1, N1, P2, N2 = (np.asarray(z, float) for z in (P1, N1, P2, N2))
@@ -249,19 +250,22 @@ def build_tt(x0, x3, etas, P1, N1, P2, N2, piece, table):
     if constant_normal(N2):
         # Reading: with one normal over T2, kappa n2 = kappa N would make kappa
         # a common factor of a and b and the resultant vanish identically;
-        # the constant normal is used as is (one kappa fewer in a, two in b).
+        # the constant normal is used as is.
         M2 = vconst(N2[0])
     else:
         M2 = vadd(vadd(vscale(vconst(N2[0]), kap), vscale(vconst(N2[1] - N2[0]), ut)),
                   vscale(vconst(N2[2] - N2[0]), vt))
-    K1 = vsub(X2, vscale(x1, kap))                 # kappa d1
+    # x2 - x1 = (t~ / kappa) D: the segment to x2 is parallel to D.  Writing
+    # d1 through kappa (kappa d1 = X2 - kappa x1 = t~ D) would make t~ a
+    # common factor of a and b and the resultant vanish identically, so the
+    # constraints at x2 are written with D in place of d1 (reading).
     K2 = vsub(vscale(vconst(x3), kap), X2)         # kappa d2
-    a = vdot(vcross(K1, vsub(vconst(x3), x1)), M2)  # kappa^2 x coplanarity (endpoint difference form)
+    a = vdot(vcross(D, vsub(vconst(x3), x1)), M2)  # coplanarity (endpoint difference form), degree 16
     bv = proj_vector(x0, x3, P1, N1, P2, N2)
-    p1 = vdot(vcross(K1, M2), vconst(bv))
+    p1 = vdot(vcross(D, M2), vconst(bv))
     p2 = vdot(vcross(K2, M2), vconst(bv))
     b = bp_add(etas[1] ** 2 * bp_mul(vdot(K2, K2), bp_mul(p1, p1)),
-               -(etas[2] ** 2) * bp_mul(vdot(K1, K1), bp_mul(p2, p2)))  # kappa^6 x square form
+               -(etas[2] ** 2) * bp_mul(vdot(D, D), bp_mul(p2, p2)))  # square form, degree 46
     return {"a": a, "b": b, "ut": ut, "vt": vt, "kap": kap, "tt": tt, "beta": beta, "s": s}
 
 
@@ -390,32 +394,31 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
             continue
         sg, la = det_sign(sysd, vs, n, da, db)
         lmax = np.max(la[np.isfinite(la)]) if np.any(np.isfinite(la)) else 0.0
-        roots = []
-        for m in range(n_intervals):
-            if sg[m] == 0.0:
-                if m > 0:
-                    roots.append((vs[m], 0))
-                continue
-            if sg[m] * sg[m + 1] < 0:
-                lo, hi, slo = vs[m], vs[m + 1], sg[m]
-                flag = 0
-                it = 0
-                while hi - lo > ROOT_TOL:
-                    mid = 0.5 * (lo + hi)
-                    sm, _ = det_sign(sysd, mid, n, da, db)
-                    if sm[0] == 0.0:
-                        lo = hi = mid
-                        break
-                    if sm[0] == slo:
-                        lo = mid
-                    else:
-                        hi = mid
-                    it += 1
-                    if it == PAPER_ITERS:
-                        _, l2 = det_sign(sysd, np.array([lo, hi]), n, da, db)
-                        if np.log(np.exp(l2[0] - lmax) + np.exp(l2[1] - lmax)) < np.log(ILL_COND_K2):
-                            flag |= F_ILL_COND
-                roots.append((0.5 * (lo + hi), flag))
+        # sign changes; a sample with det == 0 exactly is a root belonging to
+        # the interval on its left (reading 7)
+        roots = [(vs[m], 0) for m in range(1, n_intervals + 1) if sg[m] == 0.0]
+        br = [m for m in range(n_intervals) if sg[m] * sg[m + 1] < 0]
+        lo = vs[br].copy()
+        hi = vs[np.array(br, int) + 1].copy()
+        slo = sg[br].copy()
+        flag = np.zeros(len(br), int)
+        it = 0
+        # all brackets bisected together: the paper's 10 iterations, then on
+        # to ROOT_TOL
+        while len(br) and np.max(hi - lo) > ROOT_TOL:
+            mid = 0.5 * (lo + hi)
+            sm, _ = det_sign(sysd, mid, n, da, db)
+            zero = sm == 0.0  # an exact root: collapse the bracket onto it
+            left = (sm == slo) | zero
+            lo = np.where(left, mid, lo)
+            hi = np.where(left & ~zero, hi, mid)
+            it += 1
+            if it == PAPER_ITERS:
+                _, l_lo = det_sign(sysd, lo, n, da, db)
+                _, l_hi = det_sign(sysd, hi, n, da, db)
+                rel = np.logaddexp(l_lo - lmax, l_hi - lmax)
+                flag = np.where(rel < np.log(ILL_COND_K2), F_ILL_COND, 0)
+        roots += [(0.5 * (a + b), int(f)) for a, b, f in zip(lo, hi, flag)]
         for v1, vflag in roots:
             ac = u_coeffs(sysd["a"][:da + 1], v1)[0]
             bc = u_coeffs(sysd["b"][:db + 1], v1)[0]
