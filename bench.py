@@ -362,7 +362,7 @@ def timed_steps(pipe, mesh, q, steps, flush, stream, torch):
         b.record(stream)
         b.synchronize()
         c_ms, g_ms = pipe.phase_ms()
-        i_ms, p_ms = pipe.ctx.spoly_phase_ms(pipe.sol)
+        i_ms, p_ms, _tt_ms = pipe.ctx.spoly_phase_ms(pipe.sol)
         out.append({"step": a.elapsed_time(b), "chains": c_ms, "gate": g_ms, "isolation": i_ms, "polish": p_ms,
                     "paths": pipe.ctx.spoly_stats(pipe.sol)["admissible"]})
     return out

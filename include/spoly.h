@@ -84,7 +84,8 @@ typedef struct {
  *   eta[q][3]     = eta_0 .. eta_k, IOR of the outgoing side of each vertex
  *                   (Sec. 3.1); reflection ignores it
  *   types[q][2]   = SPOLY_R / SPOLY_T per bounce
- *   k[q]          = bounce count (1 is built; 2 returns SPOLY_EUNSUPPORTED) */
+ *   k[q]          = bounce count: 1, or 2 for chains with two triangles
+ *                   (both refractions, types T T; eta_0 .. eta_2 used) */
 typedef struct {
   const double* x_first;
   const double* x_last;
@@ -138,6 +139,14 @@ typedef struct {
    * projects into pixel q, so each path of a footprint workload is counted
    * once.  NULL: no filter. */
   const double* camera;
+  /* 2-bounce chains: the rational pieces replacing sqrt(beta) in the
+   * refraction mapping (Sec. 4.4), host array of 25 doubles: breaks[7]
+   * (0 = b0 < ... < b6 = 1), then (c0, c1, d1) of (c0 + c1 x) / (1 + d1 x)
+   * for each of the six pieces.  NULL: the library's default fit (maximum
+   * error 9.4e-4 on [0, 1]). */
+  const double* sqrt_table;
+  int32_t n_intervals; /* 2-bounce: uniform v1 intervals on [0, 1] (0: 4096; at most 8192) */
+  int32_t reserved3;
 } spoly_solve_opts;
 
 /* One admissible path (104 bytes).  For k = 1, tri[1] = -1 and the second
@@ -164,8 +173,12 @@ typedef struct {
   int64_t admissible;   /* paths returned */
   int64_t flagged;      /* returned paths with SPOLY_FLAG_ILL_COND */
   int64_t fallback;     /* chains re-isolated in FP64: FP32 signs not certified,
-                           or a Bezout size without an unrolled kernel */
-  int64_t reserved[6];
+                           a Bezout size without an unrolled kernel, a
+                           flat-shaded triangle, or (2-bounce) FP32 signs that
+                           change sign too often */
+  int64_t unsolved;     /* 2-bounce systems whose Bezout size exceeds 31 (not solved) */
+  int64_t k2_systems;   /* 2-bounce (chain, sqrt piece) systems */
+  int64_t reserved[4];
 } spoly_counters;
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`
@@ -188,8 +201,9 @@ const char* spoly_last_error(const spoly_ctx* ctx);
  * overlaps the box of unit directions from the triangle toward x_{k+1};
  * EXPLICIT copies the caller's list after a bounds check.  *inout: NULL to
  * allocate a new handle, or a handle to reuse.  The call synchronises once
- * to read the chain count.  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED
- * (CONE with k != 1). */
+ * to read the chain count.  EXPLICIT lists may hold 2-bounce chains
+ * (tri1 >= 0).  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (CONE with
+ * k != 1). */
 spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
                                 const spoly_chain_opts* opts, spoly_chains** inout);
 
@@ -209,7 +223,15 @@ spoly_status spoly_chains_free(spoly_chains* chains);
  * built from.  *inout: NULL for a new set or a set to reuse.  Unless
  * SPOLY_SOLVE_ASYNC is set, the call synchronises, grows the path buffer and
  * re-runs the path phase if it overflowed, and returns with counters valid.
- * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (k = 2 chains). */
+ * Chains with a second triangle (tri1 >= 0, explicit lists) are solved as
+ * 2-bounce refraction chains x0 -> tri0 -> tri1 -> x_last (Sec. 4.4-4.5,
+ * Sec. 5.2 bisection: the Bezout determinant's sign at n_intervals + 1
+ * uniform v1, 10 FP32 bisection steps per sign change, FP64 bisection to
+ * 1e-10, u1 from a(u1, v1) = 0, u2 from the rational mapping, then
+ * path-space Newton on h x n = 0 at both vertices); their paths carry
+ * SPOLY_FLAG_NEWTON.  A list with such chains is always solved
+ * synchronously, in batches.  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED
+ * (a 2-bounce chain whose query is not of types T T). */
 spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
                          const spoly_chains* chains, const spoly_solve_opts* opts,
                          spoly_solution_set** inout);

@@ -71,7 +71,8 @@ class spoly_chain_opts(ctypes.Structure):
 
 
 class spoly_solve_opts(ctypes.Structure):
-    _fields_ = [("precision", c_int32), ("flags", c_int32), ("path_capacity", c_int64), ("camera", c_void_p)]
+    _fields_ = [("precision", c_int32), ("flags", c_int32), ("path_capacity", c_int64), ("camera", c_void_p),
+                ("sqrt_table", c_void_p), ("n_intervals", c_int32), ("reserved3", c_int32)]
 
 
 class spoly_path(ctypes.Structure):
@@ -82,8 +83,9 @@ class spoly_path(ctypes.Structure):
 
 class spoly_counters(ctypes.Structure):
     _fields_ = [(n, c_int64) for n in ("candidates", "degenerate", "v_roots", "queued", "prefiltered",
-                                       "polish_lost", "u_roots", "admissible", "flagged", "fallback")] + \
-               [("reserved", c_int64 * 6)]
+                                       "polish_lost", "u_roots", "admissible", "flagged", "fallback",
+                                       "unsolved", "k2_systems")] + \
+               [("reserved", c_int64 * 4)]
 
 
 class spoly_mlp_train_opts(ctypes.Structure):
@@ -242,9 +244,19 @@ class Context:
         self.lib.spoly_chains_free(chains)
 
     def spoly_solve(self, mesh: spoly_mesh, q: spoly_queries, chains, precision: int = MIXED, flags: int = 0,
-                    path_capacity: int = 0, reuse=None, camera=None):
+                    path_capacity: int = 0, reuse=None, camera=None, sqrt_table=None, n_intervals: int = 0):
+        """sqrt_table: optional (breaks[7], coeffs[6][3]) of the 2-bounce
+        refraction mapping; None uses the library's default."""
         cam = None if camera is None else np.ascontiguousarray(camera, dtype=np.float64)
-        opts = spoly_solve_opts(int(precision), int(flags), int(path_capacity), cam.ctypes.data if cam is not None else None)
+        tab = None
+        if sqrt_table is not None:
+            breaks, coeffs = sqrt_table
+            tab = np.ascontiguousarray(np.concatenate([np.asarray(breaks, np.float64).ravel(),
+                                                       np.asarray(coeffs, np.float64).ravel()]))
+            assert tab.size == 25
+        opts = spoly_solve_opts(int(precision), int(flags), int(path_capacity),
+                                cam.ctypes.data if cam is not None else None,
+                                tab.ctypes.data if tab is not None else None, int(n_intervals), 0)
         h = c_void_p(reuse.value if reuse is not None else None)
         self.check(self.lib.spoly_solve(self.h, ctypes.byref(mesh), ctypes.byref(q), chains, ctypes.byref(opts),
                                         ctypes.byref(h)), "spoly_solve")
@@ -280,9 +292,10 @@ class Context:
         self.lib.spoly_solution_free(sol)
 
     def spoly_phase_ms(self, sol) -> tuple:
-        ms = (ctypes.c_float * 2)()
-        self.check(self.lib.spoly_phase_ms(self.h, sol, ms, 2), "spoly_phase_ms")
-        return float(ms[0]), float(ms[1])
+        """(1-bounce isolation, 1-bounce polish + paths, 2-bounce pipeline) in ms."""
+        ms = (ctypes.c_float * 3)()
+        self.check(self.lib.spoly_phase_ms(self.h, sol, ms, 3), "spoly_phase_ms")
+        return float(ms[0]), float(ms[1]), float(ms[2])
 
     def spoly_measure_peak(self, kind: int) -> float:
         t = ctypes.c_double()

@@ -5,9 +5,12 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ctx.cuh"
 #include "k1.cuh"
+#include "sqrt_table.cuh"
+#include "tt_kernels.cuh"
 
 using namespace spoly;
 
@@ -95,6 +98,114 @@ spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_qu
 
 }  // namespace spoly
 
+namespace spoly {
+
+// 2-bounce chains of a solve: systems, then per batch of systems the FP64
+// construction, the FP32 sign sampling and bisection, the FP64 polish and
+// the path phase.  Paths are appended through `path_counter`.
+spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& mv, const QueryView& qv,
+                      const int32_t* k2, const int32_t* k2_ids, int64_t n2, const spoly_solve_opts* opts,
+                      unsigned long long* path_counter, spoly_path* paths, int64_t path_cap) {
+  cudaStream_t st = ctx->stream;
+  TTParams T{};
+  T.mesh = mv;
+  T.qv = qv;
+  T.chains = k2;
+  T.chain_ids = k2_ids;
+  T.n_chains = n2;
+  if (opts->sqrt_table) {
+    const double* t = opts->sqrt_table;
+    for (int i = 0; i <= kSqrtPieces; ++i) T.sqrt_tab.breaks[i] = t[i];
+    for (int k = 0; k < kSqrtPieces; ++k)
+      for (int j = 0; j < 3; ++j) T.sqrt_tab.c[k][j] = t[kSqrtPieces + 1 + 3 * k + j];
+    if (T.sqrt_tab.breaks[0] != 0.0 || T.sqrt_tab.breaks[kSqrtPieces] != 1.0)
+      return fail(ctx, SPOLY_EINVAL, "sqrt_table: breaks must run from 0 to 1");
+    for (int i = 0; i < kSqrtPieces; ++i)
+      if (!(T.sqrt_tab.breaks[i + 1] > T.sqrt_tab.breaks[i]))
+        return fail(ctx, SPOLY_EINVAL, "sqrt_table: breaks must increase");
+  } else {
+    T.sqrt_tab = default_sqrt_table();
+  }
+  T.n_intervals = opts->n_intervals > 0 ? opts->n_intervals : 4096;
+  T.precision = opts->precision;
+  if (T.n_intervals > 8192) return fail(ctx, SPOLY_EINVAL, "n_intervals %d exceeds 8192", T.n_intervals);
+  T.paths = paths;
+  T.path_cap = path_cap;
+  T.path_counter = path_counter;
+  CK(set->tt_counters.ensure(16 * sizeof(unsigned long long)), "tt counters");
+  T.counters = static_cast<unsigned long long*>(set->tt_counters.p);
+  CK(cudaMemsetAsync(T.counters, 0, 16 * sizeof(unsigned long long), st), "tt counters");
+  CK(set->tt_chain_sys.ensure(size_t(n2) * 2 * sizeof(int32_t)), "tt chain systems");
+  CK(set->tt_masks.ensure(size_t(n2)), "tt masks");
+  T.chain_sys = static_cast<int32_t*>(set->tt_chain_sys.p);
+  CK(launch_tt_count(T, static_cast<uint8_t*>(set->tt_masks.p), ctx->num_sms, st), "tt count");
+  // exclusive prefix of the per-chain system counts (host)
+  std::vector<int32_t> cs(size_t(n2) * 2);
+  CK(cudaMemcpyAsync(cs.data(), T.chain_sys, cs.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "tt counts");
+  CK(cudaStreamSynchronize(st), "tt counts");
+  int64_t n_sys = 0;
+  for (int64_t c = 0; c < n2; ++c) {
+    cs[size_t(2 * c)] = int32_t(n_sys);
+    n_sys += cs[size_t(2 * c + 1)];
+  }
+  if (n_sys > INT32_MAX) return fail(ctx, SPOLY_EINVAL, "too many 2-bounce systems");
+  CK(cudaMemcpyAsync(T.chain_sys, cs.data(), cs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st), "tt offsets");
+  CK(set->tt_sys.ensure(size_t(std::max<int64_t>(n_sys, 1)) * sizeof(TTSys)), "tt systems");
+  T.sys = static_cast<TTSys*>(set->tt_sys.p);
+  T.sys_cap = n_sys;
+  CK(launch_tt_fill(T, static_cast<const uint8_t*>(set->tt_masks.p), ctx->num_sms, st), "tt fill");
+  // batches of whole chains, at most kBatch systems
+  constexpr int64_t kBatch = 16384;
+  const int64_t bmax = std::min<int64_t>(kBatch, std::max<int64_t>(n_sys, 1));
+  CK(set->tt_scratch.ensure(size_t(bmax) * kTTScratch * sizeof(double)), "tt scratch");
+  CK(set->tt_coef32.ensure(size_t(bmax) * kTT32 * sizeof(float)), "tt scratch");
+  CK(set->tt_queue.ensure(size_t(bmax) * 128 * sizeof(RootItem)), "tt queue");  // 128 brackets per system at most
+  T.scratch = static_cast<double*>(set->tt_scratch.p);
+  T.coef32 = static_cast<float*>(set->tt_coef32.p);
+  T.queue = static_cast<RootItem*>(set->tt_queue.p);
+  T.queue_cap = bmax * 128;
+  unsigned long long brackets_total = 0, resampled_total = 0;
+  int64_t c0 = 0;
+  while (c0 < n2) {
+    const int64_t s0 = cs[size_t(2 * c0)];
+    int64_t c1 = c0;
+    while (c1 < n2 && cs[size_t(2 * c1)] + cs[size_t(2 * c1 + 1)] - s0 <= bmax) ++c1;
+    if (c1 == c0) c1 = c0 + 1;  // one chain spans at most six systems < bmax
+    const int64_t s1 = c1 < n2 ? cs[size_t(2 * c1)] : n_sys;
+    T.sys_offset = s0;
+    T.n_sys = s1 - s0;
+    CK(cudaMemsetAsync(T.counters + TT_BRACKETS, 0, sizeof(unsigned long long), st), "tt memset");
+    CK(launch_tt_build(T, ctx->num_sms, st), "tt build");
+    CK(cudaMemsetAsync(T.counters + TT_RESAMPLED, 0, sizeof(unsigned long long), st), "tt memset");
+    CK(launch_tt_sign(T, ctx->num_sms, st), "tt sign");
+    unsigned long long nres = 0;
+    CK(cudaMemcpyAsync(&nres, T.counters + TT_RESAMPLED, sizeof(nres), cudaMemcpyDeviceToHost, st), "tt resample");
+    CK(cudaStreamSynchronize(st), "tt resample");
+    resampled_total += nres;
+    if (nres > 0) {
+      T.resample_only = 1;
+      CK(launch_tt_sign(T, ctx->num_sms, st), "tt sign (FP64 resample)");
+      T.resample_only = 0;
+    }
+    unsigned long long nb = 0;
+    CK(cudaMemcpyAsync(&nb, T.counters + TT_BRACKETS, sizeof(nb), cudaMemcpyDeviceToHost, st), "tt brackets");
+    CK(cudaStreamSynchronize(st), "tt brackets");
+    brackets_total += nb;
+    CK(launch_tt_polish(T, 0, std::min<int64_t>(int64_t(nb), T.queue_cap), ctx->num_sms, st), "tt polish");
+    CK(launch_tt_paths(T, c0, c1, ctx->num_sms, st), "tt paths");
+    c0 = c1;
+  }
+  CK(cudaMemcpyAsync(set->tt_host, T.counters, sizeof(set->tt_host), cudaMemcpyDeviceToHost, st), "tt counters");
+  CK(cudaStreamSynchronize(st), "tt counters");
+  set->tt_host[TT_BRACKETS] = brackets_total;
+  set->tt_host[TT_RESAMPLED] = resampled_total;
+  set->tt_host[TT_SYSTEMS] = (unsigned long long)n_sys;
+  set->n_k2 = n2;
+  return SPOLY_OK;
+}
+
+}  // namespace spoly
+
 extern "C" {
 
 const char* spoly_version(void) { return "spoly-gb300 0.1 (sm_103a)"; }
@@ -160,6 +271,7 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     return s;
   };
   if (ch->counter.ensure(16) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain counter"));
+  ch->n_k2 = 0;
   ChainParams P{};
   P.mesh = mv;
   P.qv = qv;
@@ -195,12 +307,15 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     e = launch_chains_explicit(P, src, n, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit"));
     int32_t herr = 0;
+    unsigned long long hk2 = 0;
     e = cudaMemcpyAsync(&herr, P.error, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hk2, P.count, 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     tmp.release();
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit sync"));
     if (herr) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain %d references a missing query or triangle", herr - 1));
     ch->n = n;
+    ch->n_k2 = int64_t(hk2);
   } else if (opts->mode == SPOLY_CHAINS_CONE) {
     if (ctx->boxes.ensure(size_t(P.tri_count) * 12 * sizeof(float)) != cudaSuccess ||
         ctx->flag.ensure(16) != cudaSuccess)
@@ -324,8 +439,12 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   spoly_status st = stage_inputs(ctx, mesh, q, &mv, &qv);
   if (st != SPOLY_OK) return st;
   if (!q->on_device) {
-    for (int64_t i = 0; i < q->n_queries; ++i)
-      if (q->k[i] != 1) return fail(ctx, SPOLY_EUNSUPPORTED, "query %lld has k = %d; only k = 1 is built", (long long)i, q->k[i]);
+    for (int64_t i = 0; i < q->n_queries; ++i) {
+      if (q->k[i] != 1 && q->k[i] != 2)
+        return fail(ctx, SPOLY_EUNSUPPORTED, "query %lld has k = %d; k = 1 and 2 are built", (long long)i, q->k[i]);
+      if (q->k[i] == 2 && (q->types[2 * i] != SPOLY_T || q->types[2 * i + 1] != SPOLY_T))
+        return fail(ctx, SPOLY_EUNSUPPORTED, "query %lld: 2-bounce chains are built for types T T", (long long)i);
+    }
   }
   spoly_solution_set* set = *inout;
   bool fresh = false;
@@ -360,6 +479,31 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   set->path_cap = pcap;
   set->side_cap = scap;
   set->host_valid = false;
+  set->n_k2 = 0;
+  // split off the 2-bounce chains
+  const int64_t n2 = chains->n_k2, n1 = nc - n2;
+  const int32_t* k1_list = static_cast<const int32_t*>(chains->buf.p);
+  const int32_t *k1_ids = nullptr, *k2_list = nullptr, *k2_ids = nullptr;
+  if (n2 > 0) {
+    if (set->part.ensure(size_t(nc) * 16) != cudaSuccess || set->part_n.ensure(16) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "chain partition"));
+    int32_t* base = static_cast<int32_t*>(set->part.p);
+    int32_t* a1 = base;
+    int32_t* i1 = base + 3 * n1;
+    int32_t* a2 = i1 + n1;
+    int32_t* i2 = a2 + 3 * n2;
+    {
+      cudaError_t e0 = cudaMemsetAsync(set->part_n.p, 0, 16, ctx->stream);
+      if (e0 == cudaSuccess)
+        e0 = launch_partition(k1_list, nc, a1, i1, a2, i2, static_cast<unsigned long long*>(set->part_n.p),
+                              ctx->num_sms, ctx->stream);
+      if (e0 != cudaSuccess) return bail(cuda_fail(ctx, e0, "chain partition"));
+    }
+    k1_list = a1;
+    k1_ids = i1;
+    k2_list = a2;
+    k2_ids = i2;
+  }
   K1Params P{};
   P.mesh = mv;
   P.qv = qv;
@@ -379,8 +523,9 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     if (P.pix.w < 1 || P.pix.h < 1 || int64_t(P.pix.w) * P.pix.h != qv.n)
       return bail(fail(ctx, SPOLY_EINVAL, "pixel filter: width x height must equal n_queries"));
   }
-  P.chains = static_cast<const int32_t*>(chains->buf.p);
-  P.n_chains = nc;
+  P.chains = k1_list;
+  P.chain_ids = k1_ids;
+  P.n_chains = n1;
   P.counters = static_cast<unsigned long long*>(set->counters.p);
   cudaError_t e;
   const bool async = (opts->flags & SPOLY_SOLVE_ASYNC) != 0;
@@ -411,12 +556,12 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     e = cudaMemsetAsync(set->counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
     if (timing) cudaEventRecord(set->ev[0], ctx->stream);
-    if (nc > 0) {
+    if (n1 > 0) {
       e = launch_k1_isolate(P, opts->precision, ctx->num_sms, ctx->stream);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_isolate"));
     }
     if (timing) cudaEventRecord(set->ev[1], ctx->stream);
-    if (async) break;
+    if (async && n2 == 0) break;
     e = read_counters();
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "isolation"));
     const int64_t queued = int64_t(set->host[C_QUEUED]);
@@ -437,14 +582,23 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   // Stage 2: FP64 v-polish (in place, once) and the path phase.  Only the
   // path phase is re-run if the path buffer overflowed: it reads the polished
   // queue and is idempotent once its counters are reset.
-  if (nc > 0) {
+  if (n1 > 0) {
     e = launch_k1_polish(P, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
     e = launch_k1_paths(P, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_paths"));
   }
   if (timing) cudaEventRecord(set->ev[2], ctx->stream);
-  if (!async) {
+  auto run_tt = [&]() -> spoly_status {
+    if (n2 == 0) return SPOLY_OK;
+    return solve_tt(ctx, set, mv, qv, k2_list, k2_ids, n2, opts,
+                    static_cast<unsigned long long*>(set->counters.p) + C_ADMISSIBLE,
+                    static_cast<spoly_path*>(set->paths.p), set->path_cap);
+  };
+  st = run_tt();
+  if (st != SPOLY_OK) return bail(st);
+  if (timing) cudaEventRecord(set->ev[3], ctx->stream);
+  if (!async || n2 > 0) {
     e = read_counters();
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
     const int64_t paths = int64_t(set->host[C_ADMISSIBLE]);
@@ -458,8 +612,12 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
                             ctx->stream);
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
       }
-      e = launch_k1_paths(P, ctx->num_sms, ctx->stream);
-      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_paths"));
+      if (n1 > 0) {
+        e = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_paths"));
+      }
+      st = run_tt();
+      if (st != SPOLY_OK) return bail(st);
       e = read_counters();
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
       if (int64_t(set->host[C_ADMISSIBLE]) > set->path_cap)
@@ -488,6 +646,19 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
   out->admissible = int64_t(h[C_ADMISSIBLE]);
   out->flagged = int64_t(h[C_FLAGGED]);
   out->fallback = int64_t(h[C_SIDE]);
+  if (set->n_k2 > 0) {  // 2-bounce chains of the same solve (their paths are already in admissible)
+    const unsigned long long* t = set->tt_host;
+    out->candidates += set->n_k2;
+    out->degenerate += int64_t(t[TT_DEGENERATE]);
+    out->v_roots += int64_t(t[TT_BRACKETS]);
+    out->queued += int64_t(t[TT_BRACKETS]);
+    out->polish_lost += int64_t(t[TT_POLISH_LOST]);
+    out->u_roots += int64_t(t[TT_UROOTS]);
+    out->flagged += int64_t(t[TT_FLAGGED]);
+    out->unsolved = int64_t(t[TT_TOO_LARGE]);
+    out->fallback += int64_t(t[TT_RESAMPLED]);
+    out->k2_systems = int64_t(t[TT_SYSTEMS]);
+  }
   return SPOLY_OK;
 }
 
@@ -523,6 +694,10 @@ spoly_status spoly_phase_ms(spoly_ctx* ctx, const spoly_solution_set* set, float
   CK(cudaEventSynchronize(set->ev[2]), "phase timing");
   CK(cudaEventElapsedTime(&ms[0], set->ev[0], set->ev[1]), "phase timing");
   CK(cudaEventElapsedTime(&ms[1], set->ev[1], set->ev[2]), "phase timing");
+  if (n >= 3) {
+    ms[2] = 0.0f;
+    if (set->n_k2 > 0) CK(cudaEventElapsedTime(&ms[2], set->ev[2], set->ev[3]), "phase timing");
+  }
   return SPOLY_OK;
 }
 
@@ -545,6 +720,9 @@ spoly_status spoly_solution_free(spoly_solution_set* set) {
   set->queue.release();
   set->paths.release();
   set->counters.release();
+  for (DevBuf* b : {&set->part, &set->part_n, &set->tt_counters, &set->tt_chain_sys, &set->tt_masks, &set->tt_sys,
+                    &set->tt_scratch, &set->tt_coef32, &set->tt_queue})
+    b->release();
   delete set;
   return SPOLY_OK;
 }

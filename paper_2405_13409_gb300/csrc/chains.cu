@@ -310,6 +310,7 @@ __global__ void chains_explicit_kernel(ChainParams P, const int32_t* src, int64_
     P.out[3 * c] = ok ? q : 0;
     P.out[3 * c + 1] = ok ? t0 : 0;
     P.out[3 * c + 2] = ok ? t1 : -1;
+    if (ok && t1 >= 0) atomicAdd(P.count, 1ull);  // 2-bounce chains
   }
 }
 

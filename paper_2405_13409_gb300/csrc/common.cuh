@@ -138,6 +138,7 @@ constexpr double kPolishTol = 1e-12; // FP64 polish bracket width in v
 constexpr float kIsoTol32 = 1e-6f;   // FP32 isolation bracket width in v
 constexpr double kIsoTol64 = 1e-12;  // FP64 isolation bracket width in v (plain mode)
 constexpr double kPrefilterMargin = 0.1;  // u-range margin of the pre-polish filter
+constexpr double kPrefilterDv = 1e-3;     // side samples (in v) of the pre-polish filter
 constexpr double kSideReach = 0.25;       // side search reach (in v) of a displaced FP32 root
 constexpr float kTangent32 = 1e-4f;  // tangent-root test, FP32 isolation
 constexpr double kTangent64 = 1e-12; // tangent-root test, FP64 isolation

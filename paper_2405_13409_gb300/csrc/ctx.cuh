@@ -45,6 +45,7 @@ struct spoly_ctx {
 struct spoly_chains {
   spoly::DevBuf buf;        // [cap][3] int32
   int64_t n = 0;
+  int64_t n_k2 = 0;         // chains with a second triangle (tri1 >= 0)
   spoly::DevBuf counter;    // unsigned long long + int32 error flag
 };
 
@@ -60,6 +61,10 @@ struct spoly_solution_set {
   bool host_valid = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing
   bool timed = false;
+  // 2-bounce chains: partitioned lists, systems, per-batch scratch
+  spoly::DevBuf part, part_n, tt_counters, tt_chain_sys, tt_masks, tt_sys, tt_scratch, tt_coef32, tt_queue;
+  unsigned long long tt_host[16] = {0};
+  int64_t n_k2 = 0;
 };
 
 namespace spoly {

@@ -8,6 +8,7 @@ struct K1Params {
   MeshView mesh;
   QueryView qv;
   const int32_t* chains;  // [n_chains][3] (query, tri0, tri1)
+  const int32_t* chain_ids;  // chain index reported in the paths (NULL: position in `chains`)
   int64_t n_chains;
   RootItem* queue;        // bracket queue between isolation and polish
   int64_t queue_cap;
@@ -20,6 +21,10 @@ struct K1Params {
 };
 
 #ifndef SPOLY_HOST_BUILD
+// Splits a chain list into its 1-bounce (tri1 < 0) and 2-bounce chains, each
+// with the original chain indices; counts[0], counts[1] receive the sizes.
+cudaError_t launch_partition(const int32_t* chains, int64_t n, int32_t* k1, int32_t* k1_ids, int32_t* k2,
+                             int32_t* k2_ids, unsigned long long* counts, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st);

@@ -59,22 +59,28 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
   const int nb = isolate<T, RD>(r, deg, lo, hi, tol, tang, rscale, blo, bhi, bfl);
   n_vroots += nb;
   // Pre-polish filter: keep a bracket only if a(u, v) = 0 has a real u within
-  // kPrefilterMargin of [0, 1 - v] (or a(., v) is degenerate).  The margin is
-  // far wider than the error of the bracket, so no admissible root is lost.
+  // kPrefilterMargin of [0, 1 - v] (or a(., v) is degenerate), at the bracket
+  // or kPrefilterDv away from it on either side in v: where the curve a = 0
+  // runs nearly parallel to the u axis, u(v) amplifies the error of the FP32
+  // root, and the side samples catch it.
   int nq = 0;
   for (int k = 0; k < nb; ++k) {
     const T zm = T(0.5) * (blo[k] + bhi[k]);
-    const T v = zm * T(s.sc.t);
-    T am[3];
-    a_at<T>(s.a, s.na, zm, am);
-    T w[2];
-    uint32_t wf[2];
     const T m = T(kPrefilterMargin);
-    const int nw = quad_roots<T>(am[0], am[1], am[2], T(1e-3), w, wf);
-    bool keep = (s.na == 0) || (nw == 0 && fabs(am[0]) + fabs(am[1]) + fabs(am[2]) == T(0));
-    for (int i = 0; i < nw; ++i) {
-      const T u = w[i] * T(s.sc.s);
-      if (u >= -m && u <= T(1) - v + m) keep = true;
+    bool keep = (s.na == 0);
+    for (int side = 0; side < 3 && !keep; ++side) {
+      const T z = zm + T(side == 0 ? 0.0 : (side == 1 ? -kPrefilterDv : kPrefilterDv) / s.sc.t);
+      const T v = z * T(s.sc.t);
+      T am[3];
+      a_at<T>(s.a, s.na, z, am);
+      T w[2];
+      uint32_t wf[2];
+      const int nw = quad_roots<T>(am[0], am[1], am[2], T(1e-3), w, wf);
+      if (nw == 0 && fabs(am[0]) + fabs(am[1]) + fabs(am[2]) == T(0)) keep = true;
+      for (int i = 0; i < nw; ++i) {
+        const T u = w[i] * T(s.sc.s);
+        if (u >= -m && u <= T(1) - v + m) keep = true;
+      }
     }
     if (!keep) {
       ++n_pref;
@@ -134,6 +140,19 @@ SPOLY_D int k1_isolate_dispatch(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], 
   return -2;
 }
 
+// Flat-shaded triangles (bit-identical vertex normals) degenerate the system:
+// a loses u-degree, det = lc(b)^(n-m) Res gains a high-multiplicity spurious
+// root, and FP32 isolation can lose true roots beside it.  They take the FP64
+// isolation in mixed mode (integer compares: no FP64 pipe work).
+SPOLY_D bool flat_shaded(const TriD& tr) {
+  auto eq = [](d3 a, d3 b) {
+    return __double_as_longlong(a.x) == __double_as_longlong(b.x) &&
+           __double_as_longlong(a.y) == __double_as_longlong(b.y) &&
+           __double_as_longlong(a.z) == __double_as_longlong(b.z);
+  };
+  return eq(tr.n0, tr.n1) && eq(tr.n0, tr.n2);
+}
+
 #ifndef SPOLY_HOST_BUILD
 template <typename T>
 __global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
@@ -158,6 +177,10 @@ __global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
         } else {
           K1Sys<6> s;
           r = k1_system<6>(tr, qd, s) ? k1_isolate_dispatch<T, 6>(s, items, int(c), n_v, n_pref) : -1;
+        }
+        if (sizeof(T) == 4 && r != -1 && flat_shaded(tr)) {
+          r = -2;  // the FP32 brackets are discarded; the side kernel re-isolates in FP64
+          n_v = n_pref = 0;
         }
         if (r == -1) n_deg = 1;
         if (r == -2) n_side = 1;

@@ -1,5 +1,7 @@
 // FP64 polish kernel of the 1-bounce solve (path phase, Sec. 5.3), plus the
 // host launchers of the 1-bounce kernels.
+#include <algorithm>
+
 #include "k1_polish.cuh"
 
 namespace spoly {
@@ -61,9 +63,35 @@ __global__ void __launch_bounds__(128) k1_path_kernel(K1Params P) {
     const unsigned long long slot = warp_append(P.counters + C_ADMISSIBLE, unsigned(np));
     for (int k = 0; k < np; ++k) {
       const unsigned long long idx = slot + k;
+      if (P.chain_ids) out[k].chain = __ldg(P.chain_ids + out[k].chain);
       if (idx < (unsigned long long)P.path_cap) P.paths[idx] = out[k];
     }
   }
+}
+
+__global__ void partition_kernel(const int32_t* __restrict__ chains, int64_t n, int32_t* k1, int32_t* k1_ids,
+                                 int32_t* k2, int32_t* k2_ids, unsigned long long* counts) {
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < n; base += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t c = base + threadIdx.x;
+    const bool ok = c < n;
+    const bool two = ok && chains[3 * c + 2] >= 0;
+    const unsigned long long s1 = warp_append(counts, (ok && !two) ? 1u : 0u);
+    const unsigned long long s2 = warp_append(counts + 1, two ? 1u : 0u);
+    if (!ok) continue;
+    int32_t* dst = two ? k2 + 3 * s2 : k1 + 3 * s1;
+    dst[0] = chains[3 * c];
+    dst[1] = chains[3 * c + 1];
+    dst[2] = chains[3 * c + 2];
+    (two ? k2_ids[s2] : k1_ids[s1]) = int32_t(c);
+  }
+}
+
+cudaError_t launch_partition(const int32_t* chains, int64_t n, int32_t* k1, int32_t* k1_ids, int32_t* k2,
+                             int32_t* k2_ids, unsigned long long* counts, int num_sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((n + 255) / 256, int64_t(num_sms) * 8);
+  partition_kernel<<<int(g), 256, 0, st>>>(chains, n, k1, k1_ids, k2, k2_ids, counts);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, cudaStream_t st);

@@ -1,0 +1,345 @@
+// TT chains, FP64 phase 1: piece enumeration and construction of the
+// bivariate system (Sec. 4.4-4.5) per (chain, sqrt piece).
+#include "tt_kernels.cuh"
+
+namespace spoly {
+
+// Argument of the sqrt approximant at a point p with normal n: x = beta / s,
+// beta = |n|^2 |d|^2 - eta'^2 (|n|^2 |d|^2 - (d.n)^2), d = p - x0.
+SPOLY_D double sqrt_arg(d3 p, d3 n, d3 x0, double er, double s) {
+  const d3 d = p - x0;
+  const double nd = dot(n, n) * dot(d, d), dn = dot(d, n);
+  return (nd - er * er * (nd - dn * dn)) / s;
+}
+
+SPOLY_D int piece_of(const SqrtTable& tb, double x) {
+  x = fmin(fmax(x, 0.0), 1.0);
+  int k = 0;
+  while (k < kSqrtPieces - 1 && x >= tb.breaks[k + 1]) ++k;
+  return k;
+}
+
+// Pieces of the approximant spanned by x over the triangle (centroid and
+// vertices), as a bit mask.
+SPOLY_D unsigned tt_pieces(const TriD& t1, d3 x0, double e0, double e1, const SqrtTable& tb, double* s_out) {
+  const d3 c = (1.0 / 3.0) * (t1.p0 + t1.p1 + t1.p2);
+  const d3 nc = (1.0 / 3.0) * (t1.n0 + t1.n1 + t1.n2);
+  const double s = dot(nc, nc) * dot(c - x0, c - x0);
+  const double er = e0 / e1;
+  unsigned m = 1u << piece_of(tb, sqrt_arg(c, nc, x0, er, s));
+  m |= 1u << piece_of(tb, sqrt_arg(t1.p0, t1.n0, x0, er, s));
+  m |= 1u << piece_of(tb, sqrt_arg(t1.p1, t1.n1, x0, er, s));
+  m |= 1u << piece_of(tb, sqrt_arg(t1.p2, t1.n2, x0, er, s));
+  *s_out = s;
+  return m;
+}
+
+// Pieces spanned by each chain: count into chain_sys[2c + 1], mask kept.
+__global__ void tt_count_kernel(TTParams P, uint8_t* masks) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < P.n_chains; c += stride) {
+    const int q = P.chains[3 * c], t1 = P.chains[3 * c + 1];
+    const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
+    const TriD a = load_tri(P.mesh.tri, P.mesh.n_tris, t1);
+    double s;
+    const unsigned mask = tt_pieces(a, qd.x0, qd.eta0, qd.eta1, P.sqrt_tab, &s);
+    masks[c] = uint8_t(mask);
+    P.chain_sys[2 * c + 1] = __popc(mask);
+  }
+}
+
+// One system per spanned piece at chain_sys[2c] + k: a chain's systems are
+// contiguous and ordered by chain.
+__global__ void tt_fill_kernel(TTParams P, const uint8_t* masks) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < P.n_chains; c += stride) {
+    const unsigned mask = masks[c];
+    const int cnt = __popc(mask);
+    int k = 0;
+    for (int pc = 0; pc < kSqrtPieces; ++pc)
+      if (mask & (1u << pc)) {
+        const int64_t i = int64_t(P.chain_sys[2 * c]) + k++;
+        if (i < P.sys_cap) {
+          TTSys sy{};
+          sy.chain = int32_t(c);
+          sy.piece = pc;
+          sy.da = sy.db = sy.n = -1;
+          sy.flags = cnt > 1 ? SPOLY_FLAG_SQRT_SPLIT : 0u;
+          P.sys[i] = sy;
+        }
+      }
+  }
+}
+
+// Projection axis of the square form at x2 (reading R2 at the second
+// vertex): m = (x3 - c1) x n2c; first of x, z, y with |m_hat . e| >= 0.25.
+SPOLY_D int tt_axis(const TriD& t1, const TriD& t2, d3 x3) {
+  const d3 c1 = (1.0 / 3.0) * (t1.p0 + t1.p1 + t1.p2);
+  const d3 n2 = (1.0 / 3.0) * (t2.n0 + t2.n1 + t2.n2);
+  d3 m = cross(x3 - c1, n2);
+  const double mn = norm(m);
+  if (mn > 0.0) m = (1.0 / mn) * m;
+  if (fabs(m.x) >= kSwitch) return 0;
+  if (fabs(m.z) >= kSwitch) return 2;
+  if (fabs(m.y) >= kSwitch) return 1;
+  return 0;
+}
+
+SPOLY_D bool constant_normal(const TriD& t) {
+  const d3 a = (1.0 / norm(t.n0)) * t.n0, b = (1.0 / norm(t.n1)) * t.n1, c = (1.0 / norm(t.n2)) * t.n2;
+  const double e = fmax(fmax(fmax(fabs(b.x - a.x), fabs(b.y - a.y)), fmax(fabs(b.z - a.z), fabs(c.x - a.x))),
+                        fmax(fabs(c.y - a.y), fabs(c.z - a.z)));
+  return e < 1e-12;
+}
+
+// Builds a, b, u~, v~, kappa of one system into scratch column `col`.
+SPOLY_D void tt_construct(const TriD& t1, const TriD& t2, const QueryD& qd, d3 x3, double eta2, int piece,
+                          const SqrtTable& tb, double* base, int64_t st) {
+  Arena A{base, st, 0};
+  const GP a = A.take(kTTDa), b = A.take(kTTDb), ut = A.take(kTTDmap), vt = A.take(kTTDmap), kap = A.take(kTTDmap);
+  const d3 x0 = qd.x0;
+  const double er = qd.eta0 / qd.eta1;
+  // x1, n1 (normal turned to the incident side, reading of Eq. eq_refr_rational)
+  const d3 c1 = (1.0 / 3.0) * (t1.p0 + t1.p1 + t1.p2);
+  const d3 nc = (1.0 / 3.0) * (t1.n0 + t1.n1 + t1.n2);
+  const double sg = dot(c1 - x0, nc) > 0.0 ? -1.0 : 1.0;
+  const double s = dot(nc, nc) * dot(c1 - x0, c1 - x0);
+  const GV d0 = gv_take(A, 1), n1 = gv_take(A, 1), s2 = gv_take(A, 1), se1 = gv_take(A, 1), x31 = gv_take(A, 1);
+  gv_set_lin(d0, t1.p0 - x0, t1.p1 - t1.p0, t1.p2 - t1.p0);
+  gv_set_lin(n1, sg * t1.n0, sg * (t1.n1 - t1.n0), sg * (t1.n2 - t1.n0));
+  gv_set_lin(s2, t1.p0 - t2.p0, t1.p1 - t1.p0, t1.p2 - t1.p0);
+  gv_set_lin(x31, x3 - t1.p0, -1.0 * (t1.p1 - t1.p0), -1.0 * (t1.p2 - t1.p0));
+  const d3 e21 = t2.p1 - t2.p0, e22 = t2.p2 - t2.p0;
+  // se1 = s2 x e21 (linear)
+  {
+    const d3 c0 = mk(s2.x.at(0, 0), s2.y.at(0, 0), s2.z.at(0, 0));
+    const d3 cu = mk(s2.x.at(1, 0), s2.y.at(1, 0), s2.z.at(1, 0));
+    const d3 cv = mk(s2.x.at(0, 1), s2.y.at(0, 1), s2.z.at(0, 1));
+    gv_set_lin(se1, cross(c0, e21), cross(cu, e21), cross(cv, e21));
+  }
+  const GP n1sq = A.take(2), dd = A.take(2), dn = A.take(2);
+  gp_zero(n1sq);
+  gp_zero(dd);
+  gp_zero(dn);
+  gv_dot_mac(n1sq, n1, n1, 1.0);
+  gv_dot_mac(dd, d0, d0, 1.0);
+  gv_dot_mac(dn, d0, n1, 1.0);
+  const GP nd = A.take(4), beta = A.take(4), Q = A.take(4), num = A.take(4);
+  gp_zero(nd);
+  gp_mac(nd, n1sq, dd, 1.0);
+  gp_zero(beta);
+  gp_axpy(beta, nd, 1.0 - er * er);
+  gp_mac(beta, dn, dn, er * er);
+  const double c0 = tb.c[piece][0], cc1 = tb.c[piece][1], d1 = tb.c[piece][2];
+  gp_zero(Q);
+  gp_axpy(Q, beta, d1);
+  Q.at(0, 0) += s;
+  gp_zero(num);
+  gp_axpy(num, beta, cc1);
+  num.at(0, 0) += c0 * s;
+  // tang = d0 |n1|^2 - n1 (d0 . n1): degree 3
+  const GV tang = gv_take(A, 3);
+  gv_zero(tang);
+  gp_mac(tang.x, d0.x, n1sq, 1.0);
+  gp_mac(tang.y, d0.y, n1sq, 1.0);
+  gp_mac(tang.z, d0.z, n1sq, 1.0);
+  gp_mac(tang.x, n1.x, dn, -1.0);
+  gp_mac(tang.y, n1.y, dn, -1.0);
+  gp_mac(tang.z, n1.z, dn, -1.0);
+  // D = eta' Q tang - sqrt(s) num n1: degree 7
+  const GV D = gv_take(A, 7);
+  gv_zero(D);
+  const double rs = sqrt(s);
+  gp_mac(D.x, Q, tang.x, er);
+  gp_mac(D.y, Q, tang.y, er);
+  gp_mac(D.z, Q, tang.z, er);
+  gp_mac(D.x, num, n1.x, -rs);
+  gp_mac(D.y, num, n1.y, -rs);
+  gp_mac(D.z, num, n1.z, -rs);
+  // de2 = D x e22; u~ = de2 . s2; kappa = de2 . e21; v~ = se1 . D
+  const GV de2 = gv_take(A, 7);
+  gv_zero(de2);
+  gp_axpy(de2.x, D.y, e22.z);
+  gp_axpy(de2.x, D.z, -e22.y);
+  gp_axpy(de2.y, D.z, e22.x);
+  gp_axpy(de2.y, D.x, -e22.z);
+  gp_axpy(de2.z, D.x, e22.y);
+  gp_axpy(de2.z, D.y, -e22.x);
+  gp_zero(ut);
+  gv_dot_mac(ut, de2, s2, 1.0);
+  gp_zero(kap);
+  gv_dot_const_mac(kap, de2, e21, 1.0);
+  gp_zero(vt);
+  gv_dot_mac(vt, se1, D, 1.0);
+  // M2 = kappa n20 + u~ (n21 - n20) + v~ (n22 - n20), or the constant normal
+  const GV M2 = gv_take(A, 8);
+  gv_zero(M2);
+  if (constant_normal(t2)) {
+    M2.x.at(0, 0) = t2.n0.x;
+    M2.y.at(0, 0) = t2.n0.y;
+    M2.z.at(0, 0) = t2.n0.z;
+  } else {
+    const d3 g1 = t2.n1 - t2.n0, g2 = t2.n2 - t2.n0;
+    gp_axpy(M2.x, kap, t2.n0.x);
+    gp_axpy(M2.y, kap, t2.n0.y);
+    gp_axpy(M2.z, kap, t2.n0.z);
+    gp_axpy(M2.x, ut, g1.x);
+    gp_axpy(M2.y, ut, g1.y);
+    gp_axpy(M2.z, ut, g1.z);
+    gp_axpy(M2.x, vt, g2.x);
+    gp_axpy(M2.y, vt, g2.y);
+    gp_axpy(M2.z, vt, g2.z);
+  }
+  // K2 = kappa (x3 - p20) - u~ e21 - v~ e22
+  const GV K2 = gv_take(A, 8);
+  gv_zero(K2);
+  const d3 w3 = x3 - t2.p0;
+  gp_axpy(K2.x, kap, w3.x);
+  gp_axpy(K2.y, kap, w3.y);
+  gp_axpy(K2.z, kap, w3.z);
+  gp_axpy(K2.x, ut, -e21.x);
+  gp_axpy(K2.y, ut, -e21.y);
+  gp_axpy(K2.z, ut, -e21.z);
+  gp_axpy(K2.x, vt, -e22.x);
+  gp_axpy(K2.y, vt, -e22.y);
+  gp_axpy(K2.z, vt, -e22.z);
+  // a = (D x (x3 - x1)) . M2
+  const GV C = gv_take(A, 8);
+  gv_zero(C);
+  gp_mac(C.x, D.y, x31.z, 1.0);
+  gp_mac(C.x, D.z, x31.y, -1.0);
+  gp_mac(C.y, D.z, x31.x, 1.0);
+  gp_mac(C.y, D.x, x31.z, -1.0);
+  gp_mac(C.z, D.x, x31.y, 1.0);
+  gp_mac(C.z, D.y, x31.x, -1.0);
+  gp_zero(a);
+  gv_dot_mac(a, C, M2, 1.0);
+  // b = eta1^2 |K2|^2 p1^2 - eta2^2 |D|^2 p2^2
+  const int ax = tt_axis(t1, t2, x3);
+  const GP p1 = A.take(16), p2 = A.take(16), k2sq = A.take(16), dsq = A.take(16);
+  gp_zero(p1);
+  gp_zero(p2);
+  gp_zero(k2sq);
+  gp_zero(dsq);
+  gv_cross_axis_mac(p1, D, M2, ax, 1.0);
+  gv_cross_axis_mac(p2, K2, M2, ax, 1.0);
+  gv_dot_mac(k2sq, K2, K2, 1.0);
+  gv_dot_mac(dsq, D, D, 1.0);
+  const GP p1sq = A.take(32), p2sq = A.take(32);
+  gp_zero(p1sq);
+  gp_zero(p2sq);
+  gp_mac(p1sq, p1, p1, 1.0);
+  gp_mac(p2sq, p2, p2, 1.0);
+  gp_zero(b);
+  // the factors' true degrees (|K2|^2 16, p1^2 30; |D|^2 14, p2^2 32) keep
+  // the products within degree 46; their slots are larger
+  gp_mac_trunc(b, k2sq, p1sq, qd.eta1 * qd.eta1);
+  gp_mac_trunc(b, dsq, p2sq, -eta2 * eta2);
+}
+
+// Trimmed u-degree (reading R1) and the u scaling of the FP32 copy.
+SPOLY_D void tt_finish(TTSys& sy, double* base, int64_t st, float* c32, int64_t st32) {
+  const GP a{base + int64_t(kOffA) * st, st, kTTDa}, b{base + int64_t(kOffB) * st, st, kTTDb};
+  double ra[kTTDa + 1], rb[kTTDb + 1];
+  double am = 0.0, bm = 0.0;
+  for (int i = 0; i <= kTTDa; ++i) {
+    double m = 0.0;
+    for (int j = 0; i + j <= kTTDa; ++j) m = fmax(m, fabs(a.at(i, j)));
+    ra[i] = m;
+    am = fmax(am, m);
+  }
+  for (int i = 0; i <= kTTDb; ++i) {
+    double m = 0.0;
+    for (int j = 0; i + j <= kTTDb; ++j) m = fmax(m, fabs(b.at(i, j)));
+    rb[i] = m;
+    bm = fmax(bm, m);
+  }
+  int da = -1, db = -1;
+  for (int i = 0; i <= kTTDa; ++i)
+    if (ra[i] > kTrim * am) da = i;
+  for (int i = 0; i <= kTTDb; ++i)
+    if (rb[i] > kTrim * bm) db = i;
+  sy.da = da;
+  sy.db = db;
+  sy.n = (da < 0 || db < 0) ? -1 : max(da, db);
+  if (sy.n < 1) {
+    sy.n = -1;
+    return;
+  }
+  // least-squares slope of log2(row max) over the kept rows of both
+  double sx = 0, sy2 = 0, sxx = 0, sxy = 0, cnt = 0;
+  for (int i = 0; i <= da; ++i)
+    if (ra[i] > 0.0) {
+      const double l = log2(ra[i] / am);
+      sx += i;
+      sy2 += l;
+      sxx += double(i) * i;
+      sxy += i * l;
+      cnt += 1;
+    }
+  for (int i = 0; i <= db; ++i)
+    if (rb[i] > 0.0) {
+      const double l = log2(rb[i] / bm);
+      sx += i;
+      sy2 += l;
+      sxx += double(i) * i;
+      sxy += i * l;
+      cnt += 1;
+    }
+  const double den = cnt * sxx - sx * sx;
+  const double g = den > 0.0 ? (cnt * sxy - sx * sy2) / den : 0.0;
+  int ks = int(rint(-g));
+  ks = max(-20, min(20, ks));
+  sy.ks = ks;
+  // scaled, normalised FP32 copy
+  double am2 = 0.0, bm2 = 0.0;
+  for (int i = 0; i <= da; ++i) am2 = fmax(am2, ldexp(ra[i], ks * i));
+  for (int i = 0; i <= db; ++i) bm2 = fmax(bm2, ldexp(rb[i], ks * i));
+  for (int i = 0; i <= kTTDa; ++i)
+    for (int j = 0; i + j <= kTTDa; ++j)
+      c32[int64_t(bidx(kTTDa, i, j)) * st32] = i <= da ? float(ldexp(a.at(i, j), ks * i) / am2) : 0.0f;
+  const int ob = bsize(kTTDa);
+  for (int i = 0; i <= kTTDb; ++i)
+    for (int j = 0; i + j <= kTTDb; ++j)
+      c32[int64_t(ob + bidx(kTTDb, i, j)) * st32] = i <= db ? float(ldexp(b.at(i, j), ks * i) / bm2) : 0.0f;
+}
+
+__global__ void __launch_bounds__(128) tt_build_kernel(TTParams P) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n_sys; i += stride) {
+    TTSys sy = P.sys[P.sys_offset + i];
+    const int64_t c = sy.chain;
+    const int q = P.chains[3 * c], t1 = P.chains[3 * c + 1], t2 = P.chains[3 * c + 2];
+    const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
+    const double eta2 = P.qv.eta[3 * q + 2];
+    const TriD a = load_tri(P.mesh.tri, P.mesh.n_tris, t1);
+    const TriD b = load_tri(P.mesh.tri, P.mesh.n_tris, t2);
+    double* col = P.scratch + i;
+    tt_construct(a, b, qd, qd.x2, eta2, sy.piece, P.sqrt_tab, col, P.n_sys);
+    tt_finish(sy, col, P.n_sys, P.coef32 + i, P.n_sys);
+    P.sys[P.sys_offset + i] = sy;
+  }
+}
+
+cudaError_t launch_tt_count(const TTParams& P, uint8_t* masks, int num_sms, cudaStream_t st) {
+  if (P.n_chains <= 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((P.n_chains + 127) / 128, int64_t(num_sms) * 8);
+  tt_count_kernel<<<int(g), 128, 0, st>>>(P, masks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tt_fill(const TTParams& P, const uint8_t* masks, int num_sms, cudaStream_t st) {
+  if (P.n_chains <= 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((P.n_chains + 127) / 128, int64_t(num_sms) * 8);
+  tt_fill_kernel<<<int(g), 128, 0, st>>>(P, masks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tt_build(const TTParams& P, int num_sms, cudaStream_t st) {
+  if (P.n_sys <= 0) return cudaSuccess;
+  const int64_t g = std::min<int64_t>((P.n_sys + 127) / 128, int64_t(num_sms) * 8);
+  tt_build_kernel<<<int(g), 128, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace spoly

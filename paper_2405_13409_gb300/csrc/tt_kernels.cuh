@@ -1,0 +1,61 @@
+// Parameters and launchers of the 2-bounce refraction (TT) kernels.
+#pragma once
+#include <algorithm>
+
+#include "tt.cuh"
+
+namespace spoly {
+
+// Counter slots of the TT pipeline (its own counter array).
+enum TTCounter {
+  TT_SYSTEMS = 0,   // (chain, sqrt piece) systems
+  TT_DEGENERATE,    // systems whose a or b vanishes, or n < 1
+  TT_TOO_LARGE,     // systems with a Bezout size above kTTMaxN (not solved)
+  TT_BRACKETS,      // sign changes after the FP32 bisection (queue items)
+  TT_BRACKET_OVERFLOW,
+  TT_POLISH_LOST,   // brackets without an FP64 sign change nearby
+  TT_UROOTS,        // (u1, v1) pairs sent to the path-space Newton
+  TT_ADMISSIBLE,    // paths written
+  TT_FLAGGED,       // with SPOLY_FLAG_ILL_COND
+  TT_RESAMPLED,     // systems whose FP32 signs changed too often, sampled again in FP64
+  TT_COUNT
+};
+
+constexpr uint32_t kTTResample = 1u << 29;  // TTSys flag: sample again in FP64
+
+struct TTParams {
+  MeshView mesh;
+  QueryView qv;
+  const int32_t* chains;   // [n_chains][3] (query, tri0, tri1)
+  const int32_t* chain_ids;  // original chain index per chain (NULL: identity)
+  int64_t n_chains;
+  SqrtTable sqrt_tab;
+  int32_t n_intervals;     // uniform samples - 1 over v1 in [0, 1]
+  int32_t precision;       // SPOLY_MIXED: FP32 sign sampling; SPOLY_PLAIN_FP64: FP64
+  int32_t resample_only;   // sign pass over the systems flagged kTTResample (FP64)
+  int32_t* chain_sys;      // [n_chains][2] first system, count
+  TTSys* sys;
+  int64_t sys_cap;
+  int64_t n_sys;           // systems of this batch (build, sign)
+  int64_t sys_offset;      // first system of this batch
+  double* scratch;         // [kTTScratch][n_sys] FP64 (batch-local)
+  float* coef32;           // [kTT32][n_sys] FP32 (batch-local)
+  RootItem* queue;         // brackets: zlo = zhi = v1 after the polish; chain = system (global index)
+  int64_t queue_cap;
+  unsigned long long* counters;  // [TT_COUNT]
+  spoly_path* paths;
+  int64_t path_cap;
+  unsigned long long* path_counter;  // shared with the 1-bounce paths
+};
+
+// Systems: counts per chain into chain_sys[2c + 1] and piece masks; then,
+// with chain_sys[2c] set to the exclusive prefix of the counts, the records.
+cudaError_t launch_tt_count(const TTParams& P, uint8_t* masks, int num_sms, cudaStream_t st);
+cudaError_t launch_tt_fill(const TTParams& P, const uint8_t* masks, int num_sms, cudaStream_t st);
+// Per batch of systems [sys_offset, sys_offset + n_sys):
+cudaError_t launch_tt_build(const TTParams& P, int num_sms, cudaStream_t st);
+cudaError_t launch_tt_sign(const TTParams& P, int num_sms, cudaStream_t st);
+cudaError_t launch_tt_polish(const TTParams& P, int64_t item_begin, int64_t item_end, int num_sms, cudaStream_t st);
+cudaError_t launch_tt_paths(const TTParams& P, int64_t chain_begin, int64_t chain_end, int num_sms, cudaStream_t st);
+
+}  // namespace spoly

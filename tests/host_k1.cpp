@@ -10,10 +10,10 @@ using namespace spoly;
 namespace {
 
 template <int DB>
-int isolate_one(const K1Sys<DB>& s, int precision, RootItem (&items)[kRD + 1], unsigned& nv, unsigned& np,
-                int* status) {
+int isolate_one(const TriD& tr, const K1Sys<DB>& s, int precision, RootItem (&items)[kRD + 1], unsigned& nv,
+                unsigned& np, int* status) {
   int r = -2;
-  if (precision == 1) r = k1_isolate_dispatch<float, DB>(s, items, 0, nv, np);
+  if (precision == 1 && !flat_shaded(tr)) r = k1_isolate_dispatch<float, DB>(s, items, 0, nv, np);
   status[0] = r;
   if (r != -2) return r;
   r = k1_isolate_dispatch<double, DB>(s, items, 0, nv, np);
@@ -30,7 +30,7 @@ int run(const TriD& tr, const QueryD& qd, int precision, double* out, int cap, i
   }
   RootItem items[kRD + 1];
   unsigned nv = 0, npref = 0, lost = 0, nu = 0;
-  const int nq = isolate_one<DB>(s, precision, items, nv, npref, status);
+  const int nq = isolate_one<DB>(tr, s, precision, items, nv, npref, status);
   status[1] = int(nv);
   status[2] = nq;
   int ntang = 0;

@@ -1,0 +1,211 @@
+"""GPU tests of 2-bounce refraction (TT) chains against the FP64 TT oracle:
+planted paths through the curved slab, a sample of candidate pairs, flat
+slabs with Fermat's closed form, and chain lists that mix 1- and 2-bounce
+chains."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tt
+from paper_2405_13409_gb300 import binding, scenes
+
+from .test_tt_oracle import _fermat, planted_slab_cases
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = binding.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _table():
+    g = json.load(open(os.path.join(HERE, "golden", "sqrt_pieces.json")))
+    return np.array(g["breaks"]), np.array(g["coeffs"])
+
+
+def _solve(ctx, tri, x0s, x3s, chains, precision=binding.MIXED, kk=2):
+    n = x0s.shape[0]
+    eta = np.tile([1.0, 1.5, 1.0], (n, 1))
+    types = np.full((n, 2), binding.SPOLY_T, np.int32)
+    k = np.full(n, kk, np.int32)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (tri, x0s, x3s, eta, types, k)]
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=np.ascontiguousarray(chains, np.int32))
+    sol = ctx.spoly_solve(mesh, q, ch, precision=precision, sqrt_table=_table())
+    paths = ctx.spoly_paths(sol)
+    stats = ctx.spoly_stats(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    return paths, stats, eta
+
+
+def _compare(paths, ref, tol=1e-5):
+    """Pairs GPU and oracle TT paths by (query, tri0, tri1) and (u1,v1,u2,v2)."""
+    from collections import defaultdict
+    G = defaultdict(list)
+    for p in paths:
+        G[(int(p["query"]), int(p["tri"][0]), int(p["tri"][1]))].append((p["uv"].ravel(), int(p["flags"])))
+    R = defaultdict(list)
+    for p in ref:
+        R[(int(p["query"]), int(p["tri0"]), int(p["tri1"]))].append((p["uv"].ravel(), int(p["flags"])))
+    matched, unmatched, worst = 0, [], 0.0
+    for key in set(G) | set(R):
+        a, b = list(G.get(key, [])), list(R.get(key, []))
+        used = set()
+        for x, fx in a:
+            best = None
+            for j, (y, fy) in enumerate(b):
+                if j in used:
+                    continue
+                d = float(np.max(np.abs(x - y)))
+                if d <= tol and (best is None or d < best[0]):
+                    best = (d, j)
+            if best is None:
+                unmatched.append(("gpu", key, x.tolist(), fx))
+            else:
+                used.add(best[1])
+                matched += 1
+                worst = max(worst, best[0])
+        for j, (y, fy) in enumerate(b):
+            if j not in used:
+                unmatched.append(("ref", key, y.tolist(), fy))
+    return matched, unmatched, worst
+
+
+ALLOWED = binding.FLAG_ILL_COND | binding.FLAG_EDGE
+
+
+@pytest.mark.parametrize("precision", [binding.MIXED, binding.PLAIN_FP64])
+def test_planted_slab_paths_match_oracle(ctx, precision):
+    cases = planted_slab_cases(11, 24)
+    s = scenes.slab_scene(seed=0, n_cells=16, n_recv=4)
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    chains = np.array([[i, c[2], c[3]] for i, c in enumerate(cases)], np.int32)
+    paths, stats, eta = _solve(ctx, s.tri, x0s, x3s, chains, precision)
+    breaks, coeffs = _table()
+    ref, _ = tt.solve(s.tri, x0s, x3s, eta, chains, coeffs)
+    matched, un, worst = _compare(paths, ref)
+    bad = [u for u in un if not (u[3] & ALLOWED)]
+    assert not bad, (bad, stats)
+    assert matched >= len(cases) - 1, (un, stats)
+    assert worst < 1e-9
+    # every planted path is returned
+    for i, c in enumerate(cases):
+        got = paths[paths["query"] == i]
+        assert any(np.max(np.abs(p["uv"].ravel() - c[4])) < 1e-9 for p in got), (i, c[4], got["uv"])
+    assert np.all(paths["flags"] & binding.FLAG_NEWTON)
+    assert np.all(paths["residual"] < 1e-9)
+    assert stats["unsolved"] == 0
+
+
+def test_candidate_sample_matches_oracle(ctx):
+    """Receivers below the slab and (top, bottom) pairs near the planted
+    paths' triangles: most have no path; the path sets agree."""
+    cases = planted_slab_cases(12, 6)
+    s = scenes.slab_scene(seed=0, n_cells=16, n_recv=4)
+    half = s.n_tris // 2
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    rng = np.random.default_rng(3)
+    rows = []
+    for i, c in enumerate(cases):
+        t1, t2 = c[2], c[3]
+        for d1 in (-2, -1, 0, 1, 2):
+            for d2 in (-34, -2, 0, 2, 32):
+                a, b = t1 + d1, t2 + d2
+                if 0 <= a < half and half <= b < s.n_tris:
+                    rows.append([i, a, b])
+        for _ in range(10):
+            rows.append([i, int(rng.integers(0, half)), int(rng.integers(half, s.n_tris))])
+    chains = np.array(rows, np.int32)
+    paths, stats, eta = _solve(ctx, s.tri, x0s, x3s, chains)
+    breaks, coeffs = _table()
+    ref, _ = tt.solve(s.tri, x0s, x3s, eta, chains, coeffs)
+    matched, un, worst = _compare(paths, ref)
+    bad = [u for u in un if not (u[3] & ALLOWED)]
+    assert not bad, (bad, stats)
+    assert matched >= len(cases)
+    assert len(un) <= max(1, 1e-2 * chains.shape[0])
+    assert stats["candidates"] == chains.shape[0]
+
+
+def test_flat_slab_fermat(ctx):
+    rng = np.random.default_rng(4)
+    P1 = np.array([[-1.0, -1.0, 0.0], [1.5, -1.0, 0.0], [-1.0, 1.5, 0.0]])
+    P2 = P1 + [0.0, 0.0, -0.3]
+    n = np.array([0.0, 0.0, 1.0])
+    tri = np.zeros((18, 2))
+    tri[0:9, 0] = P1.ravel()
+    tri[9:18, 0] = np.tile(n, 3)
+    tri[0:9, 1] = P2.ravel()
+    tri[9:18, 1] = np.tile(n, 3)
+    x0s = np.array([0.2, 0.1, 2.0]) + rng.normal(size=(6, 3)) * 0.2
+    x3s = np.array([0.0, 0.0, -1.0]) + rng.normal(size=(6, 3)) * 0.3
+    chains = np.array([[i, 0, 1] for i in range(6)], np.int32)
+    paths, stats, eta = _solve(ctx, tri, x0s, x3s, chains)
+    n_in = 0
+    for i in range(6):
+        want = _fermat(x0s[i], x3s[i], (1.0, 1.5, 1.0), P1, P2)
+        got = paths[paths["query"] == i]
+        inside = min(want[0], want[1], 1 - want[0] - want[1], want[2], want[3], 1 - want[2] - want[3]) > 1e-6
+        if inside:
+            n_in += 1
+            assert got.size == 1
+            np.testing.assert_allclose(got[0]["uv"].ravel(), want, atol=1e-7)
+        else:
+            assert got.size == 0
+    assert n_in >= 3
+
+
+def test_mixed_one_and_two_bounce_lists(ctx):
+    """One list with 1-bounce (tri1 = -1) and 2-bounce chains returns the
+    union of the two solves, with each path's chain index."""
+    cases = planted_slab_cases(13, 6)
+    s = scenes.slab_scene(seed=0, n_cells=16, n_recv=4)
+    n = len(cases)
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    # queries 0..n-1: 2-bounce; n..2n-1: 1-bounce refraction from x0 into the slab top to a point below it
+    eta1 = np.tile([1.0, 1.5, 1.0], (n, 1))
+    rows2 = [[i, c[2], c[3]] for i, c in enumerate(cases)]
+    rows1 = [[n + i, c[2], -1] for i, c in enumerate(cases)]
+    chains = np.array([r for pair in zip(rows2, rows1) for r in pair], np.int32)
+    xf = np.concatenate([x0s, x0s])
+    xl = np.concatenate([x3s, x3s * [1, 1, 0] + [0, 0, -0.15]])
+    eta = np.concatenate([eta1, eta1])
+    types = np.full((2 * n, 2), binding.SPOLY_T, np.int32)
+    k = np.concatenate([np.full(n, 2, np.int32), np.full(n, 1, np.int32)])
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (s.tri, xf, xl, eta, types, k)]
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=chains)
+    sol = ctx.spoly_solve(mesh, q, ch, precision=binding.MIXED, sqrt_table=_table())
+    paths = ctx.spoly_paths(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    two = paths[paths["tri"][:, 1] >= 0]
+    one = paths[paths["tri"][:, 1] < 0]
+    assert two.size >= n - 1
+    assert np.all(chains[two["chain"], 2] >= 0) and np.all(chains[one["chain"], 2] == -1)
+    assert np.all(chains[two["chain"], 0] == two["query"]) and np.all(chains[one["chain"], 0] == one["query"])
+    # the 1-bounce part equals a solve of the 1-bounce chains alone
+    only1 = np.array(rows1, np.int32)
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=only1)
+    sol = ctx.spoly_solve(mesh, q, ch, precision=binding.MIXED)
+    ref1 = ctx.spoly_paths(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    assert sorted(map(tuple, np.round(one["uv"][:, :2], 9).tolist())) == \
+        sorted(map(tuple, np.round(ref1["uv"][:, :2], 9).tolist()))
