@@ -57,7 +57,8 @@ BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["b
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
 # Kernel launches per step, counted from the ncu launch list of each
 # workload (profiles/).
-LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 18, ("glints", True): 19}
+LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 18, ("glints", True): 19,
+                     ("slab", False): 11}
 # DRAM bytes (read + write) per launch of the isolation kernel from the last
 # ncu capture (profiles/kernels_refract_64x64_r256_mixed.md).  Reported only
 # while the kernel's sources hash to the value the capture was taken on.
@@ -79,7 +80,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    p.add_argument("--workload", choices=["glints", "refract", "reflect"], default="glints")
+    p.add_argument("--workload", choices=["glints", "refract", "reflect", "slab"], default="glints")
+    p.add_argument("--slab-receivers", type=int, default=64,
+                   help="slab: receiver grid side (64: the full 64x64 grid)")
     p.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
     p.add_argument("--no-gate", action="store_true", help="glints: solve every candidate (no learned gate)")
     p.add_argument("--no-plain", action="store_true", help="glints: skip the plain FP64 comparison")
@@ -97,9 +100,15 @@ def parse():
     return p.parse_args()
 
 
-def workload(name):
+def workload(name, slab_receivers=64):
     """(scene, chain mode, scattering kind, description, camera or None)."""
     from paper_2405_13409_gb300 import binding, scenes
+    if name == "slab":
+        s = scenes.slab_scene(n_recv=slab_receivers)
+        return s, binding.CHAINS_CONE, "TT", (
+            f"2-bounce refraction slab: 16x16-cell top (z=0) and bottom (z=-0.3) heightfields (512 triangles "
+            f"each, amplitude 0.05), eta 1 -> 1.5 -> 1, light (0.2,0.1,2), {slab_receivers}x{slab_receivers} "
+            f"receivers on z=-1, forward+backward cone cull, 4097 v1 samples"), None
     if name == "glints":
         s = scenes.glint_scene()
         return s, binding.CHAINS_FOOTPRINT, "R", (
@@ -242,10 +251,24 @@ def footprint_sample(s, camera, n_pixels, seed):
     return np.concatenate(rows).astype(np.int32), n_blocks
 
 
-def run_oracle_sample(s, camera, n_units, seed):
-    """One CPU-oracle step: all triangles x n_units seeded receivers, or the
-    footprint candidates of a block of about n_units pixels (glints)."""
+def run_oracle_sample(s, camera, n_units, seed, kind="R"):
+    """One CPU-oracle step: all triangles x n_units seeded receivers, the
+    footprint candidates of a block of about n_units pixels (glints), or
+    (slab) n_units (receiver, top, bottom) tuples pairing a seeded top
+    triangle with the bottom triangle of the same cell."""
     import oracle
+    if kind == "TT":
+        from oracle import tt
+        rng = np.random.default_rng(seed)
+        half = s.n_tris // 2
+        qs = rng.integers(0, s.n_queries, n_units)
+        t1 = rng.integers(0, half, n_units)
+        chains = np.stack([qs, t1, t1 + half], -1).astype(np.int32)
+        table = tt.fit_sqrt_pieces()
+        t0 = time.perf_counter()
+        paths, _ = tt.solve(s.tri, s.x_first, s.x_last, s.eta, chains, table)
+        return chains.shape[0], time.perf_counter() - t0, paths.size, \
+            f"{n_units} seeded (receiver, top triangle, bottom triangle of the same cell) tuples"
     if camera is not None:
         chains, nb = footprint_sample(s, camera, n_units, seed)
         desc = f"footprint candidates of {nb} 16x16-pixel blocks at seeded positions"
@@ -266,14 +289,14 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    s, _, kind, desc, cam = workload(args.workload)
-    units = args.ref_units or (16384 if cam is not None else 16)
+    s, _, kind, desc, cam = workload(args.workload, args.slab_receivers)
+    units = args.ref_units or (16384 if cam is not None else (8 if kind == "TT" else 16))
     cores = os.cpu_count()
     for i in range(args.warmup):
-        run_oracle_sample(s, cam, units, 1000 + i)
+        run_oracle_sample(s, cam, units, 1000 + i, kind)
     tot_c, tot_t, tot_p, sample = 0, 0.0, 0, ""
     for i in range(args.steps):
-        c, t, p, sample = run_oracle_sample(s, cam, units, 2000 + i)
+        c, t, p, sample = run_oracle_sample(s, cam, units, 2000 + i, kind)
         tot_c += c
         tot_t += t
         tot_p += p
@@ -309,9 +332,10 @@ class Pipeline:
     """One step of the hot path through the C ABI: candidate build, optional
     gate, solve.  Handles are reused across steps (grow-only buffers)."""
 
-    def __init__(self, ctx, mode, precision, camera, mlp=None, tau=0.0):
+    def __init__(self, ctx, mode, precision, camera, mlp=None, tau=0.0, ranges=None):
         self.ctx, self.mode, self.precision, self.camera = ctx, mode, precision, camera
         self.mlp, self.tau = mlp, tau
+        self.ranges = ranges  # 2-bounce cone: ((first range), (second range))
         self.chains = self.gated = self.sol = None
         self.ev = None
 
@@ -321,8 +345,12 @@ class Pipeline:
         if torch is not None:
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             ev[0].record(stream)
-        self.chains = self.ctx.spoly_build_chains(mesh, q, self.mode, margin=1e-3, reuse=self.chains,
-                                                  camera=self.camera)
+        if self.ranges:
+            self.chains = self.ctx.spoly_build_chains(mesh, q, self.mode, margin=1e-3, reuse=self.chains,
+                                                      tri_range=self.ranges[0], second_range=self.ranges[1])
+        else:
+            self.chains = self.ctx.spoly_build_chains(mesh, q, self.mode, margin=1e-3, reuse=self.chains,
+                                                      camera=self.camera)
         if ev:
             ev[1].record(stream)
         solve_on = self.chains
@@ -362,8 +390,9 @@ def timed_steps(pipe, mesh, q, steps, flush, stream, torch):
         b.record(stream)
         b.synchronize()
         c_ms, g_ms = pipe.phase_ms()
-        i_ms, p_ms, _tt_ms = pipe.ctx.spoly_phase_ms(pipe.sol)
+        i_ms, p_ms, tt_ms = pipe.ctx.spoly_phase_ms(pipe.sol)
         out.append({"step": a.elapsed_time(b), "chains": c_ms, "gate": g_ms, "isolation": i_ms, "polish": p_ms,
+                    "k2": tt_ms,
                     "paths": pipe.ctx.spoly_stats(pipe.sol)["admissible"]})
     return out
 
@@ -388,7 +417,7 @@ def main():
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
     ctx = binding.Context(local, stream.cuda_stream)
-    s, mode, kind, desc, camera = workload(args.workload)
+    s, mode, kind, desc, camera = workload(args.workload, args.slab_receivers)
     precision = binding.MIXED if args.precision == "mixed" else binding.PLAIN_FP64
     host = [np.ascontiguousarray(a) for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
     d = [torch.from_numpy(a).to(dev) for a in host]
@@ -424,14 +453,20 @@ def main():
             ctx.spoly_mlp_save(mlp, args.gate_file)
             json.dump(gate_info, open(args.gate_file + ".json", "w"))
 
-    pipe = Pipeline(ctx, mode, precision, camera, mlp, tau)
+    ranges = ((0, s.n_tris // 2), (s.n_tris // 2, s.n_tris)) if kind == "TT" else None
+    pipe = Pipeline(ctx, mode, precision, camera, mlp, tau, ranges)
     for _ in range(args.warmup):
         pipe.step(mesh, q)
     torch.cuda.synchronize()
     n_cand = ctx.spoly_chains_count(pipe.chains)
     n_solved = ctx.spoly_chains_count(pipe.gated) if use_gate else n_cand
     stats = ctx.spoly_stats(pipe.sol)
-    pairs = n_cand if mode == binding.CHAINS_FOOTPRINT else s.n_queries * s.n_tris
+    if mode == binding.CHAINS_FOOTPRINT:
+        pairs = n_cand
+    elif kind == "TT":
+        pairs = s.n_queries * (s.n_tris // 2) ** 2  # every (receiver, top, bottom) tuple the cull stands for
+    else:
+        pairs = s.n_queries * s.n_tris
 
     # timed region: device-resident inputs, L2 flushed between steps
     clocks = ClockSampler(local)
@@ -515,17 +550,29 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    ph = {k: statistics.mean(r[k] for r in rec) for k in ("chains", "gate", "isolation", "polish")}
+    ph = {k: statistics.mean(r[k] for r in rec) for k in ("chains", "gate", "isolation", "polish", "k2")}
     ph["step"] = total_ms / args.steps
     iso = ph["isolation"]
-    achieved64 = FP64_FLOPS[kind] * n_solved / (iso * 1e-3) / 1e12
+    achieved64 = FP64_FLOPS.get(kind, 0) * n_solved / (iso * 1e-3) / 1e12 if iso > 0 else 0.0
     roof_iso = {"bound": "alu", "pipe": "fp64", "kernel": "k1_isolate_kernel<float>",
                 "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s", "frac": achieved64 / peak64,
                 "peak_source": "measured FP64 FMA microbenchmark (spoly_measure_peak)",
                 "traffic": TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None,
                 "nominal_fp64_tflops": NOMINAL_FP64_TFLOPS, "measured_fp32_tflops": peak32,
-                "fp32_laplace_tflops": FP32_LAPLACE_FLOPS[kind] * n_solved / (iso * 1e-3) / 1e12}
+                "fp32_laplace_tflops": FP32_LAPLACE_FLOPS.get(kind, 0) * n_solved / (iso * 1e-3) / 1e12 if iso > 0
+                else 0.0}
     roofline = roof_iso
+    if kind == "TT":
+        # 2-bounce sign phase work: per determinant evaluation ~4/3 n^3 flop (Bezout
+        # entries n^3/3 FMA + elimination n^3/3 FMA) + ~1,900 flop of Horner
+        # evaluation of the coefficients; timed over the whole 2-bounce phase
+        tt_flops = 4.0 / 3.0 * stats.get("k2_eval_n3", 0) + 1900.0 * stats.get("k2_evals", 0)
+        ach = tt_flops / (ph["k2"] * 1e-3) / 1e12 if ph["k2"] > 0 else 0.0
+        roofline = {"bound": "alu", "pipe": "fp32", "kernel": "2-bounce phase (tt_sign_kernel dominant)",
+                    "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32 if peak32 else None,
+                    "peak_source": "measured FP32 FMA microbenchmark (spoly_measure_peak)", "traffic": None,
+                    "flop_model": "4/3 n^3 + 1900 per Bezout determinant evaluation",
+                    "evals_per_step": stats.get("k2_evals", 0)}
     if use_gate:
         gate_tflops = GATE_FLOPS * n_cand / (ph["gate"] * 1e-3) / 1e12
         roof_gate = {"bound": "tensor", "kernel": "gate_kernel (features + BF16 mma.sync MLP + compaction)",
@@ -558,8 +605,9 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        units = 24576 if camera is not None else (64 if kind == "T" else 256)
-        c, tcpu, _, sample = run_oracle_sample(s, camera, min(units, s.n_queries), 7)
+        units = 24576 if camera is not None else (64 if kind == "T" else (16 if kind == "TT" else 256))
+        c, tcpu, _, sample = run_oracle_sample(s, camera, units if kind == "TT" else min(units, s.n_queries), 7,
+                                               kind)
         line["cpu_baseline"] = {"value": c / tcpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line))

@@ -105,14 +105,21 @@ typedef struct {
 
 typedef struct {
   int32_t mode;
-  int32_t reserved;
+  /* CONE with second_end > 0: 2-bounce refraction chains (all queries k = 2,
+   * types T T, sharing x0 and the IORs) whose second triangle lies in
+   * [second_begin, second_end); the first lies in [tri_begin, tri_end).  A
+   * chain survives when its segment direction can lie in the first
+   * triangle's refracted-direction box from x0, in the direction box from
+   * the first triangle's bounding box to the second's, and in the negated
+   * refracted-direction box of the second triangle lit from x_last. */
+  int32_t second_begin;
   int32_t tri_begin; /* triangle range [tri_begin, tri_end); tri_end <= 0: all */
   int32_t tri_end;
   double margin;     /* CONE: slack added to every unit-direction box (>= 0) */
   const int32_t* explicit_chains; /* EXPLICIT: [n][3] (query, tri0, tri1) */
   int64_t n_explicit;
   int32_t explicit_on_device;
-  int32_t reserved2;
+  int32_t second_end;
   /* FOOTPRINT: host array of 16 doubles: camera origin xyz, forward xyz,
    * right xyz, up xyz (unit, orthogonal), tan(vertical fov / 2), aspect
    * (width / height), width, height.  Pixel (ix, iy) = query iy * width + ix
@@ -178,7 +185,9 @@ typedef struct {
                            change sign too often */
   int64_t unsolved;     /* 2-bounce systems whose Bezout size exceeds 31 (not solved) */
   int64_t k2_systems;   /* 2-bounce (chain, sqrt piece) systems */
-  int64_t reserved[4];
+  int64_t k2_evals;     /* 2-bounce Bezout determinant evaluations */
+  int64_t k2_eval_n3;   /* sum of n^3 over those evaluations (work of the sign phase) */
+  int64_t reserved[2];
 } spoly_counters;
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`

@@ -393,7 +393,6 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
         if da < 0 or db < 0 or n < 1:
             continue
         sg, la = det_sign(sysd, vs, n, da, db)
-        lmax = np.max(la[np.isfinite(la)]) if np.any(np.isfinite(la)) else 0.0
         # sign changes; a sample with det == 0 exactly is a root belonging to
         # the interval on its left (reading 7)
         roots = [(vs[m], 0) for m in range(1, n_intervals + 1) if sg[m] == 0.0]
@@ -414,9 +413,15 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
             hi = np.where(left & ~zero, hi, mid)
             it += 1
             if it == PAPER_ITERS:
+                # reading 7 (k = 2), normalised locally: |det| across the
+                # bracket against the largest |det| of the five samples
+                # around it (|det| spans hundreds of orders of magnitude over
+                # [0, 1]); a simple root gives about 2^-10 / 2.5
                 _, l_lo = det_sign(sysd, lo, n, da, db)
                 _, l_hi = det_sign(sysd, hi, n, da, db)
-                rel = np.logaddexp(l_lo - lmax, l_hi - lmax)
+                bi = np.array(br, int)
+                lloc = np.max(np.stack([la[np.clip(bi + o, 0, n_intervals)] for o in (-2, -1, 0, 1, 2, 3)]), 0)
+                rel = np.logaddexp(l_lo - lloc, l_hi - lloc)
                 flag = np.where(rel < np.log(ILL_COND_K2), F_ILL_COND, 0)
         roots += [(0.5 * (a + b), int(f)) for a, b, f in zip(lo, hi, flag)]
         for v1, vflag in roots:

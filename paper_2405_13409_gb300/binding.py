@@ -64,9 +64,9 @@ class spoly_queries(ctypes.Structure):
 
 
 class spoly_chain_opts(ctypes.Structure):
-    _fields_ = [("mode", c_int32), ("reserved", c_int32), ("tri_begin", c_int32), ("tri_end", c_int32),
+    _fields_ = [("mode", c_int32), ("second_begin", c_int32), ("tri_begin", c_int32), ("tri_end", c_int32),
                 ("margin", ctypes.c_double), ("explicit_chains", c_void_p), ("n_explicit", c_int64),
-                ("explicit_on_device", c_int32), ("reserved2", c_int32), ("camera", c_void_p),
+                ("explicit_on_device", c_int32), ("second_end", c_int32), ("camera", c_void_p),
                 ("cell", ctypes.c_double)]
 
 
@@ -84,8 +84,8 @@ class spoly_path(ctypes.Structure):
 class spoly_counters(ctypes.Structure):
     _fields_ = [(n, c_int64) for n in ("candidates", "degenerate", "v_roots", "queued", "prefiltered",
                                        "polish_lost", "u_roots", "admissible", "flagged", "fallback",
-                                       "unsolved", "k2_systems")] + \
-               [("reserved", c_int64 * 4)]
+                                       "unsolved", "k2_systems", "k2_evals", "k2_eval_n3")] + \
+               [("reserved", c_int64 * 2)]
 
 
 class spoly_mlp_train_opts(ctypes.Structure):
@@ -215,12 +215,13 @@ class Context:
                              int(x_first.shape[0]), _on_device(x_first), 0)
 
     def spoly_build_chains(self, mesh: spoly_mesh, q: spoly_queries, mode: int, margin: float = 1e-3,
-                           explicit=None, tri_range=(0, 0), reuse=None, camera=None, cell: float = 0.0):
+                           explicit=None, tri_range=(0, 0), reuse=None, camera=None, cell: float = 0.0,
+                           second_range=(0, 0)):
         cam = None if camera is None else np.ascontiguousarray(camera, dtype=np.float64)
-        opts = spoly_chain_opts(mode, 0, int(tri_range[0]), int(tri_range[1]), float(margin),
+        opts = spoly_chain_opts(mode, int(second_range[0]), int(tri_range[0]), int(tri_range[1]), float(margin),
                                 _ptr(explicit) if explicit is not None else 0,
                                 int(explicit.shape[0]) if explicit is not None else 0,
-                                _on_device(explicit) if explicit is not None else 0, 0,
+                                _on_device(explicit) if explicit is not None else 0, int(second_range[1]),
                                 cam.ctypes.data if cam is not None else None, float(cell))
         h = c_void_p(reuse.value if reuse is not None else None)
         self.check(self.lib.spoly_build_chains(self.h, ctypes.byref(mesh), ctypes.byref(q), ctypes.byref(opts),

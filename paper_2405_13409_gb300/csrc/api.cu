@@ -233,7 +233,7 @@ spoly_status spoly_ctx_destroy(spoly_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf* b : {&ctx->mesh, &ctx->xf, &ctx->xl, &ctx->eta, &ctx->types, &ctx->kk, &ctx->boxes, &ctx->flag,
-                    &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries, &ctx->fp_boxes})
+                    &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries, &ctx->fp_boxes, &ctx->tt_pairs})
     b->release();
   delete ctx;
   return SPOLY_OK;
@@ -316,6 +316,63 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (herr) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain %d references a missing query or triangle", herr - 1));
     ch->n = n;
     ch->n_k2 = int64_t(hk2);
+  } else if (opts->mode == SPOLY_CHAINS_CONE && opts->second_end > 0) {
+    // 2-bounce refraction chains: second triangle in [second_begin, second_end)
+    const int32_t sb = opts->second_begin, se = opts->second_end;
+    if (sb < 0 || se > mv.n_tris || sb >= se)
+      return bail(fail(ctx, SPOLY_EINVAL, "second triangle range [%d, %d) outside [0, %lld)", sb, se,
+                       (long long)mv.n_tris));
+    TTConeParams T{};
+    T.mesh = mv;
+    T.qv = qv;
+    T.t1_begin = tb;
+    T.n1 = te - tb;
+    T.t2_begin = sb;
+    T.n2 = se - sb;
+    T.margin = opts->margin;
+    if (ctx->flag.ensure(16) != cudaSuccess || ctx->boxes.ensure(size_t(T.n1) * 12 * sizeof(float)) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "cone scratch"));
+    T.fwd = static_cast<float*>(ctx->boxes.p);
+    int32_t shared = 0;
+    e = launch_tt_cone_shared(T, static_cast<int32_t*>(ctx->flag.p), ctx->num_sms, ctx->stream, &shared);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "tt cone"));
+    if (!shared)
+      return bail(fail(ctx, SPOLY_EUNSUPPORTED,
+                       "2-bounce cone: every query must be k = 2, types T T, with the same x0 and IORs"));
+    // receiver-independent pairs, then the per-receiver test; both grow to
+    // the exact count when their first capacity is exceeded
+    int64_t pcap = std::max<int64_t>(4096, int64_t(T.n1) * T.n2 / 16);
+    unsigned long long np = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (ctx->tt_pairs.ensure(size_t(pcap) * 8) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "pair list"));
+      T.pairs = static_cast<int32_t*>(ctx->tt_pairs.p);
+      T.pair_cap = pcap;
+      T.pair_count = P.count;
+      e = cudaMemsetAsync(P.count, 0, 8, ctx->stream);
+      if (e == cudaSuccess) e = launch_tt_cone_pairs(T, ctx->num_sms, ctx->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&np, P.count, 8, cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "tt cone pairs"));
+      if (int64_t(np) <= pcap) break;
+      pcap = int64_t(np);
+    }
+    int64_t cap = std::max<int64_t>(int64_t(ch->buf.bytes / 12), qv.n * 64 + 4096);
+    unsigned long long nc2 = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (ch->buf.ensure(size_t(cap) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+      T.out = static_cast<int32_t*>(ch->buf.p);
+      T.cap = cap;
+      T.count = P.count;
+      e = cudaMemsetAsync(P.count, 0, 8, ctx->stream);
+      if (e == cudaSuccess) e = launch_tt_cone_chains(T, int64_t(np), ctx->num_sms, ctx->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&nc2, P.count, 8, cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "tt cone chains"));
+      if (int64_t(nc2) <= cap) break;
+      cap = int64_t(nc2);
+    }
+    ch->n = int64_t(nc2);
+    ch->n_k2 = int64_t(nc2);
   } else if (opts->mode == SPOLY_CHAINS_CONE) {
     if (ctx->boxes.ensure(size_t(P.tri_count) * 12 * sizeof(float)) != cudaSuccess ||
         ctx->flag.ensure(16) != cudaSuccess)
@@ -658,6 +715,8 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
     out->unsolved = int64_t(t[TT_TOO_LARGE]);
     out->fallback += int64_t(t[TT_RESAMPLED]);
     out->k2_systems = int64_t(t[TT_SYSTEMS]);
+    out->k2_evals = int64_t(t[TT_EVALS]);
+    out->k2_eval_n3 = int64_t(t[TT_EVAL_N3]);
   }
   return SPOLY_OK;
 }

@@ -351,4 +351,167 @@ cudaError_t launch_chains_cone(const ChainParams& P, int num_sms, cudaStream_t s
   return cudaGetLastError();
 }
 
+namespace {
+
+// ------------------------------------------------ 2-bounce (TT) cone cull
+// For chains x0 -> T1 -> T2 -> x3 of two refractions.  Every path's segment
+// direction unit(x2 - x1) lies in (i) T1's refracted-direction box from x0
+// (forward), (ii) the unit box from T1's bounding box toward T2's, and
+// (iii) the negated refracted-direction box of T2 seen from x3 with the
+// indices swapped (backward: light from x3 refracted into the slab), which
+// also points from T2's bounding box toward T1's.  Pairs failing any of
+// these are dropped; (i) and (ii) do not depend on the receiver.
+
+// Forward boxes of the first range: [n1][12] as tri_boxes_kernel writes.
+__global__ void tt_fwd_boxes_kernel(TTConeParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.n1) return;
+  const int t = P.t1_begin + i;
+  const d3 x0 = mk(P.qv.x_first[0], P.qv.x_first[1], P.qv.x_first[2]);
+  Iv3 o, bb;
+  bool empty = false;
+  const bool ok = out_box(P.mesh, t, x0, SPOLY_T, P.qv.eta[0], P.qv.eta[1], o, bb, empty);
+  float* B = P.fwd + int64_t(i) * 12;
+  const Iv comps[3] = {o.x, o.y, o.z};
+  const Iv bcomp[3] = {bb.x, bb.y, bb.z};
+  for (int c = 0; c < 3; ++c) {
+    const Iv w = widen(comps[c], P.margin);
+    B[c] = empty ? 2.f : (ok ? __double2float_rd(w.lo) : -1.f);
+    B[3 + c] = empty ? -2.f : (ok ? __double2float_ru(w.hi) : 1.f);
+    B[6 + c] = __double2float_rd(bcomp[c].lo);
+    B[9 + c] = __double2float_ru(bcomp[c].hi);
+  }
+}
+
+// Pairs (T1, T2) that pass (i) and (ii).
+__global__ void tt_pairs_kernel(TTConeParams P) {
+  const int64_t n = int64_t(P.n1) * P.n2;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t c = base + lane;
+    bool keep = false;
+    int i = 0, j = 0;
+    if (c < n) {
+      i = int(c / P.n2);
+      j = int(c % P.n2);
+      const int t2 = P.t2_begin + j;
+      float lo[3], hi[3];
+      for (int k = 0; k < 3; ++k) {
+        const double a = P.mesh.tri[int64_t(k) * P.mesh.n_tris + t2], b = P.mesh.tri[int64_t(3 + k) * P.mesh.n_tris + t2],
+                     d = P.mesh.tri[int64_t(6 + k) * P.mesh.n_tris + t2];
+        lo[k] = __double2float_rd(fmin(a, fmin(b, d)));
+        hi[k] = __double2float_ru(fmax(a, fmax(b, d)));
+      }
+      keep = box_overlaps(P.fwd + int64_t(i) * 12, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) continue;
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(P.pair_count, (unsigned long long)__popc(m));
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (keep) {
+      const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
+      if (idx < (unsigned long long)P.pair_cap) {
+        P.pairs[2 * idx] = i;
+        P.pairs[2 * idx + 1] = j;
+      }
+    }
+  }
+}
+
+// Per (query, pair): the backward box of T2 from x3 (iii); survivors are the
+// chains.  One FP64 interval evaluation per (query, T2) is recomputed per
+// pair; pairs of one T2 are rare enough that this is not the bottleneck.
+__global__ void tt_cone_chains_kernel(TTConeParams P, int64_t n_pairs) {
+  const int64_t n = P.qv.n * n_pairs;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t c = base + lane;
+    bool keep = false;
+    int64_t q = 0;
+    int i = 0, j = 0;
+    if (c < n) {
+      q = c / n_pairs;
+      const int64_t f = c % n_pairs;
+      i = P.pairs[2 * f];
+      j = P.pairs[2 * f + 1];
+      const int t2 = P.t2_begin + j;
+      const d3 x3 = mk(P.qv.x_last[3 * q], P.qv.x_last[3 * q + 1], P.qv.x_last[3 * q + 2]);
+      Iv3 o, bb;
+      bool empty = false;
+      const bool ok = out_box(P.mesh, t2, x3, SPOLY_T, P.qv.eta[3 * q + 2], P.qv.eta[3 * q + 1], o, bb, empty);
+      if (empty) {
+        keep = false;
+      } else if (!ok) {
+        keep = true;
+      } else {
+        float B[12];
+        const Iv comps[3] = {o.x, o.y, o.z};
+        const Iv bcomp[3] = {bb.x, bb.y, bb.z};
+        for (int k = 0; k < 3; ++k) {
+          const Iv w = widen(comps[k], P.margin);
+          B[k] = __double2float_rd(w.lo);
+          B[3 + k] = __double2float_ru(w.hi);
+          B[6 + k] = __double2float_rd(bcomp[k].lo);
+          B[9 + k] = __double2float_ru(bcomp[k].hi);
+        }
+        const float* F = P.fwd + int64_t(i) * 12;
+        // backward directions (from T2 toward T1) against T1's bounding box
+        keep = box_overlaps(B, F[6], F[9], F[7], F[10], F[8], F[11]);
+        // negated backward box against the forward box
+        for (int k = 0; k < 3 && keep; ++k) keep = (-B[3 + k] <= F[3 + k]) && (F[k] <= -B[k]);
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) continue;
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(P.count, (unsigned long long)__popc(m));
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (keep) {
+      const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
+      if (idx < (unsigned long long)P.cap) {
+        P.out[3 * idx] = int32_t(q);
+        P.out[3 * idx + 1] = P.t1_begin + i;
+        P.out[3 * idx + 2] = P.t2_begin + j;
+      }
+    }
+  }
+}
+
+// Queries must share x0, the IORs and the types T T (all k = 2).
+__global__ void tt_shared_kernel(QueryView Q, int32_t* flag) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < Q.n; q += stride) {
+    bool same = true;
+    for (int c = 0; c < 3; ++c) same &= Q.x_first[3 * q + c] == Q.x_first[c] && Q.eta[3 * q + c] == Q.eta[c];
+    same &= Q.types[2 * q] == SPOLY_T && Q.types[2 * q + 1] == SPOLY_T && Q.k[q] == 2;
+    if (!same) atomicExch(flag, 0);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tt_cone_shared(const TTConeParams& P, int32_t* flag, int num_sms, cudaStream_t st, int32_t* host) {
+  set_flag_kernel<<<1, 1, 0, st>>>(flag, 1);
+  tt_shared_kernel<<<num_sms * 4, 256, 0, st>>>(P.qv, flag);
+  cudaError_t e = cudaMemcpyAsync(host, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+cudaError_t launch_tt_cone_pairs(const TTConeParams& P, int num_sms, cudaStream_t st) {
+  tt_fwd_boxes_kernel<<<(P.n1 + 127) / 128, 128, 0, st>>>(P);
+  tt_pairs_kernel<<<num_sms * 8, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tt_cone_chains(const TTConeParams& P, int64_t n_pairs, int num_sms, cudaStream_t st) {
+  if (n_pairs <= 0) return cudaSuccess;
+  tt_cone_chains_kernel<<<num_sms * 16, 256, 0, st>>>(P, n_pairs);
+  return cudaGetLastError();
+}
+
+
 }  // namespace spoly

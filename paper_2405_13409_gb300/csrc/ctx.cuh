@@ -40,6 +40,7 @@ struct spoly_ctx {
   spoly::DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
   spoly::DevBuf boxes, flag;                    // cone cull scratch
   spoly::DevBuf cam, bounds, fp_scratch, fp_entries, fp_boxes;  // footprint builder
+  spoly::DevBuf tt_pairs;                // 2-bounce cone: receiver-independent pairs
 };
 
 struct spoly_chains {
@@ -63,7 +64,7 @@ struct spoly_solution_set {
   bool timed = false;
   // 2-bounce chains: partitioned lists, systems, per-batch scratch
   spoly::DevBuf part, part_n, tt_counters, tt_chain_sys, tt_masks, tt_sys, tt_scratch, tt_coef32, tt_queue;
-  unsigned long long tt_host[16] = {0};
+  unsigned long long tt_host[16] = {0};  // TT_COUNT <= 16
   int64_t n_k2 = 0;
 };
 

@@ -48,6 +48,25 @@ cudaError_t launch_chains_explicit(const ChainParams& P, const int32_t* src, int
                                    cudaStream_t st);
 cudaError_t launch_chains_cone(const ChainParams& P, int num_sms, cudaStream_t st);
 
+// Cone cull of 2-bounce refraction chains (first triangle in
+// [t1_begin, t1_begin + n1), second in [t2_begin, t2_begin + n2)).
+struct TTConeParams {
+  MeshView mesh;
+  QueryView qv;
+  int32_t t1_begin, n1, t2_begin, n2;
+  double margin;
+  float* fwd;                 // [n1][12]
+  int32_t* pairs;             // [pair_cap][2] local indices
+  int64_t pair_cap;
+  unsigned long long* pair_count;
+  int32_t* out;               // [cap][3]
+  int64_t cap;
+  unsigned long long* count;
+};
+cudaError_t launch_tt_cone_shared(const TTConeParams& P, int32_t* flag, int num_sms, cudaStream_t st, int32_t* host);
+cudaError_t launch_tt_cone_pairs(const TTConeParams& P, int num_sms, cudaStream_t st);
+cudaError_t launch_tt_cone_chains(const TTConeParams& P, int64_t n_pairs, int num_sms, cudaStream_t st);
+
 // Pixel-footprint builder (footprint.cu).
 struct FpGrid {
   double x0, y0, cell;

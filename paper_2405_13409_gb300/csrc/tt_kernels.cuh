@@ -18,8 +18,11 @@ enum TTCounter {
   TT_ADMISSIBLE,    // paths written
   TT_FLAGGED,       // with SPOLY_FLAG_ILL_COND
   TT_RESAMPLED,     // systems whose FP32 signs changed too often, sampled again in FP64
+  TT_EVALS,         // Bezout determinant evaluations (samples + bisection steps)
+  TT_EVAL_N3,       // sum over evaluations of n^3 (work model of the sign kernel)
   TT_COUNT
 };
+static_assert(TT_COUNT <= 16, "the solution set keeps 16 host copies of the TT counters");
 
 constexpr uint32_t kTTResample = 1u << 29;  // TTSys flag: sample again in FP64
 

@@ -17,6 +17,7 @@ struct SignSmem {
   float lg[kMaxSamples];
   T blo[kMaxBrackets], bhi[kMaxBrackets];
   int8_t bs[kMaxBrackets];
+  int bm[kMaxBrackets];  // sample index of the bracket's left end
   uint32_t bfl[kMaxBrackets];
   float wmax[kSignWarps];
   int nb;
@@ -77,6 +78,7 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
         S.bhi[k] = hi;
         S.bs[k] = int8_t(s0);
         S.bfl[k] = 0u;
+        S.bm[k] = m;
       }
     }
   }
@@ -117,7 +119,14 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
         float la, lb;
         sign_t<T, N>(S, lo, sy, warp, lane, &la);
         sign_t<T, N>(S, hi, sy, warp, lane, &lb);
-        const float top = fmaxf(la, lb) - S.lmax;
+        // reading 7 (k = 2), normalised by the largest |det| of the five
+        // samples around the bracket
+        float lloc = -1e30f;
+        for (int o = -2; o <= 3; ++o) {
+          const int mm = min(max(S.bm[k] + o, 0), NI);
+          if (S.sgn[mm] != 0) lloc = fmaxf(lloc, S.lg[mm]);
+        }
+        const float top = fmaxf(la, lb) - lloc;
         const float rel = top + log2f(1.0f + exp2f(fminf(la, lb) - fmaxf(la, lb)));
         if (lane == 0 && rel < log2f(float(kTTIllCond))) S.bfl[k] = SPOLY_FLAG_ILL_COND;
       }
@@ -129,6 +138,10 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
   }
   __syncthreads();
   if (tid == 0) {
+    unsigned long long ev = (unsigned long long)(NI + 1);
+    for (int k = 0; k < nb; ++k) ev += (S.blo[k] < S.bhi[k]) ? kTTPaperIters + 2 : 0;
+    atomicAdd(P.counters + TT_EVALS, ev);
+    atomicAdd(P.counters + TT_EVAL_N3, ev * (unsigned long long)(sy.n * sy.n * sy.n));
     S.base = int(atomicAdd(P.counters + TT_BRACKETS, (unsigned long long)nb));
     sy.first_item = S.base;
     sy.n_items = nb;

@@ -209,3 +209,44 @@ def test_mixed_one_and_two_bounce_lists(ctx):
     ctx.spoly_chains_free(ch)
     assert sorted(map(tuple, np.round(one["uv"][:, :2], 9).tolist())) == \
         sorted(map(tuple, np.round(ref1["uv"][:, :2], 9).tolist()))
+
+
+def _slab_queries(s, x3s):
+    n = x3s.shape[0]
+    xf = np.tile(s.x_first[0], (n, 1))
+    return (xf, np.ascontiguousarray(x3s), np.tile([1.0, 1.5, 1.0], (n, 1)),
+            np.full((n, 2), binding.SPOLY_T, np.int32), np.full(n, 2, np.int32))
+
+
+def test_tt_cone_keeps_planted_and_exhaustive_paths(ctx):
+    """The 2-bounce cone cull over the slab keeps every planted pair and every
+    pair with a path in an exhaustive solve of four receivers (all 262,144
+    (top, bottom) pairs each)."""
+    cases = planted_slab_cases(14, 4)
+    s = scenes.slab_scene(seed=0, n_cells=16, n_recv=4)
+    half = s.n_tris // 2
+    x3s = np.array([c[1] for c in cases])
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (s.tri, *_slab_queries(s, x3s))]
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_CONE, margin=1e-3, tri_range=(0, half),
+                                second_range=(half, s.n_tris))
+    kept = ctx.spoly_chains_copy(ch)
+    ctx.spoly_chains_free(ch)
+    keys = set(map(tuple, kept.tolist()))
+    for i, c in enumerate(cases):
+        assert (i, c[2], c[3]) in keys
+    # exhaustive: every (top, bottom) pair for each receiver
+    t1 = np.repeat(np.arange(half), half)
+    t2 = np.tile(np.arange(half, s.n_tris), half)
+    allc = np.concatenate([np.stack([np.full(t1.size, i), t1, t2], -1) for i in range(len(cases))]).astype(np.int32)
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=allc)
+    sol = ctx.spoly_solve(mesh, q, ch, precision=binding.MIXED, sqrt_table=_table())
+    paths = ctx.spoly_paths(sol)
+    stats = ctx.spoly_stats(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    print("tt cone: kept", kept.shape[0], "of", allc.shape[0], "exhaustive paths", paths.size, stats)
+    assert paths.size >= len(cases)
+    for p in paths:
+        assert (int(p["query"]), int(p["tri"][0]), int(p["tri"][1])) in keys, p
+    assert kept.shape[0] < 0.05 * allc.shape[0]
