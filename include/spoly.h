@@ -136,6 +136,13 @@ typedef struct {
                               FP32 Laplace + isolation; FP64 polish and checks */
 #define SPOLY_SOLVE_ASYNC 1  /* do not synchronise or read counters back */
 #define SPOLY_SOLVE_TIMING 2 /* record CUDA events around the solve's phases */
+#define SPOLY_SOLVE_PERSISTENT 4 /* 1-bounce isolation as one persistent grid whose warps take chunks of
+                                    chains from a global ticket counter (launch shape: spoly_autotune's
+                                    choice, else 128 threads, 4 blocks per SM, 64 chains per ticket) */
+#define SPOLY_SOLVE_GRAPH 8  /* lists without 2-bounce chains: the solve's launches are captured once
+                                into a CUDA graph and replayed while the chain list, buffers and
+                                options stay the same (needs a non-default stream); a replay whose
+                                queues or path buffer overflow falls back to the staged solve */
 
 typedef struct {
   int32_t precision;       /* SPOLY_PLAIN_FP64 or SPOLY_MIXED */
@@ -269,6 +276,26 @@ spoly_status spoly_phase_ms(spoly_ctx* ctx, const spoly_solution_set* set, float
 #define SPOLY_PEAK_FP32_FMA 0
 #define SPOLY_PEAK_FP64_FMA 1
 spoly_status spoly_measure_peak(spoly_ctx* ctx, int32_t kind, double* tflops);
+
+/* One measured launch shape of the persistent 1-bounce isolation kernel. */
+typedef struct {
+  int32_t block;         /* threads per block (64 or 128) */
+  int32_t blocks_per_sm; /* requested resident blocks per SM (capped by occupancy) */
+  int32_t chunk;         /* chains per work-queue ticket */
+  float ms;              /* best of three timed launches on the given chains */
+} spoly_tune_entry;
+
+/* Autotuner of the persistent isolation kernel (north star (2)): times
+ * every shape of block in {64, 128} x blocks per SM in {1, 2, 4, 8} x chunk
+ * in {32, 64, 128, 256} on the 1-bounce chains of `chains` (precision
+ * SPOLY_MIXED or SPOLY_PLAIN_FP64), keeps the fastest in the context for
+ * later SPOLY_SOLVE_PERSISTENT solves, and writes it to *best (may be NULL)
+ * and up to `cap` entries to table (host, may be NULL; *n_table receives
+ * the number of shapes).  Allocates and frees its scratch.  Errors: EINVAL
+ * (no 1-bounce chains), ENOMEM, ECUDA. */
+spoly_status spoly_autotune(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
+                            const spoly_chains* chains, int32_t precision, spoly_tune_entry* table, int32_t cap,
+                            int32_t* n_table, spoly_tune_entry* best);
 
 /* Frees a solution set. */
 spoly_status spoly_solution_free(spoly_solution_set* set);

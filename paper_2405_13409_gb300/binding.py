@@ -44,6 +44,8 @@ PLAIN_FP64 = 0
 MIXED = 1
 SOLVE_ASYNC = 1
 SOLVE_TIMING = 2
+SOLVE_PERSISTENT = 4
+SOLVE_GRAPH = 8
 PEAK_FP32_FMA = 0
 PEAK_FP64_FMA = 1
 MLP_FEATURES = 24
@@ -86,6 +88,10 @@ class spoly_counters(ctypes.Structure):
                                        "polish_lost", "u_roots", "admissible", "flagged", "fallback",
                                        "unsolved", "k2_systems", "k2_evals", "k2_eval_n3")] + \
                [("reserved", c_int64 * 2)]
+
+
+class spoly_tune_entry(ctypes.Structure):
+    _fields_ = [("block", c_int32), ("blocks_per_sm", c_int32), ("chunk", c_int32), ("ms", ctypes.c_float)]
 
 
 class spoly_mlp_train_opts(ctypes.Structure):
@@ -152,6 +158,9 @@ def load():
                                  ctypes.POINTER(ctypes.c_double)], c_int32),
         "spoly_gate": ([P, P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P, ctypes.c_float,
                         ctypes.POINTER(P)], c_int32),
+        "spoly_autotune": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P, c_int32,
+                            ctypes.POINTER(spoly_tune_entry), c_int32, ctypes.POINTER(c_int32),
+                            ctypes.POINTER(spoly_tune_entry)], c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -302,6 +311,17 @@ class Context:
         t = ctypes.c_double()
         self.check(self.lib.spoly_measure_peak(self.h, int(kind), ctypes.byref(t)), "spoly_measure_peak")
         return float(t.value)
+
+    def spoly_autotune(self, mesh: spoly_mesh, q: spoly_queries, chains, precision: int = MIXED):
+        """Times the persistent isolation kernel's launch shapes on `chains`
+        and keeps the fastest in the context.  Returns (best, table)."""
+        tab = (spoly_tune_entry * 64)()
+        n = c_int32()
+        best = spoly_tune_entry()
+        self.check(self.lib.spoly_autotune(self.h, ctypes.byref(mesh), ctypes.byref(q), chains, int(precision), tab, 64,
+                                           ctypes.byref(n), ctypes.byref(best)), "spoly_autotune")
+        rows = [(t.block, t.blocks_per_sm, t.chunk, float(t.ms)) for t in tab[:n.value]]
+        return (best.block, best.blocks_per_sm, best.chunk, float(best.ms)), rows
 
     # ------------------------------------------------------------ gate
     def spoly_mlp_create(self, seed: int = 0):

@@ -605,6 +605,74 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     if (r == cudaSuccess) r = cudaStreamSynchronize(ctx->stream);
     return r;
   };
+  const bool persistent = (opts->flags & SPOLY_SOLVE_PERSISTENT) != 0;
+  auto isolate = [&]() -> cudaError_t {
+    return persistent ? launch_k1_isolate_persistent(P, opts->precision, ctx->num_sms, ctx->tune, ctx->stream)
+                      : launch_k1_isolate(P, opts->precision, ctx->num_sms, ctx->stream);
+  };
+  // Graph mode (1-bounce lists): replay the captured launch sequence when
+  // everything it baked in is unchanged; otherwise capture it again.
+  if ((opts->flags & SPOLY_SOLVE_GRAPH) && n2 == 0 && n1 > 0) {
+    if (!ctx->stream) return bail(fail(ctx, SPOLY_EINVAL, "graph mode needs a non-default stream"));
+    bind();
+    uint64_t key[24] = {0};
+    const void* ptrs[] = {P.chains, P.queue, P.side, P.paths, P.counters, mv.tri, qv.x_first, qv.x_last, qv.eta,
+                          qv.types, qv.k};
+    for (int i = 0; i < 11; ++i) key[i] = uint64_t(reinterpret_cast<uintptr_t>(ptrs[i]));
+    key[11] = uint64_t(n1);
+    key[12] = uint64_t(P.queue_cap);
+    key[13] = uint64_t(P.side_cap);
+    key[14] = uint64_t(P.path_cap);
+    key[15] = uint64_t(opts->precision) | (uint64_t(persistent) << 8) | (uint64_t(P.pix.on) << 9);
+    key[16] = uint64_t(ctx->tune.block) | (uint64_t(ctx->tune.blocks_per_sm) << 16) | (uint64_t(ctx->tune.chunk) << 32);
+    key[17] = uint64_t(mv.n_tris);
+    key[18] = uint64_t(qv.n);
+    std::memcpy(&key[19], &P.pix.th, sizeof(double));
+    std::memcpy(&key[20], &P.pix.o[0], sizeof(double));
+    key[21] = uint64_t(reinterpret_cast<uintptr_t>(ctx->stream));
+    if (!set->gexec || std::memcmp(key, set->gkey, sizeof(key)) != 0) {
+      if (set->gexec) cudaGraphExecDestroy(set->gexec);
+      set->gexec = nullptr;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "graph capture"));
+      cudaError_t ec = cudaMemsetAsync(set->counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
+      if (ec == cudaSuccess) ec = isolate();
+      if (ec == cudaSuccess) ec = launch_k1_polish(P, ctx->num_sms, ctx->stream);
+      if (ec == cudaSuccess) ec = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+      e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (ec != cudaSuccess) e = ec;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&set->gexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        set->gexec = nullptr;
+        return bail(cuda_fail(ctx, e, "graph capture"));
+      }
+      std::memcpy(set->gkey, key, sizeof(key));
+    }
+    if (timing) cudaEventRecord(set->ev[0], ctx->stream);
+    e = cudaGraphLaunch(set->gexec, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "graph launch"));
+    if (timing) {
+      cudaEventRecord(set->ev[1], ctx->stream);
+      cudaEventRecord(set->ev[2], ctx->stream);
+      cudaEventRecord(set->ev[3], ctx->stream);
+    }
+    if (async) {
+      *inout = set;
+      return SPOLY_OK;
+    }
+    e = read_counters();
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "graph solve"));
+    if (int64_t(set->host[C_QUEUED]) <= set->queue_cap && int64_t(set->host[C_SIDE]) <= set->side_cap &&
+        int64_t(set->host[C_ADMISSIBLE]) <= set->path_cap) {
+      set->host_valid = true;
+      *inout = set;
+      return SPOLY_OK;
+    }
+    // a queue or the path buffer overflowed: the staged solve below grows them
+    // (and the next graph call captures again)
+  }
   // Stage 1: isolation.  Re-run (only in synchronous mode) until the bracket
   // queue and the side queue hold every item; each re-run grows them to the
   // exact counts, so two passes suffice.
@@ -614,7 +682,7 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
     if (timing) cudaEventRecord(set->ev[0], ctx->stream);
     if (n1 > 0) {
-      e = launch_k1_isolate(P, opts->precision, ctx->num_sms, ctx->stream);
+      e = isolate();
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_isolate"));
     }
     if (timing) cudaEventRecord(set->ev[1], ctx->stream);
@@ -771,6 +839,79 @@ spoly_status spoly_measure_peak(spoly_ctx* ctx, int32_t kind, double* tflops) {
   return SPOLY_OK;
 }
 
+spoly_status spoly_autotune(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, const spoly_chains* chains,
+                            int32_t precision, spoly_tune_entry* table, int32_t cap, int32_t* n_table,
+                            spoly_tune_entry* best) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!chains || (cap > 0 && !table)) return fail(ctx, SPOLY_EINVAL, "autotune: bad arguments");
+  if (precision != SPOLY_PLAIN_FP64 && precision != SPOLY_MIXED) return fail(ctx, SPOLY_EINVAL, "autotune: precision");
+  if (chains->n_k2 > 0) return fail(ctx, SPOLY_EINVAL, "autotune: the chain list holds 2-bounce chains");
+  if (chains->n <= 0) return fail(ctx, SPOLY_EINVAL, "autotune: no chains");
+  CK(cudaSetDevice(ctx->device), "set device");
+  MeshView mv;
+  QueryView qv;
+  spoly_status st = stage_inputs(ctx, mesh, q, &mv, &qv);
+  if (st != SPOLY_OK) return st;
+  const int64_t n = chains->n;
+  DevBuf counters, queue, side;
+  const int64_t qcap = n / 2 + 4096, scap = n / 16 + 1024;
+  CK(counters.ensure(C_COUNT * sizeof(unsigned long long)), "autotune scratch");
+  CK(queue.ensure(size_t(qcap) * sizeof(RootItem)), "autotune scratch");
+  CK(side.ensure(size_t(scap) * sizeof(int32_t)), "autotune scratch");
+  K1Params P{};
+  P.mesh = mv;
+  P.qv = qv;
+  P.chains = static_cast<const int32_t*>(chains->buf.p);
+  P.n_chains = n;
+  P.counters = static_cast<unsigned long long*>(counters.p);
+  P.queue = static_cast<RootItem*>(queue.p);
+  P.queue_cap = qcap;
+  P.side = static_cast<int32_t*>(side.p);
+  P.side_cap = scap;
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a), "autotune events");
+  CK(cudaEventCreate(&b), "autotune events");
+  spoly_tune_entry top{0, 0, 0, 3.0e38f};
+  int32_t k = 0;
+  cudaError_t e = cudaSuccess;
+  for (int block : {64, 128})
+    for (int bps : {1, 2, 4, 8})
+      for (int chunk : {32, 64, 128, 256}) {
+        K1Launch cfg;
+        cfg.block = block;
+        cfg.blocks_per_sm = bps;
+        cfg.chunk = chunk;
+        float bestms = 3.0e38f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first run warms up
+          e = cudaMemsetAsync(counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
+          if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
+          if (e == cudaSuccess) e = launch_k1_isolate_persistent(P, precision, ctx->num_sms, cfg, ctx->stream);
+          if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(b);
+          float ms = 0.0f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+          if (rep > 0) bestms = std::min(bestms, ms);
+        }
+        if (e != cudaSuccess) break;
+        const spoly_tune_entry ent{block, bps, chunk, bestms};
+        if (k < cap) table[k] = ent;
+        ++k;
+        if (bestms < top.ms) top = ent;
+      }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  counters.release();
+  queue.release();
+  side.release();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+  ctx->tune.block = top.block;
+  ctx->tune.blocks_per_sm = top.blocks_per_sm;
+  ctx->tune.chunk = top.chunk;
+  if (n_table) *n_table = k;
+  if (best) *best = top;
+  return SPOLY_OK;
+}
+
 spoly_status spoly_solution_free(spoly_solution_set* set) {
   if (!set) return SPOLY_EINVAL;
   for (auto& ev : set->ev)
@@ -782,6 +923,7 @@ spoly_status spoly_solution_free(spoly_solution_set* set) {
   for (DevBuf* b : {&set->part, &set->part_n, &set->tt_counters, &set->tt_chain_sys, &set->tt_masks, &set->tt_sys,
                     &set->tt_scratch, &set->tt_coef32, &set->tt_queue})
     b->release();
+  if (set->gexec) cudaGraphExecDestroy(set->gexec);
   delete set;
   return SPOLY_OK;
 }

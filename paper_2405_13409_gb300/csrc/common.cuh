@@ -188,6 +188,7 @@ enum Counter {
   C_PATHS_WRITTEN,
   C_QUEUE_OVERFLOW,
   C_SIDE,         // chains sent to the generic-size kernel
+  C_TICKET,       // work-queue ticket of the persistent isolation kernel
   C_COUNT
 };
 

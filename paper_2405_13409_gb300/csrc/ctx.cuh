@@ -6,6 +6,7 @@
 #include <cstddef>
 
 #include "common.cuh"
+#include "k1.cuh"
 
 namespace spoly {
 
@@ -41,6 +42,7 @@ struct spoly_ctx {
   spoly::DevBuf boxes, flag;                    // cone cull scratch
   spoly::DevBuf cam, bounds, fp_scratch, fp_entries, fp_boxes;  // footprint builder
   spoly::DevBuf tt_pairs;                // 2-bounce cone: receiver-independent pairs
+  spoly::K1Launch tune;                  // persistent isolation launch shape (spoly_autotune)
 };
 
 struct spoly_chains {
@@ -66,6 +68,9 @@ struct spoly_solution_set {
   spoly::DevBuf part, part_n, tt_counters, tt_chain_sys, tt_masks, tt_sys, tt_scratch, tt_coef32, tt_queue;
   unsigned long long tt_host[16] = {0};  // TT_COUNT <= 16
   int64_t n_k2 = 0;
+  // captured 1-bounce solve (SPOLY_SOLVE_GRAPH) and the inputs it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t gkey[24] = {0};
 };
 
 namespace spoly {

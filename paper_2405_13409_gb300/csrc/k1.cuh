@@ -26,6 +26,16 @@ struct K1Params {
 cudaError_t launch_partition(const int32_t* chains, int64_t n, int32_t* k1, int32_t* k1_ids, int32_t* k2,
                              int32_t* k2_ids, unsigned long long* counts, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st);
+// Launch shape of the persistent isolation kernel (block size 32..128, a
+// multiple of 32; resident blocks per SM, capped by occupancy; chains per
+// ticket, a multiple of 32).  counters[C_TICKET] must start at zero.
+struct K1Launch {
+  int block = 128;
+  int blocks_per_sm = 4;
+  int chunk = 64;
+};
+cudaError_t launch_k1_isolate_persistent(const K1Params& P, int precision, int num_sms, const K1Launch& cfg,
+                                         cudaStream_t st);
 cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st);
 cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st);
 

@@ -154,49 +154,75 @@ SPOLY_D bool flat_shaded(const TriD& tr) {
 }
 
 #ifndef SPOLY_HOST_BUILD
+// Isolation of the 32 chains [base, base + 32) by one warp: per-chain
+// numerics, then warp-aggregated counters and appends.  All lanes call it.
+template <typename T>
+SPOLY_D void isolate_warp(const K1Params& P, int64_t base, int lane) {
+  const int64_t c = base + lane;
+  RootItem items[kRD + 1];
+  int nq = 0;
+  unsigned n_v = 0, n_pref = 0, n_deg = 0, n_cand = 0, n_side = 0;
+  if (c < P.n_chains) {
+    const int q = __ldg(P.chains + 3 * c);
+    const int t = __ldg(P.chains + 3 * c + 1);
+    if (__ldg(P.qv.k + q) == 1) {
+      n_cand = 1;
+      const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
+      const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
+      int r = 0;
+      if (qd.type == SPOLY_R) {
+        K1Sys<4> s;
+        r = k1_system<4>(tr, qd, s) ? k1_isolate_dispatch<T, 4>(s, items, int(c), n_v, n_pref) : -1;
+      } else {
+        K1Sys<6> s;
+        r = k1_system<6>(tr, qd, s) ? k1_isolate_dispatch<T, 6>(s, items, int(c), n_v, n_pref) : -1;
+      }
+      if (sizeof(T) == 4 && r != -1 && flat_shaded(tr)) {
+        r = -2;  // the FP32 brackets are discarded; the side kernel re-isolates in FP64
+        n_v = n_pref = 0;
+      }
+      if (r == -1) n_deg = 1;
+      if (r == -2) n_side = 1;
+      nq = r > 0 ? r : 0;
+    }
+  }
+  warp_count(P.counters + C_CANDIDATES, n_cand);
+  warp_count(P.counters + C_DEGENERATE, n_deg);
+  warp_count(P.counters + C_VROOTS, n_v);
+  warp_count(P.counters + C_PREFILTERED, n_pref);
+  const unsigned long long sslot = warp_append(P.counters + C_SIDE, n_side);
+  if (n_side && sslot < (unsigned long long)P.side_cap) P.side[sslot] = int32_t(c);
+  const unsigned long long slot = warp_append(P.counters + C_QUEUED, unsigned(nq));
+  for (int k = 0; k < nq; ++k) {
+    const unsigned long long idx = slot + k;
+    if (idx < (unsigned long long)P.queue_cap) P.queue[idx] = items[k];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < P.n_chains; base += stride) {
-    const int64_t c = base + lane;
-    RootItem items[kRD + 1];
-    int nq = 0;
-    unsigned n_v = 0, n_pref = 0, n_deg = 0, n_cand = 0, n_side = 0;
-    if (c < P.n_chains) {
-      const int q = __ldg(P.chains + 3 * c);
-      const int t = __ldg(P.chains + 3 * c + 1);
-      if (__ldg(P.qv.k + q) == 1) {
-        n_cand = 1;
-        const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
-        const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
-        int r = 0;
-        if (qd.type == SPOLY_R) {
-          K1Sys<4> s;
-          r = k1_system<4>(tr, qd, s) ? k1_isolate_dispatch<T, 4>(s, items, int(c), n_v, n_pref) : -1;
-        } else {
-          K1Sys<6> s;
-          r = k1_system<6>(tr, qd, s) ? k1_isolate_dispatch<T, 6>(s, items, int(c), n_v, n_pref) : -1;
-        }
-        if (sizeof(T) == 4 && r != -1 && flat_shaded(tr)) {
-          r = -2;  // the FP32 brackets are discarded; the side kernel re-isolates in FP64
-          n_v = n_pref = 0;
-        }
-        if (r == -1) n_deg = 1;
-        if (r == -2) n_side = 1;
-        nq = r > 0 ? r : 0;
-      }
-    }
-    warp_count(P.counters + C_CANDIDATES, n_cand);
-    warp_count(P.counters + C_DEGENERATE, n_deg);
-    warp_count(P.counters + C_VROOTS, n_v);
-    warp_count(P.counters + C_PREFILTERED, n_pref);
-    const unsigned long long sslot = warp_append(P.counters + C_SIDE, n_side);
-    if (n_side && sslot < (unsigned long long)P.side_cap) P.side[sslot] = int32_t(c);
-    const unsigned long long slot = warp_append(P.counters + C_QUEUED, unsigned(nq));
-    for (int k = 0; k < nq; ++k) {
-      const unsigned long long idx = slot + k;
-      if (idx < (unsigned long long)P.queue_cap) P.queue[idx] = items[k];
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < P.n_chains; base += stride)
+    isolate_warp<T>(P, base, lane);
+}
+
+// Persistent variant: a fixed grid whose warps take `chunk` chains at a time
+// from a global ticket counter (counters[C_TICKET]) until the list is
+// exhausted, so chains of uneven cost (Bezout sizes, root counts, the FP64
+// side path) balance across the GPU.
+template <typename T>
+__global__ void __launch_bounds__(128) k1_isolate_persistent_kernel(K1Params P, int chunk) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(P.counters + C_TICKET, (unsigned long long)chunk);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b >= (unsigned long long)P.n_chains) break;
+    for (int sub = 0; sub < chunk; sub += 32) {
+      const int64_t base = int64_t(b) + sub;
+      if (base >= P.n_chains) break;
+      isolate_warp<T>(P, base, lane);
     }
   }
 }

@@ -108,6 +108,23 @@ cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cud
   return launch_k1_generic(P, num_sms, st);
 }
 
+cudaError_t launch_k1_isolate_persistent_f32(const K1Params& P, int grid, int block, int chunk, cudaStream_t st);
+cudaError_t launch_k1_isolate_persistent_f64(const K1Params& P, int grid, int block, int chunk, cudaStream_t st);
+int k1_isolate_persistent_f32_blocks_per_sm(int block);
+int k1_isolate_persistent_f64_blocks_per_sm(int block);
+
+cudaError_t launch_k1_isolate_persistent(const K1Params& P, int precision, int num_sms, const K1Launch& cfg,
+                                         cudaStream_t st) {
+  const bool f64 = precision == SPOLY_PLAIN_FP64;
+  const int occ = f64 ? k1_isolate_persistent_f64_blocks_per_sm(cfg.block) : k1_isolate_persistent_f32_blocks_per_sm(cfg.block);
+  const int bps = std::max(1, std::min(cfg.blocks_per_sm, occ));
+  const int grid = num_sms * bps;
+  cudaError_t e = f64 ? launch_k1_isolate_persistent_f64(P, grid, cfg.block, cfg.chunk, st)
+                      : launch_k1_isolate_persistent_f32(P, grid, cfg.block, cfg.chunk, st);
+  if (e != cudaSuccess) return e;
+  return launch_k1_generic(P, num_sms, st);
+}
+
 cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st) {
   k1_polish_kernel<<<num_sms * 8, 128, 0, st>>>(P);
   return cudaGetLastError();
