@@ -20,7 +20,11 @@ whose complete admissible path set is produced per second (the gate proves
 most of them empty).  Also reported: admissible paths per second.
 
 --workload refract / reflect time the 1-bounce caustic and reflection
-workloads (bounding-cone cull / exhaustive, no gate).
+workloads (bounding-cone cull / exhaustive, no gate); --workload slab the
+2-bounce refraction slab; --workload batched the batched mixed workload
+(independent queries of 1 or 2 bounces with explicit candidate lists:
+per-chain cone test, learned gate on the 1-bounce chains, persistent
+isolation with an autotuned launch shape, 2-bounce pipeline).
 --impl reference times the FP64 CPU oracle on the same metric.
 """
 from __future__ import annotations
@@ -58,7 +62,7 @@ BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["b
 # Kernel launches per step, counted from the ncu launch list of each
 # workload (profiles/).
 LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 18, ("glints", True): 19,
-                     ("slab", False): 11}
+                     ("slab", False): 11, ("batched", True): 40, ("batched", False): 39}
 # DRAM bytes (read + write) per launch of the isolation kernel from the last
 # ncu capture (profiles/kernels_refract_64x64_r256_mixed.md).  Reported only
 # while the kernel's sources hash to the value the capture was taken on.
@@ -80,7 +84,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    p.add_argument("--workload", choices=["glints", "refract", "reflect", "slab"], default="glints")
+    p.add_argument("--workload", choices=["glints", "refract", "reflect", "slab", "batched"], default="glints")
+    p.add_argument("--batch-queries", type=int, default=4096, help="batched: number of queries")
     p.add_argument("--slab-receivers", type=int, default=64,
                    help="slab: receiver grid side (64: the full 64x64 grid)")
     p.add_argument("--precision", choices=["mixed", "plain"], default="mixed")
@@ -100,9 +105,16 @@ def parse():
     return p.parse_args()
 
 
-def workload(name, slab_receivers=64):
+def workload(name, slab_receivers=64, batch_queries=4096):
     """(scene, chain mode, scattering kind, description, camera or None)."""
     from paper_2405_13409_gb300 import binding, scenes
+    if name == "batched":
+        s = scenes.batched_scene(n_queries=batch_queries)
+        return s, binding.CHAINS_EXPLICIT_CONE, "mixed", (
+            f"batched mixed workload: {batch_queries} queries, bounce count uniform in {{1,2}}, candidate counts "
+            f"log-uniform in 1e2..1e5 ({s.chains.shape[0]:,} explicit chains), per-query geometry from the "
+            f"refraction generator (1 bounce) or the 16x16-cell slab (2 bounces); per-chain cone test, learned "
+            f"gate on 1-bounce chains, persistent isolation with an autotuned launch shape"), None
     if name == "slab":
         s = scenes.slab_scene(n_recv=slab_receivers)
         return s, binding.CHAINS_CONE, "TT", (
@@ -257,6 +269,23 @@ def run_oracle_sample(s, camera, n_units, seed, kind="R"):
     (slab) n_units (receiver, top, bottom) tuples pairing a seeded top
     triangle with the bottom triangle of the same cell."""
     import oracle
+    if kind == "mixed":
+        # a seeded sample of the explicit list per bounce count; the rate is
+        # weighted by the list's own 1/2-bounce mix
+        from oracle import tt
+        rng = np.random.default_rng(seed)
+        two = s.chains[:, 2] >= 0
+        i1 = rng.choice(np.where(~two)[0], min(n_units * 256, int((~two).sum())), replace=False)
+        i2 = rng.choice(np.where(two)[0], min(n_units, int(two.sum())), replace=False)
+        t0 = time.perf_counter()
+        p1, _ = oracle.solve(s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, s.chains[np.sort(i1)])
+        t1 = time.perf_counter()
+        p2, _ = tt.solve(s.tri, s.x_first, s.x_last, s.eta, s.chains[np.sort(i2)], tt.fit_sqrt_pieces())
+        t2 = time.perf_counter()
+        n1, n2 = int((~two).sum()), int(two.sum())
+        per_chain = (n1 * (t1 - t0) / max(1, i1.size) + n2 * (t2 - t1) / max(1, i2.size)) / (n1 + n2)
+        return 1, per_chain, 0, (f"{i1.size} seeded 1-bounce and {i2.size} seeded 2-bounce chains of the explicit list; "
+                                 f"time per chain weighted by the list's {n1:,}/{n2:,} mix")
     if kind == "TT":
         from oracle import tt
         rng = np.random.default_rng(seed)
@@ -289,8 +318,8 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    s, _, kind, desc, cam = workload(args.workload, args.slab_receivers)
-    units = args.ref_units or (16384 if cam is not None else (8 if kind == "TT" else 16))
+    s, _, kind, desc, cam = workload(args.workload, args.slab_receivers, args.batch_queries)
+    units = args.ref_units or (16384 if cam is not None else (8 if kind in ("TT", "mixed") else 16))
     cores = os.cpu_count()
     for i in range(args.warmup):
         run_oracle_sample(s, cam, units, 1000 + i, kind)
@@ -332,10 +361,12 @@ class Pipeline:
     """One step of the hot path through the C ABI: candidate build, optional
     gate, solve.  Handles are reused across steps (grow-only buffers)."""
 
-    def __init__(self, ctx, mode, precision, camera, mlp=None, tau=0.0, ranges=None):
+    def __init__(self, ctx, mode, precision, camera, mlp=None, tau=0.0, ranges=None, explicit=None, flags=0):
         self.ctx, self.mode, self.precision, self.camera = ctx, mode, precision, camera
         self.mlp, self.tau = mlp, tau
         self.ranges = ranges  # 2-bounce cone: ((first range), (second range))
+        self.explicit = explicit  # explicit chain list (device tensor [n, 3])
+        self.flags = flags
         self.chains = self.gated = self.sol = None
         self.ev = None
 
@@ -345,7 +376,10 @@ class Pipeline:
         if torch is not None:
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             ev[0].record(stream)
-        if self.ranges:
+        if self.explicit is not None:
+            self.chains = self.ctx.spoly_build_chains(mesh, q, self.mode, margin=1e-3, reuse=self.chains,
+                                                      explicit=self.explicit)
+        elif self.ranges:
             self.chains = self.ctx.spoly_build_chains(mesh, q, self.mode, margin=1e-3, reuse=self.chains,
                                                       tri_range=self.ranges[0], second_range=self.ranges[1])
         else:
@@ -359,8 +393,8 @@ class Pipeline:
             solve_on = self.gated
         if ev:
             ev[2].record(stream)
-        self.sol = self.ctx.spoly_solve(mesh, q, solve_on, precision=self.precision, flags=binding.SOLVE_TIMING,
-                                        reuse=self.sol, camera=self.camera)
+        self.sol = self.ctx.spoly_solve(mesh, q, solve_on, precision=self.precision,
+                                        flags=binding.SOLVE_TIMING | self.flags, reuse=self.sol, camera=self.camera)
         self.ev = ev
 
     def phase_ms(self):
@@ -417,19 +451,23 @@ def main():
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
     ctx = binding.Context(local, stream.cuda_stream)
-    s, mode, kind, desc, camera = workload(args.workload, args.slab_receivers)
+    s, mode, kind, desc, camera = workload(args.workload, args.slab_receivers, args.batch_queries)
     precision = binding.MIXED if args.precision == "mixed" else binding.PLAIN_FP64
+    batched = kind == "mixed"
     host = [np.ascontiguousarray(a) for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
+    if batched:
+        host.append(np.ascontiguousarray(s.chains))
     d = [torch.from_numpy(a).to(dev) for a in host]
     mesh = ctx.mesh(d[0])
-    q = ctx.queries(*d[1:])
+    q = ctx.queries(*d[1:6])
+    explicit = d[6] if batched else None
 
     peak32 = ctx.spoly_measure_peak(binding.PEAK_FP32_FMA)
     peak64 = ctx.spoly_measure_peak(binding.PEAK_FP64_FMA)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # learned gate: trained and calibrated before the timed region
-    use_gate = camera is not None and precision == binding.MIXED and not args.no_gate
+    use_gate = (camera is not None or batched) and precision == binding.MIXED and not args.no_gate
     mlp, tau, gate_info = None, 0.0, None
     if use_gate and args.gate_file and os.path.exists(args.gate_file) and os.path.exists(args.gate_file + ".json"):
         mlp = ctx.spoly_mlp_load(args.gate_file)
@@ -439,10 +477,16 @@ def main():
     elif use_gate:
         from paper_2405_13409_gb300 import gate_train, scenes
         t0 = time.perf_counter()
-        train = [scenes.glint_scene(seed=1000 + i) for i in range(args.train_seeds)]
-        val = [scenes.glint_scene(seed=2000)]
+        if batched:  # the gate covers the 1-bounce (refraction) chains
+            train = [scenes.refract_scene(seed=1000 + i, n_recv=128) for i in range(args.train_seeds)]
+            val = [scenes.refract_scene(seed=2000, n_recv=128)]
+            gmode = binding.CHAINS_CONE
+        else:
+            train = [scenes.glint_scene(seed=1000 + i) for i in range(args.train_seeds)]
+            val = [scenes.glint_scene(seed=2000)]
+            gmode = mode
         gen_s = time.perf_counter() - t0
-        mlp, tau, gate_info = gate_train.train_gate(ctx, torch, train, val, mode, camera, steps=args.train_steps,
+        mlp, tau, gate_info = gate_train.train_gate(ctx, torch, train, val, gmode, camera, steps=args.train_steps,
                                                     seed=args.seed)
         gate_info["scene_generation_s"] = gen_s
         gate_info["train_seeds"] = [1000 + i for i in range(args.train_seeds)]
@@ -454,7 +498,17 @@ def main():
             json.dump(gate_info, open(args.gate_file + ".json", "w"))
 
     ranges = ((0, s.n_tris // 2), (s.n_tris // 2, s.n_tris)) if kind == "TT" else None
-    pipe = Pipeline(ctx, mode, precision, camera, mlp, tau, ranges)
+    tune = None
+    if batched:
+        # launch shape of the persistent isolation, tuned on the 1-bounce chains
+        one = torch.from_numpy(np.ascontiguousarray(s.chains[s.chains[:, 2] < 0])).to(dev)
+        ch1 = ctx.spoly_build_chains(mesh, q, mode, margin=1e-3, explicit=one)
+        best, table = ctx.spoly_autotune(mesh, q, ch1, precision)
+        tune = {"block": best[0], "blocks_per_sm": best[1], "chunk": best[2], "ms": best[3], "shapes": len(table)}
+        ctx.spoly_chains_free(ch1)
+        del one
+    pipe = Pipeline(ctx, mode, precision, camera, mlp, tau, ranges, explicit,
+                    binding.SOLVE_PERSISTENT if batched else 0)
     for _ in range(args.warmup):
         pipe.step(mesh, q)
     torch.cuda.synchronize()
@@ -463,6 +517,8 @@ def main():
     stats = ctx.spoly_stats(pipe.sol)
     if mode == binding.CHAINS_FOOTPRINT:
         pairs = n_cand
+    elif batched:
+        pairs = int(s.chains.shape[0])  # every explicit chain of the step
     elif kind == "TT":
         pairs = s.n_queries * (s.n_tris // 2) ** 2  # every (receiver, top, bottom) tuple the cull stands for
     else:
@@ -490,8 +546,8 @@ def main():
 
     # plain FP64 path on the same candidates: no gate, every step in FP64
     plain = None
-    if camera is not None and not args.no_plain and precision == binding.MIXED:
-        pp = Pipeline(ctx, mode, binding.PLAIN_FP64, camera)
+    if (camera is not None or batched) and not args.no_plain and precision == binding.MIXED:
+        pp = Pipeline(ctx, mode, binding.PLAIN_FP64, camera, explicit=explicit)
         pp.step(mesh, q)
         torch.cuda.synchronize()
         k = max(1, min(args.steps, args.plain_steps))
@@ -513,9 +569,12 @@ def main():
         pinned = [torch.from_numpy(a).pin_memory() for a in host]
         dd = [torch.empty_like(x, device=dev) for x in pinned]
         emesh = ctx.mesh(dd[0])
-        eq = ctx.queries(*dd[1:])
         out = torch.empty(max(1, 2 * n_paths + 1024) * binding.PATH_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
         cap = out.numel() // binding.PATH_DTYPE.itemsize
+
+        eq = ctx.queries(*dd[1:6])
+        if batched:
+            pipe.explicit = dd[6]
 
         def e2e_step():
             for dst, src in zip(dd, pinned):
@@ -562,7 +621,7 @@ def main():
                 "fp32_laplace_tflops": FP32_LAPLACE_FLOPS.get(kind, 0) * n_solved / (iso * 1e-3) / 1e12 if iso > 0
                 else 0.0}
     roofline = roof_iso
-    if kind == "TT":
+    if kind == "TT" or (batched and ph["k2"] >= max(ph["gate"], iso, ph["chains"])):
         # 2-bounce sign phase work: per determinant evaluation ~4/3 n^3 flop (Bezout
         # entries n^3/3 FMA + elimination n^3/3 FMA) + ~1,900 flop of Horner
         # evaluation of the coefficients; timed over the whole 2-bounce phase
@@ -580,8 +639,11 @@ def main():
                      "frac": gate_tflops / BF16_PEAK_TFLOPS, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
                      "traffic": None, "flops_per_candidate": GATE_FLOPS}
         # the dominant phase of the step carries the headline roofline
-        roofline = roof_gate if ph["gate"] >= iso else roof_iso
-        roofline = dict(roofline, other={"isolation": roof_iso if roofline is roof_gate else roof_gate})
+        if not (batched and roofline.get("pipe") == "fp32"):
+            roofline = roof_gate if ph["gate"] >= iso else roof_iso
+            roofline = dict(roofline, other={"isolation": roof_iso if roofline is roof_gate else roof_gate})
+        else:
+            roofline = dict(roofline, other={"gate": roof_gate, "isolation": roof_iso})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -597,6 +659,7 @@ def main():
         "phase_ms": ph,
         "plain_fp64": plain,
         "gate": gate_info,
+        "autotune": tune,
         "roofline": roofline,
         "gpu_launches": LAUNCHES_PER_STEP.get((args.workload, use_gate), 7) * args.steps,
         "clocks": clk,
@@ -605,9 +668,9 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        units = 24576 if camera is not None else (64 if kind == "T" else (16 if kind == "TT" else 256))
-        c, tcpu, _, sample = run_oracle_sample(s, camera, units if kind == "TT" else min(units, s.n_queries), 7,
-                                               kind)
+        units = 24576 if camera is not None else (64 if kind == "T" else (16 if kind in ("TT", "mixed") else 256))
+        c, tcpu, _, sample = run_oracle_sample(s, camera, units if kind in ("TT", "mixed") else min(units, s.n_queries),
+                                               7, kind)
         line["cpu_baseline"] = {"value": c / tcpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line))

@@ -102,6 +102,7 @@ typedef struct {
 #define SPOLY_CHAINS_CONE 1     /* pairs passing a conservative direction-box test */
 #define SPOLY_CHAINS_EXPLICIT 2 /* caller's list */
 #define SPOLY_CHAINS_FOOTPRINT 3 /* pixel footprints of a pinhole camera (query q = pixel q) */
+#define SPOLY_CHAINS_EXPLICIT_CONE 4 /* caller's list, each chain kept only if it passes the CONE test */
 
 typedef struct {
   int32_t mode;
@@ -215,7 +216,12 @@ const char* spoly_last_error(const spoly_ctx* ctx);
  * directions over the triangle (reflected or refracted per the query,
  * interval arithmetic over the triangle's bounding box and normal range)
  * overlaps the box of unit directions from the triangle toward x_{k+1};
- * EXPLICIT copies the caller's list after a bounds check.  *inout: NULL to
+ * EXPLICIT copies the caller's list after a bounds check; EXPLICIT_CONE
+ * keeps the chains of the caller's list (any mix of queries, bounce counts
+ * and triangles) that pass the CONE test of their own bounce count, per
+ * query x0, IORs and types (1 bounce: as CONE; 2 bounces of two refractions:
+ * the three tests of the 2-bounce CONE; other 2-bounce types are kept),
+ * in no particular order.  *inout: NULL to
  * allocate a new handle, or a handle to reuse.  The call synchronises once
  * to read the chain count.  EXPLICIT lists may hold 2-bounce chains
  * (tri1 >= 0).  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (CONE with
@@ -425,9 +431,10 @@ spoly_status spoly_mlp_calibrate(spoly_ctx* ctx, spoly_mlp* mlp, const float* fe
                                  int64_t n, double target_recall, float* tau_logit, double* pass_fraction);
 
 /* Gates a chain list: features, network and compaction in one kernel; the
- * chains whose logit is >= tau_logit are written to *inout (created when
- * NULL, else reused and grown; it must not be `in`).  Their order is not
- * preserved.  Synchronises (reads the count back). */
+ * 1-bounce chains whose logit is >= tau_logit, and every 2-bounce chain
+ * (tri1 >= 0: outside the network's domain), are written to *inout (created
+ * when NULL, else reused and grown; it must not be `in`).  Their order is
+ * not preserved.  Synchronises (reads the count back). */
 spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* mlp, const spoly_mesh* mesh, const spoly_queries* q,
                         const spoly_chains* in, float tau_logit, spoly_chains** inout);
 

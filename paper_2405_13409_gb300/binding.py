@@ -39,6 +39,7 @@ CHAINS_ALL = 0
 CHAINS_CONE = 1
 CHAINS_EXPLICIT = 2
 CHAINS_FOOTPRINT = 3
+CHAINS_EXPLICIT_CONE = 4
 
 PLAIN_FP64 = 0
 MIXED = 1

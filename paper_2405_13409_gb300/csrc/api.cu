@@ -157,7 +157,7 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
   // batches of whole chains, at most kBatch systems
   constexpr int64_t kBatch = 16384;
   const int64_t bmax = std::min<int64_t>(kBatch, std::max<int64_t>(n_sys, 1));
-  CK(set->tt_scratch.ensure(size_t(bmax) * kTTScratch * sizeof(double)), "tt scratch");
+  CK(set->tt_scratch.ensure(size_t(bmax) * kTTKeep * sizeof(double)), "tt scratch");
   CK(set->tt_coef32.ensure(size_t(bmax) * kTT32 * sizeof(float)), "tt scratch");
   CK(set->tt_queue.ensure(size_t(bmax) * 128 * sizeof(RootItem)), "tt queue");  // 128 brackets per system at most
   T.scratch = static_cast<double*>(set->tt_scratch.p);
@@ -191,7 +191,7 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
     CK(cudaMemcpyAsync(&nb, T.counters + TT_BRACKETS, sizeof(nb), cudaMemcpyDeviceToHost, st), "tt brackets");
     CK(cudaStreamSynchronize(st), "tt brackets");
     brackets_total += nb;
-    CK(launch_tt_polish(T, 0, std::min<int64_t>(int64_t(nb), T.queue_cap), ctx->num_sms, st), "tt polish");
+    CK(launch_tt_polish(T, ctx->num_sms, st), "tt polish");
     CK(launch_tt_paths(T, c0, c1, ctx->num_sms, st), "tt paths");
     c0 = c1;
   }
@@ -315,6 +315,45 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit sync"));
     if (herr) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain %d references a missing query or triangle", herr - 1));
     ch->n = n;
+    ch->n_k2 = int64_t(hk2);
+  } else if (opts->mode == SPOLY_CHAINS_EXPLICIT_CONE) {
+    // the caller's list, validated, then culled chain by chain
+    const int64_t n = opts->n_explicit;
+    if (!opts->explicit_chains || n <= 0) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain list is empty"));
+    if (!(opts->margin >= 0.0)) return bail(fail(ctx, SPOLY_EINVAL, "cone margin must be >= 0"));
+    DevBuf valid, tmp;
+    if (valid.ensure(size_t(n) * 12) != cudaSuccess || ctx->flag.ensure(16) != cudaSuccess)
+      return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
+    const int32_t* src = opts->explicit_chains;
+    if (!opts->explicit_on_device) {
+      if (tmp.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
+      e = cudaMemcpyAsync(tmp.p, src, size_t(n) * 12, cudaMemcpyHostToDevice, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain copy"));
+      src = static_cast<const int32_t*>(tmp.p);
+    }
+    P.out = static_cast<int32_t*>(valid.p);
+    P.cap = n;
+    e = launch_chains_explicit(P, src, n, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit"));
+    int32_t herr = 0;
+    e = cudaMemcpyAsync(&herr, P.error, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit sync"));
+    if (herr) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain %d references a missing query or triangle", herr - 1));
+    unsigned long long* k2 = static_cast<unsigned long long*>(ctx->flag.p) + 1;
+    e = cudaMemsetAsync(P.count, 0, 8, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(k2, 0, 8, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain counters"));
+    if (ch->buf.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+    P.out = static_cast<int32_t*>(ch->buf.p);
+    e = launch_chains_explicit_cone(P, static_cast<const int32_t*>(valid.p), n, k2, ctx->num_sms, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit_cone"));
+    unsigned long long hn = 0, hk2 = 0;
+    e = cudaMemcpyAsync(&hn, P.count, 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hk2, k2, 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit_cone sync"));
+    ch->n = int64_t(hn);
     ch->n_k2 = int64_t(hk2);
   } else if (opts->mode == SPOLY_CHAINS_CONE && opts->second_end > 0) {
     // 2-bounce refraction chains: second triangle in [second_begin, second_end)

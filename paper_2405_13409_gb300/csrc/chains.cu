@@ -493,6 +493,83 @@ __global__ void tt_shared_kernel(QueryView Q, int32_t* flag) {
 
 }  // namespace
 
+// ------------------------------------- explicit lists, culled per chain
+// Box of one triangle lit from x: [12] floats (outgoing lo/hi xyz, widened
+// by the margin and rounded outward; bounding box lo/hi xyz).  A triangle
+// with no bound gets the full box, one with no transmitted direction an
+// empty one.
+SPOLY_D void chain_box(const MeshView& M, int t, d3 x, int type, double eta_in, double eta_out, double margin,
+                       float (&B)[12]) {
+  Iv3 o, bb;
+  bool empty = false;
+  const bool ok = out_box(M, t, x, type, eta_in, eta_out, o, bb, empty);
+  const Iv comps[3] = {o.x, o.y, o.z};
+  const Iv bcomp[3] = {bb.x, bb.y, bb.z};
+  for (int k = 0; k < 3; ++k) {
+    const Iv w = widen(comps[k], margin);
+    B[k] = empty ? 2.f : (ok ? __double2float_rd(w.lo) : -1.f);
+    B[3 + k] = empty ? -2.f : (ok ? __double2float_ru(w.hi) : 1.f);
+    B[6 + k] = __double2float_rd(bcomp[k].lo);
+    B[9 + k] = __double2float_ru(bcomp[k].hi);
+  }
+}
+
+// The CONE test of one chain: 1 bounce as cone_pairs_general_kernel; 2
+// bounces of two refractions as tt_pairs_kernel (i, ii) and
+// tt_cone_chains_kernel (iii).  Other 2-bounce types are kept.
+SPOLY_D bool chain_cone_keep(const MeshView& M, const QueryView& Q, int64_t q, int t0, int t1, double margin) {
+  const d3 x0 = mk(Q.x_first[3 * q], Q.x_first[3 * q + 1], Q.x_first[3 * q + 2]);
+  const d3 xl = mk(Q.x_last[3 * q], Q.x_last[3 * q + 1], Q.x_last[3 * q + 2]);
+  const int k = Q.k[q];
+  if (k == 1 || t1 < 0) {
+    float B[12];
+    chain_box(M, t0, x0, Q.types[2 * q], Q.eta[3 * q], Q.eta[3 * q + 1], margin, B);
+    return to_box_overlaps(B, float(xl.x), float(xl.y), float(xl.z));
+  }
+  if (Q.types[2 * q] != SPOLY_T || Q.types[2 * q + 1] != SPOLY_T) return true;
+  float F[12], B[12];
+  chain_box(M, t0, x0, SPOLY_T, Q.eta[3 * q], Q.eta[3 * q + 1], margin, F);
+  chain_box(M, t1, xl, SPOLY_T, Q.eta[3 * q + 2], Q.eta[3 * q + 1], margin, B);
+  if (!box_overlaps(F, B[6], B[9], B[7], B[10], B[8], B[11])) return false;  // (i), (ii)
+  if (!box_overlaps(B, F[6], F[9], F[7], F[10], F[8], F[11])) return false;  // (iii) toward T1
+  for (int c = 0; c < 3; ++c)
+    if (!((-B[3 + c] <= F[3 + c]) && (F[c] <= -B[c]))) return false;  // negated backward box vs forward
+  return true;
+}
+
+__global__ void explicit_cone_kernel(ChainParams P, const int32_t* src, int64_t n, unsigned long long* k2) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t c = base + lane;
+    bool keep = false;
+    int32_t q = 0, t0 = 0, t1 = -1;
+    if (c < n) {
+      q = src[3 * c];
+      t0 = src[3 * c + 1];
+      t1 = src[3 * c + 2];
+      keep = chain_cone_keep(P.mesh, P.qv, q, t0, t1, P.margin);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) continue;
+    const unsigned m2 = __ballot_sync(0xffffffffu, keep && t1 >= 0);
+    unsigned long long b0 = 0;
+    if (lane == 0) {
+      b0 = atomicAdd(P.count, (unsigned long long)__popc(m));
+      if (m2) atomicAdd(k2, (unsigned long long)__popc(m2));
+    }
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (keep) {
+      const unsigned long long idx = b0 + __popc(m & ((1u << lane) - 1u));
+      if (idx < (unsigned long long)P.cap) {
+        P.out[3 * idx] = q;
+        P.out[3 * idx + 1] = t0;
+        P.out[3 * idx + 2] = t1;
+      }
+    }
+  }
+}
+
 cudaError_t launch_tt_cone_shared(const TTConeParams& P, int32_t* flag, int num_sms, cudaStream_t st, int32_t* host) {
   set_flag_kernel<<<1, 1, 0, st>>>(flag, 1);
   tt_shared_kernel<<<num_sms * 4, 256, 0, st>>>(P.qv, flag);
@@ -513,5 +590,12 @@ cudaError_t launch_tt_cone_chains(const TTConeParams& P, int64_t n_pairs, int nu
   return cudaGetLastError();
 }
 
+
+cudaError_t launch_chains_explicit_cone(const ChainParams& P, const int32_t* src, int64_t n, unsigned long long* k2,
+                                        int num_sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  explicit_cone_kernel<<<num_sms * 8, 256, 0, st>>>(P, src, n, k2);
+  return cudaGetLastError();
+}
 
 }  // namespace spoly

@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(128) gate_kernel(GateParams G) {
     const float z = sz[tid];
     if (valid && G.logits) G.logits[row] = z;
     if (G.out_chains) {
-      const bool keep = valid && z >= G.tau_logit;
+      // 2-bounce chains are outside the network's domain and pass ungated
+      const bool keep = valid && (z >= G.tau_logit || __ldg(G.chains + 3 * row + 2) >= 0);
       const unsigned long long slot = warp_append(G.out_n, keep ? 1u : 0u);
       if (keep) {
         G.out_chains[3 * slot] = __ldg(G.chains + 3 * row);

@@ -57,6 +57,10 @@ cudaError_t launch_chains_all(const ChainParams& P, int num_sms, cudaStream_t st
 cudaError_t launch_chains_explicit(const ChainParams& P, const int32_t* src, int64_t n, int num_sms,
                                    cudaStream_t st);
 cudaError_t launch_chains_cone(const ChainParams& P, int num_sms, cudaStream_t st);
+// Survivors of a validated explicit list under the CONE test of each chain's
+// bounce count, appended to P.out (P.count; *k2 counts the 2-bounce ones).
+cudaError_t launch_chains_explicit_cone(const ChainParams& P, const int32_t* src, int64_t n, unsigned long long* k2,
+                                        int num_sms, cudaStream_t st);
 
 // Cone cull of 2-bounce refraction chains (first triangle in
 // [t1_begin, t1_begin + n1), second in [t2_begin, t2_begin + n2)).

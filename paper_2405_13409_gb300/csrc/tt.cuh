@@ -47,9 +47,9 @@ struct TTSys {
   int32_t pad;
 };
 
-// Scratch of one system (FP64, interleaved: element e of system s at
-// base[e * stride + s]): the final a, b and the mapping polynomials, then
-// the intermediates of the construction.
+// Arena of one system (FP64, element e at base[e * stride]): the final a, b
+// and the mapping polynomials (the kept part, copied to the system's scratch
+// row), then the intermediates of the construction.
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + bsize(kTTDa);
 constexpr int kOffUt = kOffB + bsize(kTTDb);
@@ -66,7 +66,7 @@ constexpr int kTTScratch = kTTKeep + kTTWork;
 constexpr int kTT32 = bsize(kTTDa) + bsize(kTTDb);
 
 #ifndef SPOLY_HOST_BUILD
-// A bivariate polynomial of total degree D in interleaved scratch.
+// A bivariate polynomial of total degree D (coefficient k at p[k * st]).
 struct GP {
   double* p;
   int64_t st;
@@ -86,39 +86,72 @@ struct Arena {
   }
 };
 
+// The construction helpers below are warp-cooperative: all 32 lanes of a
+// warp call them together with the same arguments (polynomials in the
+// warp's shared-memory arena); each returns after a __syncwarp, so its
+// results are visible to every lane.
+
+// (i, j) of the graded index t of a degree-D polynomial: row offsets are
+// off(i) = i (2D + 3 - i) / 2.
+SPOLY_D void flat_to_ij(int D, int t, int& i, int& j) {
+  const float B = float(2 * D + 3);
+  int r = int((B - sqrtf(fmaxf(B * B - 8.0f * float(t), 0.0f))) * 0.5f);
+  r = max(0, min(r, D));
+  while (r > 0 && r * (2 * D + 3 - r) / 2 > t) --r;
+  while (r < D && (r + 1) * (2 * D + 3 - (r + 1)) / 2 <= t) ++r;
+  i = r;
+  j = t - r * (2 * D + 3 - r) / 2;
+}
+
 SPOLY_D void gp_zero(const GP& c) {
-  for (int i = 0; i < bsize(c.D); ++i) c.k(i) = 0.0;
+  for (int t = threadIdx.x & 31; t < bsize(c.D); t += 32) c.k(t) = 0.0;
+  __syncwarp();
+}
+
+// c(0, 0) += x
+SPOLY_D void gp_add00(const GP& c, double x) {
+  if ((threadIdx.x & 31) == 0) c.at(0, 0) += x;
+  __syncwarp();
+}
+
+// c += s * a * b, keeping only the terms of total degree <= c.D (the others
+// vanish when the factors' true degrees are below their slots').  Lanes take
+// the terms of b; the terms of a run in step, one __syncwarp apart, so two
+// lanes never update one coefficient at once.
+SPOLY_D void gp_mac_trunc(const GP& c, const GP& a, const GP& b, double s) {
+  const int lane = threadIdx.x & 31;
+  const int nb = bsize(b.D);
+  for (int t0 = 0; t0 < nb; t0 += 32) {
+    const int t = t0 + lane;
+    int i2 = 0, j2 = 0;
+    double y = 0.0;
+    if (t < nb) {
+      flat_to_ij(b.D, t, i2, j2);
+      y = s * b.k(t);
+    }
+    for (int i1 = 0; i1 <= a.D; ++i1)
+      for (int j1 = 0; i1 + j1 <= a.D; ++j1) {
+        const double x = a.at(i1, j1);
+        if (x == 0.0) continue;  // the same for every lane
+        if (y != 0.0 && i1 + j1 + i2 + j2 <= c.D)
+          c.at(i1 + i2, j1 + j2) = fma(x, y, c.at(i1 + i2, j1 + j2));
+        __syncwarp();
+      }
+  }
+  __syncwarp();
 }
 
 // c += s * a * b  (c.D >= a.D + b.D)
-SPOLY_D void gp_mac(const GP& c, const GP& a, const GP& b, double s) {
-  for (int i1 = 0; i1 <= a.D; ++i1)
-    for (int j1 = 0; i1 + j1 <= a.D; ++j1) {
-      const double x = s * a.at(i1, j1);
-      if (x == 0.0) continue;
-      for (int i2 = 0; i2 <= b.D; ++i2)
-        for (int j2 = 0; i2 + j2 <= b.D; ++j2) c.at(i1 + i2, j1 + j2) = fma(x, b.at(i2, j2), c.at(i1 + i2, j1 + j2));
-    }
-}
-
-// c += s * a * b, dropping the terms above c's degree (which vanish when the
-// factors' true degrees are below their slots')
-SPOLY_D void gp_mac_trunc(const GP& c, const GP& a, const GP& b, double s) {
-  for (int i1 = 0; i1 <= a.D; ++i1)
-    for (int j1 = 0; i1 + j1 <= a.D; ++j1) {
-      const double x = s * a.at(i1, j1);
-      if (x == 0.0) continue;
-      const int room = c.D - i1 - j1;
-      for (int i2 = 0; i2 <= min(b.D, room); ++i2)
-        for (int j2 = 0; i2 + j2 <= min(b.D, room); ++j2)
-          c.at(i1 + i2, j1 + j2) = fma(x, b.at(i2, j2), c.at(i1 + i2, j1 + j2));
-    }
-}
+SPOLY_D void gp_mac(const GP& c, const GP& a, const GP& b, double s) { gp_mac_trunc(c, a, b, s); }
 
 // c += s * a  (c.D >= a.D)
 SPOLY_D void gp_axpy(const GP& c, const GP& a, double s) {
-  for (int i = 0; i <= a.D; ++i)
-    for (int j = 0; i + j <= a.D; ++j) c.at(i, j) = fma(s, a.at(i, j), c.at(i, j));
+  for (int t = threadIdx.x & 31; t < bsize(a.D); t += 32) {
+    int i, j;
+    flat_to_ij(a.D, t, i, j);
+    c.at(i, j) = fma(s, a.k(t), c.at(i, j));
+  }
+  __syncwarp();
 }
 
 SPOLY_D double gp_eval(const GP& a, double u, double v) {
@@ -165,15 +198,18 @@ SPOLY_D void gv_dot_const_mac(const GP& r, const GV& a, d3 w, double s) {
 // Affine vector polynomial c0 + u cu + v cv into a degree-D slot.
 SPOLY_D void gv_set_lin(const GV& v, d3 c0, d3 cu, d3 cv) {
   gv_zero(v);
-  v.x.at(0, 0) = c0.x;
-  v.x.at(1, 0) = cu.x;
-  v.x.at(0, 1) = cv.x;
-  v.y.at(0, 0) = c0.y;
-  v.y.at(1, 0) = cu.y;
-  v.y.at(0, 1) = cv.y;
-  v.z.at(0, 0) = c0.z;
-  v.z.at(1, 0) = cu.z;
-  v.z.at(0, 1) = cv.z;
+  if ((threadIdx.x & 31) == 0) {
+    v.x.at(0, 0) = c0.x;
+    v.x.at(1, 0) = cu.x;
+    v.x.at(0, 1) = cv.x;
+    v.y.at(0, 0) = c0.y;
+    v.y.at(1, 0) = cu.y;
+    v.y.at(0, 1) = cv.y;
+    v.z.at(0, 0) = c0.z;
+    v.z.at(1, 0) = cu.z;
+    v.z.at(0, 1) = cv.z;
+  }
+  __syncwarp();
 }
 #endif
 

@@ -1,5 +1,6 @@
 // TT chains, FP64 phase 1: piece enumeration and construction of the
-// bivariate system (Sec. 4.4-4.5) per (chain, sqrt piece).
+// bivariate system (Sec. 4.4-4.5) per (chain, sqrt piece), one warp per
+// system with its polynomials in shared memory.
 #include "tt_kernels.cuh"
 
 namespace spoly {
@@ -92,7 +93,8 @@ SPOLY_D bool constant_normal(const TriD& t) {
   return e < 1e-12;
 }
 
-// Builds a, b, u~, v~, kappa of one system into scratch column `col`.
+// Builds a, b, u~, v~, kappa of one system (and the intermediates) in the
+// warp's arena `base` (stride st); all 32 lanes of the warp call it.
 SPOLY_D void tt_construct(const TriD& t1, const TriD& t2, const QueryD& qd, d3 x3, double eta2, int piece,
                           const SqrtTable& tb, double* base, int64_t st) {
   Arena A{base, st, 0};
@@ -133,10 +135,10 @@ SPOLY_D void tt_construct(const TriD& t1, const TriD& t2, const QueryD& qd, d3 x
   const double c0 = tb.c[piece][0], cc1 = tb.c[piece][1], d1 = tb.c[piece][2];
   gp_zero(Q);
   gp_axpy(Q, beta, d1);
-  Q.at(0, 0) += s;
+  gp_add00(Q, s);
   gp_zero(num);
   gp_axpy(num, beta, cc1);
-  num.at(0, 0) += c0 * s;
+  gp_add00(num, c0 * s);
   // tang = d0 |n1|^2 - n1 (d0 . n1): degree 3
   const GV tang = gv_take(A, 3);
   gv_zero(tang);
@@ -175,9 +177,9 @@ SPOLY_D void tt_construct(const TriD& t1, const TriD& t2, const QueryD& qd, d3 x
   const GV M2 = gv_take(A, 8);
   gv_zero(M2);
   if (constant_normal(t2)) {
-    M2.x.at(0, 0) = t2.n0.x;
-    M2.y.at(0, 0) = t2.n0.y;
-    M2.z.at(0, 0) = t2.n0.z;
+    gp_add00(M2.x, t2.n0.x);
+    gp_add00(M2.y, t2.n0.y);
+    gp_add00(M2.z, t2.n0.z);
   } else {
     const d3 g1 = t2.n1 - t2.n0, g2 = t2.n2 - t2.n0;
     gp_axpy(M2.x, kap, t2.n0.x);
@@ -237,23 +239,35 @@ SPOLY_D void tt_construct(const TriD& t1, const TriD& t2, const QueryD& qd, d3 x
   gp_mac_trunc(b, dsq, p2sq, -eta2 * eta2);
 }
 
-// Trimmed u-degree (reading R1) and the u scaling of the FP32 copy.
-SPOLY_D void tt_finish(TTSys& sy, double* base, int64_t st, float* c32, int64_t st32) {
-  const GP a{base + int64_t(kOffA) * st, st, kTTDa}, b{base + int64_t(kOffB) * st, st, kTTDb};
-  double ra[kTTDa + 1], rb[kTTDb + 1];
+// log2 x for x > 0 (frexp keeps tiny and huge values exact in the exponent).
+SPOLY_D double log2_pos(double x) {
+  int e;
+  const double m = frexp(x, &e);
+  return double(e) + double(log2f(float(m)));
+}
+
+// Trimmed u-degrees (reading R1), the u scaling u = 2^ks w and the scaled,
+// normalised FP32 copy `c32` ([kTT32], a then b) of the system in the warp's
+// arena; `rowmax` holds kTTDa + kTTDb + 2 doubles of shared memory.  All 32
+// lanes call it.
+SPOLY_D void tt_finish(TTSys& sy, double* base, float* c32, double* rowmax) {
+  const int lane = threadIdx.x & 31;
+  const GP a{base + kOffA, 1, kTTDa}, b{base + kOffB, 1, kTTDb};
+  constexpr int kRows = kTTDa + 1 + kTTDb + 1;
+  double* ra = rowmax;
+  double* rb = rowmax + kTTDa + 1;
+  for (int r = lane; r < kRows; r += 32) {
+    const bool in_a = r <= kTTDa;
+    const GP& p = in_a ? a : b;
+    const int i = in_a ? r : r - kTTDa - 1;
+    double m = 0.0;
+    for (int j = 0; i + j <= p.D; ++j) m = fmax(m, fabs(p.at(i, j)));
+    rowmax[r] = m;
+  }
+  __syncwarp();
   double am = 0.0, bm = 0.0;
-  for (int i = 0; i <= kTTDa; ++i) {
-    double m = 0.0;
-    for (int j = 0; i + j <= kTTDa; ++j) m = fmax(m, fabs(a.at(i, j)));
-    ra[i] = m;
-    am = fmax(am, m);
-  }
-  for (int i = 0; i <= kTTDb; ++i) {
-    double m = 0.0;
-    for (int j = 0; i + j <= kTTDb; ++j) m = fmax(m, fabs(b.at(i, j)));
-    rb[i] = m;
-    bm = fmax(bm, m);
-  }
+  for (int i = 0; i <= kTTDa; ++i) am = fmax(am, ra[i]);
+  for (int i = 0; i <= kTTDb; ++i) bm = fmax(bm, rb[i]);
   int da = -1, db = -1;
   for (int i = 0; i <= kTTDa; ++i)
     if (ra[i] > kTrim * am) da = i;
@@ -268,24 +282,26 @@ SPOLY_D void tt_finish(TTSys& sy, double* base, int64_t st, float* c32, int64_t 
   }
   // least-squares slope of log2(row max) over the kept rows of both
   double sx = 0, sy2 = 0, sxx = 0, sxy = 0, cnt = 0;
-  for (int i = 0; i <= da; ++i)
-    if (ra[i] > 0.0) {
-      const double l = log2(ra[i] / am);
+  for (int r = lane; r < kRows; r += 32) {
+    const bool in_a = r <= kTTDa;
+    const int i = in_a ? r : r - kTTDa - 1;
+    const double m = rowmax[r];
+    if (m > 0.0 && i <= (in_a ? da : db)) {
+      const double l = log2_pos(m / (in_a ? am : bm));
       sx += i;
       sy2 += l;
       sxx += double(i) * i;
       sxy += i * l;
       cnt += 1;
     }
-  for (int i = 0; i <= db; ++i)
-    if (rb[i] > 0.0) {
-      const double l = log2(rb[i] / bm);
-      sx += i;
-      sy2 += l;
-      sxx += double(i) * i;
-      sxy += i * l;
-      cnt += 1;
-    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy2 += __shfl_xor_sync(0xffffffffu, sy2, o);
+    sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
+    sxy += __shfl_xor_sync(0xffffffffu, sxy, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
   const double den = cnt * sxx - sx * sx;
   const double g = den > 0.0 ? (cnt * sxy - sx * sy2) / den : 0.0;
   int ks = int(rint(-g));
@@ -295,29 +311,41 @@ SPOLY_D void tt_finish(TTSys& sy, double* base, int64_t st, float* c32, int64_t 
   double am2 = 0.0, bm2 = 0.0;
   for (int i = 0; i <= da; ++i) am2 = fmax(am2, ldexp(ra[i], ks * i));
   for (int i = 0; i <= db; ++i) bm2 = fmax(bm2, ldexp(rb[i], ks * i));
-  for (int i = 0; i <= kTTDa; ++i)
-    for (int j = 0; i + j <= kTTDa; ++j)
-      c32[int64_t(bidx(kTTDa, i, j)) * st32] = i <= da ? float(ldexp(a.at(i, j), ks * i) / am2) : 0.0f;
-  const int ob = bsize(kTTDa);
-  for (int i = 0; i <= kTTDb; ++i)
-    for (int j = 0; i + j <= kTTDb; ++j)
-      c32[int64_t(ob + bidx(kTTDb, i, j)) * st32] = i <= db ? float(ldexp(b.at(i, j), ks * i) / bm2) : 0.0f;
+  const double ia = 1.0 / am2, ib = 1.0 / bm2;
+  for (int t = lane; t < kTT32; t += 32) {
+    const bool in_a = t < bsize(kTTDa);
+    const int idx = in_a ? t : t - bsize(kTTDa);
+    int i, j;
+    flat_to_ij(in_a ? kTTDa : kTTDb, idx, i, j);
+    const double c = in_a ? a.k(idx) : b.k(idx);
+    c32[t] = i <= (in_a ? da : db) ? float(ldexp(c, ks * i) * (in_a ? ia : ib)) : 0.0f;
+  }
 }
 
-__global__ void __launch_bounds__(128) tt_build_kernel(TTParams P) {
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.n_sys; i += stride) {
+// One warp per system: construction in the warp's shared-memory arena, then
+// the kept polynomials to the system's scratch row and the FP32 copy.
+constexpr int kBuildWarps = 6;
+constexpr int kArena = kTTScratch + kTTDa + kTTDb + 2;  // doubles per warp
+
+__global__ void __launch_bounds__(kBuildWarps * 32) tt_build_kernel(TTParams P) {
+  extern __shared__ double build_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* arena = build_smem + int64_t(warp) * kArena;
+  const int64_t nw = int64_t(gridDim.x) * kBuildWarps;
+  for (int64_t i = int64_t(blockIdx.x) * kBuildWarps + warp; i < P.n_sys; i += nw) {
     TTSys sy = P.sys[P.sys_offset + i];
     const int64_t c = sy.chain;
     const int q = P.chains[3 * c], t1 = P.chains[3 * c + 1], t2 = P.chains[3 * c + 2];
     const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
     const double eta2 = P.qv.eta[3 * q + 2];
-    const TriD a = load_tri(P.mesh.tri, P.mesh.n_tris, t1);
-    const TriD b = load_tri(P.mesh.tri, P.mesh.n_tris, t2);
-    double* col = P.scratch + i;
-    tt_construct(a, b, qd, qd.x2, eta2, sy.piece, P.sqrt_tab, col, P.n_sys);
-    tt_finish(sy, col, P.n_sys, P.coef32 + i, P.n_sys);
-    P.sys[P.sys_offset + i] = sy;
+    const TriD ta = load_tri(P.mesh.tri, P.mesh.n_tris, t1);
+    const TriD tb = load_tri(P.mesh.tri, P.mesh.n_tris, t2);
+    tt_construct(ta, tb, qd, qd.x2, eta2, sy.piece, P.sqrt_tab, arena, 1);
+    double* keep = P.scratch + i * kTTKeep;
+    for (int t = lane; t < kTTKeep; t += 32) keep[t] = arena[t];
+    tt_finish(sy, arena, P.coef32 + i * kTT32, arena + kTTScratch);
+    if (lane == 0) P.sys[P.sys_offset + i] = sy;
+    __syncwarp();
   }
 }
 
@@ -337,8 +365,15 @@ cudaError_t launch_tt_fill(const TTParams& P, const uint8_t* masks, int num_sms,
 
 cudaError_t launch_tt_build(const TTParams& P, int num_sms, cudaStream_t st) {
   if (P.n_sys <= 0) return cudaSuccess;
-  const int64_t g = std::min<int64_t>((P.n_sys + 127) / 128, int64_t(num_sms) * 8);
-  tt_build_kernel<<<int(g), 128, 0, st>>>(P);
+  const size_t smem = size_t(kBuildWarps) * kArena * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(tt_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t g = std::min<int64_t>((P.n_sys + kBuildWarps - 1) / kBuildWarps, int64_t(num_sms));
+  tt_build_kernel<<<int(g), kBuildWarps * 32, smem, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ enum TTCounter {
 static_assert(TT_COUNT <= 16, "the solution set keeps 16 host copies of the TT counters");
 
 constexpr uint32_t kTTResample = 1u << 29;  // TTSys flag: sample again in FP64
+constexpr uint32_t kTTValid = 1u << 30;     // RootItem flag: polished (zlo = zhi = v1)
 
 struct TTParams {
   MeshView mesh;
@@ -41,8 +42,8 @@ struct TTParams {
   int64_t sys_cap;
   int64_t n_sys;           // systems of this batch (build, sign)
   int64_t sys_offset;      // first system of this batch
-  double* scratch;         // [kTTScratch][n_sys] FP64 (batch-local)
-  float* coef32;           // [kTT32][n_sys] FP32 (batch-local)
+  double* scratch;         // [n_sys][kTTKeep] FP64: a, b, u~, v~, kappa (batch-local)
+  float* coef32;           // [n_sys][kTT32] FP32: scaled, normalised a and b (batch-local)
   RootItem* queue;         // brackets: zlo = zhi = v1 after the polish; chain = system (global index)
   int64_t queue_cap;
   unsigned long long* counters;  // [TT_COUNT]
@@ -58,7 +59,8 @@ cudaError_t launch_tt_fill(const TTParams& P, const uint8_t* masks, int num_sms,
 // Per batch of systems [sys_offset, sys_offset + n_sys):
 cudaError_t launch_tt_build(const TTParams& P, int num_sms, cudaStream_t st);
 cudaError_t launch_tt_sign(const TTParams& P, int num_sms, cudaStream_t st);
-cudaError_t launch_tt_polish(const TTParams& P, int64_t item_begin, int64_t item_end, int num_sms, cudaStream_t st);
+// FP64 polish of the batch's brackets (after the sign pass).
+cudaError_t launch_tt_polish(const TTParams& P, int num_sms, cudaStream_t st);
 cudaError_t launch_tt_paths(const TTParams& P, int64_t chain_begin, int64_t chain_end, int num_sms, cudaStream_t st);
 
 }  // namespace spoly

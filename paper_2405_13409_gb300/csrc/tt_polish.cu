@@ -1,84 +1,10 @@
-// TT chains, FP64 phase: polish of every FP32 bracket by bisection of the
-// FP64 Bezout determinant (one warp per bracket), then the path phase per
-// chain: u1 from a(u1, v1*) = 0, u2 from the rational mapping (Eq. eq_rct),
+// TT chains, path phase per chain (after the FP64 polish in tt_sign.cuh):
+// u1 from a(u1, v1*) = 0, u2 from the rational mapping (Eq. eq_rct),
 // path-space Newton on h x n = 0 at both vertices (Eq. eq_ch), sidedness,
 // in-triangle tests and de-duplication of the chain's paths.
-#include "tt_det.cuh"
+#include "tt_kernels.cuh"
 
 namespace spoly {
-
-constexpr uint32_t kValid = 1u << 30;
-
-SPOLY_D int sign64(const TTParams& P, const TTSys& sy, int64_t col, double v, int lane, double* sa, double* sb) {
-  const double* base = P.scratch + col;
-  const int64_t st = P.n_sys;
-  const int ks = sy.ks;
-  auto ca = [&](int i, int j) { return ldexp(base[int64_t(kOffA + bidx(kTTDa, i, j)) * st], ks * i); };
-  auto cb = [&](int i, int j) { return ldexp(base[int64_t(kOffB + bidx(kTTDb, i, j)) * st], ks * i); };
-  float l2;
-  if (sy.n <= 16) return tt_sign_at<double, 16>(v, sy.da, sy.db, sy.n, lane, ca, cb, sa, sb, &l2);
-  return tt_sign_at<double, 32>(v, sy.da, sy.db, sy.n, lane, ca, cb, sa, sb, &l2);
-}
-
-// One warp per bracket of this batch.
-__global__ void __launch_bounds__(128) tt_polish_kernel(TTParams P, int64_t item_begin, int64_t item_end) {
-  __shared__ double sa[4][32], sb[4][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t nw = int64_t(gridDim.x) * 4;
-  for (int64_t it = item_begin + int64_t(blockIdx.x) * 4 + warp; it < item_end; it += nw) {
-    RootItem item = P.queue[it];
-    const TTSys sy = P.sys[item.chain];
-    const int64_t col = item.chain - P.sys_offset;
-    double lo = item.zlo, hi = item.zhi;
-    bool ok = true;
-    if (lo < hi) {
-      int slo = sign64(P, sy, col, lo, lane, sa[warp], sb[warp]);
-      int shi = sign64(P, sy, col, hi, lane, sa[warp], sb[warp]);
-      // The FP32 bracket may sit beside the FP64 root: widen it (within one
-      // sample interval on each side) until the FP64 signs differ.
-      const double reach = 1.0 / P.n_intervals;
-      double w = hi - lo;
-      while (slo != 0 && shi != 0 && slo == shi && w < 2.0 * reach) {
-        w *= 2.0;
-        const double c = 0.5 * (lo + hi);
-        lo = fmax(0.0, c - w);
-        hi = fmin(1.0, c + w);
-        slo = sign64(P, sy, col, lo, lane, sa[warp], sb[warp]);
-        shi = sign64(P, sy, col, hi, lane, sa[warp], sb[warp]);
-      }
-      if (slo == 0) {
-        hi = lo;
-      } else if (shi == 0) {
-        lo = hi;
-      } else if (slo == shi) {
-        ok = false;
-      } else {
-        while (hi - lo > kTTRootTol) {
-          const double mid = 0.5 * (lo + hi);
-          if (!(mid > lo && mid < hi)) break;
-          const int s = sign64(P, sy, col, mid, lane, sa[warp], sb[warp]);
-          if (s == 0) {
-            lo = hi = mid;
-            break;
-          }
-          if (s == slo)
-            lo = mid;
-          else
-            hi = mid;
-        }
-      }
-    }
-    if (lane == 0) {
-      if (ok) {
-        item.zlo = item.zhi = 0.5 * (lo + hi);
-        item.flags |= kValid;
-      } else {
-        atomicAdd(P.counters + TT_POLISH_LOST, 1ull);
-      }
-      P.queue[it] = item;
-    }
-  }
-}
 
 // ------------------------------------------------------------- path phase
 struct TTPath {
@@ -215,8 +141,8 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
         const TTSys sy = P.sys[si];
         if (sy.n < 1) continue;
         const int64_t col = si - P.sys_offset;
-        const double* sc = P.scratch + col;
-        const int64_t st = P.n_sys;
+        const double* sc = P.scratch + col * kTTKeep;
+        const int64_t st = 1;
         const GP A{const_cast<double*>(sc) + int64_t(kOffA) * st, st, kTTDa};
         const GP B{const_cast<double*>(sc) + int64_t(kOffB) * st, st, kTTDb};
         const GP UT{const_cast<double*>(sc) + int64_t(kOffUt) * st, st, kTTDmap};
@@ -224,7 +150,7 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
         const GP KA{const_cast<double*>(sc) + int64_t(kOffKap) * st, st, kTTDmap};
         for (int k = 0; k < sy.n_items; ++k) {
           const RootItem item = P.queue[sy.first_item + k];
-          if (!(item.flags & kValid)) continue;
+          if (!(item.flags & kTTValid)) continue;
           const double v = item.zlo;
           // u1 from a(u1, v*) = 0 on [-delta, 1 - v* + delta]
           double ac[kTTDa + 1];
@@ -334,13 +260,6 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
       P.paths[idx] = p;
     }
   }
-}
-
-cudaError_t launch_tt_polish(const TTParams& P, int64_t item_begin, int64_t item_end, int num_sms, cudaStream_t st) {
-  if (item_end <= item_begin) return cudaSuccess;
-  const int64_t g = std::min<int64_t>((item_end - item_begin + 3) / 4, int64_t(num_sms) * 8);
-  tt_polish_kernel<<<int(g), 128, 0, st>>>(P, item_begin, item_end);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_tt_paths(const TTParams& P, int64_t chain_begin, int64_t chain_end, int num_sms, cudaStream_t st) {

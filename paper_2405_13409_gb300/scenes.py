@@ -193,6 +193,57 @@ def slab_scene(seed: int = 0, n_cells: int = 16, n_recv: int = 64, thickness: fl
                        "top": (0, top.shape[1]), "bottom": (top.shape[1], tri.shape[1])})
 
 
+def batched_scene(seed: int = 0, n_queries: int = 4096, c_min: float = 1e2, c_max: float = 1e5) -> Scene:
+    """Batched mixed workload: independent queries with bounce count uniform
+    in {1, 2} and candidate counts log-uniform in [c_min, c_max], each with
+    its own geometry from the refraction or the slab generator (seed + 1 + q).
+
+    1 bounce: the refraction heightfield (amplitude 0.08, eta 1 -> 1.5, light
+    (0, 0, 2)) with max(64, ceil(sqrt(C / 2))) cells a side, so that it holds
+    at least C triangles; the query's chains are C distinct triangles.
+    2 bounces: the 16x16-cell slab (top at z = 0, bottom at z = -0.3, eta
+    (1, 1.5, 1), light (0.2, 0.1, 2)); the chains are C distinct (top, bottom)
+    pairs.  Receivers are uniform on z = -1 over [-1.5, 1.5]^2.  All meshes
+    are concatenated; chains are grouped by query."""
+    rng = np.random.default_rng(seed)
+    ks = rng.integers(1, 3, n_queries).astype(np.int32)
+    counts = np.exp(rng.uniform(np.log(c_min), np.log(c_max), n_queries)).astype(np.int64)
+    recv = np.column_stack([rng.uniform(-1.5, 1.5, (n_queries, 2)), np.full(n_queries, -1.0)])
+    meshes, chains = [], []
+    xf = np.empty((n_queries, 3))
+    eta = np.tile(np.array([1.0, 1.5, 1.0]), (n_queries, 1))
+    types = np.full((n_queries, 2), TYPE_T, dtype=np.int32)
+    offset = 0
+    for q in range(n_queries):
+        qs = seed + 1 + q
+        qrng = np.random.default_rng([seed, q])
+        c = int(counts[q])
+        if ks[q] == 1:
+            n = max(64, int(math.ceil(math.sqrt(c / 2.0))))
+            z_fn, grad_fn = sinusoid_surface(qs, 0.08)
+            tri = heightfield_mesh(n, z_fn, grad_fn)
+            t = qrng.choice(tri.shape[1], c, replace=False).astype(np.int64) + offset
+            ch = np.column_stack([np.full(c, q), t, np.full(c, -1)])
+            xf[q] = (0.0, 0.0, 2.0)
+        else:
+            z1, g1 = sinusoid_surface(qs, 0.05)
+            z2, g2 = sinusoid_surface(qs + 1, 0.05)
+            top = heightfield_mesh(16, z1, g1)
+            bot = heightfield_mesh(16, z2, g2, z_offset=-0.3)
+            tri = np.concatenate([top, bot], axis=1)
+            nt = top.shape[1]
+            pick = qrng.choice(nt * nt, c, replace=False).astype(np.int64)
+            ch = np.column_stack([np.full(c, q), offset + pick // nt, offset + nt + pick % nt])
+            xf[q] = (0.2, 0.1, 2.0)
+        meshes.append(tri)
+        chains.append(ch)
+        offset += tri.shape[1]
+    tri = np.ascontiguousarray(np.concatenate(meshes, axis=1))
+    ch = np.concatenate(chains).astype(np.int32)
+    return Scene(f"batched_{n_queries}", tri, xf, np.ascontiguousarray(recv), eta, types, ks, chains=ch,
+                 meta={"seed": seed, "n_queries": n_queries, "counts": counts, "c_range": (c_min, c_max)})
+
+
 def glint_surface(seed: int, n_terms: int = 64, n_cells: int = 1024):
     """Sum of random-phase plane waves of wavelength 2..20 cells, slope 0.02 each."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,127 @@
+"""GPU tests of the batched mixed workload's pieces: the per-chain cone test
+of explicit lists (EXPLICIT_CONE) is conservative for both bounce counts,
+the learned gate passes 2-bounce chains through, and the whole batch solved
+in one call equals the unculled solve."""
+import numpy as np
+import pytest
+
+from paper_2405_13409_gb300 import binding, scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bctx():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    stream = torch.cuda.Stream()
+    c = binding.Context(0, stream.cuda_stream)
+    yield c, stream
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def batch(bctx):
+    ctx, stream = bctx
+    s = scenes.batched_scene(seed=3, n_queries=32, c_min=300, c_max=8000)
+    with torch.cuda.stream(stream):
+        d = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+             for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, s.chains)]
+    stream.synchronize()
+    return s, d, ctx.mesh(d[0]), ctx.queries(*d[1:6])
+
+
+def _keys(p):
+    return sorted(zip(p["query"].tolist(), p["tri"][:, 0].tolist(), p["tri"][:, 1].tolist(),
+                      np.round(p["uv"].reshape(-1, 4), 8).tolist()))
+
+
+def test_batched_scene_shape():
+    s = scenes.batched_scene(seed=1, n_queries=16, c_min=100, c_max=1000)
+    counts = s.meta["counts"]
+    assert s.chains.shape[0] == counts.sum()
+    q = s.chains[:, 0]
+    assert np.all(np.diff(q) >= 0)  # grouped by query
+    for i in range(16):
+        ch = s.chains[q == i]
+        assert ch.shape[0] == counts[i]
+        assert np.all((ch[:, 2] >= 0) == (s.k[i] == 2))
+        assert np.unique(ch[:, 1:], axis=0).shape[0] == ch.shape[0]  # distinct candidates
+    assert s.chains[:, 1:].max() < s.n_tris
+
+
+@pytest.mark.parametrize("precision", [binding.MIXED, binding.PLAIN_FP64])
+def test_explicit_cone_is_conservative(bctx, batch, precision):
+    ctx, stream = bctx
+    s, d, mesh, q = batch
+    full = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=d[6])
+    cut = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT_CONE, margin=1e-3, explicit=d[6])
+    n_full, n_cut = ctx.spoly_chains_count(full), ctx.spoly_chains_count(cut)
+    assert n_full == s.chains.shape[0]
+    assert 0 < n_cut < n_full // 10
+    kept = ctx.spoly_chains_copy(cut)
+    src = {tuple(r) for r in s.chains.tolist()}
+    assert all(tuple(r) in src for r in kept.tolist())
+    a = ctx.spoly_solve(mesh, q, full, precision=precision)
+    b = ctx.spoly_solve(mesh, q, cut, precision=precision, flags=binding.SOLVE_PERSISTENT)
+    pa, pb = ctx.spoly_paths(a), ctx.spoly_paths(b)
+    ctx.spoly_solution_free(a)
+    ctx.spoly_solution_free(b)
+    ctx.spoly_chains_free(full)
+    ctx.spoly_chains_free(cut)
+    assert pa.size > 5
+    assert _keys(pa) == _keys(pb)
+
+
+def _rows(a):
+    return sorted(map(tuple, a.tolist()))
+
+
+def test_explicit_cone_equals_range_cone(bctx):
+    """On every (receiver, triangle) pair, or every (receiver, top, bottom)
+    tuple of a slab, the per-chain test keeps exactly the chains of the
+    range-based cone cull (the same predicates)."""
+    ctx, stream = bctx
+    r = scenes.refract_scene(seed=2, n_cells=32, n_recv=12)
+    sl = scenes.slab_scene(seed=0, n_cells=16, n_recv=2)
+    half = sl.n_tris // 2
+    for s, ranges in ((r, None), (sl, ((0, half), (half, sl.n_tris)))):
+        with torch.cuda.stream(stream):
+            d = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                 for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
+        stream.synchronize()
+        mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+        if ranges is None:
+            ref = ctx.spoly_build_chains(mesh, q, binding.CHAINS_CONE, margin=1e-3)
+            allc = scenes.all_pairs(s.n_queries, s.n_tris)
+        else:
+            ref = ctx.spoly_build_chains(mesh, q, binding.CHAINS_CONE, margin=1e-3, tri_range=ranges[0],
+                                         second_range=ranges[1])
+            qq, t1, t2 = np.meshgrid(np.arange(s.n_queries), np.arange(half), np.arange(half, s.n_tris),
+                                     indexing="ij")
+            allc = np.stack([qq.ravel(), t1.ravel(), t2.ravel()], -1).astype(np.int32)
+        exp = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT_CONE, margin=1e-3,
+                                     explicit=torch.from_numpy(allc).cuda())
+        a, b = ctx.spoly_chains_copy(ref), ctx.spoly_chains_copy(exp)
+        ctx.spoly_chains_free(ref)
+        ctx.spoly_chains_free(exp)
+        assert 0 < a.shape[0] < allc.shape[0] // 20
+        assert _rows(a) == _rows(b)
+
+
+def test_gate_passes_two_bounce_chains(bctx, batch):
+    ctx, stream = bctx
+    s, d, mesh, q = batch
+    cut = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT_CONE, margin=1e-3, explicit=d[6])
+    mlp = ctx.spoly_mlp_create(seed=5)
+    gated = ctx.spoly_gate(mlp, mesh, q, cut, float("inf"))  # rejects every 1-bounce chain
+    kept = ctx.spoly_chains_copy(gated)
+    all_cut = ctx.spoly_chains_copy(cut)
+    assert kept.shape[0] == int((all_cut[:, 2] >= 0).sum()) > 0
+    assert np.all(kept[:, 2] >= 0)
+    ctx.spoly_chains_free(gated)
+    ctx.spoly_chains_free(cut)
+    ctx.spoly_mlp_free(mlp)
