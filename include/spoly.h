@@ -195,7 +195,8 @@ typedef struct {
   int64_t k2_systems;   /* 2-bounce (chain, sqrt piece) systems */
   int64_t k2_evals;     /* 2-bounce Bezout determinant evaluations */
   int64_t k2_eval_n3;   /* sum of n^3 over those evaluations (work of the sign phase) */
-  int64_t reserved[2];
+  int64_t k2_fp64_samples; /* samples evaluated again in FP64 (re-sampled 2-bounce systems) */
+  int64_t reserved;
 } spoly_counters;
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`

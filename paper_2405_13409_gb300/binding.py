@@ -87,8 +87,8 @@ class spoly_path(ctypes.Structure):
 class spoly_counters(ctypes.Structure):
     _fields_ = [(n, c_int64) for n in ("candidates", "degenerate", "v_roots", "queued", "prefiltered",
                                        "polish_lost", "u_roots", "admissible", "flagged", "fallback",
-                                       "unsolved", "k2_systems", "k2_evals", "k2_eval_n3")] + \
-               [("reserved", c_int64 * 2)]
+                                       "unsolved", "k2_systems", "k2_evals", "k2_eval_n3", "k2_fp64_samples")] + \
+               [("reserved", c_int64)]
 
 
 class spoly_tune_entry(ctypes.Structure):

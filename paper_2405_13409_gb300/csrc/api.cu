@@ -164,6 +164,13 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
   T.coef32 = static_cast<float*>(set->tt_coef32.p);
   T.queue = static_cast<RootItem*>(set->tt_queue.p);
   T.queue_cap = bmax * 128;
+  // kept FP32 signs of up to kNoisy re-sampled systems per batch (others are
+  // sampled again in full)
+  constexpr int64_t kNoisy = 1024;
+  CK(set->tt_noisy.ensure(size_t(kNoisy) * kTTSampleSlots * (sizeof(int8_t) + sizeof(float))), "tt noisy");
+  T.noisy_lg = static_cast<float*>(set->tt_noisy.p);
+  T.noisy_sgn = reinterpret_cast<int8_t*>(T.noisy_lg + kNoisy * kTTSampleSlots);
+  T.noisy_cap = kNoisy;
   unsigned long long brackets_total = 0, resampled_total = 0;
   int64_t c0 = 0;
   while (c0 < n2) {
@@ -177,6 +184,7 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
     CK(cudaMemsetAsync(T.counters + TT_BRACKETS, 0, sizeof(unsigned long long), st), "tt memset");
     CK(launch_tt_build(T, ctx->num_sms, st), "tt build");
     CK(cudaMemsetAsync(T.counters + TT_RESAMPLED, 0, sizeof(unsigned long long), st), "tt memset");
+    CK(cudaMemsetAsync(T.counters + TT_NOISY, 0, sizeof(unsigned long long), st), "tt memset");
     CK(launch_tt_sign(T, ctx->num_sms, st), "tt sign");
     unsigned long long nres = 0;
     CK(cudaMemcpyAsync(&nres, T.counters + TT_RESAMPLED, sizeof(nres), cudaMemcpyDeviceToHost, st), "tt resample");
@@ -824,6 +832,7 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
     out->k2_systems = int64_t(t[TT_SYSTEMS]);
     out->k2_evals = int64_t(t[TT_EVALS]);
     out->k2_eval_n3 = int64_t(t[TT_EVAL_N3]);
+    out->k2_fp64_samples = int64_t(t[TT_FP64_SAMPLES]);
   }
   return SPOLY_OK;
 }
@@ -960,7 +969,7 @@ spoly_status spoly_solution_free(spoly_solution_set* set) {
   set->paths.release();
   set->counters.release();
   for (DevBuf* b : {&set->part, &set->part_n, &set->tt_counters, &set->tt_chain_sys, &set->tt_masks, &set->tt_sys,
-                    &set->tt_scratch, &set->tt_coef32, &set->tt_queue})
+                    &set->tt_scratch, &set->tt_coef32, &set->tt_queue, &set->tt_noisy})
     b->release();
   if (set->gexec) cudaGraphExecDestroy(set->gexec);
   delete set;

@@ -44,7 +44,7 @@ struct TTSys {
   int32_t ks;      // u = 2^ks w balances the u-coefficients (FP32 copy)
   uint32_t flags;  // SPOLY_FLAG_SQRT_SPLIT
   int32_t first_item, n_items;  // bracket range in the queue (sign kernel)
-  int32_t pad;
+  int32_t noisy;   // 1 + slot of the FP32 signs kept for the FP64 re-sampling pass (0: none)
 };
 
 // Arena of one system (FP64, element e at base[e * stride]): the final a, b

@@ -20,11 +20,15 @@ enum TTCounter {
   TT_RESAMPLED,     // systems whose FP32 signs changed too often, sampled again in FP64
   TT_EVALS,         // Bezout determinant evaluations (samples + bisection steps)
   TT_EVAL_N3,       // sum over evaluations of n^3 (work model of the sign kernel)
+  TT_NOISY,         // slots taken in the kept-signs buffer (per batch)
+  TT_FP64_SAMPLES,  // samples evaluated again in FP64 by the re-sampling pass
   TT_COUNT
 };
 static_assert(TT_COUNT <= 16, "the solution set keeps 16 host copies of the TT counters");
 
 constexpr uint32_t kTTResample = 1u << 29;  // TTSys flag: sample again in FP64
+constexpr int kTTSampleSlots = 8193;         // samples per system at most (n_intervals <= 8192)
+constexpr int kTTNoisyMargin = 8;            // FP64 re-sampling: samples kept beyond the outermost FP32 change
 constexpr uint32_t kTTValid = 1u << 30;     // RootItem flag: polished (zlo = zhi = v1)
 
 struct TTParams {
@@ -47,6 +51,11 @@ struct TTParams {
   RootItem* queue;         // brackets: zlo = zhi = v1 after the polish; chain = system (global index)
   int64_t queue_cap;
   unsigned long long* counters;  // [TT_COUNT]
+  // FP32 signs and log2 |det| of re-sampled systems ([noisy_cap][kTTSampleSlots]):
+  // the FP64 pass evaluates again only the stretch where the FP32 signs changed
+  int8_t* noisy_sgn;
+  float* noisy_lg;
+  int64_t noisy_cap;
   spoly_path* paths;
   int64_t path_cap;
   unsigned long long* path_counter;  // shared with the 1-bounce paths

@@ -12,7 +12,7 @@ namespace spoly {
 
 constexpr int kSignThreads = 128;
 constexpr int kMaxBrackets = 128;  // per system: more re-samples the system in FP64 (FP32), or overflows (FP64)
-constexpr int kMaxSamples = 8193;  // n_intervals <= 8192
+constexpr int kMaxSamples = kTTSampleSlots;  // n_intervals <= 8192
 
 // The block stages the scaled FP64 coefficients of system i of the batch
 // (u = 2^ks w) in `coef`, graded layout: a then b.
@@ -40,6 +40,8 @@ struct SignSmem {
   int nb;
   float lmax;
   int base;
+  int span_lo, span_hi;  // samples to evaluate
+  long long slot;
 };
 
 template <typename T, int N, int G>
@@ -56,13 +58,51 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
   const int gi = tid / G, g = tid % G;
   const int NI = P.n_intervals;
   const T dv = T(1) / T(NI);
+  if (tid == 0) {
+    S.span_lo = 0;
+    S.span_hi = NI;
+  }
+  __syncthreads();
+  if (P.resample_only && sy.noisy > 0 && sy.noisy <= P.noisy_cap) {
+    // FP64 re-sampling: the FP32 signs stand outside the stretch where they
+    // changed (widened by kTTNoisyMargin samples on each side)
+    const int64_t base = int64_t(sy.noisy - 1) * kTTSampleSlots;
+    if (tid == 0) {
+      S.span_lo = NI + 1;
+      S.span_hi = -1;
+    }
+    __syncthreads();
+    int lo = NI + 1, hi = -1;
+    for (int m = tid; m <= NI; m += kSignThreads) {
+      S.sgn[m] = P.noisy_sgn[base + m];
+      S.lg[m] = P.noisy_lg[base + m];
+    }
+    __syncthreads();
+    for (int m = tid; m < NI; m += kSignThreads)
+      if (S.sgn[m + 1] == 0 || S.sgn[m] == 0 || S.sgn[m] != S.sgn[m + 1]) {
+        lo = min(lo, m);
+        hi = max(hi, m + 1);
+      }
+    atomicMin(&S.span_lo, lo);
+    atomicMax(&S.span_hi, hi);
+    __syncthreads();
+    if (tid == 0) {
+      S.span_lo = max(0, S.span_lo - kTTNoisyMargin);
+      S.span_hi = min(NI, S.span_hi + kTTNoisyMargin);
+      if (S.span_hi >= S.span_lo) atomicAdd(P.counters + TT_FP64_SAMPLES, (unsigned long long)(S.span_hi - S.span_lo + 1));
+    }
+    __syncthreads();
+  } else if (P.resample_only && tid == 0) {
+    atomicAdd(P.counters + TT_FP64_SAMPLES, (unsigned long long)(NI + 1));
+  }
+  const int m_lo = S.span_lo, m_hi = S.span_hi;
   // samples: the whole block steps together, so every warp stays converged
 #pragma unroll 1
-  for (int m0 = 0; m0 <= NI; m0 += kGroups) {
+  for (int m0 = m_lo; m0 <= m_hi; m0 += kGroups) {
     const int m = m0 + gi;
     float l2;
-    const int s = sign_g<T, N, G>(S, T(min(m, NI)) * dv, sy, g, &l2);
-    if (m <= NI && g == 0) {
+    const int s = sign_g<T, N, G>(S, T(min(m, m_hi)) * dv, sy, g, &l2);
+    if (m <= m_hi && g == 0) {
       S.sgn[m] = int8_t(s);
       S.lg[m] = l2;
     }
@@ -107,12 +147,28 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
   __syncthreads();
   if (sizeof(T) == 4 && S.nb > kMaxBrackets) {
     // FP32 rounding noise in a near-singular stretch of v: the system is
-    // sampled again in FP64 (re-sampling pass)
+    // sampled again in FP64 (re-sampling pass), which keeps these signs
+    // outside the stretch
     if (tid == 0) {
       atomicAdd(P.counters + TT_RESAMPLED, 1ull);
+      atomicAdd(P.counters + TT_EVALS, (unsigned long long)(NI + 1));
+      atomicAdd(P.counters + TT_EVAL_N3, (unsigned long long)(NI + 1) * (unsigned long long)(sy.n * sy.n * sy.n));
+      S.slot = (long long)atomicAdd(P.counters + TT_NOISY, 1ull);
+    }
+    __syncthreads();
+    const long long slot = S.slot;
+    if (slot < P.noisy_cap) {
+      const int64_t base = int64_t(slot) * kTTSampleSlots;
+      for (int m = tid; m <= NI; m += kSignThreads) {
+        P.noisy_sgn[base + m] = S.sgn[m];
+        P.noisy_lg[base + m] = S.lg[m];
+      }
+    }
+    if (tid == 0) {
       sy.first_item = 0;
       sy.n_items = 0;
       sy.flags |= kTTResample;
+      sy.noisy = slot < P.noisy_cap ? int32_t(slot + 1) : 0;
       P.sys[P.sys_offset + i] = sy;
     }
     return;
@@ -166,7 +222,7 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
   }
   __syncthreads();
   if (tid == 0) {
-    unsigned long long ev = (unsigned long long)(NI + 1);
+    unsigned long long ev = (unsigned long long)(m_hi >= m_lo ? m_hi - m_lo + 1 : 0);
     for (int k = 0; k < nb; ++k) ev += (S.blo[k] < S.bhi[k]) ? kTTPaperIters + 2 : 0;
     atomicAdd(P.counters + TT_EVALS, ev);
     atomicAdd(P.counters + TT_EVAL_N3, ev * (unsigned long long)(sy.n * sy.n * sy.n));
