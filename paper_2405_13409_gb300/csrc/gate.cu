@@ -67,6 +67,24 @@ __global__ void pack_kernel(const float* __restrict__ theta, uint32_t* __restric
   }
 }
 
+// ReLU, then BF16 rounding (nearest even) of two values in one instruction;
+// the low half holds lo.
+SPOLY_D uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// d = a b + c with c given apart (the bias), so the accumulators need no
+// initialising moves.
+SPOLY_D void mma_bf16_c(float (&d)[4], const uint32_t (&a)[4], uint2 b, float c0, float c1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%11,%10,%11};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y), "f"(c0), "f"(c1));
+}
+
 SPOLY_D void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -87,16 +105,12 @@ SPOLY_D void layer(float (&acc)[2][8][4], const uint32_t (&a)[2][4][4], const ui
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     const float b0 = bias[8 * nt + c2], b1 = bias[8 * nt + c2 + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      acc[mt][nt][0] = b0;
-      acc[mt][nt][1] = b1;
-      acc[mt][nt][2] = b0;
-      acc[mt][nt][3] = b1;
-    }
+    const uint2 b = wf[nt * 32 + lane];
+    mma_bf16_c(acc[0][nt], a[0][0], b, b0, b1);
+    mma_bf16_c(acc[1][nt], a[1][0], b, b0, b1);
   }
 #pragma unroll
-  for (int kt = 0; kt < KT; ++kt)
+  for (int kt = 1; kt < KT; ++kt)
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       const uint2 b = wf[(kt * 8 + nt) * 32 + lane];
@@ -114,14 +128,14 @@ SPOLY_D void relu_to_a(const float (&acc)[2][8][4], uint32_t (&a)[2][4][4]) {
     for (int j = 0; j < 4; ++j) {
       const float* lo = acc[mt][2 * j];
       const float* hi = acc[mt][2 * j + 1];
-      a[mt][j][0] = pack_bf16(fmaxf(lo[0], 0.f), fmaxf(lo[1], 0.f));
-      a[mt][j][1] = pack_bf16(fmaxf(lo[2], 0.f), fmaxf(lo[3], 0.f));
-      a[mt][j][2] = pack_bf16(fmaxf(hi[0], 0.f), fmaxf(hi[1], 0.f));
-      a[mt][j][3] = pack_bf16(fmaxf(hi[2], 0.f), fmaxf(hi[3], 0.f));
+      a[mt][j][0] = pack_relu_bf16(lo[0], lo[1]);
+      a[mt][j][1] = pack_relu_bf16(lo[2], lo[3]);
+      a[mt][j][2] = pack_relu_bf16(hi[0], hi[1]);
+      a[mt][j][3] = pack_relu_bf16(hi[2], hi[3]);
     }
 }
 
-__global__ void __launch_bounds__(128) gate_kernel(GateParams G) {
+__global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
   __shared__ __align__(16) uint32_t sw[kPackWords];
   __shared__ __align__(16) __nv_bfloat16 sx[kGateRows * kXStride];
   __shared__ float sz[kGateRows];

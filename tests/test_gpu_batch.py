@@ -126,7 +126,7 @@ def test_gate_passes_two_bounce_chains(bctx, batch):
     s, d, mesh, q = batch
     cut = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT_CONE, margin=1e-3, explicit=d[6])
     mlp = ctx.spoly_mlp_create(seed=5)
-    gated = ctx.spoly_gate(mlp, mesh, q, cut, float("inf"))  # rejects every 1-bounce chain
+    gated = ctx.spoly_gate(mlp, mesh, q, cut, 3e38)  # rejects every 1-bounce chain
     kept = ctx.spoly_chains_copy(gated)
     all_cut = ctx.spoly_chains_copy(cut)
     assert kept.shape[0] == int((all_cut[:, 2] >= 0).sum()) > 0
