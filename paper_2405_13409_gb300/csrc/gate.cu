@@ -493,7 +493,6 @@ spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* m, const spoly_mesh* me
   if (!ctx) return SPOLY_EINVAL;
   if (!m || !in || !inout || in == *inout) return fail(ctx, SPOLY_EINVAL, "gate: bad arguments");
   if (!std::isfinite(tau_logit)) return fail(ctx, SPOLY_EINVAL, "gate: non-finite threshold");
-  if (in->n_k2 > 0) return fail(ctx, SPOLY_EUNSUPPORTED, "gate: the network gates 1-bounce chains only");
   MeshView mv;
   QueryView qv;
   spoly_status s = stage_inputs(ctx, mesh, q, &mv, &qv);
@@ -527,7 +526,7 @@ spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* m, const spoly_mesh* me
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "gate"));
   ch->n = int64_t(cnt);
-  ch->n_k2 = 0;
+  ch->n_k2 = in->n_k2;  // every 2-bounce chain passes
   *inout = ch;
   return SPOLY_OK;
 }
