@@ -171,55 +171,40 @@ SPOLY_D bool pixel_footprint(const CamF& C, int64_t q, float zlo, float zhi, flo
   return true;
 }
 
-// pass 0: count candidates per pixel; pass 1: write them at out_off[q].
-// One warp per pixel: the entries of the consecutive cells of one row of
-// the footprint are contiguous, so the lanes test 32 of them at a time (the
-// gathers of a pixel overlap instead of following one another), and the
-// survivors are compacted by ballot, so the chain writes are coalesced.
+// pass 0: count candidates per pixel; pass 1: write them at out_off[q]
 __global__ void footprint_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
                                  const int* cell_count, const int64_t* cell_off, const int32_t* entries,
                                  int64_t* pix_count, const int64_t* pix_off, int32_t* out, int pass) {
   const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < n_pixels; q += nw) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pixels; q += stride) {
     float xl, xh, yl, yh;
-    int64_t n = 0;
-    const int64_t o = pass ? pix_off[q] : 0;
-    if (pixel_footprint(C, q, zlo, zhi, xl, xh, yl, yh)) {  // the same for every lane
+    int64_t n = 0, o = pass ? pix_off[q] : 0;
+    if (pixel_footprint(C, q, zlo, zhi, xl, xh, yl, yh)) {
       int fx0, fx1, fy0, fy1;
       cell_range(G, xl, xh, yl, yh, fx0, fx1, fy0, fy1);
-      for (int cy = fy0; cy <= fy1; ++cy) {
-        const int64_t row = int64_t(cy) * G.gx;
-        const int64_t b = cell_off[row + fx0], e = cell_off[row + fx1] + cell_count[row + fx1];
-        for (int64_t k0 = b; k0 < e; k0 += 32) {
-          const int64_t k = k0 + lane;
-          bool keep = false;
-          int32_t t = 0;
-          if (k < e) {
-            t = entries[k];
-            int cx = fx0;  // the entry's cell
-            while (cx < fx1 && cell_off[row + cx + 1] <= k) ++cx;
+      for (int cy = fy0; cy <= fy1; ++cy)
+        for (int cx = fx0; cx <= fx1; ++cx) {
+          const int64_t cell = int64_t(cy) * G.gx + cx;
+          const int64_t b = cell_off[cell], e = b + cell_count[cell];
+          for (int64_t k = b; k < e; ++k) {
+            const int32_t t = entries[k];
             float txl, txh, tyl, tyh;
             tri_bbox(boxes, t, txl, txh, tyl, tyh);
-            if (!(txh < xl || txl > xh || tyh < yl || tyl > yh)) {
-              int tx0, tx1, ty0, ty1;
-              cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
-              keep = cx == max(tx0, fx0) && cy == max(ty0, fy0);  // emitted from its first shared cell
+            if (txh < xl || txl > xh || tyh < yl || tyl > yh) continue;
+            int tx0, tx1, ty0, ty1;
+            cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
+            if (cx != max(tx0, fx0) || cy != max(ty0, fy0)) continue;  // emitted from its first shared cell
+            if (pass) {
+              out[3 * (o + n)] = int32_t(q);
+              out[3 * (o + n) + 1] = t;
+              out[3 * (o + n) + 2] = -1;
             }
+            ++n;
           }
-          const unsigned m = __ballot_sync(0xffffffffu, keep);
-          if (pass && keep) {
-            const int64_t idx = o + n + __popc(m & ((1u << lane) - 1u));
-            out[3 * idx] = int32_t(q);
-            out[3 * idx + 1] = t;
-            out[3 * idx + 2] = -1;
-          }
-          n += __popc(m);
         }
-      }
     }
-    if (!pass && lane == 0) pix_count[q] = n;
+    if (!pass) pix_count[q] = n;
   }
 }
 
@@ -351,8 +336,8 @@ cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const
   cudaError_t e = cudaMemsetAsync(L.cell_count, 0, size_t(n_cells) * 4, st);
   if (e != cudaSuccess) return e;
   grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, G, L.cell_count, L.cell_off, entries, 1);
-  footprint_kernel<<<num_sms * 16, 256, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
-                                                 L.cell_off, entries, L.pix_count, nullptr, nullptr, 0);
+  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
+                                                L.cell_off, entries, L.pix_count, nullptr, nullptr, 0);
   if ((e = exclusive_scan<int64_t>(L.pix_count, L.pix_off, n_pixels, L, st)) != cudaSuccess) return e;
   return read_total(L.pix_off, L.pix_count, true, n_pixels, total, st);
 }
@@ -363,8 +348,8 @@ cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const i
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
-  footprint_kernel<<<num_sms * 16, 256, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
-                                                 L.cell_off, entries, nullptr, L.pix_off, out, 1);
+  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
+                                                L.cell_off, entries, nullptr, L.pix_off, out, 1);
   return cudaGetLastError();
 }
 
