@@ -61,8 +61,24 @@ BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["b
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
 # Kernel launches per step, counted from the ncu launch list of each
 # workload (profiles/).
-LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 18, ("glints", True): 19,
-                     ("slab", False): 11, ("batched", True): 40, ("batched", False): 39}
+LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 18, ("glints", True): 19}
+# 2-bounce solve: systems count + fill, then per batch of <= 16,384 systems the
+# build, six FP32 sign classes, five FP64 re-sampling chunk classes and five
+# re-sampling scan classes, five polish classes and the path kernel.
+TT_FIXED, TT_PER_BATCH, TT_BATCH = 2, 23, 16384
+
+
+def launches_per_step(workload, use_gate, stats):
+    """Kernel launches of the library in one step (counted from the ncu
+    launch lists of each workload, profiles/)."""
+    if workload in ("slab", "batched"):
+        batches = -(-int(stats.get("k2_systems", 0)) // TT_BATCH)
+        tt = TT_FIXED + TT_PER_BATCH * batches
+        if workload == "slab":
+            return 5 + 1 + tt  # cone cull (flag, shared check, forward boxes, pairs, chains), partition
+        # explicit validation + cone test, gate, partition, persistent isolation, side, polish, paths
+        return 2 + (1 if use_gate else 0) + 1 + 4 + tt
+    return LAUNCHES_PER_STEP.get((workload, use_gate), 7)
 # DRAM bytes (read + write) per launch of the isolation kernel from the last
 # ncu capture (profiles/kernels_refract_64x64_r256_mixed.md).  Reported only
 # while the kernel's sources hash to the value the capture was taken on.
@@ -622,15 +638,18 @@ def main():
                 else 0.0}
     roofline = roof_iso
     if kind == "TT" or (batched and ph["k2"] >= max(ph["gate"], iso, ph["chains"])):
-        # 2-bounce sign phase work: per determinant evaluation ~4/3 n^3 flop (Bezout
-        # entries n^3/3 FMA + elimination n^3/3 FMA) + ~1,900 flop of Horner
-        # evaluation of the coefficients; timed over the whole 2-bounce phase
-        tt_flops = 4.0 / 3.0 * stats.get("k2_eval_n3", 0) + 1900.0 * stats.get("k2_evals", 0)
+        # 2-bounce sign phase work per determinant evaluation: elimination
+        # n^3/3 FMA, the Bezout row recurrence 2 n^2 FMA, ~1,900 flop of Horner
+        # evaluation of the coefficients (n from the library's work counters);
+        # timed over the whole 2-bounce phase
+        ev = stats.get("k2_evals", 0)
+        nbar = (stats.get("k2_eval_n3", 0) / ev) ** (1.0 / 3.0) if ev else 0.0
+        tt_flops = 2.0 / 3.0 * stats.get("k2_eval_n3", 0) + (4.0 * nbar * nbar + 1900.0) * ev
         ach = tt_flops / (ph["k2"] * 1e-3) / 1e12 if ph["k2"] > 0 else 0.0
         roofline = {"bound": "alu", "pipe": "fp32", "kernel": "2-bounce phase (tt_sign_kernel dominant)",
                     "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32 if peak32 else None,
                     "peak_source": "measured FP32 FMA microbenchmark (spoly_measure_peak)", "traffic": None,
-                    "flop_model": "4/3 n^3 + 1900 per Bezout determinant evaluation",
+                    "flop_model": "2/3 n^3 + 4 n^2 + 1900 per Bezout determinant evaluation",
                     "evals_per_step": stats.get("k2_evals", 0)}
     if use_gate:
         gate_tflops = GATE_FLOPS * n_cand / (ph["gate"] * 1e-3) / 1e12
@@ -661,7 +680,7 @@ def main():
         "gate": gate_info,
         "autotune": tune,
         "roofline": roofline,
-        "gpu_launches": LAUNCHES_PER_STEP.get((args.workload, use_gate), 7) * args.steps,
+        "gpu_launches": launches_per_step(args.workload, use_gate, stats) * args.steps,
         "clocks": clk,
         "e2e": e2e,
     }

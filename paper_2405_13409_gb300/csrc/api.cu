@@ -167,9 +167,11 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
   // kept FP32 signs of up to kNoisy re-sampled systems per batch (others are
   // sampled again in full)
   constexpr int64_t kNoisy = 1024;
-  CK(set->tt_noisy.ensure(size_t(kNoisy) * kTTSampleSlots * (sizeof(int8_t) + sizeof(float))), "tt noisy");
+  CK(set->tt_noisy.ensure(size_t(kNoisy) * (kTTSampleSlots * (sizeof(int8_t) + sizeof(float)) + 3 * sizeof(int32_t))),
+     "tt noisy");
   T.noisy_lg = static_cast<float*>(set->tt_noisy.p);
-  T.noisy_sgn = reinterpret_cast<int8_t*>(T.noisy_lg + kNoisy * kTTSampleSlots);
+  T.noisy_span = reinterpret_cast<int32_t*>(T.noisy_lg + kNoisy * kTTSampleSlots);
+  T.noisy_sgn = reinterpret_cast<int8_t*>(T.noisy_span + 3 * kNoisy);
   T.noisy_cap = kNoisy;
   unsigned long long brackets_total = 0, resampled_total = 0;
   int64_t c0 = 0;

@@ -12,7 +12,7 @@ SPOLY_D int64_t queue_items(const K1Params& P) {
 }
 
 // FP64 v-polish of every queued bracket, in place.
-__global__ void __launch_bounds__(128, 1) k1_polish_kernel(K1Params P) {
+__global__ void __launch_bounds__(32) k1_polish_kernel(K1Params P) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t n_items = queue_items(P);
   const int lane = threadIdx.x & 31;
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(128, 1) k1_polish_kernel(K1Params P) {
 
 // Path phase of every polished bracket; admissible paths appended with one
 // atomic per warp.
-__global__ void __launch_bounds__(128) k1_path_kernel(K1Params P) {
+__global__ void __launch_bounds__(32) k1_path_kernel(K1Params P) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t n_items = queue_items(P);
   const int lane = threadIdx.x & 31;
@@ -126,12 +126,14 @@ cudaError_t launch_k1_isolate_persistent(const K1Params& P, int precision, int n
 }
 
 cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st) {
-  k1_polish_kernel<<<num_sms * 8, 128, 0, st>>>(P);
+  // one-warp blocks: the few thousand brackets of a step spread evenly over
+  // the SMs (the kernel is FP64-bound per SM)
+  k1_polish_kernel<<<num_sms * 32, 32, 0, st>>>(P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st) {
-  k1_path_kernel<<<num_sms * 8, 128, 0, st>>>(P);
+  k1_path_kernel<<<num_sms * 32, 32, 0, st>>>(P);
   return cudaGetLastError();
 }
 

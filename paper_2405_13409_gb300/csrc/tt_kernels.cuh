@@ -55,6 +55,7 @@ struct TTParams {
   // the FP64 pass evaluates again only the stretch where the FP32 signs changed
   int8_t* noisy_sgn;
   float* noisy_lg;
+  int32_t* noisy_span;     // [noisy_cap][3]: batch-local system, first and last sample to evaluate again
   int64_t noisy_cap;
   spoly_path* paths;
   int64_t path_cap;

@@ -64,32 +64,16 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
   }
   __syncthreads();
   if (P.resample_only && sy.noisy > 0 && sy.noisy <= P.noisy_cap) {
-    // FP64 re-sampling: the FP32 signs stand outside the stretch where they
-    // changed (widened by kTTNoisyMargin samples on each side)
+    // FP64 re-sampling: tt_resample_chunk_kernel has evaluated the stretch
+    // where the FP32 signs changed; the kept FP32 signs stand elsewhere
     const int64_t base = int64_t(sy.noisy - 1) * kTTSampleSlots;
-    if (tid == 0) {
-      S.span_lo = NI + 1;
-      S.span_hi = -1;
-    }
-    __syncthreads();
-    int lo = NI + 1, hi = -1;
     for (int m = tid; m <= NI; m += kSignThreads) {
       S.sgn[m] = P.noisy_sgn[base + m];
       S.lg[m] = P.noisy_lg[base + m];
     }
-    __syncthreads();
-    for (int m = tid; m < NI; m += kSignThreads)
-      if (S.sgn[m + 1] == 0 || S.sgn[m] == 0 || S.sgn[m] != S.sgn[m + 1]) {
-        lo = min(lo, m);
-        hi = max(hi, m + 1);
-      }
-    atomicMin(&S.span_lo, lo);
-    atomicMax(&S.span_hi, hi);
-    __syncthreads();
     if (tid == 0) {
-      S.span_lo = max(0, S.span_lo - kTTNoisyMargin);
-      S.span_hi = min(NI, S.span_hi + kTTNoisyMargin);
-      if (S.span_hi >= S.span_lo) atomicAdd(P.counters + TT_FP64_SAMPLES, (unsigned long long)(S.span_hi - S.span_lo + 1));
+      S.span_lo = 1;
+      S.span_hi = 0;
     }
     __syncthreads();
   } else if (P.resample_only && tid == 0) {
@@ -154,14 +138,31 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
       atomicAdd(P.counters + TT_EVALS, (unsigned long long)(NI + 1));
       atomicAdd(P.counters + TT_EVAL_N3, (unsigned long long)(NI + 1) * (unsigned long long)(sy.n * sy.n * sy.n));
       S.slot = (long long)atomicAdd(P.counters + TT_NOISY, 1ull);
+      S.span_lo = NI + 1;
+      S.span_hi = -1;
     }
     __syncthreads();
     const long long slot = S.slot;
     if (slot < P.noisy_cap) {
       const int64_t base = int64_t(slot) * kTTSampleSlots;
+      int lo = NI + 1, hi = -1;
       for (int m = tid; m <= NI; m += kSignThreads) {
         P.noisy_sgn[base + m] = S.sgn[m];
         P.noisy_lg[base + m] = S.lg[m];
+        if (m < NI && (S.sgn[m + 1] == 0 || S.sgn[m] == 0 || S.sgn[m] != S.sgn[m + 1])) {
+          lo = min(lo, m);
+          hi = max(hi, m + 1);
+        }
+      }
+      atomicMin(&S.span_lo, lo);
+      atomicMax(&S.span_hi, hi);
+      __syncthreads();
+      // the stretch where the FP32 signs changed, widened by kTTNoisyMargin
+      // samples on each side, is evaluated again in FP64
+      if (tid == 0) {
+        P.noisy_span[3 * slot] = int32_t(i);
+        P.noisy_span[3 * slot + 1] = max(0, S.span_lo - kTTNoisyMargin);
+        P.noisy_span[3 * slot + 2] = min(NI, S.span_hi + kTTNoisyMargin);
       }
     }
     if (tid == 0) {
@@ -295,6 +296,68 @@ cudaError_t launch_sign_class(const TTParams& P, int n_lo, int num_sms, cudaStre
   }
   const int64_t g = std::min<int64_t>(P.n_sys, int64_t(num_sms) * per_sm);
   tt_sign_kernel<T, N, G><<<int(g), kSignThreads, smem, st>>>(P, n_lo);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------- FP64 re-sampling
+// The stretches kept by the FP32 pass, in chunks of kResampleChunk samples:
+// one block per (slot, chunk) item, items interleaved across slots so that
+// long stretches spread over the grid; the FP64 signs and log2 |det|
+// overwrite the kept FP32 values.  The sign kernel's re-sampling pass then
+// scans and bisects the merged samples.
+constexpr int kResampleChunk = 128;
+constexpr int kResampleChunks = (kTTSampleSlots + kResampleChunk - 1) / kResampleChunk;
+
+template <int N, int G>
+__global__ void __launch_bounds__(kSignThreads) tt_resample_chunk_kernel(TTParams P, int n_lo) {
+  __shared__ double coef[kTT32];
+  constexpr int kGroups = kSignThreads / G;
+  const int tid = threadIdx.x, gi = tid / G, g = tid % G;
+  const unsigned long long taken = *(volatile unsigned long long*)(P.counters + TT_NOISY);
+  const int64_t n_noisy = taken < (unsigned long long)P.noisy_cap ? int64_t(taken) : P.noisy_cap;
+  const double dv = 1.0 / P.n_intervals;
+  for (int64_t item = blockIdx.x; item < n_noisy * kResampleChunks; item += gridDim.x) {
+    const int64_t slot = item % n_noisy;
+    const int c = int(item / n_noisy);
+    const int32_t i = P.noisy_span[3 * slot], lo = P.noisy_span[3 * slot + 1], hi = P.noisy_span[3 * slot + 2];
+    const int m0 = lo + c * kResampleChunk;
+    if (m0 > hi) continue;
+    const TTSys sy = P.sys[P.sys_offset + i];
+    if (sy.n <= n_lo || sy.n > N) continue;
+    tt_stage_coef64(P, i, sy, coef);
+    __syncthreads();
+    const int m1 = min(hi, m0 + kResampleChunk - 1);
+    const int64_t base = slot * kTTSampleSlots;
+#pragma unroll 1
+    for (int mm = m0; mm <= m1; mm += kGroups) {
+      const int m = mm + gi;
+      const GroupSign r =
+          tt_group_sign<double, N, G>(coef, coef + bsize(kTTDa), double(min(m, m1)) * dv, sy.da, sy.db, sy.n, g);
+      if (m <= m1 && g == 0) {
+        P.noisy_sgn[base + m] = int8_t(r.sign);
+        P.noisy_lg[base + m] = r.log2;
+      }
+    }
+    if (tid == 0) {
+      const unsigned long long k = (unsigned long long)(m1 - m0 + 1);
+      atomicAdd(P.counters + TT_FP64_SAMPLES, k);
+      atomicAdd(P.counters + TT_EVALS, k);
+      atomicAdd(P.counters + TT_EVAL_N3, k * (unsigned long long)(sy.n * sy.n * sy.n));
+    }
+    __syncthreads();
+  }
+}
+
+template <int N, int G>
+cudaError_t launch_resample_class(const TTParams& P, int n_lo, int num_sms, cudaStream_t st) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    const cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tt_resample_chunk_kernel<N, G>, kSignThreads, 0);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+  }
+  tt_resample_chunk_kernel<N, G><<<num_sms * per_sm, kSignThreads, 0, st>>>(P, n_lo);
   return cudaGetLastError();
 }
 
