@@ -493,17 +493,21 @@ def main():
     elif use_gate:
         from paper_2405_13409_gb300 import gate_train, scenes
         t0 = time.perf_counter()
-        if batched:  # the gate covers the 1-bounce (refraction) chains
-            train = [scenes.refract_scene(seed=1000 + i, n_recv=128) for i in range(args.train_seeds)]
-            val = [scenes.refract_scene(seed=2000, n_recv=128)]
-            gmode = binding.CHAINS_CONE
+        if batched:
+            # the gate covers the 1-bounce (refraction) chains, whose meshes
+            # have 64 to 224 cells a side: training and validation scenes
+            # span that range, and the threshold keeps a wider margin
+            cells = [64 + (160 * i) // max(1, args.train_seeds - 1) for i in range(args.train_seeds)]
+            train = [scenes.refract_scene(seed=1000 + i, n_cells=c, n_recv=128) for i, c in enumerate(cells)]
+            val = [scenes.refract_scene(seed=2000, n_cells=144, n_recv=128)]
+            gmode, margin = binding.CHAINS_CONE, 2.0
         else:
             train = [scenes.glint_scene(seed=1000 + i) for i in range(args.train_seeds)]
             val = [scenes.glint_scene(seed=2000)]
-            gmode = mode
+            gmode, margin = mode, 1.0
         gen_s = time.perf_counter() - t0
-        mlp, tau, gate_info = gate_train.train_gate(ctx, torch, train, val, gmode, camera, steps=args.train_steps,
-                                                    seed=args.seed)
+        mlp, tau, gate_info = gate_train.train_gate(ctx, torch, train, val, gmode, camera, margin=margin,
+                                                    steps=args.train_steps, seed=args.seed)
         gate_info["scene_generation_s"] = gen_s
         gate_info["train_seeds"] = [1000 + i for i in range(args.train_seeds)]
         gate_info["val_seeds"] = [2000]

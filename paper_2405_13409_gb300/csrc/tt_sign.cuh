@@ -363,28 +363,28 @@ cudaError_t launch_resample_class(const TTParams& P, int n_lo, int num_sms, cuda
 
 // ------------------------------------------------------------ FP64 polish
 // Every FP32 bracket of a system is polished by bisection of the FP64
-// determinant to kTTRootTol.  One block per system (its coefficients staged
-// once), one group per bracket; loops run in warp-uniform steps (a warp
-// leaves a loop when none of its groups needs another step).  A bracket
-// whose FP64 signs agree is widened, by factors of 8 and within one sample
-// interval on each side, until they differ; if they never do it is lost.
-constexpr int kPolishWiden = 4;      // 2^-22 * 8^4 > 2^-12
+// determinant to kTTRootTol, one group per bracket.  Work items are (system,
+// chunk of one block's worth of brackets), interleaved across systems so
+// that systems with many brackets spread over the grid; each item stages
+// its system's coefficients.  Loops run in warp-uniform steps (a warp leaves
+// a loop when none of its groups needs another step).  A bracket whose FP64
+// signs agree is widened, by factors of 64 and within one sample interval on
+// each side, until they differ; if they never do it is lost.
+constexpr int kPolishWiden = 2;      // 2^-22 * 64^2 > 2^-12
 constexpr int kPolishMaxSteps = 40;  // bisection steps from one sample interval to kTTRootTol: 23
 
 template <int N, int G>
-SPOLY_D void polish_system(const double* coef, const TTParams& P, const TTSys& sy) {
-  constexpr int kGroups = kSignThreads / G;
+SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys& sy, int64_t k_begin, int64_t k_end) {
   const int tid = threadIdx.x, gi = tid / G, g = tid % G;
   const double reach = 1.0 / P.n_intervals;
   const int64_t first = sy.first_item;
-  const int64_t ni = (int64_t(sy.n_items) < P.queue_cap - first) ? int64_t(sy.n_items) : P.queue_cap - first;
   auto ev = [&](double x) {
     return tt_group_sign<double, N, G>(coef, coef + bsize(kTTDa), x, sy.da, sy.db, sy.n, g).sign;
   };
-  for (int64_t k0 = 0; k0 < ni; k0 += kGroups) {
-    const int64_t k = k0 + gi;
-    const bool valid = k < ni;
-    if (!__any_sync(kGroupFull, valid)) continue;  // the warp has no bracket this round
+  {
+    const int64_t k = k_begin + gi;
+    const bool valid = k < k_end;
+    if (!__any_sync(kGroupFull, valid)) return;  // the warp has no bracket
     RootItem item{};
     if (valid) item = P.queue[first + k];
     double lo = valid ? item.zlo : 0.0, hi = valid ? item.zhi : 1.0;
@@ -397,7 +397,7 @@ SPOLY_D void polish_system(const double* coef, const TTParams& P, const TTSys& s
       const bool need = act && slo != 0 && shi != 0 && slo == shi && w < reach;
       if (!__any_sync(kGroupFull, need)) break;
       const double c = 0.5 * (lo + hi);
-      const double w2 = fmin(8.0 * w, reach);
+      const double w2 = fmin(64.0 * w, reach);
       const double l2 = fmax(0.0, c - w2), h2 = fmin(1.0, c + w2);
       const int s1 = ev(need ? l2 : lo), s2 = ev(need ? h2 : hi);
       if (need) {
@@ -452,12 +452,20 @@ SPOLY_D void polish_system(const double* coef, const TTParams& P, const TTSys& s
 template <int N, int G>
 __global__ void __launch_bounds__(kSignThreads) tt_polish_kernel(TTParams P, int n_lo) {
   __shared__ double coef[kTT32];
-  for (int64_t i = blockIdx.x; i < P.n_sys; i += gridDim.x) {
+  constexpr int kGroups = kSignThreads / G;
+  constexpr int kChunks = (kMaxBrackets + kGroups - 1) / kGroups;
+  for (int64_t item = blockIdx.x; item < P.n_sys * kChunks; item += gridDim.x) {
+    const int64_t i = item % P.n_sys;
+    const int c = int(item / P.n_sys);
     const TTSys sy = P.sys[P.sys_offset + i];
-    if (sy.n_items <= 0 || sy.n <= n_lo || sy.n > N || sy.first_item < 0 || sy.first_item >= P.queue_cap) continue;
+    if (sy.n_items <= c * kGroups || sy.n <= n_lo || sy.n > N || sy.first_item < 0 || sy.first_item >= P.queue_cap)
+      continue;
+    const int64_t ni = (int64_t(sy.n_items) < P.queue_cap - sy.first_item) ? int64_t(sy.n_items)
+                                                                           : P.queue_cap - sy.first_item;
     tt_stage_coef64(P, i, sy, coef);
     __syncthreads();
-    polish_system<N, G>(coef, P, sy);
+    const int64_t k_end = ni < int64_t(c + 1) * kGroups ? ni : int64_t(c + 1) * kGroups;
+    polish_brackets<N, G>(coef, P, sy, int64_t(c) * kGroups, k_end);
     __syncthreads();
   }
 }
