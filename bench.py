@@ -79,19 +79,31 @@ def launches_per_step(workload, use_gate, stats):
         # explicit validation + cone test, gate, partition, persistent isolation, side, polish, paths
         return 2 + (1 if use_gate else 0) + 1 + 4 + tt
     return LAUNCHES_PER_STEP.get((workload, use_gate), 7)
-# DRAM bytes (read + write) per launch of the isolation kernel from the last
-# ncu capture (profiles/kernels_refract_64x64_r256_mixed.md).  Reported only
-# while the kernel's sources hash to the value the capture was taken on.
-KERNEL_SOURCES = ["common.cuh", "polys.cuh", "laplace_gen.cuh", "k1_sys.cuh", "k1_iso.cuh", "k1_iso_f32.cu"]
-TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) per launch from an ncu capture of the kernel on
+# the workload named, reported only while the kernel's sources hash to the
+# value the capture was taken on (profiles/ holds the captures).
+TRAFFIC = {
+    "gate_kernel": {"workload": "glints", "sources": ["gate.cu", "gate.cuh", "mlp.cuh", "common.cuh"],
+                    "sources_sha256": None, "bytes_per_launch": None},
+    "k1_isolate_kernel": {"workload": "refract",
+                          "sources": ["common.cuh", "polys.cuh", "laplace_gen.cuh", "k1_sys.cuh", "k1_iso.cuh",
+                                      "k1_iso_f32.cu"], "sources_sha256": None, "bytes_per_launch": None},
+}
 
 
-def kernel_sources_sha256() -> str:
+def kernel_sources_sha256(files) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2405_13409_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
+
+
+def traffic(kernel, workload):
+    t = TRAFFIC[kernel]
+    if t["workload"] != workload or t["sources_sha256"] is None:
+        return None
+    return t["bytes_per_launch"] if t["sources_sha256"] == kernel_sources_sha256(t["sources"]) else None
 
 
 def parse():
@@ -499,7 +511,7 @@ def main():
             # span that range, and the threshold keeps a wider margin
             cells = [64 + (160 * i) // max(1, args.train_seeds - 1) for i in range(args.train_seeds)]
             train = [scenes.refract_scene(seed=1000 + i, n_cells=c, n_recv=128) for i, c in enumerate(cells)]
-            val = [scenes.refract_scene(seed=2000, n_cells=144, n_recv=128)]
+            val = [scenes.refract_scene(seed=2000 + i, n_cells=c, n_recv=128) for i, c in enumerate((64, 144, 224))]
             gmode, margin = binding.CHAINS_CONE, 2.0
         else:
             train = [scenes.glint_scene(seed=1000 + i) for i in range(args.train_seeds)]
@@ -510,7 +522,7 @@ def main():
                                                     steps=args.train_steps, seed=args.seed)
         gate_info["scene_generation_s"] = gen_s
         gate_info["train_seeds"] = [1000 + i for i in range(args.train_seeds)]
-        gate_info["val_seeds"] = [2000]
+        gate_info["val_seeds"] = [2000 + i for i in range(len(val))]
         del train, val
         torch.cuda.empty_cache()
         if args.gate_file:
@@ -636,7 +648,7 @@ def main():
     roof_iso = {"bound": "alu", "pipe": "fp64", "kernel": "k1_isolate_kernel<float>",
                 "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s", "frac": achieved64 / peak64,
                 "peak_source": "measured FP64 FMA microbenchmark (spoly_measure_peak)",
-                "traffic": TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None,
+                "traffic": traffic("k1_isolate_kernel", args.workload),
                 "nominal_fp64_tflops": NOMINAL_FP64_TFLOPS, "measured_fp32_tflops": peak32,
                 "fp32_laplace_tflops": FP32_LAPLACE_FLOPS.get(kind, 0) * n_solved / (iso * 1e-3) / 1e12 if iso > 0
                 else 0.0}
@@ -660,7 +672,7 @@ def main():
         roof_gate = {"bound": "tensor", "kernel": "gate_kernel (features + BF16 mma.sync MLP + compaction)",
                      "achieved": gate_tflops, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": gate_tflops / BF16_PEAK_TFLOPS, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
-                     "traffic": None, "flops_per_candidate": GATE_FLOPS}
+                     "traffic": traffic("gate_kernel", args.workload), "flops_per_candidate": GATE_FLOPS}
         # the dominant phase of the step carries the headline roofline
         if not (batched and roofline.get("pipe") == "fp32"):
             roofline = roof_gate if ph["gate"] >= iso else roof_iso
