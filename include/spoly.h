@@ -431,11 +431,14 @@ spoly_status spoly_mlp_train(spoly_ctx* ctx, spoly_mlp* mlp, const float* feat, 
 spoly_status spoly_mlp_calibrate(spoly_ctx* ctx, spoly_mlp* mlp, const float* feat, const uint8_t* labels,
                                  int64_t n, double target_recall, float* tau_logit, double* pass_fraction);
 
-/* Gates a chain list: features, network and compaction in one kernel; the
- * 1-bounce chains whose logit is >= tau_logit, and every 2-bounce chain
- * (tri1 >= 0: outside the network's domain), are written to *inout (created
- * when NULL, else reused and grown; it must not be `in`).  Their order is
- * not preserved.  Synchronises (reads the count back). */
+/* Gates a chain list: features, network and compaction in one kernel.  A
+ * 1-bounce chain passes if its logit is >= tau_logit or if the zero of its
+ * tangential mismatch (the features' barycentric coordinates) lies inside
+ * the triangle (smallest coordinate >= -0.02): the network only rejects
+ * chains whose zero lies outside.  Every 2-bounce chain (tri1 >= 0: outside
+ * the network's domain) passes.  The survivors are written to *inout
+ * (created when NULL, else reused and grown; it must not be `in`).  Their
+ * order is not preserved.  Synchronises (reads the count back). */
 spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* mlp, const spoly_mesh* mesh, const spoly_queries* q,
                         const spoly_chains* in, float tau_logit, spoly_chains** inout);
 

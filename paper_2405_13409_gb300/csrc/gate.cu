@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
 #pragma unroll
       for (int j = 0; j < kFeat; ++j) f[j] = 0.0f;
     }
+    const bool inside = f[kFeatMinBary] >= kGateInside;
     uint32_t* xr = reinterpret_cast<uint32_t*>(sx + tid * kXStride);
 #pragma unroll
     for (int j = 0; j < kFeat / 2; ++j) xr[j] = pack_bf16(f[2 * j], f[2 * j + 1]);
@@ -214,8 +215,11 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
     const float z = sz[tid];
     if (valid && G.logits) G.logits[row] = z;
     if (G.out_chains) {
-      // 2-bounce chains are outside the network's domain and pass ungated
-      const bool keep = valid && (z >= G.tau_logit || __ldg(G.chains + 3 * row + 2) >= 0);
+      // 2-bounce chains are outside the network's domain and pass ungated;
+      // a chain whose tangential-mismatch zero lies inside the triangle
+      // always passes (the network only rejects chains whose zero lies
+      // outside it)
+      const bool keep = valid && (z >= G.tau_logit || inside || __ldg(G.chains + 3 * row + 2) >= 0);
       const unsigned long long slot = warp_append(G.out_n, keep ? 1u : 0u);
       if (keep) {
         G.out_chains[3 * slot] = __ldg(G.chains + 3 * row);

@@ -14,6 +14,8 @@
 namespace spoly {
 
 constexpr int kFeat = 24;
+constexpr int kFeatMinBary = 12;      // the smallest barycentric coordinate of the mismatch zero
+constexpr float kGateInside = -0.02f;  // the gate passes chains whose mismatch zero lies inside (this slack)
 constexpr int kIn = 32;
 constexpr int kHid = 64;
 

@@ -152,7 +152,11 @@ def test_gate_kernel_matches_features_and_forward(ctx, glint_small):
     finally:
         ctx.spoly_mlp_free(mlp)
     chains = ctx.spoly_chains_copy(ch)
-    want = set(map(tuple, chains[zc >= tau].tolist()))
+    # kept: logit >= tau, or the tangential-mismatch zero inside the triangle
+    # (smallest barycentric feature >= -0.02)
+    inside = f[:, 12].cpu().numpy() >= -0.02
+    want = set(map(tuple, chains[(zc >= tau) | inside].tolist()))
+    assert 0 < inside.sum() < inside.size // 4
     assert set(map(tuple, kept.tolist())) == want
     assert kept.shape[0] == len(want)
 
