@@ -126,11 +126,17 @@ def test_gate_passes_two_bounce_chains(bctx, batch):
     s, d, mesh, q = batch
     cut = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT_CONE, margin=1e-3, explicit=d[6])
     mlp = ctx.spoly_mlp_create(seed=5)
-    gated = ctx.spoly_gate(mlp, mesh, q, cut, 3e38)  # rejects every 1-bounce chain
+    # a threshold no logit reaches: only the 2-bounce chains and the 1-bounce
+    # chains whose mismatch zero lies inside the triangle pass
+    gated = ctx.spoly_gate(mlp, mesh, q, cut, 3e38)
     kept = ctx.spoly_chains_copy(gated)
     all_cut = ctx.spoly_chains_copy(cut)
-    assert kept.shape[0] == int((all_cut[:, 2] >= 0).sum()) > 0
-    assert np.all(kept[:, 2] >= 0)
+    f = torch.empty((all_cut.shape[0], 24), dtype=torch.float32, device="cuda")
+    ctx.spoly_mlp_features(mesh, q, cut, f)
+    inside = f[:, 12].cpu().numpy() >= -0.02
+    want = all_cut[(all_cut[:, 2] >= 0) | inside]
+    assert int((all_cut[:, 2] >= 0).sum()) > 0
+    assert _rows(kept) == _rows(want)
     ctx.spoly_chains_free(gated)
     ctx.spoly_chains_free(cut)
     ctx.spoly_mlp_free(mlp)
