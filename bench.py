@@ -84,7 +84,8 @@ def launches_per_step(workload, use_gate, stats):
 # value the capture was taken on (profiles/ holds the captures).
 TRAFFIC = {
     "gate_kernel": {"workload": "glints", "sources": ["gate.cu", "gate.cuh", "mlp.cuh", "common.cuh"],
-                    "sources_sha256": None, "bytes_per_launch": None},
+                    "sources_sha256": "04e0406b20593418a90127fecafba0bcf5692d5a7a3b932421478b74c21e0468",
+                    "bytes_per_launch": 429683712 + 3668992},  # profiles/kernels_glints_gate.md
     "k1_isolate_kernel": {"workload": "refract",
                           "sources": ["common.cuh", "polys.cuh", "laplace_gen.cuh", "k1_sys.cuh", "k1_iso.cuh",
                                       "k1_iso_f32.cu"], "sources_sha256": None, "bytes_per_launch": None},
@@ -452,9 +453,9 @@ def timed_steps(pipe, mesh, q, steps, flush, stream, torch):
         b.record(stream)
         b.synchronize()
         c_ms, g_ms = pipe.phase_ms()
-        i_ms, p_ms, tt_ms = pipe.ctx.spoly_phase_ms(pipe.sol)
+        i_ms, p_ms, tt_ms, sign_ms = pipe.ctx.spoly_phase_ms(pipe.sol)
         out.append({"step": a.elapsed_time(b), "chains": c_ms, "gate": g_ms, "isolation": i_ms, "polish": p_ms,
-                    "k2": tt_ms,
+                    "k2": tt_ms, "k2_sign": sign_ms,
                     "paths": pipe.ctx.spoly_stats(pipe.sol)["admissible"]})
     return out
 
@@ -641,7 +642,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    ph = {k: statistics.mean(r[k] for r in rec) for k in ("chains", "gate", "isolation", "polish", "k2")}
+    ph = {k: statistics.mean(r[k] for r in rec) for k in ("chains", "gate", "isolation", "polish", "k2", "k2_sign")}
     ph["step"] = total_ms / args.steps
     iso = ph["isolation"]
     achieved64 = FP64_FLOPS.get(kind, 0) * n_solved / (iso * 1e-3) / 1e12 if iso > 0 else 0.0
@@ -654,19 +655,24 @@ def main():
                 else 0.0}
     roofline = roof_iso
     if kind == "TT" or (batched and ph["k2"] >= max(ph["gate"], iso, ph["chains"])):
-        # 2-bounce sign phase work per determinant evaluation: elimination
-        # n^3/3 FMA, the Bezout row recurrence 2 n^2 FMA, ~1,900 flop of Horner
-        # evaluation of the coefficients (n from the library's work counters);
-        # timed over the whole 2-bounce phase
-        ev = stats.get("k2_evals", 0)
-        nbar = (stats.get("k2_eval_n3", 0) / ev) ** (1.0 / 3.0) if ev else 0.0
-        tt_flops = 2.0 / 3.0 * stats.get("k2_eval_n3", 0) + (4.0 * nbar * nbar + 1900.0) * ev
-        ach = tt_flops / (ph["k2"] * 1e-3) / 1e12 if ph["k2"] > 0 else 0.0
-        roofline = {"bound": "alu", "pipe": "fp32", "kernel": "2-bounce phase (tt_sign_kernel dominant)",
+        # the FP32 sign kernels (tt_sign_kernel<float, N, G>, all size
+        # classes), timed by the library with CUDA events around their
+        # launches.  Work per determinant evaluation: elimination n^3/3 FMA,
+        # the Bezout row recurrence 2 n^2 FMA, ~1,900 flop of Horner
+        # evaluation of the coefficients (n from the library's counters of
+        # the FP32 pass).
+        ev = stats.get("k2_evals32", 0)
+        n3 = stats.get("k2_eval32_n3", 0)
+        nbar = (n3 / ev) ** (1.0 / 3.0) if ev else 0.0
+        tt_flops = 2.0 / 3.0 * n3 + (4.0 * nbar * nbar + 1900.0) * ev
+        sign_ms = ph["k2_sign"]
+        ach = tt_flops / (sign_ms * 1e-3) / 1e12 if sign_ms > 0 else 0.0
+        roofline = {"bound": "alu", "pipe": "fp32", "kernel": "tt_sign_kernel<float, N, G> (FP32 sign pass)",
                     "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32 if peak32 else None,
                     "peak_source": "measured FP32 FMA microbenchmark (spoly_measure_peak)", "traffic": None,
                     "flop_model": "2/3 n^3 + 4 n^2 + 1900 per Bezout determinant evaluation",
-                    "evals_per_step": stats.get("k2_evals", 0)}
+                    "evals_per_step": ev, "mean_bezout_size": nbar, "sign_ms_per_step": sign_ms,
+                    "phase_ms_per_step": ph["k2"]}
     if use_gate:
         gate_tflops = GATE_FLOPS * n_cand / (ph["gate"] * 1e-3) / 1e12
         roof_gate = {"bound": "tensor", "kernel": "gate_kernel (features + BF16 mma.sync MLP + compaction)",

@@ -196,7 +196,8 @@ typedef struct {
   int64_t k2_evals;     /* 2-bounce Bezout determinant evaluations */
   int64_t k2_eval_n3;   /* sum of n^3 over those evaluations (work of the sign phase) */
   int64_t k2_fp64_samples; /* samples evaluated again in FP64 (re-sampled 2-bounce systems) */
-  int64_t reserved;
+  int64_t k2_evals32;   /* 2-bounce evaluations of the FP32 sign pass (mixed mode) */
+  int64_t k2_eval32_n3; /* sum of n^3 over them */
 } spoly_counters;
 
 /* Creates a context on CUDA device `device` that enqueues on `cuda_stream`
@@ -271,8 +272,10 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
 /* Device time of the last solve's phases, measured with CUDA events on the
  * context stream when the solve set SPOLY_SOLVE_TIMING: ms[0] = isolation
  * (coefficient, elimination and univariate phases, both isolation kernels),
- * ms[1] = FP64 polish and path phase.  n >= 2.  Synchronises on the last
- * event.  Errors: EINVAL if the solve was not timed. */
+ * ms[1] = FP64 polish and path phase, ms[2] (n >= 3) = the whole 2-bounce
+ * pipeline, ms[3] (n >= 4) = its sign passes in the solve's precision (the
+ * FP32 pass in mixed mode), summed over batches.  n >= 2.  Synchronises on
+ * the last event.  Errors: EINVAL if the solve was not timed. */
 spoly_status spoly_phase_ms(spoly_ctx* ctx, const spoly_solution_set* set, float* ms, int32_t n);
 
 /* Peak-throughput microbenchmark of a scalar pipe on the context's device:

@@ -87,8 +87,8 @@ class spoly_path(ctypes.Structure):
 class spoly_counters(ctypes.Structure):
     _fields_ = [(n, c_int64) for n in ("candidates", "degenerate", "v_roots", "queued", "prefiltered",
                                        "polish_lost", "u_roots", "admissible", "flagged", "fallback",
-                                       "unsolved", "k2_systems", "k2_evals", "k2_eval_n3", "k2_fp64_samples")] + \
-               [("reserved", c_int64)]
+                                       "unsolved", "k2_systems", "k2_evals", "k2_eval_n3", "k2_fp64_samples",
+                                       "k2_evals32", "k2_eval32_n3")]
 
 
 class spoly_tune_entry(ctypes.Structure):
@@ -303,10 +303,11 @@ class Context:
         self.lib.spoly_solution_free(sol)
 
     def spoly_phase_ms(self, sol) -> tuple:
-        """(1-bounce isolation, 1-bounce polish + paths, 2-bounce pipeline) in ms."""
-        ms = (ctypes.c_float * 3)()
-        self.check(self.lib.spoly_phase_ms(self.h, sol, ms, 3), "spoly_phase_ms")
-        return float(ms[0]), float(ms[1]), float(ms[2])
+        """(1-bounce isolation, 1-bounce polish + paths, 2-bounce pipeline,
+        2-bounce sign passes) in ms."""
+        ms = (ctypes.c_float * 4)()
+        self.check(self.lib.spoly_phase_ms(self.h, sol, ms, 4), "spoly_phase_ms")
+        return float(ms[0]), float(ms[1]), float(ms[2]), float(ms[3])
 
     def spoly_measure_peak(self, kind: int) -> float:
         t = ctypes.c_double()

@@ -107,6 +107,12 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
                       const int32_t* k2, const int32_t* k2_ids, int64_t n2, const spoly_solve_opts* opts,
                       unsigned long long* path_counter, spoly_path* paths, int64_t path_cap) {
   cudaStream_t st = ctx->stream;
+  const bool timing = (opts->flags & SPOLY_SOLVE_TIMING) != 0;
+  set->tt_sign_ms = 0.0f;
+  if (timing && !set->tt_ev[0]) {
+    CK(cudaEventCreate(&set->tt_ev[0]), "tt timing");
+    CK(cudaEventCreate(&set->tt_ev[1]), "tt timing");
+  }
   TTParams T{};
   T.mesh = mv;
   T.qv = qv;
@@ -187,10 +193,17 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
     CK(launch_tt_build(T, ctx->num_sms, st), "tt build");
     CK(cudaMemsetAsync(T.counters + TT_RESAMPLED, 0, sizeof(unsigned long long), st), "tt memset");
     CK(cudaMemsetAsync(T.counters + TT_NOISY, 0, sizeof(unsigned long long), st), "tt memset");
+    if (timing) CK(cudaEventRecord(set->tt_ev[0], st), "tt timing");
     CK(launch_tt_sign(T, ctx->num_sms, st), "tt sign");
+    if (timing) CK(cudaEventRecord(set->tt_ev[1], st), "tt timing");
     unsigned long long nres = 0;
     CK(cudaMemcpyAsync(&nres, T.counters + TT_RESAMPLED, sizeof(nres), cudaMemcpyDeviceToHost, st), "tt resample");
     CK(cudaStreamSynchronize(st), "tt resample");
+    if (timing) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, set->tt_ev[0], set->tt_ev[1]), "tt timing");
+      set->tt_sign_ms += ms;
+    }
     resampled_total += nres;
     if (nres > 0) {
       T.resample_only = 1;
@@ -835,6 +848,8 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
     out->k2_evals = int64_t(t[TT_EVALS]);
     out->k2_eval_n3 = int64_t(t[TT_EVAL_N3]);
     out->k2_fp64_samples = int64_t(t[TT_FP64_SAMPLES]);
+    out->k2_evals32 = int64_t(t[TT_EVALS32]);
+    out->k2_eval32_n3 = int64_t(t[TT_EVAL32_N3]);
   }
   return SPOLY_OK;
 }
@@ -875,6 +890,7 @@ spoly_status spoly_phase_ms(spoly_ctx* ctx, const spoly_solution_set* set, float
     ms[2] = 0.0f;
     if (set->n_k2 > 0) CK(cudaEventElapsedTime(&ms[2], set->ev[2], set->ev[3]), "phase timing");
   }
+  if (n >= 4) ms[3] = set->n_k2 > 0 ? set->tt_sign_ms : 0.0f;
   return SPOLY_OK;
 }
 
@@ -965,6 +981,8 @@ spoly_status spoly_autotune(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_
 spoly_status spoly_solution_free(spoly_solution_set* set) {
   if (!set) return SPOLY_EINVAL;
   for (auto& ev : set->ev)
+    if (ev) cudaEventDestroy(ev);
+  for (auto& ev : set->tt_ev)
     if (ev) cudaEventDestroy(ev);
   set->side.release();
   set->queue.release();

@@ -63,6 +63,8 @@ struct spoly_solution_set {
   unsigned long long host[spoly::C_COUNT] = {0};
   bool host_valid = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing
+  cudaEvent_t tt_ev[2] = {nullptr, nullptr};                  // 2-bounce sign pass timing
+  float tt_sign_ms = 0.0f;
   bool timed = false;
   // 2-bounce chains: partitioned lists, systems, per-batch scratch
   spoly::DevBuf part, part_n, tt_counters, tt_chain_sys, tt_masks, tt_sys, tt_scratch, tt_coef32, tt_queue, tt_noisy;

@@ -22,6 +22,8 @@ enum TTCounter {
   TT_EVAL_N3,       // sum over evaluations of n^3 (work model of the sign kernel)
   TT_NOISY,         // slots taken in the kept-signs buffer (per batch)
   TT_FP64_SAMPLES,  // samples evaluated again in FP64 by the re-sampling pass
+  TT_EVALS32,       // determinant evaluations of the FP32 sign pass
+  TT_EVAL32_N3,     // sum of n^3 over them
   TT_COUNT
 };
 static_assert(TT_COUNT <= 16, "the solution set keeps 16 host copies of the TT counters");

@@ -137,6 +137,8 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
       atomicAdd(P.counters + TT_RESAMPLED, 1ull);
       atomicAdd(P.counters + TT_EVALS, (unsigned long long)(NI + 1));
       atomicAdd(P.counters + TT_EVAL_N3, (unsigned long long)(NI + 1) * (unsigned long long)(sy.n * sy.n * sy.n));
+      atomicAdd(P.counters + TT_EVALS32, (unsigned long long)(NI + 1));
+      atomicAdd(P.counters + TT_EVAL32_N3, (unsigned long long)(NI + 1) * (unsigned long long)(sy.n * sy.n * sy.n));
       S.slot = (long long)atomicAdd(P.counters + TT_NOISY, 1ull);
       S.span_lo = NI + 1;
       S.span_hi = -1;
@@ -227,6 +229,10 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
     for (int k = 0; k < nb; ++k) ev += (S.blo[k] < S.bhi[k]) ? kTTPaperIters + 2 : 0;
     atomicAdd(P.counters + TT_EVALS, ev);
     atomicAdd(P.counters + TT_EVAL_N3, ev * (unsigned long long)(sy.n * sy.n * sy.n));
+    if (sizeof(T) == 4) {
+      atomicAdd(P.counters + TT_EVALS32, ev);
+      atomicAdd(P.counters + TT_EVAL32_N3, ev * (unsigned long long)(sy.n * sy.n * sy.n));
+    }
     S.base = int(atomicAdd(P.counters + TT_BRACKETS, (unsigned long long)nb));
     sy.first_item = S.base;
     sy.n_items = nb;
