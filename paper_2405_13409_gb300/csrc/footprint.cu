@@ -7,7 +7,9 @@
 // so every surface point a pixel can see lies inside it.  A triangle is
 // emitted once per pixel, from the first grid cell its bounding box shares
 // with the footprint.  Emission is two-pass (count, exclusive scan, fill), so
-// the chain list is ordered by pixel without global atomics.
+// the chain list is ordered by pixel without global atomics; the count pass
+// keeps each pixel's first candidates, so the fill copies them instead of
+// traversing the grid again.
 #include <algorithm>
 #include <cstring>
 
@@ -171,40 +173,80 @@ SPOLY_D bool pixel_footprint(const CamF& C, int64_t q, float zlo, float zhi, flo
   return true;
 }
 
-// pass 0: count candidates per pixel; pass 1: write them at out_off[q]
-__global__ void footprint_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
-                                 const int* cell_count, const int64_t* cell_off, const int32_t* entries,
-                                 int64_t* pix_count, const int64_t* pix_off, int32_t* out, int pass) {
+constexpr int kPixCand = 64;  // candidates per pixel kept by the count pass for the compaction
+
+// Candidates of pixel q in emission order: each one goes to emit(t); returns
+// their number.
+template <typename Emit>
+SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const CamF& C, float zlo, float zhi,
+                                 int64_t q, const int* cell_count, const int64_t* cell_off, const int32_t* entries,
+                                 Emit emit) {
+  float xl, xh, yl, yh;
+  int64_t n = 0;
+  if (!pixel_footprint(C, q, zlo, zhi, xl, xh, yl, yh)) return 0;
+  int fx0, fx1, fy0, fy1;
+  cell_range(G, xl, xh, yl, yh, fx0, fx1, fy0, fy1);
+  for (int cy = fy0; cy <= fy1; ++cy)
+    for (int cx = fx0; cx <= fx1; ++cx) {
+      const int64_t cell = int64_t(cy) * G.gx + cx;
+      const int64_t b = cell_off[cell], e = b + cell_count[cell];
+      for (int64_t k = b; k < e; ++k) {
+        const int32_t t = entries[k];
+        float txl, txh, tyl, tyh;
+        tri_bbox(boxes, t, txl, txh, tyl, tyh);
+        if (txh < xl || txl > xh || tyh < yl || tyl > yh) continue;
+        int tx0, tx1, ty0, ty1;
+        cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
+        if (cx != max(tx0, fx0) || cy != max(ty0, fy0)) continue;  // emitted from its first shared cell
+        emit(n, t);
+        ++n;
+      }
+    }
+  return n;
+}
+
+// Count pass: candidates per pixel, the first kPixCand of them kept in
+// `cand` ([n_pixels][kPixCand]) so that the fill needs no second traversal.
+__global__ void footprint_count_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
+                                       const int* cell_count, const int64_t* cell_off, const int32_t* entries,
+                                       int64_t* pix_count, int32_t* cand) {
   const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pixels; q += stride) {
-    float xl, xh, yl, yh;
-    int64_t n = 0, o = pass ? pix_off[q] : 0;
-    if (pixel_footprint(C, q, zlo, zhi, xl, xh, yl, yh)) {
-      int fx0, fx1, fy0, fy1;
-      cell_range(G, xl, xh, yl, yh, fx0, fx1, fy0, fy1);
-      for (int cy = fy0; cy <= fy1; ++cy)
-        for (int cx = fx0; cx <= fx1; ++cx) {
-          const int64_t cell = int64_t(cy) * G.gx + cx;
-          const int64_t b = cell_off[cell], e = b + cell_count[cell];
-          for (int64_t k = b; k < e; ++k) {
-            const int32_t t = entries[k];
-            float txl, txh, tyl, tyh;
-            tri_bbox(boxes, t, txl, txh, tyl, tyh);
-            if (txh < xl || txl > xh || tyh < yl || tyl > yh) continue;
-            int tx0, tx1, ty0, ty1;
-            cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
-            if (cx != max(tx0, fx0) || cy != max(ty0, fy0)) continue;  // emitted from its first shared cell
-            if (pass) {
-              out[3 * (o + n)] = int32_t(q);
-              out[3 * (o + n) + 1] = t;
-              out[3 * (o + n) + 2] = -1;
-            }
-            ++n;
-          }
+    int32_t* mine = cand + q * kPixCand;
+    pix_count[q] = pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
+                                    [&](int64_t k, int32_t t) {
+                                      if (k < kPixCand) mine[k] = t;
+                                    });
+  }
+}
+
+// Fill: one warp per pixel copies its kept candidates to out[pix_off[q]..]
+// (coalesced); a pixel with more than kPixCand traverses again on lane 0.
+__global__ void footprint_fill_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
+                                      const int* cell_count, const int64_t* cell_off, const int32_t* entries,
+                                      const int64_t* pix_count, const int64_t* pix_off, const int32_t* cand,
+                                      int32_t* out) {
+  const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < n_pixels; q += nw) {
+    const int64_t n = pix_count[q], o = pix_off[q];
+    if (n <= kPixCand) {
+      for (int64_t k = lane; k < n; k += 32) {
+        out[3 * (o + k)] = int32_t(q);
+        out[3 * (o + k) + 1] = cand[q * kPixCand + k];
+        out[3 * (o + k) + 2] = -1;
+      }
+    } else if (lane == 0) {
+      pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries, [&](int64_t k, int32_t t) {
+        if (k < n) {
+          out[3 * (o + k)] = int32_t(q);
+          out[3 * (o + k) + 1] = t;
+          out[3 * (o + k) + 2] = -1;
         }
+      });
     }
-    if (!pass) pix_count[q] = n;
   }
 }
 
@@ -252,6 +294,7 @@ struct FpLayout {
   int64_t* pix_count;
   int64_t* pix_off;
   int64_t *sums1, *sums1_off, *sums2;
+  int32_t* pix_cand;  // [n_pixels][kPixCand]
 };
 
 static size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -259,7 +302,7 @@ static size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 size_t footprint_scratch_bytes(int64_t n_cells, int64_t n_pixels) {
   const int64_t nb = (std::max(n_cells, n_pixels) + kScanBlock - 1) / kScanBlock;
   return up256(n_cells * 4) + up256(n_cells * 8) + 2 * up256(n_pixels * 8) + 2 * up256(nb * 8 + 64) +
-         up256(3 * kScanBlock * 8);
+         up256(3 * kScanBlock * 8) + up256(size_t(n_pixels) * kPixCand * 4);
 }
 
 static FpLayout fp_layout(void* scratch, int64_t n_cells, int64_t n_pixels) {
@@ -279,6 +322,8 @@ static FpLayout fp_layout(void* scratch, int64_t n_cells, int64_t n_pixels) {
   L.sums1_off = reinterpret_cast<int64_t*>(p);
   p += up256(nb * 8 + 64);
   L.sums2 = reinterpret_cast<int64_t*>(p);
+  p += up256(3 * kScanBlock * 8);
+  L.pix_cand = reinterpret_cast<int32_t*>(p);
   return L;
 }
 
@@ -336,8 +381,8 @@ cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const
   cudaError_t e = cudaMemsetAsync(L.cell_count, 0, size_t(n_cells) * 4, st);
   if (e != cudaSuccess) return e;
   grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, G, L.cell_count, L.cell_off, entries, 1);
-  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
-                                                L.cell_off, entries, L.pix_count, nullptr, nullptr, 0);
+  footprint_count_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels,
+                                                      L.cell_count, L.cell_off, entries, L.pix_count, L.pix_cand);
   if ((e = exclusive_scan<int64_t>(L.pix_count, L.pix_off, n_pixels, L, st)) != cudaSuccess) return e;
   return read_total(L.pix_off, L.pix_count, true, n_pixels, total, st);
 }
@@ -348,8 +393,9 @@ cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const i
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
-  footprint_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels, L.cell_count,
-                                                L.cell_off, entries, nullptr, L.pix_off, out, 1);
+  footprint_fill_kernel<<<num_sms * 16, 256, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels,
+                                                      L.cell_count, L.cell_off, entries, L.pix_count, L.pix_off,
+                                                      L.pix_cand, out);
   return cudaGetLastError();
 }
 
