@@ -61,7 +61,7 @@ BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["b
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
 # Kernel launches per step, counted from the ncu launch list of each
 # workload (profiles/).
-LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 18, ("glints", True): 19}
+LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 19, ("glints", True): 20}
 # 2-bounce solve: systems count + fill, then per batch of <= 16,384 systems the
 # build, six FP32 sign classes, five FP64 re-sampling chunk classes and five
 # re-sampling scan classes, five polish classes and the path kernel.

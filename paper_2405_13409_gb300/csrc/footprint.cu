@@ -9,7 +9,7 @@
 // with the footprint.  Emission is two-pass (count, exclusive scan, fill), so
 // the chain list is ordered by pixel without global atomics; the count pass
 // keeps each pixel's first candidates, so the fill copies them instead of
-// traversing the grid again.
+// traversing the grid again (pixels with more candidates traverse it again).
 #include <algorithm>
 #include <cstring>
 
@@ -173,7 +173,7 @@ SPOLY_D bool pixel_footprint(const CamF& C, int64_t q, float zlo, float zhi, flo
   return true;
 }
 
-constexpr int kPixCand = 64;  // candidates per pixel kept by the count pass for the compaction
+constexpr int kPixCand = 128;  // candidates per pixel kept by the count pass for the fill
 
 // Candidates of pixel q in emission order: each one goes to emit(t); returns
 // their number.
@@ -222,31 +222,40 @@ __global__ void footprint_count_kernel(const float4* boxes, GridGeom G, const in
 }
 
 // Fill: one warp per pixel copies its kept candidates to out[pix_off[q]..]
-// (coalesced); a pixel with more than kPixCand traverses again on lane 0.
-__global__ void footprint_fill_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
-                                      const int* cell_count, const int64_t* cell_off, const int32_t* entries,
-                                      const int64_t* pix_count, const int64_t* pix_off, const int32_t* cand,
-                                      int32_t* out) {
-  const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
+// (coalesced); pixels with more than kPixCand are left to the overflow pass.
+__global__ void footprint_fill_kernel(int64_t n_pixels, const int64_t* pix_count, const int64_t* pix_off,
+                                      const int32_t* cand, int32_t* out) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; q < n_pixels; q += nw) {
     const int64_t n = pix_count[q], o = pix_off[q];
-    if (n <= kPixCand) {
-      for (int64_t k = lane; k < n; k += 32) {
+    if (n > kPixCand) continue;
+    for (int64_t k = lane; k < n; k += 32) {
+      out[3 * (o + k)] = int32_t(q);
+      out[3 * (o + k) + 1] = cand[q * kPixCand + k];
+      out[3 * (o + k) + 2] = -1;
+    }
+  }
+}
+
+// Overflow pass: a pixel with more than kPixCand candidates traverses the
+// grid again (one pixel per thread) and writes all of them.
+__global__ void footprint_overflow_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C,
+                                          int64_t n_pixels, const int* cell_count, const int64_t* cell_off,
+                                          const int32_t* entries, const int64_t* pix_count, const int64_t* pix_off,
+                                          int32_t* out) {
+  const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pixels; q += stride) {
+    const int64_t n = pix_count[q], o = pix_off[q];
+    if (n <= kPixCand) continue;
+    pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries, [&](int64_t k, int32_t t) {
+      if (k < n) {
         out[3 * (o + k)] = int32_t(q);
-        out[3 * (o + k) + 1] = cand[q * kPixCand + k];
+        out[3 * (o + k) + 1] = t;
         out[3 * (o + k) + 2] = -1;
       }
-    } else if (lane == 0) {
-      pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries, [&](int64_t k, int32_t t) {
-        if (k < n) {
-          out[3 * (o + k)] = int32_t(q);
-          out[3 * (o + k) + 1] = t;
-          out[3 * (o + k) + 2] = -1;
-        }
-      });
-    }
+    });
   }
 }
 
@@ -393,9 +402,10 @@ cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const i
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
-  footprint_fill_kernel<<<num_sms * 16, 256, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels,
-                                                      L.cell_count, L.cell_off, entries, L.pix_count, L.pix_off,
-                                                      L.pix_cand, out);
+  footprint_fill_kernel<<<num_sms * 16, 256, 0, st>>>(n_pixels, L.pix_count, L.pix_off, L.pix_cand, out);
+  footprint_overflow_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels,
+                                                         L.cell_count, L.cell_off, entries, L.pix_count, L.pix_off,
+                                                         out);
   return cudaGetLastError();
 }
 
