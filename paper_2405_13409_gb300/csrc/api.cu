@@ -639,17 +639,6 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     P.pix.aspect = c[13];
     P.pix.w = int(c[14]);
     P.pix.h = int(c[15]);
-    P.pixf.on = 1;
-    for (int i = 0; i < 3; ++i) {
-      P.pixf.o[i] = float(c[i]);
-      P.pixf.f[i] = float(c[3 + i]);
-      P.pixf.r[i] = float(c[6 + i]);
-      P.pixf.u[i] = float(c[9 + i]);
-    }
-    P.pixf.isx = float(1.0 / (c[12] * c[13]));
-    P.pixf.isy = float(1.0 / c[12]);
-    P.pixf.w = float(P.pix.w);
-    P.pixf.h = float(P.pix.h);
     if (P.pix.w < 1 || P.pix.h < 1 || int64_t(P.pix.w) * P.pix.h != qv.n)
       return bail(fail(ctx, SPOLY_EINVAL, "pixel filter: width x height must equal n_queries"));
   }

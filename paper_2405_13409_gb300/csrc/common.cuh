@@ -164,46 +164,6 @@ SPOLY_HD bool project_pixel(const PixelFilter& C, double x, double y, double z, 
   return true;
 }
 
-// FP32 copy of the pixel filter's camera for the isolation's pre-filter.
-struct PixelCamF {
-  int on;
-  float o[3], f[3], r[3], u[3];
-  float isx, isy;  // 1 / (tan aspect), 1 / tan
-  float w, h;
-};
-
-// Pre-filter of a root estimate (u, v) of query (pixel) q on triangle t:
-// true when x1 = p0 + u (p1 - p0) + v (p2 - p0) projects within
-// kPixelMargin pixels of pixel q (or the check is inconclusive).  The path
-// phase keeps a path only if x1 projects into pixel q.  The triangle is
-// read again here, so the check keeps no registers live before it runs.
-struct PixelCheck {
-  const PixelCamF* cam;
-  const double* tri;  // mesh SoA [18][n_tris]
-  int64_t n_tris, t, q;
-};
-constexpr float kPixelMargin = 0.5f;  // pixels
-
-SPOLY_HD bool pixel_near(const PixelCheck& c, float u, float v) {
-  const PixelCamF& m = *c.cam;
-  float d[3];
-  for (int i = 0; i < 3; ++i) {
-    const float p0 = float(c.tri[int64_t(i) * c.n_tris + c.t]);
-    const float p1 = float(c.tri[int64_t(3 + i) * c.n_tris + c.t]);
-    const float p2 = float(c.tri[int64_t(6 + i) * c.n_tris + c.t]);
-    d[i] = p0 + u * (p1 - p0) + v * (p2 - p0) - m.o[i];
-  }
-  const float fz = d[0] * m.f[0] + d[1] * m.f[1] + d[2] * m.f[2];
-  if (!(fz > 1e-6f)) return true;
-  const float sx = (d[0] * m.r[0] + d[1] * m.r[1] + d[2] * m.r[2]) * m.isx / fz;
-  const float sy = (d[0] * m.u[0] + d[1] * m.u[1] + d[2] * m.u[2]) * m.isy / fz;
-  const float fx = (sx + 1.0f) * 0.5f * m.w, fy = (1.0f - sy) * 0.5f * m.h;
-  const int64_t w = int64_t(m.w);
-  const float qy = float(c.q / w), qx = float(c.q - (c.q / w) * w);
-  return fx >= qx - kPixelMargin && fx <= qx + 1.0f + kPixelMargin && fy >= qy - kPixelMargin &&
-         fy <= qy + 1.0f + kPixelMargin;
-}
-
 // Root-bracket queue item between the isolation and polish kernels.
 struct RootItem {
   double zlo, zhi;   // bracket in the scaled hidden variable z = v / t

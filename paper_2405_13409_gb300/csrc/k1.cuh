@@ -18,7 +18,6 @@ struct K1Params {
   spoly_path* paths;
   int64_t path_cap;
   PixelFilter pix;  // optional: keep a path of query q only if x1 projects into pixel q
-  PixelCamF pixf;   // its FP32 copy for the isolation's pre-filter
 };
 
 #ifndef SPOLY_HOST_BUILD

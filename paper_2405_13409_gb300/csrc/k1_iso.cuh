@@ -14,7 +14,7 @@ namespace spoly {
 // -1 if r vanishes identically.
 template <typename T, int RD, int DB>
 SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD + 1], int chain,
-                      unsigned& n_vroots, unsigned& n_pref, const PixelCheck* pc = nullptr) {
+                      unsigned& n_vroots, unsigned& n_pref) {
   // Power-of-two normalisation of r and trimming of negligible leading terms
   // (their contribution over the domain is below kTrim of the largest term).
   const double inv_t = scale2(1.0, -s.sc.kt);  // 1 / t, exact
@@ -79,7 +79,7 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
       if (nw == 0 && fabs(am[0]) + fabs(am[1]) + fabs(am[2]) == T(0)) keep = true;
       for (int i = 0; i < nw; ++i) {
         const T u = w[i] * T(s.sc.s);
-        if (u >= -m && u <= T(1) - v + m && (!pc || pixel_near(*pc, float(u), float(v)))) keep = true;
+        if (u >= -m && u <= T(1) - v + m) keep = true;
       }
     }
     if (!keep) {
@@ -102,7 +102,7 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
 // the shared post-processing.
 template <typename T, int N, int DB>
 SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int chain, unsigned& n_vroots,
-                             unsigned& n_pref, const PixelCheck* pc = nullptr) {
+                             unsigned& n_pref) {
   constexpr int ED = 2 + DB - 1;
   constexpr int RD = N * (ED - N + 1);
   T r[RD + 1];
@@ -118,24 +118,24 @@ SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int
     if constexpr (N == 5 && DB == 6) laplace_T5<T>(E, r);
     if constexpr (N == 6 && DB == 6) laplace_T6<T>(E, r);
   }
-  return k1_finish<T, RD, DB>(s, r, items, chain, n_vroots, n_pref, pc);
+  return k1_finish<T, RD, DB>(s, r, items, chain, n_vroots, n_pref);
 }
 
 // Isolation with the unrolled expansion of the candidate's Bezout size;
 // -2 when the size has none (handled by the generic runtime-size path).
 template <typename T, int DB>
 SPOLY_D int k1_isolate_dispatch(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int chain, unsigned& n_v,
-                                unsigned& n_pref, const PixelCheck* pc = nullptr) {
+                                unsigned& n_pref) {
   if constexpr (DB == 4) {
-    if (s.n == 3) return k1_isolate_sized<T, 3, 4>(s, items, chain, n_v, n_pref, pc);
-    if (s.n == 4) return k1_isolate_sized<T, 4, 4>(s, items, chain, n_v, n_pref, pc);
-    if (s.n == 2) return k1_isolate_sized<T, 2, 4>(s, items, chain, n_v, n_pref, pc);
+    if (s.n == 3) return k1_isolate_sized<T, 3, 4>(s, items, chain, n_v, n_pref);
+    if (s.n == 4) return k1_isolate_sized<T, 4, 4>(s, items, chain, n_v, n_pref);
+    if (s.n == 2) return k1_isolate_sized<T, 2, 4>(s, items, chain, n_v, n_pref);
   } else {
-    if (s.n == 6) return k1_isolate_sized<T, 6, 6>(s, items, chain, n_v, n_pref, pc);
-    if (s.n == 5) return k1_isolate_sized<T, 5, 6>(s, items, chain, n_v, n_pref, pc);
-    if (s.n == 4) return k1_isolate_sized<T, 4, 6>(s, items, chain, n_v, n_pref, pc);
-    if (s.n == 3) return k1_isolate_sized<T, 3, 6>(s, items, chain, n_v, n_pref, pc);
-    if (s.n == 2) return k1_isolate_sized<T, 2, 6>(s, items, chain, n_v, n_pref, pc);
+    if (s.n == 6) return k1_isolate_sized<T, 6, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 5) return k1_isolate_sized<T, 5, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 4) return k1_isolate_sized<T, 4, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 3) return k1_isolate_sized<T, 3, 6>(s, items, chain, n_v, n_pref);
+    if (s.n == 2) return k1_isolate_sized<T, 2, 6>(s, items, chain, n_v, n_pref);
   }
   return -2;
 }
@@ -169,15 +169,13 @@ SPOLY_D void isolate_warp(const K1Params& P, int64_t base, int lane) {
       n_cand = 1;
       const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
       const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
-      const PixelCheck pcheck{&P.pixf, P.mesh.tri, P.mesh.n_tris, t, q};
-      const PixelCheck* pc = P.pixf.on ? &pcheck : nullptr;
       int r = 0;
       if (qd.type == SPOLY_R) {
         K1Sys<4> s;
-        r = k1_system<4>(tr, qd, s) ? k1_isolate_dispatch<T, 4>(s, items, int(c), n_v, n_pref, pc) : -1;
+        r = k1_system<4>(tr, qd, s) ? k1_isolate_dispatch<T, 4>(s, items, int(c), n_v, n_pref) : -1;
       } else {
         K1Sys<6> s;
-        r = k1_system<6>(tr, qd, s) ? k1_isolate_dispatch<T, 6>(s, items, int(c), n_v, n_pref, pc) : -1;
+        r = k1_system<6>(tr, qd, s) ? k1_isolate_dispatch<T, 6>(s, items, int(c), n_v, n_pref) : -1;
       }
       if (sizeof(T) == 4 && r != -1 && flat_shaded(tr)) {
         r = -2;  // the FP32 brackets are discarded; the side kernel re-isolates in FP64
