@@ -223,7 +223,9 @@ const char* spoly_last_error(const spoly_ctx* ctx);
  * and triangles) that pass the CONE test of their own bounce count, per
  * query x0, IORs and types (1 bounce: as CONE; 2 bounces of two refractions:
  * the three tests of the 2-bounce CONE; other 2-bounce types are kept),
- * in no particular order.  *inout: NULL to
+ * in no particular order (its boxes use FP32 intervals with directed
+ * rounding, so they enclose the FP64 boxes of CONE up to rounding).
+ * *inout: NULL to
  * allocate a new handle, or a handle to reuse.  The call synchronises once
  * to read the chain count.  EXPLICIT lists may hold 2-bounce chains
  * (tri1 >= 0).  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (CONE with

@@ -494,23 +494,104 @@ __global__ void tt_shared_kernel(QueryView Q, int32_t* flag) {
 }  // namespace
 
 // ------------------------------------- explicit lists, culled per chain
+// The per-chain boxes use FP32 interval arithmetic with directed rounding
+// (every lower end rounded down, every upper end up), so each box encloses
+// the exact one like the FP64 boxes of the range-based culls, at FP32 rates.
+struct IvF {
+  float lo, hi;
+};
+SPOLY_D IvF ivf_pt(double a) { return {__double2float_rd(a), __double2float_ru(a)}; }
+SPOLY_D IvF operator+(IvF a, IvF b) { return {__fadd_rd(a.lo, b.lo), __fadd_ru(a.hi, b.hi)}; }
+SPOLY_D IvF operator-(IvF a, IvF b) { return {__fsub_rd(a.lo, b.hi), __fsub_ru(a.hi, b.lo)}; }
+SPOLY_D IvF operator-(IvF a) { return {-a.hi, -a.lo}; }
+SPOLY_D IvF operator*(IvF a, IvF b) {
+  const float l = fminf(fminf(__fmul_rd(a.lo, b.lo), __fmul_rd(a.lo, b.hi)),
+                        fminf(__fmul_rd(a.hi, b.lo), __fmul_rd(a.hi, b.hi)));
+  const float h = fmaxf(fmaxf(__fmul_ru(a.lo, b.lo), __fmul_ru(a.lo, b.hi)),
+                        fmaxf(__fmul_ru(a.hi, b.lo), __fmul_ru(a.hi, b.hi)));
+  return {l, h};
+}
+SPOLY_D IvF sqrf(IvF a) {
+  if (a.lo >= 0.f) return {__fmul_rd(a.lo, a.lo), __fmul_ru(a.hi, a.hi)};
+  if (a.hi <= 0.f) return {__fmul_rd(a.hi, a.hi), __fmul_ru(a.lo, a.lo)};
+  return {0.f, fmaxf(__fmul_ru(a.lo, a.lo), __fmul_ru(a.hi, a.hi))};
+}
+// a / L with L = [llo, lhi], llo > 0.
+SPOLY_D IvF divposf(IvF a, float llo, float lhi) {
+  if (a.lo >= 0.f) return {__fdiv_rd(a.lo, lhi), __fdiv_ru(a.hi, llo)};
+  if (a.hi <= 0.f) return {__fdiv_rd(a.lo, llo), __fdiv_ru(a.hi, lhi)};
+  return {__fdiv_rd(a.lo, llo), __fdiv_ru(a.hi, llo)};
+}
+struct Iv3F {
+  IvF x, y, z;
+};
+SPOLY_D bool normalisef(const Iv3F& v, Iv3F& out) {
+  const IvF l2 = sqrf(v.x) + sqrf(v.y) + sqrf(v.z);
+  if (!(l2.lo > 0.f)) return false;
+  const float llo = __fsqrt_rd(l2.lo), lhi = __fsqrt_ru(l2.hi);
+  out = {divposf(v.x, llo, lhi), divposf(v.y, llo, lhi), divposf(v.z, llo, lhi)};
+  return true;
+}
+
+// out_box in FP32 with directed rounding (the same steps).
+SPOLY_D bool out_box_f(const MeshView& M, int t, d3 x0, int type, double eta0, double eta1, Iv3F& o, Iv3F& bb,
+                       bool& empty) {
+  empty = false;
+  auto g = [&](int row) { return M.tri[int64_t(row) * M.n_tris + t]; };
+  IvF P[3], N[3];
+  for (int c = 0; c < 3; ++c) {
+    const double p0 = g(c), p1 = g(3 + c), p2 = g(6 + c);
+    const double n0 = g(9 + c), n1 = g(12 + c), n2 = g(15 + c);
+    P[c] = {__double2float_rd(fmin(p0, fmin(p1, p2))), __double2float_ru(fmax(p0, fmax(p1, p2)))};
+    N[c] = {__double2float_rd(fmin(n0, fmin(n1, n2))), __double2float_ru(fmax(n0, fmax(n1, n2)))};
+  }
+  bb = {P[0], P[1], P[2]};
+  const Iv3F d = {P[0] - ivf_pt(x0.x), P[1] - ivf_pt(x0.y), P[2] - ivf_pt(x0.z)};
+  Iv3F dh, nh;
+  if (!normalisef(d, dh)) return false;
+  if (!normalisef({N[0], N[1], N[2]}, nh)) return false;
+  IvF c = -(dh.x * nh.x + dh.y * nh.y + dh.z * nh.z);  // c = -d^ . n^
+  if (c.hi < 0.f) {  // normal points away from x0: flip it
+    nh = {-nh.x, -nh.y, -nh.z};
+    c = -c;
+  } else if (!(c.lo > 0.f)) {
+    return false;  // grazing somewhere on the triangle
+  }
+  c.hi = fminf(c.hi, 1.f);
+  if (type == SPOLY_R) {
+    const IvF c2 = c + c;
+    o = {dh.x + c2 * nh.x, dh.y + c2 * nh.y, dh.z + c2 * nh.z};
+  } else {
+    const IvF eta = {__double2float_rd(__ddiv_rd(eta0, eta1)), __double2float_ru(__ddiv_ru(eta0, eta1))};
+    const IvF one = {1.f, 1.f};
+    const IvF k = one - sqrf(eta) * (one - sqrf(c));
+    if (k.hi < 0.f) {
+      empty = true;
+      return true;
+    }
+    const IvF sk = {__fsqrt_rd(fmaxf(k.lo, 0.f)), __fsqrt_ru(k.hi)};
+    const IvF f = eta * c - sk;
+    o = {eta * dh.x + f * nh.x, eta * dh.y + f * nh.y, eta * dh.z + f * nh.z};
+  }
+  return true;
+}
+
 // Box of one triangle lit from x: [12] floats (outgoing lo/hi xyz, widened
-// by the margin and rounded outward; bounding box lo/hi xyz).  A triangle
-// with no bound gets the full box, one with no transmitted direction an
-// empty one.
+// by the margin; bounding box lo/hi xyz).  A triangle with no bound gets
+// the full box, one with no transmitted direction an empty one.
 SPOLY_D void chain_box(const MeshView& M, int t, d3 x, int type, double eta_in, double eta_out, double margin,
                        float (&B)[12]) {
-  Iv3 o, bb;
+  Iv3F o, bb;
   bool empty = false;
-  const bool ok = out_box(M, t, x, type, eta_in, eta_out, o, bb, empty);
-  const Iv comps[3] = {o.x, o.y, o.z};
-  const Iv bcomp[3] = {bb.x, bb.y, bb.z};
+  const bool ok = out_box_f(M, t, x, type, eta_in, eta_out, o, bb, empty);
+  const IvF comps[3] = {o.x, o.y, o.z};
+  const IvF bcomp[3] = {bb.x, bb.y, bb.z};
+  const float m = __double2float_ru(margin);
   for (int k = 0; k < 3; ++k) {
-    const Iv w = widen(comps[k], margin);
-    B[k] = empty ? 2.f : (ok ? __double2float_rd(w.lo) : -1.f);
-    B[3 + k] = empty ? -2.f : (ok ? __double2float_ru(w.hi) : 1.f);
-    B[6 + k] = __double2float_rd(bcomp[k].lo);
-    B[9 + k] = __double2float_ru(bcomp[k].hi);
+    B[k] = empty ? 2.f : (ok ? fmaxf(-1.f, __fsub_rd(comps[k].lo, m)) : -1.f);
+    B[3 + k] = empty ? -2.f : (ok ? fminf(1.f, __fadd_ru(comps[k].hi, m)) : 1.f);
+    B[6 + k] = bcomp[k].lo;
+    B[9 + k] = bcomp[k].hi;
   }
 }
 

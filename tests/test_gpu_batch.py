@@ -91,8 +91,9 @@ def _rows(a):
 
 def test_explicit_cone_equals_range_cone(bctx):
     """On every (receiver, triangle) pair, or every (receiver, top, bottom)
-    tuple of a slab, the per-chain test keeps exactly the chains of the
-    range-based cone cull (the same predicates)."""
+    tuple of a slab, the per-chain test (FP32 intervals with directed
+    rounding) keeps every chain of the range-based cone cull (the same
+    predicates on FP64 intervals) and at most a few more."""
     ctx, stream = bctx
     r = scenes.refract_scene(seed=2, n_cells=32, n_recv=12)
     sl = scenes.slab_scene(seed=0, n_cells=16, n_recv=2)
@@ -118,7 +119,9 @@ def test_explicit_cone_equals_range_cone(bctx):
         ctx.spoly_chains_free(ref)
         ctx.spoly_chains_free(exp)
         assert 0 < a.shape[0] < allc.shape[0] // 20
-        assert _rows(a) == _rows(b)
+        ra, rb = set(_rows(a)), set(_rows(b))
+        assert ra <= rb
+        assert len(rb) <= 1.02 * len(ra) + 4
 
 
 def test_gate_passes_two_bounce_chains(bctx, batch):
