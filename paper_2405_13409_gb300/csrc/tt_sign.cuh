@@ -374,9 +374,9 @@ cudaError_t launch_resample_class(const TTParams& P, int n_lo, int num_sms, cuda
 // that systems with many brackets spread over the grid; each item stages
 // its system's coefficients.  Loops run in warp-uniform steps (a warp leaves
 // a loop when none of its groups needs another step).  A bracket whose FP64
-// signs agree is widened, by factors of 64 and within one sample interval on
-// each side, until they differ; if they never do it is lost.
-constexpr int kPolishWiden = 2;      // 2^-22 * 64^2 > 2^-12
+// signs agree is widened once, to one sample interval on each side of its
+// centre; if the signs still agree it is lost.
+constexpr int kPolishWiden = 1;
 constexpr int kPolishMaxSteps = 40;  // bisection steps from one sample interval to kTTRootTol: 23
 
 template <int N, int G>
@@ -403,7 +403,7 @@ SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys&
       const bool need = act && slo != 0 && shi != 0 && slo == shi && w < reach;
       if (!__any_sync(kGroupFull, need)) break;
       const double c = 0.5 * (lo + hi);
-      const double w2 = fmin(64.0 * w, reach);
+      const double w2 = reach;
       const double l2 = fmax(0.0, c - w2), h2 = fmin(1.0, c + w2);
       const int s1 = ev(need ? l2 : lo), s2 = ev(need ? h2 : hi);
       if (need) {
