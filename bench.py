@@ -370,6 +370,19 @@ def reference_arm(args):
     return 0
 
 
+def job_rate(local_ms, units_per_rank, steps, world, device="cpu"):
+    """Replicas (one per rank, no data exchange): the job's time is the
+    slowest rank's, and the rate counts the units of every rank.  Returns
+    (max over ranks of local_ms, units per second of the whole job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * units_per_rank * steps / (ms * 1e-3)
+
+
 def match_paths(got, ref, tol=1e-5):
     """Paths of `ref` with a path of `got` on the same (pixel, triangle)
     within tol in (u, v); returns (matched, max |delta(u, v)| over matches)."""
@@ -568,12 +581,7 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(r["step"] for r in rec)
-    t = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * pairs * args.steps / (total_ms * 1e-3)
+    total_ms, value = job_rate(sum(r["step"] for r in rec), pairs, args.steps, world, dev)
     n_paths = rec[-1]["paths"]
     got_paths = ctx.spoly_paths(pipe.sol)
 
@@ -630,12 +638,9 @@ def main():
             torch.cuda.synchronize()
             e_ms.append(1e3 * (time.perf_counter() - t0))
             d2h = min(n, cap) * binding.PATH_DTYPE.itemsize + 8
-        te = torch.tensor([sum(e_ms)], device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * pairs * args.steps / (float(te.item()) * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": sum(a.nbytes for a in host), "d2h_bytes_per_step": d2h,
-               "ms_per_step": float(te.item()) / args.steps}
+        e_total, e_value = job_rate(sum(e_ms), pairs, args.steps, world, dev)
+        e2e = {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": sum(a.nbytes for a in host),
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_total / args.steps}
 
     if rank != 0:
         if world > 1:
