@@ -77,3 +77,51 @@ def assert_parity(gpu, ref, n_candidates, tol=1e-5, min_recall=1.0, max_flagged_
     flagged = st["gpu_only_flagged"] + st["ref_only_flagged"]
     assert flagged <= max(1, max_flagged_frac * n_candidates), st
     return st
+
+
+# Pixel-footprint helpers for the glint tests (numpy, independent of the library).
+def project_pixels(cam, x):
+    o, f, r, u = cam[0:3], cam[3:6], cam[6:9], cam[9:12]
+    th, asp, w, h = cam[12], cam[13], int(cam[14]), int(cam[15])
+    d = x - o
+    fz = d @ f
+    sx = (d @ r) / (fz * th * asp)
+    sy = (d @ u) / (fz * th)
+    fx = (sx + 1) * 0.5 * w
+    fy = (1 - sy) * 0.5 * h
+    ok = (fz > 0) & (fx >= 0) & (fx < w) & (fy >= 0) & (fy < h)
+    pix = np.floor(fy).astype(np.int64) * w + np.floor(fx).astype(np.int64)
+    return np.where(ok, pix, -1)
+
+
+def footprint_numpy(s, cam):
+    """Brute force: triangles whose xy bbox meets each pixel's footprint box."""
+    T = s.tri
+    xs, ys, zs = T[[0, 3, 6]], T[[1, 4, 7]], T[[2, 5, 8]]
+    txl, txh, tyl, tyh = xs.min(0), xs.max(0), ys.min(0), ys.max(0)
+    zlo, zhi = float(np.float32(zs.min())), float(np.float32(zs.max()))
+    o, f, r, u = cam[0:3], cam[3:6], cam[6:9], cam[9:12]
+    th, asp, w, h = cam[12], cam[13], int(cam[14]), int(cam[15])
+    out = set()
+    for q in range(w * h):
+        ix, iy = q % w, q // w
+        pts = []
+        for k in range(4):
+            sx = -1 + 2 * (ix + (k & 1)) / w
+            sy = 1 - 2 * (iy + (k >> 1)) / h
+            d = f + sx * th * asp * r + sy * th * u
+            if d[2] >= 0:
+                pts = None
+                break
+            for z in (zlo, zhi):
+                t = (z - o[2]) / d[2]
+                pts.append(o + t * d)
+        if pts is None:
+            continue
+        pts = np.array(pts)
+        m = 1e-5 * (1 + max(abs(pts[:, 0].min()), abs(pts[:, 1].max())))
+        xl, xh = pts[:, 0].min() - m, pts[:, 0].max() + m
+        yl, yh = pts[:, 1].min() - m, pts[:, 1].max() + m
+        hit = np.where(~((txh < xl) | (txl > xh) | (tyh < yl) | (tyl > yh)))[0]
+        out.update((q, int(t)) for t in hit)
+    return out

@@ -44,16 +44,24 @@ def _features(ctx, mesh, q, ch):
 
 @pytest.fixture(scope="module")
 def glint_small(ctx):
+    """A small glint scene and its pixel-footprint candidates, enumerated in
+    numpy (the oracle's inputs never come from the library) and passed to
+    the library as an explicit list."""
+    from .parity import footprint_numpy
     s = scenes.glint_scene(seed=3, n_cells=128, res=64, n_terms=16)
     cam = s.meta["camera"].as_array()
-    d, mesh, q, ch = _chains(ctx, s, binding.CHAINS_FOOTPRINT, cam)
+    fp = np.array(sorted(footprint_numpy(s, cam)), np.int32)
+    s.chains = np.stack([fp[:, 0], fp[:, 1], -np.ones(fp.shape[0], np.int32)], -1).astype(np.int32)
+    d = _dev(s)
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=s.chains)
     yield s, cam, d, mesh, q, ch
     ctx.spoly_chains_free(ch)
 
 
 def test_features_match_oracle_glints(ctx, glint_small):
     s, cam, d, mesh, q, ch = glint_small
-    chains = ctx.spoly_chains_copy(ch)
+    chains = s.chains
     got = _features(ctx, mesh, q, ch).cpu().numpy().astype(np.float64)
     want = G.chain_features(s.tri, s.x_first, s.x_last, s.eta, s.types, chains)
     # FP32 features: the mismatch is a difference of unit vectors (error
@@ -71,8 +79,10 @@ def test_features_match_oracle_glints(ctx, glint_small):
 
 def test_features_match_oracle_refraction(ctx):
     s = scenes.refract_scene(seed=0, n_cells=16, n_recv=8)
-    d, mesh, q, ch = _chains(ctx, s, binding.CHAINS_ALL)
-    chains = ctx.spoly_chains_copy(ch)
+    chains = scenes.all_pairs(s.n_queries, s.n_tris)
+    d = _dev(s)
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=chains)
     got = _features(ctx, mesh, q, ch).cpu().numpy().astype(np.float64)
     ctx.spoly_chains_free(ch)
     want = G.chain_features(s.tri, s.x_first, s.x_last, s.eta, s.types, chains)

@@ -10,6 +10,8 @@ import oracle
 from paper_2405_13409_gb300 import binding, scenes
 
 from .parity import assert_parity
+from .parity import footprint_numpy as _footprint_numpy
+from .parity import project_pixels as _project
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -29,58 +31,13 @@ def ctx():
 @pytest.fixture(scope="module")
 def small():
     s = scenes.glint_scene(seed=3, n_cells=256, res=64, n_terms=16)
-    return s, s.meta["camera"].as_array()
+    cam = s.meta["camera"].as_array()
+    s.meta["footprint"] = _footprint_numpy(s, cam)  # computed once for the module
+    return s, cam
 
 
 def _dev(s):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
-
-
-def _project(cam, x):
-    o, f, r, u = cam[0:3], cam[3:6], cam[6:9], cam[9:12]
-    th, asp, w, h = cam[12], cam[13], int(cam[14]), int(cam[15])
-    d = x - o
-    fz = d @ f
-    sx = (d @ r) / (fz * th * asp)
-    sy = (d @ u) / (fz * th)
-    fx = (sx + 1) * 0.5 * w
-    fy = (1 - sy) * 0.5 * h
-    ok = (fz > 0) & (fx >= 0) & (fx < w) & (fy >= 0) & (fy < h)
-    pix = np.floor(fy).astype(np.int64) * w + np.floor(fx).astype(np.int64)
-    return np.where(ok, pix, -1)
-
-
-def _footprint_numpy(s, cam):
-    """Brute force: triangles whose xy bbox meets each pixel's footprint box."""
-    T = s.tri
-    xs, ys, zs = T[[0, 3, 6]], T[[1, 4, 7]], T[[2, 5, 8]]
-    txl, txh, tyl, tyh = xs.min(0), xs.max(0), ys.min(0), ys.max(0)
-    zlo, zhi = float(np.float32(zs.min())), float(np.float32(zs.max()))
-    o, f, r, u = cam[0:3], cam[3:6], cam[6:9], cam[9:12]
-    th, asp, w, h = cam[12], cam[13], int(cam[14]), int(cam[15])
-    out = set()
-    for q in range(w * h):
-        ix, iy = q % w, q // w
-        pts = []
-        for k in range(4):
-            sx = -1 + 2 * (ix + (k & 1)) / w
-            sy = 1 - 2 * (iy + (k >> 1)) / h
-            d = f + sx * th * asp * r + sy * th * u
-            if d[2] >= 0:
-                pts = None
-                break
-            for z in (zlo, zhi):
-                t = (z - o[2]) / d[2]
-                pts.append(o + t * d)
-        if pts is None:
-            continue
-        pts = np.array(pts)
-        m = 1e-5 * (1 + max(abs(pts[:, 0].min()), abs(pts[:, 1].max())))
-        xl, xh = pts[:, 0].min() - m, pts[:, 0].max() + m
-        yl, yh = pts[:, 1].min() - m, pts[:, 1].max() + m
-        hit = np.where(~((txh < xl) | (txl > xh) | (tyh < yl) | (tyl > yh)))[0]
-        out.update((q, int(t)) for t in hit)
-    return out
 
 
 def test_footprint_chains_match_brute_force(ctx, small):
@@ -90,7 +47,7 @@ def test_footprint_chains_match_brute_force(ctx, small):
     ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_FOOTPRINT, camera=cam)
     got = ctx.spoly_chains_copy(ch)
     ctx.spoly_chains_free(ch)
-    want = _footprint_numpy(s, cam)
+    want = s.meta["footprint"]
     gset = set(map(tuple, got[:, :2].tolist()))
     assert len(gset) == got.shape[0], "duplicate candidates"
     # FP32 footprint boxes vs FP64 numpy: allow boundary ties only
@@ -104,16 +61,19 @@ def test_pixel_filtered_solve_matches_oracle(ctx, small, precision):
     d = _dev(s)
     mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
     ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_FOOTPRINT, camera=cam)
-    chains = ctx.spoly_chains_copy(ch)
+    n_chains = ctx.spoly_chains_count(ch)
     sol = ctx.spoly_solve(mesh, q, ch, precision=precision, camera=cam)
     paths = ctx.spoly_paths(sol)
     ctx.spoly_solution_free(sol)
     ctx.spoly_chains_free(ch)
+    # the oracle solves the brute-force footprint (numpy), not the library's list
+    fp = np.array(sorted(s.meta["footprint"]), np.int32)
+    chains = np.stack([fp[:, 0], fp[:, 1], -np.ones(fp.shape[0], np.int32)], -1).astype(np.int32)
     ref, _ = oracle.solve(s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, chains)
     keep = _project(cam, ref["x"][:, :3]) == ref["query"]
     ref = ref[keep]
     assert ref.size > 10
-    assert_parity(paths, ref, chains.shape[0])
+    assert_parity(paths, ref, max(n_chains, chains.shape[0]))
     assert np.all(_project(cam, paths["x"][:, :3]) == paths["query"])
 
 
