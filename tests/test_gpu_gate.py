@@ -224,7 +224,8 @@ def test_trained_gate_keeps_paths_and_skips_candidates(ctx):
     mixed solve returns at least 99.9% of the plain FP64 solve's
     pixel-filtered paths (matched at 1e-5 in (u, v)) while solving at most
     2% of the candidates; an untrained network calibrated the same way
-    keeps far more."""
+    keeps far more.  On sampled pixel blocks the gated solve matches the
+    FP64 oracle."""
     from paper_2405_13409_gb300 import gate_train
     train = [scenes.glint_scene(seed=1000 + i) for i in range(2)]
     val = [scenes.glint_scene(seed=2000)]
@@ -264,4 +265,16 @@ def test_trained_gate_keeps_paths_and_skips_candidates(ctx):
           "untrained pass", base_frac, rep)
     assert recall >= 0.999, (recall, rep)
     assert n_gated <= 0.02 * n_all, (n_gated, n_all)
+    # the same full-size gated solve against the FP64 oracle on sampled
+    # 16x16-pixel blocks: their footprint candidates enumerated in numpy,
+    # the oracle's paths kept where x1 projects into the candidate's pixel
+    import bench
+    import oracle
+    from .parity import assert_parity, project_pixels
+    chains_s, nb = bench.footprint_sample(ev, cam, 16 * 256, seed=17)
+    refo, _ = oracle.solve(ev.tri, ev.x_first, ev.x_last, ev.eta, ev.types, ev.k, chains_s)
+    refo = refo[project_pixels(cam, refo["x"][:, :3]) == refo["query"]]
+    mine = got[np.isin(got["query"], np.unique(chains_s[:, 0]))]
+    assert refo.size > 10, refo.size
+    assert_parity(mine, refo, chains_s.shape[0], min_recall=0.999)
     assert n_gated < 0.05 * base_frac * n_all
