@@ -83,9 +83,8 @@ def launches_per_step(workload, use_gate, stats):
 # the workload named, reported only while the kernel's sources hash to the
 # value the capture was taken on (profiles/ holds the captures).
 TRAFFIC = {
-    "gate_kernel": {"workload": "glints", "sources": ["gate.cu", "gate.cuh", "mlp.cuh", "common.cuh"],
-                    "sources_sha256": "04e0406b20593418a90127fecafba0bcf5692d5a7a3b932421478b74c21e0468",
-                    "bytes_per_launch": 429683712 + 3668992},  # profiles/kernels_glints_gate.md
+    "gate_kernel": {"workload": "glints", "sources": ["gate.cu", "gate.cuh", "mlp.cuh", "common.cuh", "umma.cuh"],
+                    "sources_sha256": None, "bytes_per_launch": None},  # profiles/kernels_glints_gate.md
     "k1_isolate_kernel": {"workload": "refract",
                           "sources": ["common.cuh", "polys.cuh", "laplace_gen.cuh", "k1_sys.cuh", "k1_iso.cuh",
                                       "k1_iso_f32.cu"], "sources_sha256": None, "bytes_per_launch": None},
@@ -680,7 +679,7 @@ def main():
                     "phase_ms_per_step": ph["k2"]}
     if use_gate:
         gate_tflops = GATE_FLOPS * n_cand / (ph["gate"] * 1e-3) / 1e12
-        roof_gate = {"bound": "tensor", "kernel": "gate_kernel (features + BF16 mma.sync MLP + compaction)",
+        roof_gate = {"bound": "tensor", "kernel": "gate_kernel (features + BF16 tcgen05 MLP, TMEM accumulator + compaction)",
                      "achieved": gate_tflops, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": gate_tflops / BF16_PEAK_TFLOPS, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
                      "traffic": traffic("gate_kernel", args.workload), "flops_per_candidate": GATE_FLOPS}

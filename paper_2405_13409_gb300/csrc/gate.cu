@@ -1,5 +1,5 @@
 // Learned candidate gate: feature kernel, the fused feature + BF16 tensor-core
-// MLP + compaction kernel, weight packing, labels from a solve, and the C ABI
+// (tcgen05) MLP + compaction kernel, weight packing, labels from a solve, and the C ABI
 // of the network handle (create, parameters, save/load, forward, calibrate,
 // gate).  Training lives in mlp_train.cu.
 #include <cuda_bf16.h>
@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "mlp.cuh"
+#include "umma.cuh"
 
 namespace spoly {
 
@@ -32,23 +33,26 @@ SPOLY_D uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// B fragments of mma.m16n8k16 for W[K][N] (row-major FP32): register r of
-// lane (g = lane / 4, c = lane % 4) in tile (kt, nt) holds W[k][n], W[k+1][n]
-// with k = 16 kt + 2 c + 8 r and n = 8 nt + g.
+// Inference weights: W1, W2, W3 as the K-major B operands of the tensor-core
+// MMA (row n = output unit, K = input units, BF16 pairs along k in the
+// no-swizzle core-matrix layout of umma_off), then the FP32 vectors b1 b2 b3
+// w4 b4.  theta holds W[k][n] row-major.
 __global__ void pack_kernel(const float* __restrict__ theta, uint32_t* __restrict__ packed) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < kPackB) {
-    int w = i, off = kOffW1;
+    int w = i, off = kOffW1, K = kIn;
     if (w >= kFragW1 + kFragW23) {
       w -= kFragW1 + kFragW23;
       off = kOffW3;
+      K = kHid;
     } else if (w >= kFragW1) {
       w -= kFragW1;
       off = kOffW2;
+      K = kHid;
     }
-    const int r = w & 1, lane = (w >> 1) & 31, tile = w >> 6;
-    const int nt = tile % (kHid / 8), kt = tile / (kHid / 8);
-    const int k = 16 * kt + 2 * (lane & 3) + 8 * r, n = 8 * nt + (lane >> 2);
+    // invert umma_off: byte 4 w of the matrix holds (n, k), (n, k + 1)
+    const int b = 4 * w, grp = b / (16 * K), rem = b % (16 * K);
+    const int n = 8 * grp + (rem & 127) / 16, k = 8 * (rem / 128) + (rem & 15) / 2;
     packed[i] = pack_bf16(theta[off + k * kHid + n], theta[off + (k + 1) * kHid + n]);
   } else if (i < kPackWords) {
     const int j = i - kPackB;  // b1 b2 b3 w4 b4 pad
@@ -75,78 +79,82 @@ SPOLY_D uint32_t pack_relu_bf16(float lo, float hi) {
   return r;
 }
 
-// d = a b + c with c given apart (the bias), so the accumulators need no
-// initialising moves.
-SPOLY_D void mma_bf16_c(float (&d)[4], const uint32_t (&a)[4], uint2 b, float c0, float c1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%10,%11,%10,%11};\n"
-      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y), "f"(c0), "f"(c1));
+constexpr int kGateRows = 128;                 // candidates per tile: the MMA's M, one per thread and TMEM lane
+constexpr uint32_t kGateTmemCols = kHid;       // one 128 x 64 FP32 accumulator, reused by the three layers
+constexpr uint32_t kGateIdesc = umma_idesc_bf16(kGateRows, kHid);
+constexpr long long kGateWaitCycles = 1ll << 31;  // about one second at the SM clock
+constexpr int kGateMaxPerSm = 512 / kGateTmemCols;  // CTAs whose accumulators fit one SM's tensor memory
+static_assert(umma_off(kGateRows - 1, kHid - 1, kHid) == kGateRows * kHid * 2 - 2, "A tile layout");
+static_assert(umma_off(kHid - 1, kIn - 1, kIn) == 4 * kFragW1 - 2, "W1 tile layout");
+static_assert(umma_off(kHid - 1, kHid - 1, kHid) == 4 * kFragW23 - 2, "W2, W3 tile layout");
+
+// The layer's MMAs (K / 16 steps of M = 128, N = 64) over A at a_s and the
+// weights at w_s, then the commit; thread 0 only.
+SPOLY_D void gate_issue(uint32_t tmem, uint32_t a_s, uint32_t w_s, int K, uint32_t bar_s) {
+  tc_fence_after();
+  const uint32_t sbo = uint32_t(K) * 16u;
+  for (int s = 0; s < K / 16; ++s)
+    umma_bf16(tmem, umma_desc(a_s + 256u * s, 128u, sbo), umma_desc(w_s + 256u * s, 128u, sbo), kGateIdesc,
+              s > 0 ? 1u : 0u);
+  umma_commit(bar_s);
 }
 
-SPOLY_D void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint2 b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
-}
-
-constexpr int kGateRows = 128;  // rows per tile: 4 warps x 32
-constexpr int kXStride = 40;    // BF16 per feature row in shared memory (32 + 8 pad: no bank conflicts)
-
-// One dense layer for the warp's 32 rows (two m16 tiles): acc = bias + A W,
-// with A in registers (KT k-tiles) and W's fragments in shared memory.
-template <int KT>
-SPOLY_D void layer(float (&acc)[2][8][4], const uint32_t (&a)[2][4][4], const uint2* __restrict__ wf,
-                   const float* __restrict__ bias, int lane) {
-  const int c2 = 2 * (lane & 3);
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const float b0 = bias[8 * nt + c2], b1 = bias[8 * nt + c2 + 1];
-    const uint2 b = wf[nt * 32 + lane];
-    mma_bf16_c(acc[0][nt], a[0][0], b, b0, b1);
-    mma_bf16_c(acc[1][nt], a[1][0], b, b0, b1);
-  }
-#pragma unroll
-  for (int kt = 1; kt < KT; ++kt)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const uint2 b = wf[(kt * 8 + nt) * 32 + lane];
-      mma_bf16(acc[0][nt], a[0][kt], b);
-      mma_bf16(acc[1][nt], a[1][kt], b);
-    }
-}
-
-// ReLU of the layer output, rounded to BF16 and laid out as the next layer's
-// A fragments: output n-tiles 2j and 2j+1 form input k-tile j.
-SPOLY_D void relu_to_a(const float (&acc)[2][8][4], uint32_t (&a)[2][4][4]) {
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float* lo = acc[mt][2 * j];
-      const float* hi = acc[mt][2 * j + 1];
-      a[mt][j][0] = pack_relu_bf16(lo[0], lo[1]);
-      a[mt][j][1] = pack_relu_bf16(lo[2], lo[3]);
-      a[mt][j][2] = pack_relu_bf16(hi[0], hi[1]);
-      a[mt][j][3] = pack_relu_bf16(hi[2], hi[3]);
-    }
-}
-
+// Fused gate over tiles of 128 candidates: features (FP32), three BF16 layers
+// on the tensor cores (tcgen05.mma, accumulator in tensor memory), the FP32
+// output layer, the threshold, compaction.  Thread t owns row t of the tile:
+// it writes the row's features and hidden activations into the A tile and
+// reads the row's accumulator from TMEM lane t.  Every wait for the tensor
+// core is bounded; a wait that gives up sets *G.status, ends the CTA's loop,
+// and the CTA still frees its tensor memory.
 __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
-  __shared__ __align__(16) uint32_t sw[kPackWords];
-  __shared__ __align__(16) __nv_bfloat16 sx[kGateRows * kXStride];
-  __shared__ float sz[kGateRows];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ __align__(1024) uint8_t sa[kGateRows * kHid * 2];  // A: 128 rows x K (32 or 64) BF16
+  __shared__ __align__(1024) uint32_t sw[kPackWords];            // W1 W2 W3 (B tiles), then FP32 vectors
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
   for (int i = 4 * tid; i < kPackWords; i += 4 * blockDim.x)
     *reinterpret_cast<uint4*>(sw + i) = __ldg(reinterpret_cast<const uint4*>(G.packed + i));
-  const uint2* w1 = reinterpret_cast<const uint2*>(sw);
-  const uint2* w2 = reinterpret_cast<const uint2*>(sw + kFragW1);
-  const uint2* w3 = reinterpret_cast<const uint2*>(sw + kFragW1 + kFragW23);
+  __syncwarp();  // tcgen05.alloc and dealloc are executed by a converged warp
+  if (warp == 0) tmem_alloc(&tmem_slot, kGateTmemCols);
+  if (tid == 0) mbar_init(&bar, 1);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t t_row = tmem + (uint32_t(warp * 32) << 16);  // the warp's 32 lanes
+  const uint32_t a_s = smem_addr(sa), w_s = smem_addr(sw), bar_s = smem_addr(&bar);
   const float* bv = reinterpret_cast<const float*>(sw + kPackB);
-  const int g = lane >> 2, c2 = 2 * (lane & 3);
+  uint8_t* a_row32 = sa + (tid >> 3) * (kIn * 16) + (tid & 7) * 16;   // row tid of a K = 32 tile
+  uint8_t* a_row64 = sa + (tid >> 3) * (kHid * 16) + (tid & 7) * 16;  // row tid of a K = 64 tile
+  uint32_t parity = 0;
+  bool bad = false;
+  // completion of the layer just issued; warp-uniform result
+  auto wait = [&]() {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_s, parity, kGateWaitCycles));
+    parity ^= 1u;
+    tc_fence_after();
+    return ok;
+  };
+  // relu(acc + bias) rounded to BF16 into the A tile (K = 64) of the next layer
+  auto hidden = [&](const float* bias) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[32];
+      tmem_ld32(t_row + 32u * h, v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float* x = v + 8 * c;
+        const float* bb = bias + 32 * h + 8 * c;
+        uint4 q;
+        q.x = pack_relu_bf16(x[0] + bb[0], x[1] + bb[1]);
+        q.y = pack_relu_bf16(x[2] + bb[2], x[3] + bb[3]);
+        q.z = pack_relu_bf16(x[4] + bb[4], x[5] + bb[5]);
+        q.w = pack_relu_bf16(x[6] + bb[6], x[7] + bb[7]);
+        *reinterpret_cast<uint4*>(a_row64 + (4 * h + c) * 128) = q;
+      }
+    }
+  };
   for (int64_t base = int64_t(blockIdx.x) * kGateRows; base < G.n; base += int64_t(gridDim.x) * kGateRows) {
     const int64_t row = base + tid;
     const bool valid = row < G.n;
@@ -168,58 +176,62 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
       for (int j = 0; j < kFeat; ++j) f[j] = 0.0f;
     }
     const bool inside = f[kFeatMinBary] >= kGateInside;
-    uint32_t* xr = reinterpret_cast<uint32_t*>(sx + tid * kXStride);
+    // layer 1 input: features 0-23, zeros 24-31
 #pragma unroll
-    for (int j = 0; j < kFeat / 2; ++j) xr[j] = pack_bf16(f[2 * j], f[2 * j + 1]);
-#pragma unroll
-    for (int j = kFeat / 2; j < kIn / 2; ++j) xr[j] = 0u;
-    __syncthreads();  // also orders the weight staging before the first tile
-
-    uint32_t a[2][4][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int kt = 0; kt < 2; ++kt) {
-        const __nv_bfloat16* p = sx + (warp * 32 + mt * 16 + g) * kXStride + kt * 16 + c2;
-        a[mt][kt][0] = *reinterpret_cast<const uint32_t*>(p);
-        a[mt][kt][1] = *reinterpret_cast<const uint32_t*>(p + 8 * kXStride);
-        a[mt][kt][2] = *reinterpret_cast<const uint32_t*>(p + 8);
-        a[mt][kt][3] = *reinterpret_cast<const uint32_t*>(p + 8 * kXStride + 8);
+    for (int c = 0; c < kIn / 8; ++c) {
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (8 * c < kFeat) {
+        q.x = pack_bf16(f[8 * c], f[8 * c + 1]);
+        q.y = pack_bf16(f[8 * c + 2], f[8 * c + 3]);
+        q.z = pack_bf16(f[8 * c + 4], f[8 * c + 5]);
+        q.w = pack_bf16(f[8 * c + 6], f[8 * c + 7]);
       }
-    float acc[2][8][4];
-    layer<2>(acc, a, w1, bv, lane);
-    relu_to_a(acc, a);
-    layer<4>(acc, a, w2, bv + kHid, lane);
-    relu_to_a(acc, a);
-    layer<4>(acc, a, w3, bv + 2 * kHid, lane);
-    const float* w4 = bv + 3 * kHid;
+      *reinterpret_cast<uint4*>(a_row32 + c * 128) = q;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    if (__syncthreads_or(bad)) break;
+    if (tid == 0) gate_issue(tmem, a_s, w_s, kIn, bar_s);
+    bool ok = wait();
+    if (ok) hidden(bv);
+    fence_async_smem();
+    tc_fence_before();
+    if (__syncthreads_or(!ok)) {
+      bad = true;
+      break;
+    }
+    if (tid == 0) gate_issue(tmem, a_s, w_s + 4u * kFragW1, kHid, bar_s);
+    ok = wait();
+    if (ok) hidden(bv + kHid);
+    fence_async_smem();
+    tc_fence_before();
+    if (__syncthreads_or(!ok)) {
+      bad = true;
+      break;
+    }
+    if (tid == 0) gate_issue(tmem, a_s, w_s + 4u * (kFragW1 + kFragW23), kHid, bar_s);
+    ok = wait();
+    // output layer in FP32: z = b4 + w4 . relu(acc + b3)
+    float z = bv[4 * kHid];
+    if (ok) {
+      const float* b3 = bv + 2 * kHid;
+      const float* w4 = bv + 3 * kHid;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      float zl = 0.0f, zh = 0.0f;
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tmem_ld32(t_row + 32u * h, v);
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const float wa = w4[8 * nt + c2], wb = w4[8 * nt + c2 + 1];
-        zl += fmaxf(acc[mt][nt][0], 0.f) * wa + fmaxf(acc[mt][nt][1], 0.f) * wb;
-        zh += fmaxf(acc[mt][nt][2], 0.f) * wa + fmaxf(acc[mt][nt][3], 0.f) * wb;
-      }
-      zl += __shfl_xor_sync(0xffffffffu, zl, 1);
-      zl += __shfl_xor_sync(0xffffffffu, zl, 2);
-      zh += __shfl_xor_sync(0xffffffffu, zh, 1);
-      zh += __shfl_xor_sync(0xffffffffu, zh, 2);
-      if ((lane & 3) == 0) {
-        sz[warp * 32 + mt * 16 + g] = zl + bv[4 * kHid];
-        sz[warp * 32 + mt * 16 + g + 8] = zh + bv[4 * kHid];
+        for (int j = 0; j < 32; ++j) z = fmaf(fmaxf(v[j] + b3[32 * h + j], 0.0f), w4[32 * h + j], z);
       }
     }
-    __syncthreads();
-    const float z = sz[tid];
-    if (valid && G.logits) G.logits[row] = z;
+    bad = !ok;
+    if (valid && ok && G.logits) G.logits[row] = z;
     if (G.out_chains) {
       // 2-bounce chains are outside the network's domain and pass ungated;
       // a chain whose tangential-mismatch zero lies inside the triangle
       // always passes (the network only rejects chains whose zero lies
       // outside it)
-      const bool keep = valid && (z >= G.tau_logit || inside || __ldg(G.chains + 3 * row + 2) >= 0);
+      const bool keep = valid && ok && (z >= G.tau_logit || inside || __ldg(G.chains + 3 * row + 2) >= 0);
       const unsigned long long slot = warp_append(G.out_n, keep ? 1u : 0u);
       if (keep) {
         G.out_chains[3 * slot] = __ldg(G.chains + 3 * row);
@@ -227,6 +239,21 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
         G.out_chains[3 * slot + 2] = __ldg(G.chains + 3 * row + 2);
       }
     }
+  }
+  tc_fence_before();
+  if (__syncthreads_or(bad)) {
+    // a wait gave up: report it, and give the MMA still in flight one more
+    // bounded wait before its accumulator is freed
+    if (tid == 0) {
+      if (G.status) atomicOr(G.status, 1ull);
+      mbar_wait(bar_s, parity ^ 1u, kGateWaitCycles);
+    }
+    __syncthreads();
+  }
+  __syncwarp();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, kGateTmemCols);
   }
 }
 
@@ -239,14 +266,32 @@ __global__ void labels_kernel(const spoly_path* __restrict__ paths, int64_t n_pa
   }
 }
 
+// Resident blocks of `threads` threads per SM for a kernel without dynamic
+// shared memory, from its registers (allocated per warp in units of 256) and
+// static shared memory against the SM's limits.  The occupancy API answers
+// one block per SM for the tensor-memory kernel below, which limits only its
+// tensor memory to 64 of 512 columns per block.
+int resident_blocks(const void* fn, int threads) {
+  cudaFuncAttributes a{};
+  int dev = 0, regs = 0, smem = 0, thr = 0, reserved = 0;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+    return 1;
+  const int warps = (threads + 31) / 32;
+  const int per_warp = (a.numRegs * 32 + 255) / 256 * 256;
+  int b = thr / (32 * warps);
+  if (per_warp > 0) b = std::min(b, regs / (per_warp * warps));
+  b = std::min(b, smem / int(a.sharedSizeBytes + size_t(reserved)));
+  return std::max(b, 1);
+}
+
 cudaError_t launch_gate(const GateParams& G, int num_sms, cudaStream_t st) {
   if (G.n <= 0) return cudaSuccess;
   static int per_sm = 0;  // resident blocks per SM (same for every launch of this kernel)
-  if (per_sm == 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gate_kernel, 128, 0) != cudaSuccess || b < 1) b = 1;
-    per_sm = b;
-  }
+  if (per_sm == 0) per_sm = std::min(resident_blocks(reinterpret_cast<const void*>(gate_kernel), 128), kGateMaxPerSm);
   int64_t grid = (G.n + kGateRows - 1) / kGateRows;
   grid = std::min<int64_t>(grid, int64_t(num_sms) * per_sm);
   gate_kernel<<<int(grid), 128, 0, st>>>(G);
@@ -287,6 +332,7 @@ spoly_status alloc_mlp(spoly_ctx* ctx, spoly_mlp** out) {
   if (e == cudaSuccess) e = m->adam_m.ensure(kParams * sizeof(float));
   if (e == cudaSuccess) e = m->adam_v.ensure(kParams * sizeof(float));
   if (e == cudaSuccess) e = m->packed.ensure(kPackWords * sizeof(uint32_t));
+  if (e == cudaSuccess) e = m->status.ensure(16);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_m.p, 0, kParams * sizeof(float), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->adam_v.p, 0, kParams * sizeof(float), ctx->stream);
   if (e != cudaSuccess) {
@@ -337,7 +383,7 @@ spoly_status spoly_mlp_create(spoly_ctx* ctx, uint64_t seed, spoly_mlp** out) {
 
 spoly_status spoly_mlp_free(spoly_mlp* m) {
   if (!m) return SPOLY_EINVAL;
-  for (DevBuf* b : {&m->theta, &m->adam_m, &m->adam_v, &m->packed, &m->xb, &m->yb, &m->z1, &m->z2, &m->z3, &m->dz1,
+  for (DevBuf* b : {&m->theta, &m->adam_m, &m->adam_v, &m->packed, &m->status, &m->xb, &m->yb, &m->z1, &m->z2, &m->z3, &m->dz1,
                     &m->dz2, &m->dz3, &m->grad, &m->loss, &m->lists, &m->list_n, &m->logits})
     b->release();
   delete m;
@@ -457,8 +503,13 @@ spoly_status spoly_mlp_forward(spoly_ctx* ctx, const spoly_mlp* m, const float* 
   G.n = n;
   G.packed = static_cast<const uint32_t*>(m->packed.p);
   G.logits = logits;
+  G.status = static_cast<unsigned long long*>(m->status.p);
+  unsigned long long status = 0;
+  CK(cudaMemsetAsync(m->status.p, 0, 8, ctx->stream), "mlp_forward status");
   CK(launch_gate(G, ctx->num_sms, ctx->stream), "mlp_forward");
+  CK(cudaMemcpyAsync(&status, m->status.p, 8, cudaMemcpyDeviceToHost, ctx->stream), "mlp_forward status");
   CK(cudaStreamSynchronize(ctx->stream), "mlp_forward sync");
+  if (status) return fail(ctx, SPOLY_ETIMEOUT, "mlp_forward: a tensor-core completion wait gave up");
   return SPOLY_OK;
 }
 
@@ -524,12 +575,14 @@ spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* m, const spoly_mesh* me
   G.tau_logit = tau_logit;
   G.out_chains = static_cast<int32_t*>(ch->buf.p);
   G.out_n = static_cast<unsigned long long*>(ch->counter.p);
+  G.status = G.out_n + 1;  // second word of the cleared counter
   e = launch_gate(G, ctx->num_sms, ctx->stream);
-  unsigned long long cnt = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, ch->counter.p, 8, cudaMemcpyDeviceToHost, ctx->stream);
+  unsigned long long cnt[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, ch->counter.p, 16, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "gate"));
-  ch->n = int64_t(cnt);
+  if (cnt[1]) return bail(fail(ctx, SPOLY_ETIMEOUT, "gate: a tensor-core completion wait gave up"));
+  ch->n = int64_t(cnt[0]);
   ch->n_k2 = in->n_k2;  // every 2-bounce chain passes
   *inout = ch;
   return SPOLY_OK;

@@ -10,7 +10,8 @@ struct spoly_mlp {
   spoly::DevBuf theta;   // FP32 master parameters [kParams]
   spoly::DevBuf adam_m;  // Adam first moments [kParams]
   spoly::DevBuf adam_v;  // Adam second moments [kParams]
-  spoly::DevBuf packed;  // BF16 fragment-ordered inference weights [kPackWords]
+  spoly::DevBuf packed;  // BF16 tensor-core operand tiles and FP32 vectors of inference [kPackWords]
+  spoly::DevBuf status;  // inference status word (non-zero: a bounded wait gave up)
   int64_t adam_step = 0;
   // Training scratch (grown on demand).
   spoly::DevBuf xb, yb, z1, z2, z3, dz1, dz2, dz3, grad, loss, lists, list_n, logits;
@@ -21,7 +22,8 @@ namespace spoly {
 // Gate inference over n rows: features from `feat` ([n][24] FP32) when it is
 // non-null, else computed from `chains`.  Writes logits (if non-null) and
 // appends the chains whose logit reaches tau_logit to out_chains (if
-// non-null), counting them in *out_n.
+// non-null), counting them in *out_n.  *status (if non-null) becomes non-zero
+// when a wait for the tensor core gave up; the outputs are then incomplete.
 struct GateParams {
   MeshView mesh;
   QueryView qv;
@@ -33,6 +35,7 @@ struct GateParams {
   float* logits;
   int32_t* out_chains;
   unsigned long long* out_n;
+  unsigned long long* status;
 };
 
 cudaError_t launch_gate(const GateParams& G, int num_sms, cudaStream_t st);
