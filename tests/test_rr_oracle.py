@@ -1,0 +1,150 @@
+"""Pins of the 2-bounce reflection (RR) oracle: the scaled reflected
+direction (Eq. eq_431_di) against the mirror law, the system degrees
+against Table tab_sum, paths planted by forward ray tracing, reciprocity
+(the reversed chain has the reversed paths), and the flat-mirror case,
+which reduces to a one-bounce reflection towards the mirror image of x3
+solved by the independent one-bounce oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rr, tt
+
+
+def _refl(d, n):
+    n = n / np.linalg.norm(n)
+    return d - 2.0 * (d @ n) * n
+
+
+def _corridor(rng, tilt=0.1):
+    """A floor triangle (normals about +z) and a ceiling triangle (normals
+    about -z) with perturbed vertices and shading normals."""
+    P1 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0.0]]) + rng.normal(size=(3, 3)) * 0.05
+    N1 = np.array([0, 0, 1.0]) + rng.normal(size=(3, 3)) * tilt
+    P2 = np.array([[0, 0, 1.0], [0, 1, 1.0], [1, 0, 1.0]]) + rng.normal(size=(3, 3)) * 0.05
+    N2 = np.array([0, 0, -1.0]) + rng.normal(size=(3, 3)) * tilt
+    return P1, N1, P2, N2
+
+
+def _trace(x0, P1, N1, P2, N2, u1, v1, reach=0.4):
+    """Forward trace: reflect at (u1, v1) on T1, intersect T2's plane,
+    reflect there; x3 lies on the outgoing ray.  Returns (x3, w, t)."""
+    x1 = P1[0] + u1 * (P1[1] - P1[0]) + v1 * (P1[2] - P1[0])
+    n1 = N1[0] + u1 * (N1[1] - N1[0]) + v1 * (N1[2] - N1[0])
+    d1 = _refl(x1 - x0, n1)
+    A = np.stack([P2[1] - P2[0], P2[2] - P2[0], -d1], 1)
+    u2, v2, t = np.linalg.solve(A, x1 - P2[0])
+    x2 = x1 + t * d1
+    n2 = N2[0] + u2 * (N2[1] - N2[0]) + v2 * (N2[2] - N2[0])
+    d2 = _refl(d1, n2)
+    return x2 + reach * d2 / np.linalg.norm(d2), np.array([u1, v1, u2, v2]), t
+
+
+def test_reflected_direction_is_the_mirror_law():
+    """Eq. eq_431_di: D(u, v) = |n|^2 |d0| times the mirror-reflected unit
+    direction, exactly (a positive multiple)."""
+    rng = np.random.default_rng(0)
+    for _ in range(30):
+        P1, N1, _, _ = _corridor(rng, 0.3)
+        x0 = rng.normal(size=3) + [0, 0, 2]
+        x1p, n1p = tt.tri_polys(P1, N1)
+        D = rr.reflected_direction(x0, x1p, n1p)
+        u, v = rng.random(2) * 0.5
+        x1 = P1[0] + u * (P1[1] - P1[0]) + v * (P1[2] - P1[0])
+        n1 = N1[0] + u * (N1[1] - N1[0]) + v * (N1[2] - N1[0])
+        d0 = x1 - x0
+        want = (n1 @ n1) * np.linalg.norm(d0) * _refl(d0 / np.linalg.norm(d0), n1)
+        got = np.array([tt.bp_eval(D[k], u, v) for k in range(3)])
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+def test_system_degrees_within_table_bounds():
+    """Table tab_sum: RR degrees 10 and 16 (total); the u-degree of the
+    Bezout matrix is at most 16."""
+    rng = np.random.default_rng(1)
+    P1, N1, P2, N2 = _corridor(rng)
+    s = rr.build_rr([0.2, 0.2, 0.6], [0.6, 0.5, 0.4], P1, N1, P2, N2)
+    for key, bound in (("a", 10), ("b", 16)):
+        c = s[key]
+        i, j = np.nonzero(np.abs(c) > 1e-14 * np.abs(c).max())
+        assert (i + j).max() <= bound
+    assert max(tt.deg_u(s["a"]), tt.deg_u(s["b"])) <= 16
+
+
+def _planted(seed):
+    rng = np.random.default_rng(seed)
+    while True:
+        P1, N1, P2, N2 = _corridor(rng)
+        x0 = np.array([0.2, 0.2, 0.6]) + rng.normal(size=3) * 0.05
+        u1, v1 = 0.2 + 0.25 * rng.random(), 0.2 + 0.25 * rng.random()
+        x3, w, t = _trace(x0, P1, N1, P2, N2, u1, v1)
+        if t > 0 and min(w[2], w[3], 1 - w[2] - w[3]) > 0.02:
+            return x0, x3, P1, N1, P2, N2, w
+
+
+@pytest.mark.parametrize("seed", [2, 3, 4, 5, 6])
+def test_planted_paths_found(seed):
+    """A path planted by forward tracing over curved (shading-normal)
+    triangles is recovered to 1e-9; every path returned satisfies the
+    reflection law at both vertices and lies in both triangles."""
+    x0, x3, P1, N1, P2, N2, w = _planted(seed)
+    out = rr.solve_candidate(x0, x3, P1, N1, P2, N2)
+    assert any(np.max(np.abs(p["uv"] - w)) < 1e-9 for p in out), (w, [p["uv"] for p in out])
+    for p in out:
+        r1, r2, side, _ = rr.residuals(p["uv"], x0, x3, P1, N1, P2, N2)
+        assert side and max(np.linalg.norm(r1), np.linalg.norm(r2)) < 1e-9
+        u1, v1, u2, v2 = p["uv"]
+        assert min(u1, v1, 1 - u1 - v1) >= 0 and min(u2, v2, 1 - u2 - v2) >= 0
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_reciprocity(seed):
+    """Light paths are reversible: the chain x3 -> T2 -> T1 -> x0 has the
+    same paths with the vertex order swapped."""
+    x0, x3, P1, N1, P2, N2, w = _planted(seed)
+    fwd = rr.solve_candidate(x0, x3, P1, N1, P2, N2)
+    bwd = rr.solve_candidate(x3, x0, P2, N2, P1, N1)
+    a = sorted(tuple(np.round(p["uv"], 8)) for p in fwd)
+    b = sorted(tuple(np.round(np.r_[p["uv"][2:], p["uv"][:2]], 8)) for p in bwd)
+    assert len(a) >= 1 and a == b
+
+
+def test_flat_mirror_reduces_to_one_bounce():
+    """With a flat second triangle (one normal), x0 -> T1 -> T2 -> x3 is the
+    one-bounce reflection x0 -> T1 -> x3' (x3' the mirror image of x3 in
+    T2's plane) whose segment x1 -> x3' crosses the plane inside T2.  The
+    one-bounce paths come from the C oracle."""
+    oracle.build()
+    rng = np.random.default_rng(9)
+    hits = 0
+    for trial in range(6):
+        P1 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0.0]]) + rng.normal(size=(3, 3)) * 0.05
+        N1 = np.array([0, 0, 1.0]) + rng.normal(size=(3, 3)) * 0.15
+        P2 = np.array([[-2, -2, 1.0], [4, -2, 1.0], [-2, 4, 1.0]])  # large flat ceiling
+        N2 = np.tile([0, 0, -1.0], (3, 1))
+        x0 = np.array([0.3, 0.2, 0.5]) + rng.normal(size=3) * 0.05
+        x3 = np.array([0.4, 0.5, 0.5]) + rng.normal(size=3) * 0.05
+        x3m = x3.copy()
+        x3m[2] = 2.0 - x3[2]  # mirror image in z = 1
+        tri = np.zeros((18, 1))
+        for v in range(3):
+            tri[3 * v:3 * v + 3, 0] = P1[v]
+            tri[9 + 3 * v:12 + 3 * v, 0] = N1[v]
+        one, _ = oracle.solve(tri, x0[None], x3m[None], np.ones((1, 3)), np.zeros((1, 2), np.int32),
+                              np.ones(1, np.int32), np.array([[0, 0, -1]], np.int32))
+        want = []
+        for p in one:
+            u1, v1 = p["uv"][0], p["uv"][1]
+            x1 = P1[0] + u1 * (P1[1] - P1[0]) + v1 * (P1[2] - P1[0])
+            t = (1.0 - x1[2]) / (x3m[2] - x1[2])
+            x2 = x1 + t * (x3m - x1)
+            A = np.stack([P2[1] - P2[0], P2[2] - P2[0]], 1)
+            u2, v2 = np.linalg.lstsq(A, x2 - P2[0], rcond=None)[0]
+            if 0 < t < 1 and min(u2, v2, 1 - u2 - v2) >= 0:
+                want.append((u1, v1, u2, v2))
+        got = [p["uv"] for p in rr.solve_candidate(x0, x3, P1, N1, P2, N2)]
+        assert len(got) == len(want), (trial, got, want)
+        for w in want:
+            assert any(np.max(np.abs(g - w)) < 1e-8 for g in got), (trial, w, got)
+        hits += len(want)
+    assert hits >= 4
