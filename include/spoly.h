@@ -84,8 +84,9 @@ typedef struct {
  *   eta[q][3]     = eta_0 .. eta_k, IOR of the outgoing side of each vertex
  *                   (Sec. 3.1); reflection ignores it
  *   types[q][2]   = SPOLY_R / SPOLY_T per bounce
- *   k[q]          = bounce count: 1, or 2 for chains with two triangles
- *                   (both refractions, types T T; eta_0 .. eta_2 used) */
+ *   k[q]          = bounce count: 1, or 2 for chains with two triangles:
+ *                   two refractions (types T T; eta_0 .. eta_2 used) or
+ *                   two reflections (types R R) */
 typedef struct {
   const double* x_first;
   const double* x_last;
@@ -250,14 +251,18 @@ spoly_status spoly_chains_free(spoly_chains* chains);
  * SPOLY_SOLVE_ASYNC is set, the call synchronises, grows the path buffer and
  * re-runs the path phase if it overflowed, and returns with counters valid.
  * Chains with a second triangle (tri1 >= 0, explicit lists) are solved as
- * 2-bounce refraction chains x0 -> tri0 -> tri1 -> x_last (Sec. 4.4-4.5,
+ * 2-bounce chains x0 -> tri0 -> tri1 -> x_last of two refractions (TT:
+ * the rational sqrt pieces of Sec. 4.4) or two reflections (RR: the exact
+ * reflected direction of Eq. eq_431_di and the system of Eq. eq_rr1), by
+ * the same solver (Sec. 4.4-4.5,
  * Sec. 5.2 bisection: the Bezout determinant's sign at n_intervals + 1
  * uniform v1, 10 FP32 bisection steps per sign change, FP64 bisection to
  * 1e-10, u1 from a(u1, v1) = 0, u2 from the rational mapping, then
  * path-space Newton on h x n = 0 at both vertices); their paths carry
  * SPOLY_FLAG_NEWTON.  A list with such chains is always solved
  * synchronously, in batches.  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED
- * (a 2-bounce chain whose query is not of types T T). */
+ * (a 2-bounce chain whose query is not of types T T or R R; on device
+ * queries such chains are not checked and return no paths). */
 spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
                          const spoly_chains* chains, const spoly_solve_opts* opts,
                          spoly_solution_set** inout);

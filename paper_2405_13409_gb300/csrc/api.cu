@@ -561,8 +561,9 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     for (int64_t i = 0; i < q->n_queries; ++i) {
       if (q->k[i] != 1 && q->k[i] != 2)
         return fail(ctx, SPOLY_EUNSUPPORTED, "query %lld has k = %d; k = 1 and 2 are built", (long long)i, q->k[i]);
-      if (q->k[i] == 2 && (q->types[2 * i] != SPOLY_T || q->types[2 * i + 1] != SPOLY_T))
-        return fail(ctx, SPOLY_EUNSUPPORTED, "query %lld: 2-bounce chains are built for types T T", (long long)i);
+      if (q->k[i] == 2 && q->types[2 * i] != q->types[2 * i + 1])
+        return fail(ctx, SPOLY_EUNSUPPORTED, "query %lld: 2-bounce chains are built for types T T and R R",
+                    (long long)i);
     }
   }
   spoly_solution_set* set = *inout;

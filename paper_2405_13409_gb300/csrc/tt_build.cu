@@ -43,7 +43,8 @@ __global__ void tt_count_kernel(TTParams P, uint8_t* masks) {
     const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
     const TriD a = load_tri(P.mesh.tri, P.mesh.n_tris, t1);
     double s;
-    const unsigned mask = tt_pieces(a, qd.x0, qd.eta0, qd.eta1, P.sqrt_tab, &s);
+    // an RR chain (exact reflected direction) is one system
+    const unsigned mask = chain_kind(P.qv.types, q) == kChainRR ? 1u : tt_pieces(a, qd.x0, qd.eta0, qd.eta1, P.sqrt_tab, &s);
     masks[c] = uint8_t(mask);
     P.chain_sys[2 * c + 1] = __popc(mask);
   }
@@ -239,6 +240,145 @@ SPOLY_D void tt_construct(const TriD& t1, const TriD& t2, const QueryD& qd, d3 x
   gp_mac_trunc(b, dsq, p2sq, -eta2 * eta2);
 }
 
+// Edge e of T2 in the tangent t2 = n2 x e of the RR product form at x2
+// (reading of the switch "if the equation degenerates", Sec. 3.3, as for one
+// bounce): with m = (x3 - c1) x n2c, e21 unless |m^ . e21^| < kSwitch and
+// |m^ . e22^| > |m^ . e21^|, then e22.  FP64, as in the oracle.
+SPOLY_D d3 rr_edge(const TriD& t1, const TriD& t2, d3 x3) {
+  const d3 c1 = (1.0 / 3.0) * (t1.p0 + t1.p1 + t1.p2);
+  const d3 n2 = (1.0 / 3.0) * (t2.n0 + t2.n1 + t2.n2);
+  const d3 m = cross(x3 - c1, n2);
+  const d3 e1 = t2.p1 - t2.p0, e2 = t2.p2 - t2.p0;
+  const double mn = norm(m);
+  if (!(mn > 0.0)) return e1;
+  const double c1v = fabs(dot(m, e1)) / (mn * norm(e1)), c2v = fabs(dot(m, e2)) / (mn * norm(e2));
+  return (c1v < kSwitch && c2v > c1v) ? e2 : e1;
+}
+
+// Builds a, b, u~, v~, kappa of an RR system (Sec. 4.5, Eq. eq_rr1) in the
+// warp's arena: the scaled reflected direction D = d0 |n1|^2 - 2 (d0.n1) n1
+// (Eq. eq_431_di) is a polynomial, so the mapping (Eq. eq_rct) is exact and
+// a chain is one system.  a = (D x (x3 - x1)) . M2 (degree 8) and
+// b = (D.M2)(K2.T2) + (D.T2)(K2.M2) (degree 15) with M2 = kappa n2,
+// K2 = kappa d2, T2 = M2 x e.  All 32 lanes call it.
+constexpr int kRRWork = 5 * 3 * bsize(1) + 2 * bsize(2) + 2 * 3 * bsize(3) + 3 * 3 * bsize(kTTDmap) + 3 * bsize(4) +
+                        2 * bsize(7) + 2 * bsize(8);
+static_assert(kRRWork <= kTTWork, "the RR temporaries fit the TT arena");
+
+SPOLY_D void rr_construct(const TriD& t1, const TriD& t2, d3 x0, d3 x3, double* base, int64_t st) {
+  Arena A{base, st, 0};
+  const GP a = A.take(kTTDa), b = A.take(kTTDb), ut = A.take(kTTDmap), vt = A.take(kTTDmap), kap = A.take(kTTDmap);
+  const GV d0 = gv_take(A, 1), n1 = gv_take(A, 1), s2 = gv_take(A, 1), se1 = gv_take(A, 1), x31 = gv_take(A, 1);
+  gv_set_lin(d0, t1.p0 - x0, t1.p1 - t1.p0, t1.p2 - t1.p0);
+  gv_set_lin(n1, t1.n0, t1.n1 - t1.n0, t1.n2 - t1.n0);
+  gv_set_lin(s2, t1.p0 - t2.p0, t1.p1 - t1.p0, t1.p2 - t1.p0);
+  gv_set_lin(x31, x3 - t1.p0, -1.0 * (t1.p1 - t1.p0), -1.0 * (t1.p2 - t1.p0));
+  const d3 e21 = t2.p1 - t2.p0, e22 = t2.p2 - t2.p0;
+  {
+    const d3 c0 = mk(s2.x.at(0, 0), s2.y.at(0, 0), s2.z.at(0, 0));
+    const d3 cu = mk(s2.x.at(1, 0), s2.y.at(1, 0), s2.z.at(1, 0));
+    const d3 cv = mk(s2.x.at(0, 1), s2.y.at(0, 1), s2.z.at(0, 1));
+    gv_set_lin(se1, cross(c0, e21), cross(cu, e21), cross(cv, e21));
+  }
+  const GP n1sq = A.take(2), dn = A.take(2);
+  gp_zero(n1sq);
+  gp_zero(dn);
+  gv_dot_mac(n1sq, n1, n1, 1.0);
+  gv_dot_mac(dn, d0, n1, 1.0);
+  // D = d0 |n1|^2 - 2 (d0 . n1) n1: degree 3
+  const GV D = gv_take(A, 3);
+  gv_zero(D);
+  gp_mac(D.x, d0.x, n1sq, 1.0);
+  gp_mac(D.y, d0.y, n1sq, 1.0);
+  gp_mac(D.z, d0.z, n1sq, 1.0);
+  gp_mac(D.x, n1.x, dn, -2.0);
+  gp_mac(D.y, n1.y, dn, -2.0);
+  gp_mac(D.z, n1.z, dn, -2.0);
+  // de2 = D x e22; u~ = de2 . s2 (4); kappa = de2 . e21 (3); v~ = se1 . D (4)
+  const GV de2 = gv_take(A, 3);
+  gv_zero(de2);
+  gp_axpy(de2.x, D.y, e22.z);
+  gp_axpy(de2.x, D.z, -e22.y);
+  gp_axpy(de2.y, D.z, e22.x);
+  gp_axpy(de2.y, D.x, -e22.z);
+  gp_axpy(de2.z, D.x, e22.y);
+  gp_axpy(de2.z, D.y, -e22.x);
+  gp_zero(ut);
+  gv_dot_mac(ut, de2, s2, 1.0);
+  gp_zero(kap);
+  gv_dot_const_mac(kap, de2, e21, 1.0);
+  gp_zero(vt);
+  gv_dot_mac(vt, se1, D, 1.0);
+  // M2 = kappa n20 + u~ (n21 - n20) + v~ (n22 - n20) (degree 4), or the
+  // constant normal; slots of the mapping's size
+  const GV M2 = gv_take(A, kTTDmap);
+  gv_zero(M2);
+  if (constant_normal(t2)) {
+    gp_add00(M2.x, t2.n0.x);
+    gp_add00(M2.y, t2.n0.y);
+    gp_add00(M2.z, t2.n0.z);
+  } else {
+    const d3 g1 = t2.n1 - t2.n0, g2 = t2.n2 - t2.n0;
+    gp_axpy(M2.x, kap, t2.n0.x);
+    gp_axpy(M2.y, kap, t2.n0.y);
+    gp_axpy(M2.z, kap, t2.n0.z);
+    gp_axpy(M2.x, ut, g1.x);
+    gp_axpy(M2.y, ut, g1.y);
+    gp_axpy(M2.z, ut, g1.z);
+    gp_axpy(M2.x, vt, g2.x);
+    gp_axpy(M2.y, vt, g2.y);
+    gp_axpy(M2.z, vt, g2.z);
+  }
+  // K2 = kappa (x3 - p20) - u~ e21 - v~ e22 (degree 4)
+  const GV K2 = gv_take(A, kTTDmap);
+  gv_zero(K2);
+  const d3 w3 = x3 - t2.p0;
+  gp_axpy(K2.x, kap, w3.x);
+  gp_axpy(K2.y, kap, w3.y);
+  gp_axpy(K2.z, kap, w3.z);
+  gp_axpy(K2.x, ut, -e21.x);
+  gp_axpy(K2.y, ut, -e21.y);
+  gp_axpy(K2.z, ut, -e21.z);
+  gp_axpy(K2.x, vt, -e22.x);
+  gp_axpy(K2.y, vt, -e22.y);
+  gp_axpy(K2.z, vt, -e22.z);
+  // T2 = M2 x e (degree 4)
+  const d3 e = rr_edge(t1, t2, x3);
+  const GV T2 = gv_take(A, kTTDmap);
+  gv_zero(T2);
+  gp_axpy(T2.x, M2.y, e.z);
+  gp_axpy(T2.x, M2.z, -e.y);
+  gp_axpy(T2.y, M2.z, e.x);
+  gp_axpy(T2.y, M2.x, -e.z);
+  gp_axpy(T2.z, M2.x, e.y);
+  gp_axpy(T2.z, M2.y, -e.x);
+  // a = (D x (x3 - x1)) . M2
+  const GV C = gv_take(A, 4);
+  gv_zero(C);
+  gp_mac(C.x, D.y, x31.z, 1.0);
+  gp_mac(C.x, D.z, x31.y, -1.0);
+  gp_mac(C.y, D.z, x31.x, 1.0);
+  gp_mac(C.y, D.x, x31.z, -1.0);
+  gp_mac(C.z, D.x, x31.y, 1.0);
+  gp_mac(C.z, D.y, x31.x, -1.0);
+  gp_zero(a);
+  gv_dot_mac(a, C, M2, 1.0);
+  // b = (D.M2)(K2.T2) + (D.T2)(K2.M2); the factors' true degrees (7, 8) sit
+  // below their slots' sums, which the products truncate to
+  const GP dm = A.take(7), kt = A.take(8), dt = A.take(7), km = A.take(8);
+  gp_zero(dm);
+  gp_zero(kt);
+  gp_zero(dt);
+  gp_zero(km);
+  gv_dot_mac(dm, D, M2, 1.0);
+  gv_dot_mac(kt, K2, T2, 1.0);
+  gv_dot_mac(dt, D, T2, 1.0);
+  gv_dot_mac(km, K2, M2, 1.0);
+  gp_zero(b);
+  gp_mac(b, dm, kt, 1.0);
+  gp_mac(b, dt, km, 1.0);
+}
+
 // log2 x for x > 0 (frexp keeps tiny and huge values exact in the exponent).
 SPOLY_D double log2_pos(double x) {
   int e;
@@ -340,7 +480,18 @@ __global__ void __launch_bounds__(kBuildWarps * 32) tt_build_kernel(TTParams P) 
     const double eta2 = P.qv.eta[3 * q + 2];
     const TriD ta = load_tri(P.mesh.tri, P.mesh.n_tris, t1);
     const TriD tb = load_tri(P.mesh.tri, P.mesh.n_tris, t2);
-    tt_construct(ta, tb, qd, qd.x2, eta2, sy.piece, P.sqrt_tab, arena, 1);
+    const int kind = chain_kind(P.qv.types, q);
+    if (kind == kChainRR) {
+      rr_construct(ta, tb, qd.x0, qd.x2, arena, 1);
+    } else if (kind == kChainTT) {
+      tt_construct(ta, tb, qd, qd.x2, eta2, sy.piece, P.sqrt_tab, arena, 1);
+    } else {
+      // mixed bounce types are not built: a zero system has no roots
+      Arena A{arena, 1, 0};
+      const GP a = A.take(kTTDa), b = A.take(kTTDb);
+      gp_zero(a);
+      gp_zero(b);
+    }
     double* keep = P.scratch + i * kTTKeep;
     for (int t = lane; t < kTTKeep; t += 32) keep[t] = arena[t];
     tt_finish(sy, arena, P.coef32 + i * kTT32, arena + kTTScratch);

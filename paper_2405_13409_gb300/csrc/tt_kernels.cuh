@@ -28,6 +28,17 @@ enum TTCounter {
 };
 static_assert(TT_COUNT <= 16, "the solution set keeps 16 host copies of the TT counters");
 
+// The 2-bounce chain kinds of the pipeline, from the query's bounce types:
+// two refractions (TT) or two reflections (RR); mixed types are not built.
+constexpr int kChainTT = 0;
+constexpr int kChainRR = 1;
+constexpr int kChainOther = -1;
+SPOLY_D int chain_kind(const int32_t* types, int q) {
+  const int a = types[2 * q], b = types[2 * q + 1];
+  if (a == SPOLY_T && b == SPOLY_T) return kChainTT;
+  if (a == SPOLY_R && b == SPOLY_R) return kChainRR;
+  return kChainOther;
+}
 constexpr uint32_t kTTResample = 1u << 29;  // TTSys flag: sample again in FP64
 constexpr int kTTSampleSlots = 8193;         // samples per system at most (n_intervals <= 8192)
 constexpr int kTTNoisyMargin = 8;            // FP64 re-sampling: samples kept beyond the outermost FP32 change

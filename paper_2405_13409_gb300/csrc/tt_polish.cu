@@ -1,4 +1,5 @@
-// TT chains, path phase per chain (after the FP64 polish in tt_sign.cuh):
+// 2-bounce chains (TT, RR), path phase per chain (after the FP64 polish in
+// tt_sign.cuh):
 // u1 from a(u1, v1*) = 0, u2 from the rational mapping (Eq. eq_rct),
 // path-space Newton on h x n = 0 at both vertices (Eq. eq_ch), sidedness,
 // in-triangle tests and de-duplication of the chain's paths.
@@ -16,13 +17,15 @@ struct TTPath {
 
 SPOLY_D d3 unit3(d3 a) { return (1.0 / norm(a)) * a; }
 
-// h x n / (|h| |n|) at a refraction vertex with h = eta_out d1_hat - eta_in
-// d0_hat, and the sidedness test (both directions on one side).
-SPOLY_D d3 refr_residual(d3 xp, d3 x, d3 xn, d3 n, double ein, double eout, bool* side) {
+// h x n / (|h| |n|) with h = eta_out d1_hat - eta_in d0_hat (Eq. eq_ch;
+// reflection: both IORs 1), and the sidedness test: refraction crosses the
+// surface (d0 . n and d1 . n of one sign), reflection stays on its side
+// (opposite signs).
+SPOLY_D d3 vertex_residual(d3 xp, d3 x, d3 xn, d3 n, double ein, double eout, bool refl, bool* side) {
   const d3 d0 = x - xp, d1 = xn - x;
   const d3 h = eout * unit3(d1) - ein * unit3(d0);
   const double s0 = dot(d0, n), s1 = dot(d1, n);
-  *side = ((s0 < 0.0) == (s1 < 0.0)) && s0 != 0.0 && s1 != 0.0;
+  *side = (refl ? ((s0 < 0.0) != (s1 < 0.0)) : ((s0 < 0.0) == (s1 < 0.0))) && s0 != 0.0 && s1 != 0.0;
   return (1.0 / (norm(h) * norm(n))) * cross(h, n);
 }
 
@@ -30,6 +33,7 @@ struct TTGeom {
   TriD t1, t2;
   d3 x0, x3;
   double e0, e1, e2;
+  bool refl;  // two reflections (RR); else two refractions (TT)
 };
 
 SPOLY_D void tt_points(const TTGeom& G, const double (&w)[4], d3& x1, d3& n1, d3& x2, d3& n2) {
@@ -51,8 +55,8 @@ SPOLY_D void tt_F(const TTGeom& G, const double (&w)[4], d3 a1, d3 b1, d3 a2, d3
   d3 x1, n1, x2, n2;
   tt_points(G, w, x1, n1, x2, n2);
   bool s;
-  const d3 r1 = refr_residual(G.x0, x1, x2, n1, G.e0, G.e1, &s);
-  const d3 r2 = refr_residual(x1, x2, G.x3, n2, G.e1, G.e2, &s);
+  const d3 r1 = vertex_residual(G.x0, x1, x2, n1, G.e0, G.e1, G.refl, &s);
+  const d3 r2 = vertex_residual(x1, x2, G.x3, n2, G.e1, G.e2, G.refl, &s);
   f[0] = dot(r1, a1);
   f[1] = dot(r1, b1);
   f[2] = dot(r2, a2);
@@ -129,9 +133,10 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
       const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
       G.x0 = qd.x0;
       G.x3 = qd.x2;
-      G.e0 = qd.eta0;
-      G.e1 = qd.eta1;
-      G.e2 = P.qv.eta[3 * q + 2];
+      G.refl = chain_kind(P.qv.types, q) == kChainRR;
+      G.e0 = G.refl ? 1.0 : qd.eta0;
+      G.e1 = G.refl ? 1.0 : qd.eta1;
+      G.e2 = G.refl ? 1.0 : P.qv.eta[3 * q + 2];
       const int s0 = P.chain_sys[2 * c], ns = P.chain_sys[2 * c + 1];
       const d3 c1 = (1.0 / 3.0) * (G.t1.p0 + G.t1.p1 + G.t1.p2);
       const d3 ncen = (1.0 / 3.0) * (G.t1.n0 + G.t1.n1 + G.t1.n2);
@@ -204,8 +209,8 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
             d3 x1, n1, x2, n2;
             tt_points(G, w, x1, n1, x2, n2);
             bool sd1, sd2;
-            const d3 r1 = refr_residual(G.x0, x1, x2, n1, G.e0, G.e1, &sd1);
-            const d3 r2 = refr_residual(x1, x2, G.x3, n2, G.e1, G.e2, &sd2);
+            const d3 r1 = vertex_residual(G.x0, x1, x2, n1, G.e0, G.e1, G.refl, &sd1);
+            const d3 r2 = vertex_residual(x1, x2, G.x3, n2, G.e1, G.e2, G.refl, &sd2);
             const double res = fmax(norm(r1), norm(r2));
             if (!sd1 || !sd2 || !(res < kResidual)) continue;
             const double m1 = fmin(fmin(w[0], w[1]), 1.0 - w[0] - w[1]);

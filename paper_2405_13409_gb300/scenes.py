@@ -193,6 +193,26 @@ def slab_scene(seed: int = 0, n_cells: int = 16, n_recv: int = 64, thickness: fl
                        "top": (0, top.shape[1]), "bottom": (top.shape[1], tri.shape[1])})
 
 
+def corridor_scene(seed: int = 0, n_cells: int = 16, n_recv: int = 16, height: float = 1.0) -> Scene:
+    """2-bounce RR corridor between two mirrors: a floor heightfield (seed)
+    at z = 0 with its normals up and a ceiling heightfield (seed + 1) at
+    z = height with its normals turned down, both amplitude 0.05 over
+    [-1, 1]^2; light (-0.6, 0.1, 0.5) between them; n_recv x n_recv
+    receivers on z = 0.5 over [-0.8, 0.8]^2.  Triangles [0, T/2) are the
+    floor, [T/2, T) the ceiling.  Chains are left to the caller."""
+    z1, g1 = sinusoid_surface(seed, 0.05)
+    z2, g2 = sinusoid_surface(seed + 1, 0.05)
+    floor = heightfield_mesh(n_cells, z1, g1)
+    ceil = heightfield_mesh(n_cells, z2, g2, z_offset=height)
+    ceil[9:18] *= -1.0  # the ceiling reflects downwards
+    tri = np.concatenate([floor, ceil], axis=1)
+    recv = receiver_grid(n_recv, 0.5, half=0.8)
+    xf, xl, eta, types, k = _queries((-0.6, 0.1, 0.5), recv, (1.0, 1.0, 1.0), (TYPE_R, TYPE_R), 2)
+    return Scene(f"corridor_rr_{n_cells}x{n_cells}_r{n_recv}", tri, xf, xl, eta, types, k, chains=None,
+                 meta={"seed": seed, "n_cells": n_cells, "n_recv": n_recv,
+                       "floor": (0, floor.shape[1]), "ceiling": (floor.shape[1], tri.shape[1])})
+
+
 def batched_scene(seed: int = 0, n_queries: int = 4096, c_min: float = 1e2, c_max: float = 1e5) -> Scene:
     """Batched mixed workload: independent queries with bounce count uniform
     in {1, 2} and candidate counts log-uniform in [c_min, c_max], each with

@@ -1,0 +1,130 @@
+"""GPU tests of 2-bounce reflection (RR) chains against the FP64 RR oracle:
+planted paths through the corridor of two heightfield mirrors in both
+precisions, a sample of candidate pairs around them, and one list mixing RR
+chains with 1-bounce reflection chains."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rr
+from paper_2405_13409_gb300 import binding, scenes
+
+from .test_gpu_tt import _compare
+from .test_rr_oracle import planted_corridor_cases
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALLOWED = binding.FLAG_ILL_COND | binding.FLAG_EDGE
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = binding.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def corridor():
+    return scenes.corridor_scene(seed=0, n_cells=16, n_recv=2)
+
+
+def _solve(ctx, tri, x0s, x3s, chains, k, types, precision=binding.MIXED):
+    n = x0s.shape[0]
+    eta = np.ones((n, 3))
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (tri, x0s, x3s, eta, types, k)]
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=np.ascontiguousarray(chains, np.int32))
+    sol = ctx.spoly_solve(mesh, q, ch, precision=precision)
+    paths = ctx.spoly_paths(sol)
+    stats = ctx.spoly_stats(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    return paths, stats
+
+
+def _rr(n):
+    return np.full(n, 2, np.int32), np.full((n, 2), binding.SPOLY_R, np.int32)
+
+
+@pytest.mark.parametrize("precision", [binding.MIXED, binding.PLAIN_FP64])
+def test_planted_corridor_paths_match_oracle(ctx, corridor, precision):
+    cases = planted_corridor_cases(31, 24)
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    chains = np.array([[i, c[2], c[3]] for i, c in enumerate(cases)], np.int32)
+    paths, stats = _solve(ctx, corridor.tri, x0s, x3s, chains, *_rr(len(cases)), precision=precision)
+    ref = rr.solve(corridor.tri, x0s, x3s, chains)
+    matched, un, worst = _compare(paths, ref)
+    bad = [u for u in un if not (u[3] & ALLOWED)]
+    assert not bad, (bad, stats)
+    assert matched >= len(cases) - 1, (un, stats)
+    assert worst < 1e-9
+    for i, c in enumerate(cases):
+        got = paths[paths["query"] == i]
+        assert any(np.max(np.abs(p["uv"].ravel() - c[4])) < 1e-9 for p in got), (i, c[4], got["uv"])
+    assert np.all(paths["flags"] & binding.FLAG_NEWTON)
+    assert np.all(paths["residual"] < 1e-9)
+    assert stats["unsolved"] == 0
+
+
+def test_corridor_candidate_sample_matches_oracle(ctx, corridor):
+    """(floor, ceiling) pairs around planted paths' triangles and random
+    pairs: most have no path; the path sets agree with the oracle's."""
+    cases = planted_corridor_cases(32, 4)
+    half = corridor.n_tris // 2
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    rng = np.random.default_rng(4)
+    rows = []
+    for i, c in enumerate(cases):
+        for d1 in (-1, 0, 1, 32):
+            for d2 in (-32, -1, 0, 2):
+                a, b = c[2] + d1, c[3] + d2
+                if 0 <= a < half and half <= b < corridor.n_tris:
+                    rows.append([i, a, b])
+        for _ in range(6):
+            rows.append([i, int(rng.integers(0, half)), int(rng.integers(half, corridor.n_tris))])
+    chains = np.array(rows, np.int32)
+    paths, stats = _solve(ctx, corridor.tri, x0s, x3s, chains, *_rr(len(cases)))
+    ref = rr.solve(corridor.tri, x0s, x3s, chains)
+    matched, un, worst = _compare(paths, ref)
+    bad = [u for u in un if not (u[3] & ALLOWED)]
+    assert not bad, (bad, stats)
+    assert matched >= len(cases)
+    assert len(un) <= max(1, 1e-2 * chains.shape[0])
+    assert worst < 1e-9
+    assert stats["candidates"] == chains.shape[0]
+
+
+def test_rr_and_one_bounce_chains_in_one_list(ctx, corridor):
+    """One explicit list with RR chains and 1-bounce reflection chains on
+    the floor: each part equals its own oracle (RR oracle, C oracle)."""
+    oracle.build()
+    cases = planted_corridor_cases(33, 6)
+    n2 = len(cases)
+    half = corridor.n_tris // 2
+    x0s = np.array([c[0] for c in cases] + [[-0.6, 0.1, 0.5]] * 4)
+    x3s = np.array([c[1] for c in cases] + [[0.3, -0.2, 0.6], [0.1, 0.4, 0.7], [-0.2, -0.5, 0.4], [0.5, 0.5, 0.5]])
+    k = np.array([2] * n2 + [1] * 4, np.int32)
+    types = np.full((n2 + 4, 2), binding.SPOLY_R, np.int32)
+    rows = [[i, c[2], c[3]] for i, c in enumerate(cases)]
+    for q in range(n2, n2 + 4):
+        rows += [[q, t, -1] for t in range(half)]
+    chains = np.array(rows, np.int32)
+    paths, stats = _solve(ctx, corridor.tri, x0s, x3s, chains, k, types)
+    two = paths[paths["tri"][:, 1] >= 0]
+    one = paths[paths["tri"][:, 1] < 0]
+    ref2 = rr.solve(corridor.tri, x0s, x3s, chains[:n2])
+    m2, un2, w2 = _compare(two, ref2)
+    assert not [u for u in un2 if not (u[3] & ALLOWED)], un2
+    assert m2 >= n2 and w2 < 1e-9
+    ref1, _ = oracle.solve(corridor.tri, x0s, x3s, np.ones((n2 + 4, 3)), types, k, chains[n2:])
+    got = sorted((int(p["query"]), int(p["tri"][0])) for p in one)
+    want = sorted((int(p["query"]), int(p["tri0"])) for p in ref1)
+    assert got == want and len(want) >= 4

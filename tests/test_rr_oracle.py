@@ -148,3 +148,75 @@ def test_flat_mirror_reduces_to_one_bounce():
             assert any(np.max(np.abs(g - w)) < 1e-8 for g in got), (trial, w, got)
         hits += len(want)
     assert hits >= 4
+
+
+def _tri(T, t):
+    P = np.stack([T[0:3, t], T[3:6, t], T[6:9, t]])
+    N = np.stack([T[9:12, t], T[12:15, t], T[15:18, t]])
+    return P, N
+
+
+def planted_corridor_cases(seed, n, n_cells=16):
+    """Paths planted by forward tracing in the corridor scene: a light near
+    the scene's, a random point of a random floor triangle, the mirror
+    reflection to the ceiling triangle the ray hits (Moller-Trumbore over
+    all of them), the reflection there; x3 on the outgoing ray at z = 0.5.
+    Returns [(x0, x3, t_floor, t_ceiling, (u1, v1, u2, v2))]."""
+    from paper_2405_13409_gb300 import scenes
+    s = scenes.corridor_scene(seed=0, n_cells=n_cells, n_recv=2)
+    T = s.tri
+    half = s.n_tris // 2
+    C0 = T[0:3, half:].T
+    E1 = T[3:6, half:].T - C0
+    E2 = T[6:9, half:].T - C0
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        x0 = np.array([-0.6, 0.1, 0.5]) + rng.normal(size=3) * [0.2, 0.2, 0.05]
+        t1 = int(rng.integers(0, half))
+        P1, N1 = _tri(T, t1)
+        u1, v1 = rng.uniform(0.05, 0.9, 2)
+        if u1 + v1 > 0.95:
+            continue
+        x1 = P1[0] + u1 * (P1[1] - P1[0]) + v1 * (P1[2] - P1[0])
+        n1 = N1[0] + u1 * (N1[1] - N1[0]) + v1 * (N1[2] - N1[0])
+        d1 = _refl(x1 - x0, n1)
+        if d1[2] <= 0:
+            continue
+        # ray x1 + t d1 against every ceiling triangle
+        pv = np.cross(d1, E2)
+        det = np.einsum("ij,ij->i", E1, pv)
+        sv = x1 - C0
+        uu = np.einsum("ij,ij->i", sv, pv) / det
+        qv = np.cross(sv, E1)
+        vv = qv @ d1 / det
+        tt_ = np.einsum("ij,ij->i", E2, qv) / det
+        ok = (tt_ > 0) & (uu > 0.02) & (vv > 0.02) & (uu + vv < 0.98)
+        if not ok.any():
+            continue
+        j = int(np.argmin(np.where(ok, tt_, np.inf)))
+        P2, N2 = _tri(T, half + j)
+        u2, v2 = uu[j], vv[j]
+        x2 = x1 + tt_[j] * d1
+        n2 = N2[0] + u2 * (N2[1] - N2[0]) + v2 * (N2[2] - N2[0])
+        d2 = _refl(d1, n2)
+        if d2[2] >= 0:
+            continue
+        x3 = x2 + ((0.5 - x2[2]) / d2[2]) * d2
+        out.append((x0, x3, t1, half + j, np.array([u1, v1, u2, v2])))
+    return out
+
+
+def test_planted_corridor_paths_found():
+    """The corridor mesh (heightfield mirrors): planted paths are recovered
+    by the oracle from the mesh's SoA rows."""
+    from paper_2405_13409_gb300 import scenes
+    cases = planted_corridor_cases(20, 4)
+    T = scenes.corridor_scene(seed=0, n_cells=16, n_recv=2).tri
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    chains = np.array([[i, c[2], c[3]] for i, c in enumerate(cases)], np.int32)
+    ref = rr.solve(T, x0s, x3s, chains)
+    for i, c in enumerate(cases):
+        got = ref[ref["query"] == i]
+        assert any(np.max(np.abs(p["uv"] - c[4])) < 1e-9 for p in got), (i, c[4], got["uv"])
