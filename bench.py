@@ -66,15 +66,16 @@ LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", Fa
 # build, six FP32 sign classes, five FP64 re-sampling chunk classes and five
 # re-sampling scan classes, five polish classes and the path kernel.
 TT_FIXED, TT_PER_BATCH, TT_BATCH = 2, 23, 16384
+K2_KINDS = ("TT", "RR")  # 2-bounce workloads (slab, corridor)
 
 
 def launches_per_step(workload, use_gate, stats):
     """Kernel launches of the library in one step (counted from the ncu
     launch lists of each workload, profiles/)."""
-    if workload in ("slab", "batched"):
+    if workload in ("slab", "corridor", "batched"):
         batches = -(-int(stats.get("k2_systems", 0)) // TT_BATCH)
         tt = TT_FIXED + TT_PER_BATCH * batches
-        if workload == "slab":
+        if workload in ("slab", "corridor"):
             return 5 + 1 + tt  # cone cull (flag, shared check, forward boxes, pairs, chains), partition
         # explicit validation + cone test, gate, partition, persistent isolation, side, polish, paths
         return 2 + (1 if use_gate else 0) + 1 + 4 + tt
@@ -113,7 +114,13 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    p.add_argument("--workload", choices=["glints", "refract", "reflect", "slab", "batched"], default="glints")
+    p.add_argument("--workload", choices=["glints", "refract", "reflect", "slab", "corridor", "batched"],
+                   default="glints")
+    p.add_argument("--corridor-receivers", type=int, default=16,
+                   help="corridor: receiver grid side (16: 16x16 receivers)")
+    p.add_argument("--intervals", type=int, default=0,
+                   help="2-bounce chains: v1 sample intervals (0: 4096, the 2^12 + 1 samples; the paper's "
+                        "2-bounce GPU timing uses 100)")
     p.add_argument("--batch-queries", type=int, default=4096, help="batched: number of queries")
     p.add_argument("--slab-receivers", type=int, default=64,
                    help="slab: receiver grid side (64: the full 64x64 grid)")
@@ -134,9 +141,16 @@ def parse():
     return p.parse_args()
 
 
-def workload(name, slab_receivers=64, batch_queries=4096):
+def workload(name, slab_receivers=64, batch_queries=4096, corridor_receivers=16):
     """(scene, chain mode, scattering kind, description, camera or None)."""
     from paper_2405_13409_gb300 import binding, scenes
+    if name == "corridor":
+        s = scenes.corridor_scene(n_recv=corridor_receivers)
+        return s, binding.CHAINS_CONE, "RR", (
+            f"2-bounce reflection corridor: 16x16-cell floor (z=0, normals up) and ceiling (z=1, normals down) "
+            f"heightfield mirrors (512 triangles each, amplitude 0.05), light (-0.6,0.1,0.5), "
+            f"{corridor_receivers}x{corridor_receivers} receivers on z=0.5 over [-0.8,0.8]^2, forward+backward "
+            f"cone cull"), None
     if name == "batched":
         s = scenes.batched_scene(n_queries=batch_queries)
         return s, binding.CHAINS_EXPLICIT_CONE, "mixed", (
@@ -292,7 +306,7 @@ def footprint_sample(s, camera, n_pixels, seed):
     return np.concatenate(rows).astype(np.int32), n_blocks
 
 
-def run_oracle_sample(s, camera, n_units, seed, kind="R"):
+def run_oracle_sample(s, camera, n_units, seed, kind="R", n_intervals=0):
     """One CPU-oracle step: all triangles x n_units seeded receivers, the
     footprint candidates of a block of about n_units pixels (glints), or
     (slab) n_units (receiver, top, bottom) tuples pairing a seeded top
@@ -315,6 +329,17 @@ def run_oracle_sample(s, camera, n_units, seed, kind="R"):
         per_chain = (n1 * (t1 - t0) / max(1, i1.size) + n2 * (t2 - t1) / max(1, i2.size)) / (n1 + n2)
         return 1, per_chain, 0, (f"{i1.size} seeded 1-bounce and {i2.size} seeded 2-bounce chains of the explicit list; "
                                  f"time per chain weighted by the list's {n1:,}/{n2:,} mix")
+    if kind == "RR":
+        from oracle import rr
+        rng = np.random.default_rng(seed)
+        half = s.n_tris // 2
+        qs = rng.integers(0, s.n_queries, n_units)
+        t1 = rng.integers(0, half, n_units)
+        chains = np.stack([qs, t1, t1 + half], -1).astype(np.int32)
+        t0 = time.perf_counter()
+        paths = rr.solve(s.tri, s.x_first, s.x_last, chains, n_intervals or rr.N_INTERVALS)
+        return chains.shape[0], time.perf_counter() - t0, paths.size, \
+            f"{n_units} seeded (receiver, floor triangle, ceiling triangle of the same cell) tuples"
     if kind == "TT":
         from oracle import tt
         rng = np.random.default_rng(seed)
@@ -347,14 +372,14 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    s, _, kind, desc, cam = workload(args.workload, args.slab_receivers, args.batch_queries)
-    units = args.ref_units or (16384 if cam is not None else (8 if kind in ("TT", "mixed") else 16))
+    s, _, kind, desc, cam = workload(args.workload, args.slab_receivers, args.batch_queries, args.corridor_receivers)
+    units = args.ref_units or (16384 if cam is not None else (8 if kind in K2_KINDS + ("mixed",) else 16))
     cores = os.cpu_count()
     for i in range(args.warmup):
-        run_oracle_sample(s, cam, units, 1000 + i, kind)
+        run_oracle_sample(s, cam, units, 1000 + i, kind, args.intervals)
     tot_c, tot_t, tot_p, sample = 0, 0.0, 0, ""
     for i in range(args.steps):
-        c, t, p, sample = run_oracle_sample(s, cam, units, 2000 + i, kind)
+        c, t, p, sample = run_oracle_sample(s, cam, units, 2000 + i, kind, args.intervals)
         tot_c += c
         tot_t += t
         tot_p += p
@@ -403,8 +428,10 @@ class Pipeline:
     """One step of the hot path through the C ABI: candidate build, optional
     gate, solve.  Handles are reused across steps (grow-only buffers)."""
 
-    def __init__(self, ctx, mode, precision, camera, mlp=None, tau=0.0, ranges=None, explicit=None, flags=0):
+    def __init__(self, ctx, mode, precision, camera, mlp=None, tau=0.0, ranges=None, explicit=None, flags=0,
+                 n_intervals=0):
         self.ctx, self.mode, self.precision, self.camera = ctx, mode, precision, camera
+        self.n_intervals = n_intervals  # 2-bounce v1 sample intervals (0: the library's 4096)
         self.mlp, self.tau = mlp, tau
         self.ranges = ranges  # 2-bounce cone: ((first range), (second range))
         self.explicit = explicit  # explicit chain list (device tensor [n, 3])
@@ -436,7 +463,8 @@ class Pipeline:
         if ev:
             ev[2].record(stream)
         self.sol = self.ctx.spoly_solve(mesh, q, solve_on, precision=self.precision,
-                                        flags=binding.SOLVE_TIMING | self.flags, reuse=self.sol, camera=self.camera)
+                                        flags=binding.SOLVE_TIMING | self.flags, reuse=self.sol, camera=self.camera,
+                                        n_intervals=self.n_intervals)
         self.ev = ev
 
     def phase_ms(self):
@@ -493,7 +521,7 @@ def main():
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
     ctx = binding.Context(local, stream.cuda_stream)
-    s, mode, kind, desc, camera = workload(args.workload, args.slab_receivers, args.batch_queries)
+    s, mode, kind, desc, camera = workload(args.workload, args.slab_receivers, args.batch_queries, args.corridor_receivers)
     precision = binding.MIXED if args.precision == "mixed" else binding.PLAIN_FP64
     batched = kind == "mixed"
     host = [np.ascontiguousarray(a) for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k)]
@@ -543,7 +571,7 @@ def main():
             ctx.spoly_mlp_save(mlp, args.gate_file)
             json.dump(gate_info, open(args.gate_file + ".json", "w"))
 
-    ranges = ((0, s.n_tris // 2), (s.n_tris // 2, s.n_tris)) if kind == "TT" else None
+    ranges = ((0, s.n_tris // 2), (s.n_tris // 2, s.n_tris)) if kind in K2_KINDS else None
     tune = None
     if batched:
         # launch shape of the persistent isolation, tuned on the 1-bounce chains
@@ -554,7 +582,7 @@ def main():
         ctx.spoly_chains_free(ch1)
         del one
     pipe = Pipeline(ctx, mode, precision, camera, mlp, tau, ranges, explicit,
-                    binding.SOLVE_PERSISTENT if batched else 0)
+                    binding.SOLVE_PERSISTENT if batched else 0, n_intervals=args.intervals)
     for _ in range(args.warmup):
         pipe.step(mesh, q)
     torch.cuda.synchronize()
@@ -565,7 +593,7 @@ def main():
         pairs = n_cand
     elif batched:
         pairs = int(s.chains.shape[0])  # every explicit chain of the step
-    elif kind == "TT":
+    elif kind in K2_KINDS:
         pairs = s.n_queries * (s.n_tris // 2) ** 2  # every (receiver, top, bottom) tuple the cull stands for
     else:
         pairs = s.n_queries * s.n_tris
@@ -659,7 +687,7 @@ def main():
                 "fp32_laplace_tflops": FP32_LAPLACE_FLOPS.get(kind, 0) * n_solved / (iso * 1e-3) / 1e12 if iso > 0
                 else 0.0}
     roofline = roof_iso
-    if kind == "TT" or (batched and ph["k2"] >= max(ph["gate"], iso, ph["chains"])):
+    if kind in K2_KINDS or (batched and ph["k2"] >= max(ph["gate"], iso, ph["chains"])):
         # the FP32 sign kernels (tt_sign_kernel<float, N, G>, all size
         # classes), timed by the library with CUDA events around their
         # launches.  Work per determinant evaluation: elimination n^3/3 FMA,
@@ -698,6 +726,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "gate": "learned MLP" if use_gate else "off",
                    "candidates_per_step": pairs,
+                   **({"v1_intervals": args.intervals or 4096} if kind in K2_KINDS + ("mixed",) else {}),
                    "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "solved_per_s": world * n_solved * args.steps / (total_ms * 1e-3),
         "paths_per_s": world * n_paths * args.steps / (total_ms * 1e-3),
@@ -714,9 +743,9 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        units = 24576 if camera is not None else (64 if kind == "T" else (16 if kind in ("TT", "mixed") else 256))
-        c, tcpu, _, sample = run_oracle_sample(s, camera, units if kind in ("TT", "mixed") else min(units, s.n_queries),
-                                               7, kind)
+        units = 24576 if camera is not None else (64 if kind == "T" else (16 if kind in K2_KINDS + ("mixed",) else 256))
+        c, tcpu, _, sample = run_oracle_sample(s, camera, units if kind in K2_KINDS + ("mixed",) else min(units, s.n_queries),
+                                               7, kind, args.intervals)
         line["cpu_baseline"] = {"value": c / tcpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line))

@@ -107,13 +107,14 @@ typedef struct {
 
 typedef struct {
   int32_t mode;
-  /* CONE with second_end > 0: 2-bounce refraction chains (all queries k = 2,
-   * types T T, sharing x0 and the IORs) whose second triangle lies in
-   * [second_begin, second_end); the first lies in [tri_begin, tri_end).  A
-   * chain survives when its segment direction can lie in the first
-   * triangle's refracted-direction box from x0, in the direction box from
-   * the first triangle's bounding box to the second's, and in the negated
-   * refracted-direction box of the second triangle lit from x_last. */
+  /* CONE with second_end > 0: 2-bounce chains (all queries k = 2, all of
+   * types T T or all of types R R, sharing x0 and the IORs) whose second
+   * triangle lies in [second_begin, second_end); the first lies in
+   * [tri_begin, tri_end).  A chain survives when its segment direction can
+   * lie in the first triangle's refracted (reflected) direction box from
+   * x0, in the direction box from the first triangle's bounding box to the
+   * second's, and in the negated refracted (reflected) direction box of the
+   * second triangle lit from x_last. */
   int32_t second_begin;
   int32_t tri_begin; /* triangle range [tri_begin, tri_end); tri_end <= 0: all */
   int32_t tri_end;
@@ -222,8 +223,9 @@ const char* spoly_last_error(const spoly_ctx* ctx);
  * EXPLICIT copies the caller's list after a bounds check; EXPLICIT_CONE
  * keeps the chains of the caller's list (any mix of queries, bounce counts
  * and triangles) that pass the CONE test of their own bounce count, per
- * query x0, IORs and types (1 bounce: as CONE; 2 bounces of two refractions:
- * the three tests of the 2-bounce CONE; other 2-bounce types are kept),
+ * query x0, IORs and types (1 bounce: as CONE; 2 bounces of two refractions
+ * or two reflections: the three tests of the 2-bounce CONE; mixed 2-bounce
+ * types are kept),
  * in no particular order (its boxes use FP32 intervals with directed
  * rounding, so they enclose the FP64 boxes of CONE up to rounding).
  * *inout: NULL to

@@ -400,7 +400,7 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "tt cone"));
     if (!shared)
       return bail(fail(ctx, SPOLY_EUNSUPPORTED,
-                       "2-bounce cone: every query must be k = 2, types T T, with the same x0 and IORs"));
+                       "2-bounce cone: every query must be k = 2, types T T or R R (all alike), with the same x0 and IORs"));
     // receiver-independent pairs, then the per-receiver test; both grow to
     // the exact count when their first capacity is exceeded
     int64_t pcap = std::max<int64_t>(4096, int64_t(T.n1) * T.n2 / 16);

@@ -353,9 +353,10 @@ cudaError_t launch_chains_cone(const ChainParams& P, int num_sms, cudaStream_t s
 
 namespace {
 
-// ------------------------------------------------ 2-bounce (TT) cone cull
-// For chains x0 -> T1 -> T2 -> x3 of two refractions.  Every path's segment
-// direction unit(x2 - x1) lies in (i) T1's refracted-direction box from x0
+// ------------------------------------------- 2-bounce (TT, RR) cone cull
+// For chains x0 -> T1 -> T2 -> x3 of two refractions or two reflections.
+// Every path's segment direction unit(x2 - x1) lies in (i) T1's
+// refracted (reflected) direction box from x0
 // (forward), (ii) the unit box from T1's bounding box toward T2's, and
 // (iii) the negated refracted-direction box of T2 seen from x3 with the
 // indices swapped (backward: light from x3 refracted into the slab), which
@@ -370,7 +371,7 @@ __global__ void tt_fwd_boxes_kernel(TTConeParams P) {
   const d3 x0 = mk(P.qv.x_first[0], P.qv.x_first[1], P.qv.x_first[2]);
   Iv3 o, bb;
   bool empty = false;
-  const bool ok = out_box(P.mesh, t, x0, SPOLY_T, P.qv.eta[0], P.qv.eta[1], o, bb, empty);
+  const bool ok = out_box(P.mesh, t, x0, P.qv.types[0], P.qv.eta[0], P.qv.eta[1], o, bb, empty);
   float* B = P.fwd + int64_t(i) * 12;
   const Iv comps[3] = {o.x, o.y, o.z};
   const Iv bcomp[3] = {bb.x, bb.y, bb.z};
@@ -441,7 +442,8 @@ __global__ void tt_cone_chains_kernel(TTConeParams P, int64_t n_pairs) {
       const d3 x3 = mk(P.qv.x_last[3 * q], P.qv.x_last[3 * q + 1], P.qv.x_last[3 * q + 2]);
       Iv3 o, bb;
       bool empty = false;
-      const bool ok = out_box(P.mesh, t2, x3, SPOLY_T, P.qv.eta[3 * q + 2], P.qv.eta[3 * q + 1], o, bb, empty);
+      const bool ok =
+          out_box(P.mesh, t2, x3, P.qv.types[2 * q + 1], P.qv.eta[3 * q + 2], P.qv.eta[3 * q + 1], o, bb, empty);
       if (empty) {
         keep = false;
       } else if (!ok) {
@@ -480,13 +482,14 @@ __global__ void tt_cone_chains_kernel(TTConeParams P, int64_t n_pairs) {
   }
 }
 
-// Queries must share x0, the IORs and the types T T (all k = 2).
+// Queries must share x0, the IORs and the types, T T or R R (all k = 2).
 __global__ void tt_shared_kernel(QueryView Q, int32_t* flag) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < Q.n; q += stride) {
     bool same = true;
     for (int c = 0; c < 3; ++c) same &= Q.x_first[3 * q + c] == Q.x_first[c] && Q.eta[3 * q + c] == Q.eta[c];
-    same &= Q.types[2 * q] == SPOLY_T && Q.types[2 * q + 1] == SPOLY_T && Q.k[q] == 2;
+    same &= Q.types[2 * q] == Q.types[0] && Q.types[2 * q + 1] == Q.types[0] && Q.k[q] == 2;
+    same &= Q.types[0] == SPOLY_T || Q.types[0] == SPOLY_R;
     if (!same) atomicExch(flag, 0);
   }
 }
@@ -596,8 +599,10 @@ SPOLY_D void chain_box(const MeshView& M, int t, d3 x, int type, double eta_in, 
 }
 
 // The CONE test of one chain: 1 bounce as cone_pairs_general_kernel; 2
-// bounces of two refractions as tt_pairs_kernel (i, ii) and
-// tt_cone_chains_kernel (iii).  Other 2-bounce types are kept.
+// bounces of two refractions or two reflections as tt_pairs_kernel (i, ii)
+// and tt_cone_chains_kernel (iii) (for reflection the segment x1 -> x2 is
+// the ray reflected from x0 and, reversed, the one reflected from x3).
+// Mixed 2-bounce types are kept.
 SPOLY_D bool chain_cone_keep(const MeshView& M, const QueryView& Q, int64_t q, int t0, int t1, double margin) {
   const d3 x0 = mk(Q.x_first[3 * q], Q.x_first[3 * q + 1], Q.x_first[3 * q + 2]);
   const d3 xl = mk(Q.x_last[3 * q], Q.x_last[3 * q + 1], Q.x_last[3 * q + 2]);
@@ -607,10 +612,11 @@ SPOLY_D bool chain_cone_keep(const MeshView& M, const QueryView& Q, int64_t q, i
     chain_box(M, t0, x0, Q.types[2 * q], Q.eta[3 * q], Q.eta[3 * q + 1], margin, B);
     return to_box_overlaps(B, float(xl.x), float(xl.y), float(xl.z));
   }
-  if (Q.types[2 * q] != SPOLY_T || Q.types[2 * q + 1] != SPOLY_T) return true;
+  const int ty = Q.types[2 * q];
+  if ((ty != SPOLY_T && ty != SPOLY_R) || Q.types[2 * q + 1] != ty) return true;
   float F[12], B[12];
-  chain_box(M, t0, x0, SPOLY_T, Q.eta[3 * q], Q.eta[3 * q + 1], margin, F);
-  chain_box(M, t1, xl, SPOLY_T, Q.eta[3 * q + 2], Q.eta[3 * q + 1], margin, B);
+  chain_box(M, t0, x0, ty, Q.eta[3 * q], Q.eta[3 * q + 1], margin, F);
+  chain_box(M, t1, xl, ty, Q.eta[3 * q + 2], Q.eta[3 * q + 1], margin, B);
   if (!box_overlaps(F, B[6], B[9], B[7], B[10], B[8], B[11])) return false;  // (i), (ii)
   if (!box_overlaps(B, F[6], F[9], F[7], F[10], F[8], F[11])) return false;  // (iii) toward T1
   for (int c = 0; c < 3; ++c)

@@ -12,6 +12,15 @@ namespace spoly {
 
 constexpr int kSignThreads = 128;
 constexpr int kMaxBrackets = 128;  // per system: more re-samples the system in FP64 (FP32), or overflows (FP64)
+
+// FP32 sign changes above which a system's FP32 signs count as noise and it
+// is sampled again in FP64: one per 32 intervals (128 at 4096 intervals),
+// at least 16.  Re-sampling in FP64 is exact, so the limit moves work
+// between the passes and never drops a root.
+SPOLY_HD constexpr int noisy_limit(int n_intervals) {
+  return n_intervals / 32 > kMaxBrackets ? kMaxBrackets : (n_intervals / 32 < 16 ? 16 : n_intervals / 32);
+}
+static_assert(noisy_limit(4096) == kMaxBrackets && noisy_limit(100) == 16, "noise limits");
 constexpr int kMaxSamples = kTTSampleSlots;  // n_intervals <= 8192
 
 // The block stages the scaled FP64 coefficients of system i of the batch
@@ -129,7 +138,7 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
     }
   }
   __syncthreads();
-  if (sizeof(T) == 4 && S.nb > kMaxBrackets) {
+  if (sizeof(T) == 4 && S.nb > noisy_limit(NI)) {
     // FP32 rounding noise in a near-singular stretch of v: the system is
     // sampled again in FP64 (re-sampling pass), which keeps these signs
     // outside the stretch

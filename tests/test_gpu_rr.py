@@ -128,3 +128,43 @@ def test_rr_and_one_bounce_chains_in_one_list(ctx, corridor):
     got = sorted((int(p["query"]), int(p["tri"][0])) for p in one)
     want = sorted((int(p["query"]), int(p["tri0"])) for p in ref1)
     assert got == want and len(want) >= 4
+
+
+def test_rr_cone_keeps_planted_and_exhaustive_paths(ctx, corridor):
+    """The 2-bounce cone cull over the corridor (reflected-direction boxes)
+    keeps every planted pair and every pair with a path in an exhaustive
+    solve of four receivers (all 262,144 (floor, ceiling) pairs each); the
+    per-chain test of explicit lists keeps them too."""
+    cases = planted_corridor_cases(34, 4, jitter=False)
+    half = corridor.n_tris // 2
+    n = len(cases)
+    x3s = np.array([c[1] for c in cases])
+    k, types = _rr(n)
+    host = (corridor.tri, np.tile(corridor.x_first[0], (n, 1)), x3s, np.ones((n, 3)), types, k)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in host]
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_CONE, margin=1e-3, tri_range=(0, half),
+                                second_range=(half, corridor.n_tris))
+    kept = ctx.spoly_chains_copy(ch)
+    ctx.spoly_chains_free(ch)
+    keys = set(map(tuple, kept.tolist()))
+    for i, c in enumerate(cases):
+        assert (i, c[2], c[3]) in keys
+    t1 = np.repeat(np.arange(half), half)
+    t2 = np.tile(np.arange(half, corridor.n_tris), half)
+    allc = np.concatenate([np.stack([np.full(t1.size, i), t1, t2], -1) for i in range(n)]).astype(np.int32)
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT_CONE, margin=1e-3,
+                                explicit=torch.from_numpy(allc).cuda())
+    kept_exp = set(map(tuple, ctx.spoly_chains_copy(ch).tolist()))
+    ctx.spoly_chains_free(ch)
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=torch.from_numpy(allc).cuda())
+    sol = ctx.spoly_solve(mesh, q, ch, precision=binding.MIXED)
+    paths = ctx.spoly_paths(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    assert paths.size >= n
+    for p in paths:
+        key = (int(p["query"]), int(p["tri"][0]), int(p["tri"][1]))
+        assert key in keys and key in kept_exp, p
+    assert kept.shape[0] < 0.05 * allc.shape[0]
+    assert keys <= kept_exp

@@ -156,12 +156,13 @@ def _tri(T, t):
     return P, N
 
 
-def planted_corridor_cases(seed, n, n_cells=16):
+def planted_corridor_cases(seed, n, n_cells=16, jitter=True):
     """Paths planted by forward tracing in the corridor scene: a light near
     the scene's, a random point of a random floor triangle, the mirror
     reflection to the ceiling triangle the ray hits (Moller-Trumbore over
     all of them), the reflection there; x3 on the outgoing ray at z = 0.5.
-    Returns [(x0, x3, t_floor, t_ceiling, (u1, v1, u2, v2))]."""
+    jitter=False keeps the scene's light.  Returns [(x0, x3, t_floor,
+    t_ceiling, (u1, v1, u2, v2))]."""
     from paper_2405_13409_gb300 import scenes
     s = scenes.corridor_scene(seed=0, n_cells=n_cells, n_recv=2)
     T = s.tri
@@ -172,7 +173,7 @@ def planted_corridor_cases(seed, n, n_cells=16):
     rng = np.random.default_rng(seed)
     out = []
     while len(out) < n:
-        x0 = np.array([-0.6, 0.1, 0.5]) + rng.normal(size=3) * [0.2, 0.2, 0.05]
+        x0 = np.array([-0.6, 0.1, 0.5]) + (rng.normal(size=3) * [0.2, 0.2, 0.05] if jitter else 0.0)
         t1 = int(rng.integers(0, half))
         P1, N1 = _tri(T, t1)
         u1, v1 = rng.uniform(0.05, 0.9, 2)
