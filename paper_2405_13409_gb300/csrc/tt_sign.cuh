@@ -390,7 +390,7 @@ constexpr int kPolishMaxSteps = 40;  // bisection steps from one sample interval
 
 template <int N, int G>
 SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys& sy, int64_t k_begin, int64_t k_end) {
-  const int tid = threadIdx.x, gi = tid / G, g = tid % G;
+  const int lane = threadIdx.x & 31, gi = lane / G, g = lane % G;
   const double reach = 1.0 / P.n_intervals;
   const int64_t first = sy.first_item;
   auto ev = [&](double x) {
@@ -464,12 +464,32 @@ SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys&
   }
 }
 
+// The warp's copy of one system's FP64 coefficients (a then b, u-scaled).
+SPOLY_D void tt_stage_coef64_warp(const TTParams& P, int64_t i, const TTSys& sy, double* coef) {
+  const double* sc = P.scratch + i * kTTKeep;
+  for (int k = threadIdx.x & 31; k < kTT32; k += 32) {
+    const bool in_a = k < bsize(kTTDa);
+    const int idx = in_a ? k : k - bsize(kTTDa);
+    int row, col;
+    flat_to_ij(in_a ? kTTDa : kTTDb, idx, row, col);
+    coef[k] = ldexp(sc[(in_a ? kOffA : kOffB) + idx], sy.ks * row);
+  }
+}
+
+// Work items are (system, chunk of 32 / G brackets), one per warp: each warp
+// stages its system's coefficients in its own slice of shared memory, so a
+// block polishes four systems at once (most systems have one or two
+// brackets).
 template <int N, int G>
 __global__ void __launch_bounds__(kSignThreads) tt_polish_kernel(TTParams P, int n_lo) {
-  __shared__ double coef[kTT32];
-  constexpr int kGroups = kSignThreads / G;
+  constexpr int kWarps = kSignThreads / 32;
+  __shared__ double coef_all[kWarps][kTT32];
+  const int warp = threadIdx.x >> 5;
+  double* coef = coef_all[warp];
+  constexpr int kGroups = 32 / G;
   constexpr int kChunks = (kMaxBrackets + kGroups - 1) / kGroups;
-  for (int64_t item = blockIdx.x; item < P.n_sys * kChunks; item += gridDim.x) {
+  const int64_t nw = int64_t(gridDim.x) * kWarps;
+  for (int64_t item = int64_t(blockIdx.x) * kWarps + warp; item < P.n_sys * kChunks; item += nw) {
     const int64_t i = item % P.n_sys;
     const int c = int(item / P.n_sys);
     const TTSys sy = P.sys[P.sys_offset + i];
@@ -477,11 +497,11 @@ __global__ void __launch_bounds__(kSignThreads) tt_polish_kernel(TTParams P, int
       continue;
     const int64_t ni = (int64_t(sy.n_items) < P.queue_cap - sy.first_item) ? int64_t(sy.n_items)
                                                                            : P.queue_cap - sy.first_item;
-    tt_stage_coef64(P, i, sy, coef);
-    __syncthreads();
+    tt_stage_coef64_warp(P, i, sy, coef);
+    __syncwarp();
     const int64_t k_end = ni < int64_t(c + 1) * kGroups ? ni : int64_t(c + 1) * kGroups;
     polish_brackets<N, G>(coef, P, sy, int64_t(c) * kGroups, k_end);
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -494,8 +514,8 @@ cudaError_t launch_polish_class(const TTParams& P, int n_lo, int num_sms, cudaSt
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
   }
-  const int64_t g = std::min<int64_t>(P.n_sys, int64_t(num_sms) * per_sm);
-  tt_polish_kernel<N, G><<<int(g), kSignThreads, 0, st>>>(P, n_lo);
+  const int64_t g = std::min<int64_t>((P.n_sys + 3) / 4, int64_t(num_sms) * per_sm);
+  tt_polish_kernel<N, G><<<int(std::max<int64_t>(g, 1)), kSignThreads, 0, st>>>(P, n_lo);
   return cudaGetLastError();
 }
 
