@@ -30,10 +30,12 @@ namespace spoly {
 constexpr unsigned kGroupFull = 0xffffffffu;
 
 // a_i(v), b_i(v) for i = g + G s, s = 0..R (zero above the trimmed degrees).
-// `ca`, `cb`: the graded coefficient arrays of a and b (bidx layout).
+// `ca`, `cb`: the graded coefficient arrays of a and b (bidx layout).  ks
+// (FP64 only): the rows are scaled by 2^(ks i) after Horner, which equals
+// scaling every coefficient (an exact power of two).
 template <typename T, int N, int G>
 SPOLY_D void tt_group_coeffs(const T* __restrict__ ca, const T* __restrict__ cb, T v, int da, int db, int g,
-                             T (&av)[N / G + 1], T (&bv)[N / G + 1]) {
+                             T (&av)[N / G + 1], T (&bv)[N / G + 1], int ks = 0) {
   constexpr int R = N / G;
 #pragma unroll
   for (int s = 0; s <= R; ++s) {
@@ -46,6 +48,11 @@ SPOLY_D void tt_group_coeffs(const T* __restrict__ ca, const T* __restrict__ cb,
     if (i <= db) {
       const T* row = cb + bidx(kTTDb, i, 0);
       for (int j = kTTDb - i; j >= 0; --j) b = fma(b, v, row[j]);
+    }
+    if (sizeof(T) == 8 && ks != 0) {
+      const T sc = T(ldexp(1.0, ks * i));
+      a *= sc;
+      b *= sc;
     }
     av[s] = a;
     bv[s] = b;
@@ -176,9 +183,10 @@ struct GroupSign {
 // of the warp calls it (possibly with different v per group).  Kept out of
 // line: each (T, N, G) body is compiled once however often it is called.
 template <typename T, int N, int G>
-__device__ __noinline__ GroupSign tt_group_sign(const T* ca, const T* cb, T v, int da, int db, int n, int g) {
+__device__ __noinline__ GroupSign tt_group_sign(const T* ca, const T* cb, T v, int da, int db, int n, int g,
+                                                int ks = 0) {
   T av[N / G + 1], bv[N / G + 1];
-  tt_group_coeffs<T, N, G>(ca, cb, v, da, db, g, av, bv);
+  tt_group_coeffs<T, N, G>(ca, cb, v, da, db, g, av, bv, ks);
   T A[N / G][N];
   tt_group_bezout<T, N, G>(av, bv, n, g, A);
   GroupSign r;

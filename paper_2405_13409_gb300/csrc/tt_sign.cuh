@@ -388,20 +388,42 @@ cudaError_t launch_resample_class(const TTParams& P, int n_lo, int num_sms, cuda
 constexpr int kPolishWiden = 1;
 constexpr int kPolishMaxSteps = 40;  // bisection steps from one sample interval to kTTRootTol: 23
 
+// Polish of the brackets of one size class, packed: the groups of a warp take
+// consecutive queue slots, whichever systems they belong to (a system has
+// one or two brackets as a rule, and the slots of a size class are written
+// in runs by its sign kernel).  A group reads its system's FP64 coefficients
+// from the system's scratch row (through L1), scaling row i by 2^(ks i) after
+// Horner, which gives the same values as the scaled copy the sign kernels
+// stage.  Loops run in warp-uniform steps (every group calls the evaluation;
+// a group with nothing to do evaluates a fixed point of the batch's first
+// system).
 template <int N, int G>
-SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys& sy, int64_t k_begin, int64_t k_end) {
+__global__ void __launch_bounds__(kSignThreads) tt_polish_kernel(TTParams P, int n_lo) {
+  constexpr int kWarps = kSignThreads / 32;
+  constexpr int kGroups = 32 / G;
   const int lane = threadIdx.x & 31, gi = lane / G, g = lane % G;
   const double reach = 1.0 / P.n_intervals;
-  const int64_t first = sy.first_item;
-  auto ev = [&](double x) {
-    return tt_group_sign<double, N, G>(coef, coef + bsize(kTTDa), x, sy.da, sy.db, sy.n, g).sign;
-  };
-  {
-    const int64_t k = k_begin + gi;
-    const bool valid = k < k_end;
-    if (!__any_sync(kGroupFull, valid)) return;  // the warp has no bracket
+  const unsigned long long nb = P.counters[TT_BRACKETS];
+  const int64_t nq = int64_t(nb) < P.queue_cap ? int64_t(nb) : P.queue_cap;
+  const int64_t stride = int64_t(gridDim.x) * kWarps * kGroups;
+  for (int64_t base = (int64_t(blockIdx.x) * kWarps + (threadIdx.x >> 5)) * kGroups; base < nq; base += stride) {
+    const int64_t q = base + gi;
     RootItem item{};
-    if (valid) item = P.queue[first + k];
+    TTSys sy{};
+    bool valid = q < nq;
+    if (valid) {
+      item = P.queue[q];
+      const int64_t si = int64_t(item.chain) - P.sys_offset;
+      valid = si >= 0 && si < P.n_sys;
+      if (valid) {
+        sy = P.sys[item.chain];
+        valid = sy.n > n_lo && sy.n <= N;
+      }
+    }
+    if (!__any_sync(kGroupFull, valid)) continue;
+    const double* coef = valid ? P.scratch + (int64_t(item.chain) - P.sys_offset) * kTTKeep : P.scratch;
+    const int da = valid ? sy.da : 0, db = valid ? sy.db : 0, n = valid ? sy.n : 1, ks = valid ? sy.ks : 0;
+    auto ev = [&](double x) { return tt_group_sign<double, N, G>(coef, coef + bsize(kTTDa), x, da, db, n, g, ks).sign; };
     double lo = valid ? item.zlo : 0.0, hi = valid ? item.zhi : 1.0;
     const bool act = valid && lo < hi;  // lo == hi: a root exactly at a sample, kept
     bool ok = true;
@@ -412,11 +434,10 @@ SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys&
       const bool need = act && slo != 0 && shi != 0 && slo == shi && w < reach;
       if (!__any_sync(kGroupFull, need)) break;
       const double c = 0.5 * (lo + hi);
-      const double w2 = reach;
-      const double l2 = fmax(0.0, c - w2), h2 = fmin(1.0, c + w2);
+      const double l2 = fmax(0.0, c - reach), h2 = fmin(1.0, c + reach);
       const int s1 = ev(need ? l2 : lo), s2 = ev(need ? h2 : hi);
       if (need) {
-        w = w2;
+        w = reach;
         lo = l2;
         hi = h2;
         slo = s1;
@@ -440,12 +461,12 @@ SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys&
       const double mid = 0.5 * (lo + hi);
       const bool need = bis && hi - lo > kTTRootTol && mid > lo && mid < hi;
       if (!__any_sync(kGroupFull, need)) break;
-      const int s = ev(need ? mid : lo);
+      const int sgn = ev(need ? mid : lo);
       if (need) {
-        if (s == 0) {
+        if (sgn == 0) {
           lo = hi = mid;
           bis = false;
-        } else if (s == slo) {
+        } else if (sgn == slo) {
           lo = mid;
         } else {
           hi = mid;
@@ -459,49 +480,8 @@ SPOLY_D void polish_brackets(const double* coef, const TTParams& P, const TTSys&
       } else {
         atomicAdd(P.counters + TT_POLISH_LOST, 1ull);
       }
-      P.queue[first + k] = item;
+      P.queue[q] = item;
     }
-  }
-}
-
-// The warp's copy of one system's FP64 coefficients (a then b, u-scaled).
-SPOLY_D void tt_stage_coef64_warp(const TTParams& P, int64_t i, const TTSys& sy, double* coef) {
-  const double* sc = P.scratch + i * kTTKeep;
-  for (int k = threadIdx.x & 31; k < kTT32; k += 32) {
-    const bool in_a = k < bsize(kTTDa);
-    const int idx = in_a ? k : k - bsize(kTTDa);
-    int row, col;
-    flat_to_ij(in_a ? kTTDa : kTTDb, idx, row, col);
-    coef[k] = ldexp(sc[(in_a ? kOffA : kOffB) + idx], sy.ks * row);
-  }
-}
-
-// Work items are (system, chunk of 32 / G brackets), one per warp: each warp
-// stages its system's coefficients in its own slice of shared memory, so a
-// block polishes four systems at once (most systems have one or two
-// brackets).
-template <int N, int G>
-__global__ void __launch_bounds__(kSignThreads) tt_polish_kernel(TTParams P, int n_lo) {
-  constexpr int kWarps = kSignThreads / 32;
-  __shared__ double coef_all[kWarps][kTT32];
-  const int warp = threadIdx.x >> 5;
-  double* coef = coef_all[warp];
-  constexpr int kGroups = 32 / G;
-  constexpr int kChunks = (kMaxBrackets + kGroups - 1) / kGroups;
-  const int64_t nw = int64_t(gridDim.x) * kWarps;
-  for (int64_t item = int64_t(blockIdx.x) * kWarps + warp; item < P.n_sys * kChunks; item += nw) {
-    const int64_t i = item % P.n_sys;
-    const int c = int(item / P.n_sys);
-    const TTSys sy = P.sys[P.sys_offset + i];
-    if (sy.n_items <= c * kGroups || sy.n <= n_lo || sy.n > N || sy.first_item < 0 || sy.first_item >= P.queue_cap)
-      continue;
-    const int64_t ni = (int64_t(sy.n_items) < P.queue_cap - sy.first_item) ? int64_t(sy.n_items)
-                                                                           : P.queue_cap - sy.first_item;
-    tt_stage_coef64_warp(P, i, sy, coef);
-    __syncwarp();
-    const int64_t k_end = ni < int64_t(c + 1) * kGroups ? ni : int64_t(c + 1) * kGroups;
-    polish_brackets<N, G>(coef, P, sy, int64_t(c) * kGroups, k_end);
-    __syncwarp();
   }
 }
 
@@ -514,8 +494,8 @@ cudaError_t launch_polish_class(const TTParams& P, int n_lo, int num_sms, cudaSt
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
   }
-  const int64_t g = std::min<int64_t>((P.n_sys + 3) / 4, int64_t(num_sms) * per_sm);
-  tt_polish_kernel<N, G><<<int(std::max<int64_t>(g, 1)), kSignThreads, 0, st>>>(P, n_lo);
+  // the bracket count is on the device: a full grid strides over the queue
+  tt_polish_kernel<N, G><<<num_sms * per_sm, kSignThreads, 0, st>>>(P, n_lo);
   return cudaGetLastError();
 }
 
