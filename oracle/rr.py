@@ -197,7 +197,11 @@ def solve_candidate(x0, x3, P1, N1, P2, N2, n_intervals=N_INTERVALS):
             if not (-DELTA <= u1 <= 1.0 - v1 + DELTA):
                 continue
             # b(u1, v1*) must vanish with a
-            bs = np.sum(np.abs(bc) * np.maximum(1.0, abs(u1)) ** np.arange(bc.size))
+            # measured against the magnitude bound of evaluating b
+            # at (u1, v1*), sum_ij |b_ij| |u1|^i |v1*|^j (the coefficients of
+            # b(., v1*) alone all vanish when b does not depend on u)
+            babs = tt.u_coeffs(np.abs(sysd["b"][:db + 1]), abs(v1))[0]
+            bs = np.sum(babs * np.maximum(1.0, abs(u1)) ** np.arange(babs.size))
             if abs(np.polynomial.polynomial.polyval(u1, bc)) > 1e-6 * bs:
                 continue
             kap = tt.bp_eval(sysd["kap"], u1, v1)

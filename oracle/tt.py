@@ -158,7 +158,7 @@ def u_coeffs(c, v):
 
 def deg_u(c):
     """Highest u-power whose coefficient polynomial is not negligible
-    (reading R1: max-abs above 1e-13 of the polynomial's max-abs)."""
+    (max-abs above 1e-13 of the polynomial's max-abs)."""
     m = np.max(np.abs(c)) if c.size else 0.0
     if m == 0.0:
         return -1
@@ -211,7 +211,7 @@ def mapping(D, x1, P2):
 
 
 def proj_vector(x0, x3, P1, N1, P2, N2):
-    """Projection vector b of the square form at x2 (reading R2 applied to
+    """Projection vector b of the square form at x2 (the switch of Sec. 3.3, read as for one bounce, applied to
     the second vertex): the first of (1,0,0), (0,0,1), (0,1,0) whose
     |m_hat . b| >= 0.25, m = (x3 - c1) x n2 at the centroids."""
     c1 = np.asarray(P1).mean(0)
@@ -394,7 +394,7 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
             continue
         sg, la = det_sign(sysd, vs, n, da, db)
         # sign changes; a sample with det == 0 exactly is a root belonging to
-        # the interval on its left (reading 7)
+        # the interval on its left
         roots = [(vs[m], 0) for m in range(1, n_intervals + 1) if sg[m] == 0.0]
         br = [m for m in range(n_intervals) if sg[m] * sg[m + 1] < 0]
         lo = vs[br].copy()
@@ -413,7 +413,7 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
             hi = np.where(left & ~zero, hi, mid)
             it += 1
             if it == PAPER_ITERS:
-                # reading 7 (k = 2), normalised locally: |det| across the
+                # ill-conditioning (k = 2), normalised locally: |det| across the
                 # bracket against the largest |det| of the five samples
                 # around it (|det| spans hundreds of orders of magnitude over
                 # [0, 1]); a simple root gives about 2^-10 / 2.5
@@ -438,7 +438,11 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
                 u1 = float(r.real)
                 if not (-DELTA <= u1 <= 1.0 - v1 + DELTA):
                     continue
-                bs = np.sum(np.abs(bc) * np.maximum(1.0, abs(u1)) ** np.arange(bc.size))
+                # measured against the magnitude bound of evaluating b
+                # at (u1, v1*), sum_ij |b_ij| |u1|^i |v1*|^j (the coefficients of
+                # b(., v1*) alone all vanish when b does not depend on u)
+                babs = u_coeffs(np.abs(sysd["b"][:db + 1]), abs(v1))[0]
+                bs = np.sum(babs * np.maximum(1.0, abs(u1)) ** np.arange(babs.size))
                 if abs(np.polynomial.polynomial.polyval(u1, bc)) > 1e-6 * bs:
                     continue
                 kap = bp_eval(sysd["kap"], u1, v1)

@@ -73,7 +73,7 @@ __global__ void tt_fill_kernel(TTParams P, const uint8_t* masks) {
   }
 }
 
-// Projection axis of the square form at x2 (reading R2 at the second
+// Projection axis of the square form at x2 (the switch of Sec. 3.3 read as for one bounce, at the second
 // vertex): m = (x3 - c1) x n2c; first of x, z, y with |m_hat . e| >= 0.25.
 SPOLY_D int tt_axis(const TriD& t1, const TriD& t2, d3 x3) {
   const d3 c1 = (1.0 / 3.0) * (t1.p0 + t1.p1 + t1.p2);
@@ -386,7 +386,7 @@ SPOLY_D double log2_pos(double x) {
   return double(e) + double(log2f(float(m)));
 }
 
-// Trimmed u-degrees (reading R1), the u scaling u = 2^ks w and the scaled,
+// Trimmed u-degrees (a u-power counts above 1e-13 of the polynomial's max-abs), the u scaling u = 2^ks w and the scaled,
 // normalised FP32 copy `c32` ([kTT32], a then b) of the system in the warp's
 // arena; `rowmax` holds kTTDa + kTTDb + 2 doubles of shared memory.  All 32
 // lanes call it.

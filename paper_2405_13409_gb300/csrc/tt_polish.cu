@@ -179,14 +179,20 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
                                                 bfl);
           for (int r = 0; r < nr; ++r) {
             const double u = 0.5 * (blo[r] + bhi[r]);
-            // b(u, v*) must vanish with a (reading 11)
+            // b(u, v*) must vanish with a, measured against the magnitude
+            // bound of evaluating b there, sum_ij |b_ij| |u|^i |v*|^j (the
+            // coefficients of b(., v*) alone all vanish when b does not
+            // depend on u, as for two flat mirrors)
             double bv = 0.0, bs = 0.0;
-            const double au = fmax(1.0, fabs(u));
+            const double au = fmax(1.0, fabs(u)), av = fabs(v);
             for (int i = sy.db; i >= 0; --i) {
-              double row = 0.0;
-              for (int j = kTTDb - i; j >= 0; --j) row = fma(row, v, B.at(i, j));
+              double row = 0.0, rabs = 0.0;
+              for (int j = kTTDb - i; j >= 0; --j) {
+                row = fma(row, v, B.at(i, j));
+                rabs = fma(rabs, av, fabs(B.at(i, j)));
+              }
               bv = fma(bv, u, row);
-              bs = fma(bs, au, fabs(row));
+              bs = fma(bs, au, rabs);
             }
             if (fabs(bv) > 1e-6 * bs) continue;
             const double kap = gp_eval(KA, u, v);

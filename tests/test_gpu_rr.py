@@ -168,3 +168,30 @@ def test_rr_cone_keeps_planted_and_exhaustive_paths(ctx, corridor):
         assert key in keys and key in kept_exp, p
     assert kept.shape[0] < 0.05 * allc.shape[0]
     assert keys <= kept_exp
+
+
+@pytest.mark.parametrize("precision", [binding.MIXED, binding.PLAIN_FP64])
+def test_two_flat_mirrors_double_image(ctx, precision):
+    """Two flat parallel mirrors with face normals: the one path is the
+    double mirror image of x3 (closed form), as in the oracle's pin."""
+    rng = np.random.default_rng(13)
+    F = np.array([[-2.0, -2.0, 0.0], [4.0, -2.0, 0.0], [-2.0, 4.0, 0.0]])
+    h = 1.2
+    tri = np.zeros((18, 2))
+    tri[0:9, 0], tri[9:18, 0] = F.ravel(), np.tile([0.0, 0.0, 1.0], 3)
+    tri[0:9, 1], tri[9:18, 1] = (F + [0.0, 0.0, h]).ravel(), np.tile([0.0, 0.0, -1.0], 3)
+    n = 6
+    x0s = np.c_[rng.uniform(-0.3, 0.3, (n, 2)), rng.uniform(0.2, 0.8, n) * h]
+    x3s = np.c_[rng.uniform(0.2, 0.8, (n, 2)), rng.uniform(0.2, 0.8, n) * h]
+    chains = np.array([[i, 0, 1] for i in range(n)], np.int32)
+    paths, stats = _solve(ctx, tri, x0s, x3s, chains, *_rr(n), precision=precision)
+    assert paths.size == n, (paths.size, stats)
+    E = np.stack([F[1] - F[0], F[2] - F[0]], 1)
+    for i in range(n):
+        x0, x3 = x0s[i], x3s[i]
+        img = np.r_[x3[:2], -(2.0 * h - x3[2])]
+        x1 = x0 + x0[2] / (x0[2] - img[2]) * (img - x0)
+        x2 = np.r_[(x0 + (x0[2] + h) / (x0[2] - img[2]) * (img - x0))[:2], h]
+        w = np.r_[np.linalg.lstsq(E, x1 - F[0], rcond=None)[0], np.linalg.lstsq(E, x2 - F[0] - [0, 0, h], rcond=None)[0]]
+        got = paths[paths["query"] == i]
+        assert got.size == 1 and np.max(np.abs(got[0]["uv"].ravel() - w)) < 1e-9, (i, got["uv"], w)

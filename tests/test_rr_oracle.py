@@ -221,3 +221,29 @@ def test_planted_corridor_paths_found():
     for i, c in enumerate(cases):
         got = ref[ref["query"] == i]
         assert any(np.max(np.abs(p["uv"] - c[4])) < 1e-9 for p in got), (i, c[4], got["uv"])
+
+
+def test_two_flat_mirrors_double_image():
+    """Two flat parallel mirrors with face normals, floor z = 0 and ceiling
+    z = h: the path is the straight line from x0 to the image of x3 mirrored
+    in the ceiling and then in the floor (closed form).  It crosses the
+    floor at x1 and the floor's image of the ceiling (z = -h) above x2.
+    Here b does not depend on u1, and the path is still found."""
+    rng = np.random.default_rng(12)
+    F = np.array([[-2.0, -2.0, 0.0], [4.0, -2.0, 0.0], [-2.0, 4.0, 0.0]])
+    for _ in range(8):
+        h = rng.uniform(0.6, 1.5)
+        x0 = np.r_[rng.uniform(-0.3, 0.3, 2), rng.uniform(0.2, 0.8) * h]
+        x3 = np.r_[rng.uniform(-0.3, 0.3, 2) + 0.5, rng.uniform(0.2, 0.8) * h]
+        img = np.r_[x3[:2], -(2.0 * h - x3[2])]  # ceiling image, then floor image
+        t1 = x0[2] / (x0[2] - img[2])
+        t2 = (x0[2] + h) / (x0[2] - img[2])
+        x1 = x0 + t1 * (img - x0)
+        x2 = np.r_[(x0 + t2 * (img - x0))[:2], h]
+        E = np.stack([F[1] - F[0], F[2] - F[0]], 1)
+        u1, v1 = np.linalg.lstsq(E, x1 - F[0], rcond=None)[0]
+        u2, v2 = np.linalg.lstsq(E, x2 - (F[0] + [0, 0, h]), rcond=None)[0]
+        out = rr.solve_candidate(x0, x3, F, np.tile([0, 0, 1.0], (3, 1)), F + [0, 0, h],
+                                 np.tile([0, 0, -1.0], (3, 1)))
+        assert len(out) == 1, out
+        assert np.max(np.abs(out[0]["uv"] - [u1, v1, u2, v2])) < 1e-9, (out[0]["uv"], [u1, v1, u2, v2])
