@@ -21,7 +21,9 @@ most of them empty).  Also reported: admissible paths per second.
 
 --workload refract / reflect time the 1-bounce caustic and reflection
 workloads (bounding-cone cull / exhaustive, no gate); --workload slab the
-2-bounce refraction slab; --workload batched the batched mixed workload
+2-bounce refraction slab; --workload corridor the 2-bounce reflection
+corridor between two heightfield mirrors (--intervals sets the v1 sample
+intervals of 2-bounce chains); --workload batched the batched mixed workload
 (independent queries of 1 or 2 bounces with explicit candidate lists:
 per-chain cone test, learned gate on the 1-bounce chains, persistent
 isolation with an autotuned launch shape, 2-bounce pipeline).
