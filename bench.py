@@ -66,8 +66,9 @@ BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["b
 LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 19, ("glints", True): 20}
 # 2-bounce solve: systems count + fill, then per batch of <= 16,384 systems the
 # build, six FP32 sign classes, five FP64 re-sampling chunk classes and five
-# re-sampling scan classes, five polish classes and the path kernel.
-TT_FIXED, TT_PER_BATCH, TT_BATCH = 2, 23, 16384
+# re-sampling scan classes, five polish classes, the active-chain list and the
+# path kernel.
+TT_FIXED, TT_PER_BATCH, TT_BATCH = 2, 24, 16384
 K2_KINDS = ("TT", "RR")  # 2-bounce workloads (slab, corridor)
 
 

@@ -143,6 +143,9 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
   CK(cudaMemsetAsync(T.counters, 0, 16 * sizeof(unsigned long long), st), "tt counters");
   CK(set->tt_chain_sys.ensure(size_t(n2) * 2 * sizeof(int32_t)), "tt chain systems");
   CK(set->tt_masks.ensure(size_t(n2)), "tt masks");
+  CK(set->tt_active.ensure(8 + size_t(n2) * sizeof(int32_t)), "tt active chains");
+  T.active_n = static_cast<unsigned long long*>(set->tt_active.p);
+  T.active = reinterpret_cast<int32_t*>(static_cast<char*>(set->tt_active.p) + 8);
   T.chain_sys = static_cast<int32_t*>(set->tt_chain_sys.p);
   CK(launch_tt_count(T, static_cast<uint8_t*>(set->tt_masks.p), ctx->num_sms, st), "tt count");
   // exclusive prefix of the per-chain system counts (host)
@@ -990,7 +993,7 @@ spoly_status spoly_solution_free(spoly_solution_set* set) {
   set->paths.release();
   set->counters.release();
   for (DevBuf* b : {&set->part, &set->part_n, &set->tt_counters, &set->tt_chain_sys, &set->tt_masks, &set->tt_sys,
-                    &set->tt_scratch, &set->tt_coef32, &set->tt_queue, &set->tt_noisy})
+                    &set->tt_scratch, &set->tt_coef32, &set->tt_queue, &set->tt_noisy, &set->tt_active})
     b->release();
   if (set->gexec) cudaGraphExecDestroy(set->gexec);
   delete set;

@@ -67,7 +67,8 @@ struct spoly_solution_set {
   float tt_sign_ms = 0.0f;
   bool timed = false;
   // 2-bounce chains: partitioned lists, systems, per-batch scratch
-  spoly::DevBuf part, part_n, tt_counters, tt_chain_sys, tt_masks, tt_sys, tt_scratch, tt_coef32, tt_queue, tt_noisy;
+  spoly::DevBuf part, part_n, tt_counters, tt_chain_sys, tt_masks, tt_sys, tt_scratch, tt_coef32, tt_queue, tt_noisy,
+      tt_active;
   unsigned long long tt_host[16] = {0};  // TT_COUNT <= 16
   int64_t n_k2 = 0;
   // captured 1-bounce solve (SPOLY_SOLVE_GRAPH) and the inputs it was captured for

@@ -62,6 +62,8 @@ struct TTParams {
   double* scratch;         // [n_sys][kTTKeep] FP64: a, b, u~, v~, kappa (batch-local)
   float* coef32;           // [n_sys][kTT32] FP32: scaled, normalised a and b (batch-local)
   RootItem* queue;         // brackets: zlo = zhi = v1 after the polish; chain = system (global index)
+  int32_t* active;         // [n_chains] chains of the batch with a polished root (path phase)
+  unsigned long long* active_n;  // their count
   int64_t queue_cap;
   unsigned long long* counters;  // [TT_COUNT]
   // FP32 signs and log2 |det| of re-sampled systems ([noisy_cap][kTTSampleSlots]):

@@ -117,15 +117,39 @@ SPOLY_D void tt_newton(const TTGeom& G, double (&w)[4]) {
   }
 }
 
-// The path phase of one chain of this batch (one thread per chain).
-__global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_begin, int64_t chain_end) {
+// The chains of this batch with at least one polished root, listed so that
+// the path kernel's warps are full of chains with work (a few percent of
+// the chains have one).
+__global__ void tt_active_kernel(TTParams P, int64_t chain_begin, int64_t chain_end) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t base = chain_begin + int64_t(blockIdx.x) * blockDim.x; base < chain_end; base += stride) {
     const int64_t c = base + threadIdx.x;
+    bool has = false;
+    if (c < chain_end) {
+      const int s0 = P.chain_sys[2 * c], ns = P.chain_sys[2 * c + 1];
+      for (int si = s0; si < s0 + ns && !has; ++si) {
+        const TTSys sy = P.sys[si];
+        if (sy.n < 1) continue;
+        for (int k = 0; k < sy.n_items && !has && sy.first_item + k < P.queue_cap; ++k)
+          has = (P.queue[sy.first_item + k].flags & kTTValid) != 0;
+      }
+    }
+    const unsigned long long slot = warp_append(P.active_n, has ? 1u : 0u);
+    if (has) P.active[slot] = int32_t(c);
+  }
+}
+
+// The path phase of the listed chains (one thread per chain).
+__global__ void __launch_bounds__(64) tt_path_kernel(TTParams P) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t n_active = int64_t(*P.active_n);
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < n_active; base += stride) {
+    const int64_t idx = base + threadIdx.x;
+    const int64_t c = idx < n_active ? int64_t(P.active[idx]) : 0;
     TTPath out[6];
     int np = 0;
     unsigned n_u = 0;
-    if (c < chain_end) {
+    if (idx < n_active) {
       const int q = P.chains[3 * c], t1i = P.chains[3 * c + 1], t2i = P.chains[3 * c + 2];
       TTGeom G;
       G.t1 = load_tri(P.mesh.tri, P.mesh.n_tris, t1i);
@@ -154,6 +178,7 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
         const GP VT{const_cast<double*>(sc) + int64_t(kOffVt) * st, st, kTTDmap};
         const GP KA{const_cast<double*>(sc) + int64_t(kOffKap) * st, st, kTTDmap};
         for (int k = 0; k < sy.n_items; ++k) {
+          if (sy.first_item + k >= P.queue_cap) break;  // brackets past an overflowed queue were not kept
           const RootItem item = P.queue[sy.first_item + k];
           if (!(item.flags & kTTValid)) continue;
           const double v = item.zlo;
@@ -275,8 +300,14 @@ __global__ void __launch_bounds__(64) tt_path_kernel(TTParams P, int64_t chain_b
 
 cudaError_t launch_tt_paths(const TTParams& P, int64_t chain_begin, int64_t chain_end, int num_sms, cudaStream_t st) {
   if (chain_end <= chain_begin) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(P.active_n, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const int64_t ga = std::min<int64_t>((chain_end - chain_begin + 255) / 256, int64_t(num_sms) * 8);
+  tt_active_kernel<<<int(ga), 256, 0, st>>>(P, chain_begin, chain_end);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int64_t g = std::min<int64_t>((chain_end - chain_begin + 63) / 64, int64_t(num_sms) * 8);
-  tt_path_kernel<<<int(g), 64, 0, st>>>(P, chain_begin, chain_end);
+  tt_path_kernel<<<int(g), 64, 0, st>>>(P);
   return cudaGetLastError();
 }
 
