@@ -195,3 +195,68 @@ def test_two_flat_mirrors_double_image(ctx, precision):
         w = np.r_[np.linalg.lstsq(E, x1 - F[0], rcond=None)[0], np.linalg.lstsq(E, x2 - F[0] - [0, 0, h], rcond=None)[0]]
         got = paths[paths["query"] == i]
         assert got.size == 1 and np.max(np.abs(got[0]["uv"].ravel() - w)) < 1e-9, (i, got["uv"], w)
+
+
+@pytest.mark.parametrize("precision", [binding.MIXED, binding.PLAIN_FP64])
+def test_two_bounce_degenerate_inputs(ctx, precision):
+    """Degenerate 2-bounce inputs run to completion with no path through
+    them: a zero-area triangle, a sliver (collinear vertices), a triangle
+    with zero normals, and a light in the first mirror's plane.  The regular
+    chain of the same list keeps its closed-form path (double mirror image)."""
+    F = np.array([[-2.0, -2.0, 0.0], [4.0, -2.0, 0.0], [-2.0, 4.0, 0.0]])
+    h = 1.2
+    P = [F, F + [0.0, 0.0, h], np.full((3, 3), [0.3, 0.3, 0.0]), np.array([[0.0, 0, 0], [1, 1, 0], [2, 2, 0]]), F]
+    N = [np.tile([0.0, 0, 1], (3, 1)), np.tile([0.0, 0, -1], (3, 1)), np.tile([0.0, 0, 1], (3, 1)),
+         np.tile([0.0, 0, 1], (3, 1)), np.zeros((3, 3))]
+    tri = np.zeros((18, 5))
+    for t in range(5):
+        tri[0:9, t], tri[9:18, t] = P[t].ravel(), N[t].ravel()
+    x0s = np.array([[0.1, 0.0, 0.6], [0.2, 0.1, 0.0]])
+    x3s = np.array([[0.5, 0.3, 0.6], [0.5, 0.3, 0.6]])
+    chains = np.array([[0, 0, 1], [0, 2, 1], [0, 0, 2], [0, 3, 1], [0, 1, 3], [0, 4, 1], [0, 0, 4], [1, 0, 1]],
+                      np.int32)
+    paths, stats = _solve(ctx, tri, x0s, x3s, chains, *_rr(2), precision=precision)
+    assert paths.size == 1, (paths, stats)
+    p = paths[0]
+    assert (int(p["query"]), int(p["tri"][0]), int(p["tri"][1])) == (0, 0, 1)
+    x0, x3 = x0s[0], x3s[0]
+    img = np.r_[x3[:2], -(2.0 * h - x3[2])]
+    x1 = x0 + x0[2] / (x0[2] - img[2]) * (img - x0)
+    assert np.allclose(p["x"].ravel()[:3], x1, atol=1e-9) and np.all(np.isfinite(p["uv"]))
+    assert p["residual"] < 1e-9
+
+
+def test_two_bounce_types_and_empty_lists(ctx, corridor):
+    """Mixed bounce types (R T) are rejected on host queries and give no
+    paths on device queries, where the RR chains of the same list are still
+    solved; an empty explicit list is rejected."""
+    cases = planted_corridor_cases(35, 2)
+    x0s = np.array([c[0] for c in cases] + [cases[0][0]])
+    x3s = np.array([c[1] for c in cases] + [cases[0][1]])
+    k = np.full(3, 2, np.int32)
+    types = np.full((3, 2), binding.SPOLY_R, np.int32)
+    types[2] = (binding.SPOLY_R, binding.SPOLY_T)
+    chains = np.array([[0, cases[0][2], cases[0][3]], [1, cases[1][2], cases[1][3]], [2, cases[0][2], cases[0][3]]],
+                      np.int32)
+    eta = np.tile([1.0, 1.5, 1.0], (3, 1))
+    mesh = ctx.mesh(torch.from_numpy(np.ascontiguousarray(corridor.tri)).cuda())
+    qh = ctx.queries(x0s, x3s, eta, types, k)  # host arrays
+    ch = ctx.spoly_build_chains(mesh, qh, binding.CHAINS_EXPLICIT, explicit=chains)
+    with pytest.raises(binding.SpolyError) as err:
+        ctx.spoly_solve(mesh, qh, ch, precision=binding.MIXED)
+    assert err.value.status == binding.SPOLY_EUNSUPPORTED
+    ctx.spoly_chains_free(ch)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (x0s, x3s, eta, types, k)]
+    qd = ctx.queries(*d)
+    ch = ctx.spoly_build_chains(mesh, qd, binding.CHAINS_EXPLICIT, explicit=chains)
+    sol = ctx.spoly_solve(mesh, qd, ch, precision=binding.MIXED)
+    paths = ctx.spoly_paths(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    assert set(paths["query"].tolist()) == {0, 1}
+    for i in (0, 1):
+        got = paths[paths["query"] == i]
+        assert any(np.max(np.abs(g["uv"].ravel() - cases[i][4])) < 1e-9 for g in got)
+    with pytest.raises(binding.SpolyError) as err:
+        ctx.spoly_build_chains(mesh, qd, binding.CHAINS_EXPLICIT, explicit=np.zeros((0, 3), np.int32))
+    assert err.value.status == binding.SPOLY_EINVAL
