@@ -187,10 +187,13 @@ SPOLY_D void sign_system(SignSmem<T>& S, const TTParams& P, int64_t i, TTSys& sy
   }
   const int nb = min(S.nb, kMaxBrackets);
   if (tid == 0 && S.nb > kMaxBrackets) atomicAdd(P.counters + TT_BRACKET_OVERFLOW, 1ull);
-  // bisection, one bracket per group at a time (block-uniform trip counts)
+  // bisection, one bracket per group at a time (block-uniform trip counts);
+  // brackets fill the lowest groups, and a warp without one skips the round
+  // (the evaluation synchronises within the warp only)
   for (int k0 = 0; k0 < nb; k0 += kGroups) {
     const int k = k0 + gi;
     const bool valid = k < nb;
+    if (!__any_sync(kGroupFull, valid)) continue;
     T lo = valid ? S.blo[k] : T(0), hi = valid ? S.bhi[k] : T(1);
     const int slo = valid ? S.bs[k] : 1;
     bool active = valid && lo < hi;
