@@ -48,10 +48,10 @@ METRIC = "candidate solves/s & admissible paths/s on 1 GB300: learned+FP32 vs pl
 UNIT = "candidates/s"
 # Algorithmic FP64 flops per solved candidate in the isolation kernel:
 # construction of a, b (Sec. 3.5) and the FP64 Bezout entries (Eq. eq_bezout);
-# counted from the implementation.  FP32: Laplace expansion.
+# counted from the implementation's arithmetic.  FP32: Laplace expansion.
 FP64_FLOPS = {"T": 1310, "R": 650}
 FP32_LAPLACE_FLOPS = {"T": 2744, "R": 400}
-# Nominal scalar peaks derived from unit counts and clocks (DESIGN.md):
+# Nominal scalar peaks derived from unit counts and clocks:
 # FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: 1.25 TFLOP/s.
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 NOMINAL_FP64_TFLOPS = 1.25
