@@ -79,6 +79,16 @@ SPOLY_D uint32_t pack_relu_bf16(float lo, float hi) {
   return r;
 }
 
+// Two FP32 additions in one instruction (each rounded to nearest, as two
+// scalar additions would be).
+SPOLY_D void add2(float a0, float a1, float b0, float b1, float& r0, float& r1) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b0), "f"(b1));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r0), "=f"(r1) : "l"(rd));
+}
+
 constexpr int kGateRows = 128;                 // candidates per tile: the MMA's M, one per thread and TMEM lane
 constexpr uint32_t kGateTmemCols = kHid;       // one 128 x 64 FP32 accumulator, reused by the three layers
 constexpr uint32_t kGateIdesc = umma_idesc_bf16(kGateRows, kHid);
@@ -146,11 +156,14 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
       for (int c = 0; c < 4; ++c) {
         const float* x = v + 8 * c;
         const float* bb = bias + 32 * h + 8 * c;
+        float y[8];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) add2(x[e], x[e + 1], bb[e], bb[e + 1], y[e], y[e + 1]);
         uint4 q;
-        q.x = pack_relu_bf16(x[0] + bb[0], x[1] + bb[1]);
-        q.y = pack_relu_bf16(x[2] + bb[2], x[3] + bb[3]);
-        q.z = pack_relu_bf16(x[4] + bb[4], x[5] + bb[5]);
-        q.w = pack_relu_bf16(x[6] + bb[6], x[7] + bb[7]);
+        q.x = pack_relu_bf16(y[0], y[1]);
+        q.y = pack_relu_bf16(y[2], y[3]);
+        q.z = pack_relu_bf16(y[4], y[5]);
+        q.w = pack_relu_bf16(y[6], y[7]);
         *reinterpret_cast<uint4*>(a_row64 + (4 * h + c) * 128) = q;
       }
     }
@@ -221,7 +234,12 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
         float v[32];
         tmem_ld32(t_row + 32u * h, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) z = fmaf(fmaxf(v[j] + b3[32 * h + j], 0.0f), w4[32 * h + j], z);
+        for (int j = 0; j < 32; j += 2) {
+          float y0, y1;
+          add2(v[j], v[j + 1], b3[32 * h + j], b3[32 * h + j + 1], y0, y1);
+          z = fmaf(fmaxf(y0, 0.0f), w4[32 * h + j], z);
+          z = fmaf(fmaxf(y1, 0.0f), w4[32 * h + j + 1], z);
+        }
       }
     }
     bad = !ok;
