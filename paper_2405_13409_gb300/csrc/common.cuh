@@ -142,6 +142,19 @@ constexpr double kPrefilterDv = 1e-3;     // side samples (in v) of the pre-poli
 constexpr double kSideReach = 0.25;       // side search reach (in v) of a displaced FP32 root
 constexpr float kTangent32 = 1e-4f;  // tangent-root test, FP32 isolation
 constexpr double kTangent64 = 1e-12; // tangent-root test, FP64 isolation
+// Certification of the FP32 isolation (mixed precision).  A candidate is
+// re-isolated in FP64 when its FP32 resultant r
+//   - has a largest coefficient below kCert32Tiny (2^-100: partial products
+//     of the expansion may have left FP32's exponent range),
+//   - cancels by more than kCert32Cancel: sum_c R_c Z^c > kCert32Cancel *
+//     sum_c |r_c| Z^c, where R is the same expansion over |E| with every term
+//     added (the scale of its rounding errors),
+//   - or comes within kCert32Dip * sum_c |r_c| Z^c of zero at a critical
+//     point or at an end of the domain (a near-double root or an edge root,
+//     which FP32 rounding can create, remove or move across the end).
+constexpr float kCert32Tiny = 7.8886091e-31f;  // 2^-100
+constexpr float kCert32Cancel = 1e9f;
+constexpr float kCert32Dip = 1e-3f;
 
 // Pinhole camera of a footprint workload, for the pixel filter of the path
 // phase (layout of spoly_chain_opts::camera).

@@ -98,7 +98,9 @@ def generate(name: str, N: int, ED: int, absolute: bool = False) -> str:
 
 def main():
     out = ["// Generated by gen_laplace.py: straight-line memoised Laplace expansions of",
-           "// the symmetric Bezout matrix (Sec. 5.2).  Do not edit by hand.",
+           "// the symmetric Bezout matrix (Sec. 4.2), and the same expansions over |E|",
+           "// with every term added (the rounding-error scale of each coefficient).",
+           "// Do not edit by hand.",
            "#pragma once",
            '#include "common.cuh"',
            "",
@@ -106,6 +108,8 @@ def main():
            ""]
     for name, N, ED in CONFIGS:
         out.append(generate(name, N, ED))
+        out.append("")
+        out.append(generate(name, N, ED, absolute=True))
         out.append("")
     out.append("}  // namespace spoly")
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "laplace_gen.cuh")

@@ -62,7 +62,7 @@ SPOLY_D int k1_generic_one(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int c
     for (int j = 0; j < s.n; ++j) bezout_entry_rt<DB>(s.a, s.b, s.na, s.nb, s.n, i, j, E[i][j]);
   double r[kRD + 1];
   laplace_rt<DB>(E, s.n, r);
-  return k1_finish<double, kRD, DB>(s, r, items, chain, n_v, n_pref);
+  return k1_finish<double, kRD, DB>(s, r, r, items, chain, n_v, n_pref);
 }
 
 }  // namespace spoly

@@ -10,11 +10,15 @@ namespace spoly {
 
 // Post-Laplace steps shared by the sized and generic kernels: power-of-two
 // normalisation and trimming of r, recursive-derivative isolation and the
-// u-range pre-filter.  Returns the number of brackets written to `items`, or
-// -1 if r vanishes identically.
+// u-range pre-filter.  Returns the number of brackets written to `items`,
+// -1 if r vanishes identically, or (T = float) -2 when the FP32 isolation is
+// not certified (kCert32*): the candidate is then re-isolated in FP64.  `ra`
+// (T = float) holds the expansion over |E| of the same entries; FP64 callers
+// pass r again.
 template <typename T, int RD, int DB>
-SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD + 1], int chain,
-                      unsigned& n_vroots, unsigned& n_pref) {
+SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], const T (&ra)[RD + 1], RootItem (&items)[kRD + 1],
+                      int chain, unsigned& n_vroots, unsigned& n_pref) {
+  constexpr bool fp32 = sizeof(T) == 4;
   // Power-of-two normalisation of r and trimming of negligible leading terms
   // (their contribution over the domain is below kTrim of the largest term).
   const double inv_t = scale2(1.0, -s.sc.kt);  // 1 / t, exact
@@ -22,7 +26,8 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
   T mx = T(0);
 #pragma unroll
   for (int c = 0; c <= RD; ++c) mx = fmax(mx, fabs(r[c]));
-  if (!(mx > T(0))) return -1;
+  if (!(mx > T(0))) return fp32 ? -2 : -1;
+  if (fp32 && mx < T(kCert32Tiny)) return -2;
   int e2;
   frexp(mx, &e2);
 #pragma unroll
@@ -51,12 +56,31 @@ SPOLY_D int k1_finish(const K1Sys<DB>& s, T (&r)[RD + 1], RootItem (&items)[kRD 
     }
   }
   const T lo = T(-kDelta * inv_t), hi = Z;
-  constexpr bool fp32 = sizeof(T) == 4;
   const T tol = fp32 ? T(kIsoTol32 * inv_t) : T(kIsoTol64 * inv_t);
   const T tang = fp32 ? T(kTangent32) : T(kTangent64);
+  if constexpr (fp32) {
+    // cancellation ratio of the expansion, then both ends of the domain
+    const T it = T(inv_t);
+    T Rs = T(0), zz = T(1);
+#pragma unroll
+    for (int c = 0; c <= RD; ++c) {
+      if (c <= deg) Rs += ldexp(ra[c], -e2) * zz;
+      zz *= it;
+    }
+    if (!(Rs <= T(kCert32Cancel) * rscale)) return -2;
+    T flo = T(0), fhi = T(0);
+#pragma unroll
+    for (int c = RD; c >= 0; --c)
+      if (c <= deg) {
+        flo = fma(flo, lo, r[c]);
+        fhi = fma(fhi, hi, r[c]);
+      }
+    if (fabs(flo) <= T(kCert32Dip) * rscale || fabs(fhi) <= T(kCert32Dip) * rscale) return -2;
+  }
   T blo[RD + 1], bhi[RD + 1];
   uint32_t bfl[RD + 1];
-  const int nb = isolate<T, RD>(r, deg, lo, hi, tol, tang, rscale, blo, bhi, bfl);
+  const int nb = isolate<T, RD>(r, deg, lo, hi, tol, tang, rscale, blo, bhi, bfl, fp32 ? T(kCert32Dip) : T(0));
+  if (nb < 0) return -2;
   n_vroots += nb;
   // Pre-polish filter: keep a bracket only if a(u, v) = 0 has a real u within
   // kPrefilterMargin of [0, 1 - v] (or a(., v) is degenerate), at the bracket
@@ -106,6 +130,7 @@ SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int
   constexpr int ED = 2 + DB - 1;
   constexpr int RD = N * (ED - N + 1);
   T r[RD + 1];
+  T ra[RD + 1];  // FP32: the expansion over |E| (certification); unused in FP64
   {
     T E[sym_size(N, ED)];
     bezout_sym<T, N, 2, DB>(s.a, s.b, s.na, s.nb, E);
@@ -117,8 +142,23 @@ SPOLY_D int k1_isolate_sized(const K1Sys<DB>& s, RootItem (&items)[kRD + 1], int
     if constexpr (N == 4 && DB == 6) laplace_T4<T>(E, r);
     if constexpr (N == 5 && DB == 6) laplace_T5<T>(E, r);
     if constexpr (N == 6 && DB == 6) laplace_T6<T>(E, r);
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int i = 0; i < sym_size(N, ED); ++i) E[i] = fabs(E[i]);
+      if constexpr (N == 2 && DB == 4) laplace_abs_R2<T>(E, ra);
+      if constexpr (N == 3 && DB == 4) laplace_abs_R3<T>(E, ra);
+      if constexpr (N == 4 && DB == 4) laplace_abs_R4<T>(E, ra);
+      if constexpr (N == 2 && DB == 6) laplace_abs_T2<T>(E, ra);
+      if constexpr (N == 3 && DB == 6) laplace_abs_T3<T>(E, ra);
+      if constexpr (N == 4 && DB == 6) laplace_abs_T4<T>(E, ra);
+      if constexpr (N == 5 && DB == 6) laplace_abs_T5<T>(E, ra);
+      if constexpr (N == 6 && DB == 6) laplace_abs_T6<T>(E, ra);
+    } else {
+#pragma unroll
+      for (int c = 0; c <= RD; ++c) ra[c] = T(0);
+    }
   }
-  return k1_finish<T, RD, DB>(s, r, items, chain, n_vroots, n_pref);
+  return k1_finish<T, RD, DB>(s, r, ra, items, chain, n_vroots, n_pref);
 }
 
 // Isolation with the unrolled expansion of the candidate's Bezout size;

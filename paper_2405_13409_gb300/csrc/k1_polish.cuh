@@ -306,31 +306,59 @@ SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, d
   return np;
 }
 
-// Path phase of queue item i.  Roots already produced by an earlier bracket
-// of the same candidate (items of one candidate are contiguous in the queue)
-// or equal to the item's other root within 1e-9 in v are skipped.
+// Paths of both polished roots of one queue item (roots within `dtol` of an
+// earlier root of the item, or of `skip_z` roots, are skipped).
 template <int DB>
-SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue, int64_t i, int q, int t,
-                         spoly_path (&out)[6], unsigned& n_u, const PixelFilter& pix) {
-  const RootItem it = queue[i];
-  K1Sys<DB> s;
-  if (!k1_system<DB>(tr, qd, s)) return 0;
+SPOLY_D int k1_item_paths(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, const RootItem& it, int q, int t,
+                          spoly_path (&out)[6], int np, unsigned& n_u, const PixelFilter& pix,
+                          const RootItem* earlier, int64_t n_earlier) {
   const double dtol = 1e-9 / s.sc.t;
-  int np = 0;
   for (int r = 0; r < 2; ++r) {
     const uint32_t valid = r == 0 ? kRoot1Valid : kRoot2Valid;
     if (!(it.flags & valid)) continue;
     const double z = r == 0 ? it.zlo : it.zhi;
     bool dup = (r == 1 && (it.flags & kRoot1Valid) && fabs(it.zlo - z) <= dtol);
-    for (int64_t j = i - 1; j >= 0 && !dup; --j) {
-      const RootItem o = queue[j];
-      if (o.chain != it.chain) break;
+    for (int64_t j = 0; j < n_earlier && !dup; ++j) {
+      const RootItem o = earlier[j];
       if (((o.flags & kRoot1Valid) && fabs(o.zlo - z) <= dtol) || ((o.flags & kRoot2Valid) && fabs(o.zhi - z) <= dtol))
         dup = true;
     }
     if (dup) continue;
     const uint32_t vflags = r == 0 ? (it.flags & 0xffu) : ((it.flags >> 8) & 0xffu);
     np = k1_path_root<DB>(s, tr, qd, z, vflags, q, t, it.chain, out, np, n_u, pix);
+  }
+  return np;
+}
+
+// Path phase of queue item i.  The items of one candidate are contiguous in
+// the queue.  Roots equal within 1e-9 in v to a root of an earlier item of
+// the candidate, or to the item's other root, are skipped; so is a path
+// within 1e-9 in (u, v) of a path of an earlier item (two brackets around a
+// near-double root of r(v) whose Newton refinements meet), so that each
+// candidate reports a solution once, like the oracle's merge rule.
+template <int DB>
+SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue, int64_t i, int q, int t,
+                         spoly_path (&out)[6], unsigned& n_u, const PixelFilter& pix) {
+  const RootItem it = queue[i];
+  K1Sys<DB> s;
+  if (!k1_system<DB>(tr, qd, s)) return 0;
+  int64_t first = i;
+  while (first > 0 && queue[first - 1].chain == it.chain) --first;
+  int np = k1_item_paths<DB>(s, tr, qd, it, q, t, out, 0, n_u, pix, queue + first, i - first);
+  // paths of the earlier items, recomputed (rare: candidates with several brackets)
+  for (int64_t j = first; j < i && np > 0; ++j) {
+    spoly_path prev[6];
+    unsigned n_u_prev = 0;
+    const int npv = k1_item_paths<DB>(s, tr, qd, queue[j], q, t, prev, 0, n_u_prev, pix, queue + first, j - first);
+    int keep = 0;
+    for (int k = 0; k < np; ++k) {
+      bool dup = false;
+      for (int m = 0; m < npv; ++m)
+        if (fabs(prev[m].uv[0][0] - out[k].uv[0][0]) <= 1e-9 && fabs(prev[m].uv[0][1] - out[k].uv[0][1]) <= 1e-9)
+          dup = true;
+      if (!dup) out[keep++] = out[k];
+    }
+    np = keep;
   }
   return np;
 }

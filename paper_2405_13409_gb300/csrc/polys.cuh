@@ -374,11 +374,13 @@ SPOLY_D T horner_from(const T (&w)[DM + 1], int j, T x) {
 // belongs to the piece on its left.  At order 0, critical points c with
 // |p(c)| <= tang * rscale are reported as tangent roots.  Derivatives are
 // taken as p^(j) / j! (binomial weights), which has the same roots.
-// Returns the number of brackets written to (blo, bhi, bfl).
+// Returns the number of brackets written to (blo, bhi, bfl), or -3 when
+// dip > 0 and a critical point c has |p(c)| <= dip * rscale (the caller
+// treats the isolation as uncertified).
 
 template <typename T, int DM>
 SPOLY_D int isolate(const T (&p)[DM + 1], int deg, T lo, T hi, T tol, T tang, T rscale, T (&blo)[DM + 1],
-                    T (&bhi)[DM + 1], uint32_t (&bfl)[DM + 1]) {
+                    T (&bhi)[DM + 1], uint32_t (&bfl)[DM + 1], T dip = T(0)) {
   T crit[DM + 1];
   int nc = 0;
   int nout = 0;
@@ -441,6 +443,7 @@ SPOLY_D int isolate(const T (&p)[DM + 1], int deg, T lo, T hi, T tol, T tang, T 
         const T c = crit[k];
         if (!(c > lo && c < hi)) continue;
         const T f = horner_from<T, DM>(w, 0, c);
+        if (fabs(f) <= dip * rscale) return -3;
         if (fabs(f) <= tang * rscale) {
           bool dup = false;
           for (int m = 0; m < nsimple; ++m)

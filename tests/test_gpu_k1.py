@@ -161,13 +161,14 @@ def test_curved_planted_cases(ctx, type_, precision):
     ref, _ = _oracle(s, s.chains)
     assert ref.size > 1500
     # Strongly curved normals (about 15 degrees across a triangle) make many
-    # near-double roots: ill-conditioned (flagged) disagreements may reach
-    # 0.5% of candidates.  Plain FP64 keeps every unflagged path; mixed
-    # precision pushes FP32 isolation past its accuracy and must keep recall
-    # >= 99.8%.
-    recall = 1.0 if precision == binding.PLAIN_FP64 else 0.998
-    assert_parity(paths, ref, ch.shape[0], min_recall=recall, max_flagged_frac=5e-3)
+    # near-double roots.  Both precisions are held to the benchmark spec's bound:
+    # every unflagged path, and flagged disagreements on at most 1e-4 of the
+    # candidates.  In mixed precision the candidates whose FP32 isolation is
+    # not certified are re-isolated in FP64; the counter shows it happened.
+    assert_parity(paths, ref, ch.shape[0], min_recall=1.0, max_flagged_frac=1e-4)
     _check_invariants(paths)
+    if precision == binding.MIXED and type_ == 1:
+        assert stats["fallback"] > 0
 
 
 def test_host_and_device_inputs_agree(ctx):
