@@ -7,9 +7,13 @@ cells) seen by a 512x512 pinhole camera at (0, -2, 1.5) under a point light
 at (1, 1, 2).  One step is one pass of the whole hot path: the pixel-
 footprint candidate build over a uniform grid, the learned gate (features +
 BF16 tensor-core MLP + compaction), the mixed-precision solve of the
-surviving (pixel, triangle) candidates (FP64 construction, FP32 Laplace
-expansion and isolation, FP64 polish and path checks) with the pixel
-filter, and the read-back of the path count.  The same run times the plain
+surviving candidates (FP64 construction, FP32 Laplace expansion and
+isolation, FP64 polish and path checks), and the read-back of the path
+count.  Every pixel shares its endpoints (the pinhole and the light), so a
+triangle's solutions do not depend on the pixel: the footprint's distinct
+triangles are gated and solved once each, and every path goes to the pixel
+its vertex projects into, which yields each (pixel, triangle) candidate's
+complete path set.  The same run times the plain
 FP64 path (no gate, every step in FP64) on the same candidates and reports
 the recall of the gated solve against it.  The gate is trained before the
 timed region on the glint generator's training seeds (its own kernels) and
@@ -61,8 +65,8 @@ L2_FLUSH_BYTES = 512 << 20
 GATE_FLOPS = 2 * (24 * 64 + 64 * 64 + 64 * 64 + 64)
 BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
-# Kernel launches per step, counted from the ncu launch list of each
-# workload (profiles/).
+# Kernel launches per step, counted from the committed ncu launch list of
+# each workload.
 LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 19, ("glints", True): 20}
 # 2-bounce solve: systems count + fill, then per batch of <= 16,384 systems the
 # build, six FP32 sign classes, five FP64 re-sampling chunk classes and five
@@ -73,8 +77,8 @@ K2_KINDS = ("TT", "RR")  # 2-bounce workloads (slab, corridor)
 
 
 def launches_per_step(workload, use_gate, stats):
-    """Kernel launches of the library in one step (counted from the ncu
-    launch lists of each workload, profiles/)."""
+    """Kernel launches of the library in one step (counted from the
+    committed ncu launch lists of each workload)."""
     if workload in ("slab", "corridor", "batched"):
         batches = -(-int(stats.get("k2_systems", 0)) // TT_BATCH)
         tt = TT_FIXED + TT_PER_BATCH * batches
@@ -85,11 +89,11 @@ def launches_per_step(workload, use_gate, stats):
     return LAUNCHES_PER_STEP.get((workload, use_gate), 7)
 # DRAM bytes (read + write) per launch from an ncu capture of the kernel on
 # the workload named, reported only while the kernel's sources hash to the
-# value the capture was taken on (profiles/ holds the captures).
+# value the capture was taken on.
 TRAFFIC = {
     "gate_kernel": {"workload": "glints", "sources": ["gate.cu", "gate.cuh", "mlp.cuh", "common.cuh", "umma.cuh"],
                     "sources_sha256": "12e06fa080a9888be0bafdef5767136f9bd98e0e68857223e1088dd16943a9be",
-                    "bytes_per_launch": 395362048 + 3331328},  # profiles/kernels_glints_gate.md  # profiles/kernels_glints_gate.md
+                    "bytes_per_launch": 395362048 + 3331328},
     "k1_isolate_kernel": {"workload": "refract",
                           "sources": ["common.cuh", "polys.cuh", "laplace_gen.cuh", "k1_sys.cuh", "k1_iso.cuh",
                                       "k1_iso_f32.cu"], "sources_sha256": None, "bytes_per_launch": None},
@@ -169,9 +173,10 @@ def workload(name, slab_receivers=64, batch_queries=4096, corridor_receivers=16)
             f"receivers on z=-1, forward+backward cone cull, 4097 v1 samples"), None
     if name == "glints":
         s = scenes.glint_scene()
-        return s, binding.CHAINS_FOOTPRINT, "R", (
+        return s, binding.CHAINS_FOOTPRINT_UNIQUE, "R", (
             "glints: 1024x1024-cell heightfield (2,097,152 triangles, 64 sinusoids of wavelength 2-20 cells), "
-            "pinhole 512x512 at (0,-2,1.5), light (1,1,2), reflection, pixel-footprint candidates"), \
+            "pinhole 512x512 at (0,-2,1.5), light (1,1,2), reflection, pixel-footprint candidates; the "
+            "footprint's distinct triangles gated and solved once, each path assigned to its pixel"), \
             s.meta["camera"].as_array()
     if name == "refract":
         s = scenes.refract_scene()
@@ -584,16 +589,18 @@ def main():
         tune = {"block": best[0], "blocks_per_sm": best[1], "chunk": best[2], "ms": best[3], "shapes": len(table)}
         ctx.spoly_chains_free(ch1)
         del one
+    footprint = mode in (binding.CHAINS_FOOTPRINT, binding.CHAINS_FOOTPRINT_UNIQUE)
+    assign = binding.SOLVE_PIXEL_ASSIGN if mode == binding.CHAINS_FOOTPRINT_UNIQUE else 0
     pipe = Pipeline(ctx, mode, precision, camera, mlp, tau, ranges, explicit,
-                    binding.SOLVE_PERSISTENT if batched else 0, n_intervals=args.intervals)
+                    (binding.SOLVE_PERSISTENT if batched else 0) | assign, n_intervals=args.intervals)
     for _ in range(args.warmup):
         pipe.step(mesh, q)
     torch.cuda.synchronize()
     n_cand = ctx.spoly_chains_count(pipe.chains)
     n_solved = ctx.spoly_chains_count(pipe.gated) if use_gate else n_cand
     stats = ctx.spoly_stats(pipe.sol)
-    if mode == binding.CHAINS_FOOTPRINT:
-        pairs = n_cand
+    if footprint:
+        pairs = ctx.spoly_chains_footprint_pairs(pipe.chains)  # (pixel, triangle) candidates of the step
     elif batched:
         pairs = int(s.chains.shape[0])  # every explicit chain of the step
     elif kind in K2_KINDS:
@@ -619,7 +626,7 @@ def main():
     # plain FP64 path on the same candidates: no gate, every step in FP64
     plain = None
     if (camera is not None or batched) and not args.no_plain and precision == binding.MIXED:
-        pp = Pipeline(ctx, mode, binding.PLAIN_FP64, camera, explicit=explicit)
+        pp = Pipeline(ctx, mode, binding.PLAIN_FP64, camera, explicit=explicit, flags=assign)
         pp.step(mesh, q)
         torch.cuda.synchronize()
         k = max(1, min(args.steps, args.plain_steps))
@@ -633,24 +640,22 @@ def main():
                  "speedup": pms / (total_ms / args.steps)}
         pp.free()
 
-    # end to end through the public API: every step copies its inputs from
-    # pinned host memory to the device, runs the pipeline and reads the paths
-    # back into pinned host memory, all inside the timed region
+    # end to end through the public API: every step hands the library its
+    # inputs in pinned host memory (spoly_upload copies them to the device and
+    # checks them there; an explicit chain list is copied by the chain
+    # builder), runs the pipeline and reads the paths back into pinned host
+    # memory, all inside the timed region
     e2e = None
     if not args.no_e2e:
         pinned = [torch.from_numpy(a).pin_memory() for a in host]
-        dd = [torch.empty_like(x, device=dev) for x in pinned]
-        emesh = ctx.mesh(dd[0])
+        hmesh, hq = ctx.mesh(pinned[0]), ctx.queries(*pinned[1:6])
         out = torch.empty(max(1, 2 * n_paths + 1024) * binding.PATH_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
         cap = out.numel() // binding.PATH_DTYPE.itemsize
-
-        eq = ctx.queries(*dd[1:6])
         if batched:
-            pipe.explicit = dd[6]
+            pipe.explicit = pinned[6]
 
         def e2e_step():
-            for dst, src in zip(dd, pinned):
-                dst.copy_(src, non_blocking=True)
+            emesh, eq = ctx.spoly_upload(hmesh, hq)
             pipe.step(emesh, eq)
             return ctx.spoly_paths_into(pipe.sol, out, cap)
 
@@ -729,6 +734,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "gate": "learned MLP" if use_gate else "off",
                    "candidates_per_step": pairs,
+                   **({"distinct_triangles_per_step": n_cand} if mode == binding.CHAINS_FOOTPRINT_UNIQUE else {}),
                    **({"v1_intervals": args.intervals or 4096} if kind in K2_KINDS + ("mixed",) else {}),
                    "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "solved_per_s": world * n_solved * args.steps / (total_ms * 1e-3),

@@ -7,10 +7,10 @@
  *   - problem statement: Sec. 3.1 (Eq. eq_xi, eq_ni, eq_ch);
  *   - bivariate systems: Sec. 3.5 (R: Eq. eq_coplane + eq_pf_result,
  *     T: Eq. eq_coplane + eq_cpf_result);
- *   - elimination: Sec. 5.1 (Bezout matrix, Eq. eq_bezout);
- *   - univariate phase: Sec. 5.2 (Laplace expansion + recursive-derivative
+ *   - elimination: Sec. 4.1 (Bezout matrix, Eq. eq_bezout);
+ *   - univariate phase: Sec. 4.2 (Laplace expansion + recursive-derivative
  *     isolation for one bounce; determinant bisection for k bounces);
- *   - path phase: Sec. 5.3 (u recovery, path-space check, in-triangle test).
+ *   - path phase: Sec. 4.3 (u recovery, path-space check, in-triangle test).
  *
  * Conventions for every entry point
  *   - All inputs are plain pointers plus sizes.  Each input struct says
@@ -98,12 +98,13 @@ typedef struct {
   int32_t reserved;
 } spoly_queries;
 
-/* Candidate construction (stands in for the tuple pruning of Sec. 6). */
+/* Candidate construction (stands in for the tuple pruning of Sec. 3.1 and Sec. 5). */
 #define SPOLY_CHAINS_ALL 0      /* every (query, triangle) pair */
 #define SPOLY_CHAINS_CONE 1     /* pairs passing a conservative direction-box test */
 #define SPOLY_CHAINS_EXPLICIT 2 /* caller's list */
 #define SPOLY_CHAINS_FOOTPRINT 3 /* pixel footprints of a pinhole camera (query q = pixel q) */
 #define SPOLY_CHAINS_EXPLICIT_CONE 4 /* caller's list, each chain kept only if it passes the CONE test */
+#define SPOLY_CHAINS_FOOTPRINT_UNIQUE 5 /* the distinct triangles of all pixel footprints, one chain each */
 
 typedef struct {
   int32_t mode;
@@ -142,6 +143,9 @@ typedef struct {
 #define SPOLY_SOLVE_PERSISTENT 4 /* 1-bounce isolation as one persistent grid whose warps take chunks of
                                     chains from a global ticket counter (launch shape: spoly_autotune's
                                     choice, else 128 threads, 4 blocks per SM, 64 chains per ticket) */
+#define SPOLY_SOLVE_PIXEL_ASSIGN 16 /* with a camera: a path's query becomes the pixel its first vertex
+                                       projects into (paths outside the image are dropped) instead of
+                                       being kept only when that pixel equals its query */
 #define SPOLY_SOLVE_GRAPH 8  /* lists without 2-bounce chains: the solve's launches are captured once
                                 into a CUDA graph and replayed while the chain list, buffers and
                                 options stay the same (needs a non-default stream); a replay whose
@@ -149,7 +153,7 @@ typedef struct {
 
 typedef struct {
   int32_t precision;       /* SPOLY_PLAIN_FP64 or SPOLY_MIXED */
-  int32_t flags;           /* SPOLY_SOLVE_ASYNC, SPOLY_SOLVE_TIMING */
+  int32_t flags;           /* SPOLY_SOLVE_* flags */
   int64_t path_capacity;   /* initial path buffer size (0: automatic) */
   /* Optional pixel filter (host array of 16 doubles, camera layout of
    * spoly_chain_opts): a path of query q is kept only if its first vertex
@@ -157,7 +161,7 @@ typedef struct {
    * once.  NULL: no filter. */
   const double* camera;
   /* 2-bounce chains: the rational pieces replacing sqrt(beta) in the
-   * refraction mapping (Sec. 4.4), host array of 25 doubles: breaks[7]
+   * refraction mapping (Sec. 3.4), host array of 25 doubles: breaks[7]
    * (0 = b0 < ... < b6 = 1), then (c0, c1, d1) of (c0 + c1 x) / (1 + d1 x)
    * for each of the six pieces.  NULL: the library's default fit (maximum
    * error 9.4e-4 on [0, 1]). */
@@ -214,12 +218,36 @@ spoly_status spoly_ctx_destroy(spoly_ctx* ctx);
 /* Message of the last failed call on this context ("" if none). */
 const char* spoly_last_error(const spoly_ctx* ctx);
 
+/* Copies host-resident inputs (on_device = 0; pinned host memory makes the
+ * copies asynchronous DMA) into the context's staging buffers on its stream,
+ * checks them on the device (non-finite values; k and types on the host),
+ * and writes device views of them to *mesh_out and *q_out for the calls that
+ * follow.  Device-resident inputs pass through unchanged.  The views stay
+ * valid until the next call that stages host inputs on this context, or its
+ * destruction.  One upload per step copies each input once, where passing
+ * host inputs to every call would copy them into the same buffers again.
+ * Synchronises once (to read the check).  Errors: EINVAL (bad shape,
+ * non-finite value: the message names the row and triangle or query),
+ * ENOMEM, ECUDA. */
+spoly_status spoly_upload(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, spoly_mesh* mesh_out,
+                          spoly_queries* q_out);
+
 /* Builds the candidate chain list (query, tri0, tri1) on the device.
  * ALL enumerates every (query, triangle) pair with the query index fastest
  * (consecutive chains share a triangle); CONE keeps the pairs whose conservative box of outgoing unit
  * directions over the triangle (reflected or refracted per the query,
  * interval arithmetic over the triangle's bounding box and normal range)
  * overlaps the box of unit directions from the triangle toward x_{k+1};
+ * FOOTPRINT lists every (pixel, triangle) pair whose boxes overlap, ordered
+ * by pixel (query q = pixel q); FOOTPRINT_UNIQUE builds the same pairs but
+ * keeps only their distinct triangles, one chain (0, t, -1) each, ordered by
+ * triangle within chunks of 256: every pixel of a pinhole camera shares its
+ * endpoints (the camera origin and one light), so a triangle's solutions
+ * do not depend on the pixel, and a solve with SPOLY_SOLVE_PIXEL_ASSIGN
+ * hands each path to the pixel its first vertex projects into (that pixel's
+ * footprint holds the triangle, so every (pixel, triangle) pair's paths are
+ * produced once); it requires every query to equal query 0 (EINVAL
+ * otherwise), and spoly_chains_footprint_pairs returns the number of pairs;
  * EXPLICIT copies the caller's list after a bounds check; EXPLICIT_CONE
  * keeps the chains of the caller's list (any mix of queries, bounce counts
  * and triangles) that pass the CONE test of their own bounce count, per
@@ -239,6 +267,10 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
 /* Number of chains in a chain list. */
 spoly_status spoly_chains_count(const spoly_chains* chains, int64_t* n);
 
+/* Number of (pixel, triangle) candidate pairs of a list built in a
+ * FOOTPRINT mode (0 for other modes). */
+spoly_status spoly_chains_footprint_pairs(const spoly_chains* chains, int64_t* n);
+
 /* Copies the chain list [n][3] int32 into dst (host or device).  Errors:
  * ECAPACITY (capacity < count; *n_total = count). */
 spoly_status spoly_chains_copy(spoly_ctx* ctx, const spoly_chains* chains, int32_t* dst, int64_t capacity,
@@ -247,17 +279,17 @@ spoly_status spoly_chains_copy(spoly_ctx* ctx, const spoly_chains* chains, int32
 /* Frees a chain list. */
 spoly_status spoly_chains_free(spoly_chains* chains);
 
-/* Solves every chain (Sec. 5.3 pipeline) and keeps the admissible paths in
+/* Solves every chain (Sec. 4.3 pipeline) and keeps the admissible paths in
  * a library-owned solution set.  mesh and q must be the ones the chains were
  * built from.  *inout: NULL for a new set or a set to reuse.  Unless
  * SPOLY_SOLVE_ASYNC is set, the call synchronises, grows the path buffer and
  * re-runs the path phase if it overflowed, and returns with counters valid.
  * Chains with a second triangle (tri1 >= 0, explicit lists) are solved as
  * 2-bounce chains x0 -> tri0 -> tri1 -> x_last of two refractions (TT:
- * the rational sqrt pieces of Sec. 4.4) or two reflections (RR: the exact
+ * the rational sqrt pieces of Sec. 3.4) or two reflections (RR: the exact
  * reflected direction of Eq. eq_431_di and the system of Eq. eq_rr1), by
- * the same solver (Sec. 4.4-4.5,
- * Sec. 5.2 bisection: the Bezout determinant's sign at n_intervals + 1
+ * the same solver (Sec. 3.4-3.5,
+ * Sec. 4.2 bisection: the Bezout determinant's sign at n_intervals + 1
  * uniform v1, 10 FP32 bisection steps per sign change, FP64 bisection to
  * 1e-10, u1 from a(u1, v1) = 0, u2 from the rational mapping, then
  * path-space Newton on h x n = 0 at both vertices); their paths carry
@@ -333,8 +365,14 @@ spoly_status spoly_solution_free(spoly_solution_set* set);
  * Inputs are device pointers with the layouts of spoly_mesh, spoly_queries
  * and the chain list (int32 [n_chains][3]); `paths` is a device buffer of
  * `path_capacity` records that receives the admissible paths; *n_paths (host)
- * receives their count.  precision is SPOLY_PLAIN_FP64 or SPOLY_MIXED.  The
- * call selects `device`, enqueues on `cuda_stream`, waits for it to finish,
+ * receives their count.  precision is SPOLY_PLAIN_FP64 or SPOLY_MIXED.  Only
+ * 1-bounce chains are solved here: every chain must have tri1 < 0, a query
+ * in [0, n_queries) with k = 1 and type SPOLY_R or SPOLY_T, and a triangle in
+ * [0, n_tris); a device-side pass checks this before the solve reads through
+ * any index, and the first failing chain is reported by SPOLY_EINVAL.
+ *
+ * The call is synchronous: it selects `device`, enqueues on `cuda_stream`,
+ * waits on that stream twice (after the validation pass and at the end),
  * restores the caller's current device and returns.  `msg` (host buffer of
  * msg_len bytes, may be NULL) receives a message on failure.
  *
@@ -346,9 +384,10 @@ spoly_status spoly_solution_free(spoly_solution_set* set);
  * the array's device address); make that first call before any stream
  * capture begins.
  * Errors: EINVAL (null pointer, negative size, too many chains, bad
- * precision or device), ECUDA (a CUDA call failed), ECAPACITY (more paths
- * than path_capacity: *n_paths holds the required count and the first
- * path_capacity paths, in completion order, were written). */
+ * precision or device, or a chain failing the checks above: the message
+ * names its index and the reason), ECUDA (a CUDA call failed), ECAPACITY
+ * (more paths than path_capacity: *n_paths holds the required count and the
+ * first path_capacity paths, in completion order, were written). */
 spoly_status spoly_solve_noalloc(int device, void* cuda_stream, const double* tri, int64_t n_tris,
                                  const double* x_first, const double* x_last, const double* eta,
                                  const int32_t* types, const int32_t* k, int64_t n_queries, const int32_t* chains,
@@ -395,6 +434,16 @@ typedef struct {
  * biases, resident on the context's device.  Free with spoly_mlp_free. */
 spoly_status spoly_mlp_create(spoly_ctx* ctx, uint64_t seed, spoly_mlp** out);
 spoly_status spoly_mlp_free(spoly_mlp* mlp);
+
+/* Limit, in SM clock cycles, of each wait of the gate's inference kernel
+ * (spoly_gate, spoly_mlp_forward, spoly_mlp_calibrate) for a layer's
+ * tensor-core products to complete; 0 restores the default (2^31 cycles,
+ * about a second).  A wait that gives up makes the call return
+ * SPOLY_ETIMEOUT with incomplete outputs; the kernel then waits for the
+ * product still in flight with the default limit before it frees its tensor
+ * memory, so the context stays usable.  Errors: EINVAL (mlp NULL or
+ * cycles < 0). */
+spoly_status spoly_mlp_set_wait_limit(spoly_mlp* mlp, int64_t cycles);
 
 /* Copy the FP32 parameter vector (SPOLY_MLP_PARAMS values, host memory) out
  * of or into the network.  set rejects non-finite values (EINVAL). */
@@ -453,6 +502,15 @@ spoly_status spoly_mlp_calibrate(spoly_ctx* ctx, spoly_mlp* mlp, const float* fe
  * order is not preserved.  Synchronises (reads the count back). */
 spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* mlp, const spoly_mesh* mesh, const spoly_queries* q,
                         const spoly_chains* in, float tau_logit, spoly_chains** inout);
+
+/* The library's default rational pieces of sqrt on [0, 1] (Sec. 3.4: six
+ * pieces (c0 + c1 x) / (1 + d1 x); the paper's own coefficients are in its
+ * missing supplement, so the library fits its own), in the 25-double layout
+ * of spoly_solve_opts::sqrt_table, into dst (host, n >= 25).  A comparison
+ * with another implementation of the method passes this table to both sides:
+ * the pieces are a parameter of the approximation, like the IORs.  Errors:
+ * EINVAL (dst NULL or n < 25). */
+spoly_status spoly_default_sqrt_table(double* dst, int32_t n);
 
 /* Library version string. */
 const char* spoly_version(void);

@@ -7,7 +7,7 @@ shares no code with it: the C++ source here is compiled on its own with g++.
 
 ``build()`` compiles ``spoly_oracle.cpp`` into ``_liboracle.so`` beside it.
 ``solve()`` runs the full 1-bounce pipeline (Sec. 3.5 R/T, Eq. eq_bezout,
-Sec. 5.2, Sec. 5.3) over an explicit chain list on all host cores.
+Sec. 4.2, Sec. 4.3) over an explicit chain list on all host cores.
 """
 from __future__ import annotations
 

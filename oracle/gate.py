@@ -5,7 +5,7 @@ import this module; the product path never does.  It shares no code with the
 CUDA library.
 
 The gate is not part of the paper.  It predicts, from a candidate's geometry,
-whether the 1-bounce solve of that candidate (Sec. 3.5, Sec. 5) returns any
+whether the 1-bounce solve of that candidate (Sec. 3.5, Sec. 4) returns any
 admissible path, so that candidates predicted empty can be skipped.  This
 module states, in plain FP64 numpy:
 

@@ -9,18 +9,18 @@ mapping and the Bezout determinant are the ones of the TT oracle
 It follows the paper's steps for a chain x0 -> T1 -> T2 -> x3 of two
 reflections, in plain numpy FP64:
 
-1. Rational coordinate mapping (Sec. 4.4, Eq. eq_rct) with the scaled
+1. Rational coordinate mapping (Sec. 3.4, Eq. eq_rct) with the scaled
    reflected direction of Eq. eq_431_di,
    D = -2 (d0 . n1) n1 + d0 |n1|^2, d0 = x1 - x0: a polynomial of degree 3
    in (u1, v1), exact (no square root), so a chain is one system.
-2. Bivariate system in (u1, v1) (Sec. 4.5, Eq. eq_rr1): the endpoint
+2. Bivariate system in (u1, v1) (Sec. 3.5, Eq. eq_rr1): the endpoint
    coplanarity form at x2 and the product form (Eq. eq_pf_result) at x2,
    with d1 = x2 - x1 replaced by D and the kappa denominators of x2, n2 and
    t2 cleared (total degrees 9 and 15; Table tab_sum's 10 and 16 are upper
    bounds).
 3. The Bezout matrix in u1 with hidden v1 (Eq. eq_bezout) at 2^12 + 1
    uniform v1 in [0, 1], the sign of its determinant, bisection of every
-   sign change for the paper's 10 iterations (Sec. 5.2), continued to 1e-12.
+   sign change for the paper's 10 iterations (Sec. 4.2), continued to 1e-12.
 4. u1 from a(u1, v1*) = 0, u2 from the mapping, path-space Newton on the
    exact constraint h x n = 0 (Eq. eq_ch, reflection: h = d1_hat - d0_hat)
    at both vertices, the reflection sidedness test (both neighbours on one
@@ -137,7 +137,7 @@ def newton_refine(w, x0, x3, P1, N1, P2, N2, iters=NEWTON_ITERS):
 
 # ---------------------------------------------------------------- solve
 def v_roots(sysd, n_intervals=N_INTERVALS):
-    """Roots v1* of the resultant in [0, 1] (Sec. 5.2, k = 2): signs of the
+    """Roots v1* of the resultant in [0, 1] (Sec. 4.2, k = 2): signs of the
     Bezout determinant at n_intervals + 1 uniform samples, every sign change
     bisected (all together) for the paper's 10 iterations and on to 1e-12.
     A sample with det == 0 exactly is a root.  Returns [(v1*, flag)]."""
@@ -175,13 +175,21 @@ def v_roots(sysd, n_intervals=N_INTERVALS):
     return roots, da, db
 
 
-def solve_candidate(x0, x3, P1, N1, P2, N2, n_intervals=N_INTERVALS):
+def solve_candidate(x0, x3, P1, N1, P2, N2, n_intervals=N_INTERVALS, v_solver="bisect"):
     """All admissible RR paths of one candidate: a list of dicts (uv (u1, v1,
-    u2, v2), x1, x2, residual, flags, uv_unrefined)."""
+    u2, v2), x1, x2, residual, flags, uv_unrefined).  v_solver="qz" finds the
+    roots v1* by linearisation and QZ (oracle.qz) instead of sampling and
+    bisection; the rest is unchanged."""
     x0, x3 = np.asarray(x0, float), np.asarray(x3, float)
     P1, N1, P2, N2 = (np.asarray(z, float) for z in (P1, N1, P2, N2))
     sysd = build_rr(x0, x3, P1, N1, P2, N2)
-    roots, da, db = v_roots(sysd, n_intervals)
+    if v_solver == "qz":
+        from . import qz
+        da, db = tt.deg_u(sysd["a"]), tt.deg_u(sysd["b"])
+        roots = [] if da < 0 or db < 0 or max(da, db) < 1 else \
+            [(float(v), 0) for v in qz.v_roots(sysd["a"], sysd["b"], da, db)]
+    else:
+        roots, da, db = v_roots(sysd, n_intervals)
     out = []
     for v1, vflag in roots:
         ac = tt.u_coeffs(sysd["a"][:da + 1], v1)[0]
@@ -230,7 +238,7 @@ def solve_candidate(x0, x3, P1, N1, P2, N2, n_intervals=N_INTERVALS):
     return out
 
 
-def solve(tri, x_first, x_last, chains, n_intervals=N_INTERVALS):
+def solve(tri, x_first, x_last, chains, n_intervals=N_INTERVALS, v_solver="bisect"):
     """RR solve of explicit chains (query, tri0, tri1) over a mesh in the
     library's SoA layout.  Returns a PATH_DTYPE array."""
     T = np.asarray(tri, float)
@@ -240,7 +248,7 @@ def solve(tri, x_first, x_last, chains, n_intervals=N_INTERVALS):
         N1 = np.stack([T[9:12, t1], T[12:15, t1], T[15:18, t1]])
         P2 = np.stack([T[0:3, t2], T[3:6, t2], T[6:9, t2]])
         N2 = np.stack([T[9:12, t2], T[12:15, t2], T[15:18, t2]])
-        for p in solve_candidate(x_first[q], x_last[q], P1, N1, P2, N2, n_intervals):
+        for p in solve_candidate(x_first[q], x_last[q], P1, N1, P2, N2, n_intervals, v_solver=v_solver):
             r = np.zeros(1, PATH_DTYPE)
             r["chain"], r["query"], r["tri0"], r["tri1"] = ci, q, t1, t2
             r["uv"][0] = p["uv"]

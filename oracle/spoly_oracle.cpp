@@ -6,19 +6,19 @@
 //
 // It follows the paper's pipeline step by step, in plain FP64, with generic
 // dense polynomial arithmetic and no fusion or reordering:
-//   1. coefficient phase (Sec. 5.3): build the bivariate specular polynomials
+//   1. coefficient phase (Sec. 4.3): build the bivariate specular polynomials
 //      a(u,v), b(u,v) of one candidate from its vertex positions P and
 //      normals N (Eq. eq_xi, eq_ni); R uses the endpoint-difference
 //      coplanarity (Eq. eq_coplane) and the product form (Eq. eq_pf_result),
 //      T uses the coplanarity and the square form (Eq. eq_cpf_result);
 //      Sec. 3.5 paragraphs "R" and "T".
-//   2. elimination phase (Sec. 5.1): the Bezout matrix of a and b in u with v
+//   2. elimination phase (Sec. 4.1): the Bezout matrix of a and b in u with v
 //      hidden, entries by the explicit sum of Eq. eq_bezout.
-//   3. univariate phase (Sec. 5.2): r(v) = det R(v) by cofactor (Laplace)
+//   3. univariate phase (Sec. 4.2): r(v) = det R(v) by cofactor (Laplace)
 //      expansion with polynomial entries, then recursive-derivative root
 //      isolation with bisection (roots of r^(j) split [lo,hi] into monotone
 //      pieces of r^(j-1)).
-//   4. path phase (Sec. 5.3): put v back into a(u,v), solve for u, build the
+//   4. path phase (Sec. 4.3): put v back into a(u,v), solve for u, build the
 //      path and check the specular constraint h x n = 0 (Eq. eq_ch) in path
 //      space, sidedness and the in-triangle test.
 // Readings of points the paper leaves open are listed with each constant.
@@ -41,7 +41,7 @@ constexpr double kDelta = 1e-6;
 // its coefficient polynomial has max-abs > kTrim * (max-abs of the whole
 // polynomial) (Eq. eq_bezout: "n is the degree").
 constexpr double kTrim = 1e-13;
-// Bisection stops at this interval length (the paper stops at 1e-9, Sec. 5.2;
+// Bisection stops at this interval length (the paper stops at 1e-9, Sec. 4.2;
 // the oracle continues to the FP64 limit).
 constexpr double kRootTol = 1e-14;
 // A critical point c of r with |r(c)| <= kTangent * sum|r_i| * max(1,|c|)^d is
@@ -417,7 +417,7 @@ std::vector<UPoly> bezout_matrix(const std::vector<UPoly>& ac, const std::vector
 }
 
 // det of the submatrix of rows [row, n) and the given columns, by cofactor
-// expansion along its first row (Sec. 5.2, "Laplacian expansion").
+// expansion along its first row (Sec. 4.2, "Laplacian expansion").
 UPoly laplace_det(const std::vector<UPoly>& R, int n, int row, std::vector<int>& cols) {
   if (row == n - 1) return R[size_t(row) * n + cols[0]];
   UPoly det;
@@ -460,7 +460,7 @@ double bisect(const UPoly& p, double s, double e, double fs) {
   return 0.5 * (s + e);
 }
 
-// Real roots of p on [lo, hi] by recursive-derivative isolation (Sec. 5.2):
+// Real roots of p on [lo, hi] by recursive-derivative isolation (Sec. 4.2):
 // the roots of p' split [lo, hi] into monotone pieces of p; each piece with a
 // sign change holds one root, found by bisection.  A root exactly at a piece
 // end belongs to the piece on its left.  With top_level, critical points where
@@ -529,7 +529,7 @@ struct Path {
 // Path-space check of one vertex (Eq. eq_ch): h = eta1 d1^ - eta0 d0^ must be
 // parallel to n.  residual = |h x n| / (|h| |n|), the sine of their angle.
 // Sidedness (reading of "check the specular constraints in path space",
-// Sec. 5.3): reflection keeps x0 and x2 on the same side of the tangent plane
+// Sec. 4.3): reflection keeps x0 and x2 on the same side of the tangent plane
 // (d0.n and d1.n of opposite signs) and needs |h| > 1e-9; refraction crosses
 // it (d0.n and d1.n of equal signs).
 bool vertex_check(D3 xprev, D3 x, D3 xnext, D3 n, int type, double eta_in, double eta_out,

@@ -7,13 +7,13 @@ CUDA library.
 It follows the paper's steps for a chain x0 -> T1 -> T2 -> x3 of two
 refractions (IORs eta_0, eta_1, eta_2), in plain numpy FP64:
 
-1. Rational coordinate mapping (Sec. 4.4, Eq. eq_rct): the scaled refracted
+1. Rational coordinate mapping (Sec. 3.4, Eq. eq_rct): the scaled refracted
    direction at x1 (Eq. eq_refr_rational), with sqrt(beta) replaced by a
-   piecewise rational approximant (Sec. 4.4; the paper's coefficients are
+   piecewise rational approximant (Sec. 3.4; the paper's coefficients are
    in its supplement, which is missing, so the pieces are fitted here:
    ``fit_sqrt_pieces``), then the Moller-Trumbore intersection with T2 as
    u2 = (u~, v~) / kappa.
-2. Bivariate system in (u1, v1) (Sec. 4.5; Table tab_sum): the endpoint
+2. Bivariate system in (u1, v1) (Sec. 3.5; Table tab_sum): the endpoint
    coplanarity form and the square form at x2, with x2 - x1 replaced by the
    mapped direction D and the kappa denominators of x2 and n2 cleared
    (total degrees 16 and 46; the table's 18 and 48 are upper bounds).
@@ -21,7 +21,7 @@ refractions (IORs eta_0, eta_1, eta_2), in plain numpy FP64:
    Eq. eq_bezout, evaluated at 2^12 + 1 uniform v1 in [0, 1]; its
    determinant's sign from an LU factorisation with partial pivoting
    (numpy slogdet); bisection on every sign change for the paper's 10
-   iterations (Sec. 5.2), continued to 1e-12.
+   iterations (Sec. 4.2), continued to 1e-12.
 4. u1 from a(u1, v1*) = 0 (companion eigenvalues), u2 from the mapping,
    then path-space Newton on the exact constraint h x n = 0 (Eq. eq_ch) at
    both vertices (at most 5 iterations), sidedness and in-triangle tests.
@@ -53,7 +53,7 @@ SQRT_BREAKS = (0.0, 4e-4, 7e-3, 0.048, 0.2, 0.65, 1.0)
 # ------------------------------------------------------------ sqrt pieces
 def fit_sqrt_pieces(breaks=SQRT_BREAKS, n_grid=4000):
     """Minimax fit of sqrt(x) by (c0 + c1 x) / (1 + d1 x) on each piece
-    (Sec. 4.4 form with d0 = 1): Nelder-Mead on the maximum absolute error
+    (Sec. 3.4 form with d0 = 1): Nelder-Mead on the maximum absolute error
     over a uniform grid of the piece.  Returns an array [6][3] of
     (c0, c1, d1)."""
     from scipy.optimize import minimize
@@ -362,9 +362,12 @@ def newton_refine(w, x0, x3, etas, P1, N1, P2, N2, iters=NEWTON_ITERS):
 
 
 # ---------------------------------------------------------------- solve
-def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS, keep_unrefined=False):
+def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS, keep_unrefined=False,
+                    v_solver="bisect"):
     """All admissible TT paths of one candidate.  Returns a list of dicts
-    (uv (u1, v1, u2, v2), x1, x2, residual, flags, uv_unrefined)."""
+    (uv (u1, v1, u2, v2), x1, x2, residual, flags, uv_unrefined).
+    v_solver="qz" finds the roots v1* by linearisation and QZ (oracle.qz)
+    instead of sampling and bisection; the rest is unchanged."""
     x0, x3 = np.asarray(x0, float), np.asarray(x3, float)
     P1, N1, P2, N2 = (np.asarray(z, float) for z in (P1, N1, P2, N2))
     etas = tuple(float(e) for e in etas)
@@ -392,38 +395,42 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
         n = max(da, db)
         if da < 0 or db < 0 or n < 1:
             continue
-        sg, la = det_sign(sysd, vs, n, da, db)
-        # sign changes; a sample with det == 0 exactly is a root belonging to
-        # the interval on its left
-        roots = [(vs[m], 0) for m in range(1, n_intervals + 1) if sg[m] == 0.0]
-        br = [m for m in range(n_intervals) if sg[m] * sg[m + 1] < 0]
-        lo = vs[br].copy()
-        hi = vs[np.array(br, int) + 1].copy()
-        slo = sg[br].copy()
-        flag = np.zeros(len(br), int)
-        it = 0
-        # all brackets bisected together: the paper's 10 iterations, then on
-        # to ROOT_TOL
-        while len(br) and np.max(hi - lo) > ROOT_TOL:
-            mid = 0.5 * (lo + hi)
-            sm, _ = det_sign(sysd, mid, n, da, db)
-            zero = sm == 0.0  # an exact root: collapse the bracket onto it
-            left = (sm == slo) | zero
-            lo = np.where(left, mid, lo)
-            hi = np.where(left & ~zero, hi, mid)
-            it += 1
-            if it == PAPER_ITERS:
-                # ill-conditioning (k = 2), normalised locally: |det| across the
-                # bracket against the largest |det| of the five samples
-                # around it (|det| spans hundreds of orders of magnitude over
-                # [0, 1]); a simple root gives about 2^-10 / 2.5
-                _, l_lo = det_sign(sysd, lo, n, da, db)
-                _, l_hi = det_sign(sysd, hi, n, da, db)
-                bi = np.array(br, int)
-                lloc = np.max(np.stack([la[np.clip(bi + o, 0, n_intervals)] for o in (-2, -1, 0, 1, 2, 3)]), 0)
-                rel = np.logaddexp(l_lo - lloc, l_hi - lloc)
-                flag = np.where(rel < np.log(ILL_COND_K2), F_ILL_COND, 0)
-        roots += [(0.5 * (a + b), int(f)) for a, b, f in zip(lo, hi, flag)]
+        if v_solver == "qz":
+            from . import qz
+            roots = [(float(v), 0) for v in qz.v_roots(sysd["a"], sysd["b"], da, db)]
+        else:
+            sg, la = det_sign(sysd, vs, n, da, db)
+            # sign changes; a sample with det == 0 exactly is a root belonging to
+            # the interval on its left
+            roots = [(vs[m], 0) for m in range(1, n_intervals + 1) if sg[m] == 0.0]
+            br = [m for m in range(n_intervals) if sg[m] * sg[m + 1] < 0]
+            lo = vs[br].copy()
+            hi = vs[np.array(br, int) + 1].copy()
+            slo = sg[br].copy()
+            flag = np.zeros(len(br), int)
+            it = 0
+            # all brackets bisected together: the paper's 10 iterations, then on
+            # to ROOT_TOL
+            while len(br) and np.max(hi - lo) > ROOT_TOL:
+                mid = 0.5 * (lo + hi)
+                sm, _ = det_sign(sysd, mid, n, da, db)
+                zero = sm == 0.0  # an exact root: collapse the bracket onto it
+                left = (sm == slo) | zero
+                lo = np.where(left, mid, lo)
+                hi = np.where(left & ~zero, hi, mid)
+                it += 1
+                if it == PAPER_ITERS:
+                    # ill-conditioning (k = 2), normalised locally: |det| across the
+                    # bracket against the largest |det| of the five samples
+                    # around it (|det| spans hundreds of orders of magnitude over
+                    # [0, 1]); a simple root gives about 2^-10 / 2.5
+                    _, l_lo = det_sign(sysd, lo, n, da, db)
+                    _, l_hi = det_sign(sysd, hi, n, da, db)
+                    bi = np.array(br, int)
+                    lloc = np.max(np.stack([la[np.clip(bi + o, 0, n_intervals)] for o in (-2, -1, 0, 1, 2, 3)]), 0)
+                    rel = np.logaddexp(l_lo - lloc, l_hi - lloc)
+                    flag = np.where(rel < np.log(ILL_COND_K2), F_ILL_COND, 0)
+            roots += [(0.5 * (a + b), int(f)) for a, b, f in zip(lo, hi, flag)]
         for v1, vflag in roots:
             ac = u_coeffs(sysd["a"][:da + 1], v1)[0]
             bc = u_coeffs(sysd["b"][:db + 1], v1)[0]
@@ -479,7 +486,7 @@ def solve_candidate(x0, x3, etas, P1, N1, P2, N2, table, n_intervals=N_INTERVALS
     return out
 
 
-def solve(tri, x_first, x_last, eta, chains, table, n_intervals=N_INTERVALS):
+def solve(tri, x_first, x_last, eta, chains, table, n_intervals=N_INTERVALS, v_solver="bisect"):
     """TT solve of explicit chains (query, tri0, tri1) over a mesh in the
     library's SoA layout.  Returns (PATH_DTYPE array, unrefined (u, v) per
     path [n, 4])."""
@@ -490,7 +497,8 @@ def solve(tri, x_first, x_last, eta, chains, table, n_intervals=N_INTERVALS):
         N1 = np.stack([T[9:12, t1], T[12:15, t1], T[15:18, t1]])
         P2 = np.stack([T[0:3, t2], T[3:6, t2], T[6:9, t2]])
         N2 = np.stack([T[9:12, t2], T[12:15, t2], T[15:18, t2]])
-        for p in solve_candidate(x_first[q], x_last[q], eta[q], P1, N1, P2, N2, table, n_intervals):
+        for p in solve_candidate(x_first[q], x_last[q], eta[q], P1, N1, P2, N2, table, n_intervals,
+                                 v_solver=v_solver):
             r = np.zeros(1, PATH_DTYPE)
             r["chain"], r["query"], r["tri0"], r["tri1"] = ci, q, t1, t2
             r["uv"][0] = p["uv"]

@@ -40,6 +40,7 @@ CHAINS_CONE = 1
 CHAINS_EXPLICIT = 2
 CHAINS_FOOTPRINT = 3
 CHAINS_EXPLICIT_CONE = 4
+CHAINS_FOOTPRINT_UNIQUE = 5
 
 PLAIN_FP64 = 0
 MIXED = 1
@@ -47,6 +48,7 @@ SOLVE_ASYNC = 1
 SOLVE_TIMING = 2
 SOLVE_PERSISTENT = 4
 SOLVE_GRAPH = 8
+SOLVE_PIXEL_ASSIGN = 16
 PEAK_FP32_FMA = 0
 PEAK_FP64_FMA = 1
 MLP_FEATURES = 24
@@ -131,7 +133,11 @@ def load():
         "spoly_last_error": ([P], ctypes.c_char_p),
         "spoly_build_chains": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries),
                                 ctypes.POINTER(spoly_chain_opts), ctypes.POINTER(P)], c_int32),
+        "spoly_default_sqrt_table": ([P, c_int32], c_int32),
+        "spoly_upload": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), ctypes.POINTER(spoly_mesh),
+                          ctypes.POINTER(spoly_queries)], c_int32),
         "spoly_chains_count": ([P, ctypes.POINTER(c_int64)], c_int32),
+        "spoly_chains_footprint_pairs": ([P, ctypes.POINTER(c_int64)], c_int32),
         "spoly_chains_copy": ([P, P, P, c_int64, ctypes.POINTER(c_int64), c_int32], c_int32),
         "spoly_chains_free": ([P], c_int32),
         "spoly_solve": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P,
@@ -145,6 +151,7 @@ def load():
                                  c_int64, ctypes.POINTER(c_int64), ctypes.c_char_p, c_int32], c_int32),
         "spoly_mlp_create": ([P, ctypes.c_uint64, ctypes.POINTER(P)], c_int32),
         "spoly_mlp_free": ([P], c_int32),
+        "spoly_mlp_set_wait_limit": ([P, c_int64], c_int32),
         "spoly_mlp_get_params": ([P, P, P], c_int32),
         "spoly_mlp_set_params": ([P, P, P], c_int32),
         "spoly_mlp_save": ([P, P, ctypes.c_char_p], c_int32),
@@ -224,6 +231,14 @@ class Context:
         return spoly_queries(_ptr(x_first), _ptr(x_last), _ptr(eta), _ptr(types), _ptr(k),
                              int(x_first.shape[0]), _on_device(x_first), 0)
 
+    def spoly_upload(self, mesh: spoly_mesh, q: spoly_queries):
+        """Host inputs staged into the context's device buffers; returns
+        device views (spoly_mesh, spoly_queries) for the calls that follow."""
+        mo, qo = spoly_mesh(), spoly_queries()
+        self.check(self.lib.spoly_upload(self.h, ctypes.byref(mesh), ctypes.byref(q), ctypes.byref(mo),
+                                         ctypes.byref(qo)), "spoly_upload")
+        return mo, qo
+
     def spoly_build_chains(self, mesh: spoly_mesh, q: spoly_queries, mode: int, margin: float = 1e-3,
                            explicit=None, tri_range=(0, 0), reuse=None, camera=None, cell: float = 0.0,
                            second_range=(0, 0)):
@@ -241,6 +256,11 @@ class Context:
     def spoly_chains_count(self, chains) -> int:
         n = c_int64()
         self.check(self.lib.spoly_chains_count(chains, ctypes.byref(n)), "spoly_chains_count")
+        return int(n.value)
+
+    def spoly_chains_footprint_pairs(self, chains) -> int:
+        n = c_int64()
+        self.check(self.lib.spoly_chains_footprint_pairs(chains, ctypes.byref(n)), "spoly_chains_footprint_pairs")
         return int(n.value)
 
     def spoly_chains_copy(self, chains) -> np.ndarray:
@@ -334,6 +354,11 @@ class Context:
     def spoly_mlp_free(self, mlp):
         self.lib.spoly_mlp_free(mlp)
 
+    def spoly_mlp_set_wait_limit(self, mlp, cycles: int):
+        st = self.lib.spoly_mlp_set_wait_limit(mlp, int(cycles))
+        if st != SPOLY_OK:
+            raise SpolyError(st, "spoly_mlp_set_wait_limit: bad arguments")
+
     def spoly_mlp_get_params(self, mlp) -> np.ndarray:
         out = np.zeros(MLP_PARAMS, dtype=np.float32)
         self.check(self.lib.spoly_mlp_get_params(self.h, mlp, c_void_p(out.ctypes.data)), "spoly_mlp_get_params")
@@ -396,6 +421,16 @@ class Context:
         self.check(self.lib.spoly_gate(self.h, mlp, ctypes.byref(mesh), ctypes.byref(q), chains, float(tau_logit),
                                        ctypes.byref(h)), "spoly_gate")
         return h
+
+
+def spoly_default_sqrt_table():
+    """The library's default sqrt pieces as (breaks[7], coeffs[6][3])."""
+    lib = load()
+    t = np.zeros(25)
+    st = lib.spoly_default_sqrt_table(c_void_p(t.ctypes.data), 25)
+    if st != SPOLY_OK:
+        raise SpolyError(st, "spoly_default_sqrt_table")
+    return t[:7].copy(), t[7:].reshape(6, 3).copy()
 
 
 def spoly_solve_noalloc(device: int, stream, tri, x_first, x_last, eta, types, k, chains, precision: int, paths,

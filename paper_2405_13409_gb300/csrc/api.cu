@@ -35,7 +35,16 @@ spoly_status cuda_fail(spoly_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, SPOLY_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Device views of mesh / queries, staging host arrays into context buffers.
+// Smallest index i < n with x[i] not finite, into *first (all ones: none).
+__global__ void nonfinite_kernel(const double* __restrict__ x, int64_t n, unsigned long long* first) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    if (!isfinite(x[i])) atomicMin(first, (unsigned long long)i);
+}
+
+// Device views of mesh / queries.  Host arrays are copied into context
+// buffers and then checked for non-finite values on the device (one pass
+// over the copies and one read-back), which keeps the host off the data.
 spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, MeshView* mv,
                           QueryView* qv) {
   if (!mesh || !q) return fail(ctx, SPOLY_EINVAL, "mesh and queries are required");
@@ -46,18 +55,28 @@ spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_qu
       q->n_queries > INT32_MAX)
     return fail(ctx, SPOLY_EINVAL, "queries: all arrays must be non-null and 0 < n_queries <= 2^31-1");
   const int64_t T = mesh->n_tris, Q = q->n_queries;
+  // first non-finite index of the staged mesh ([0]) and query rows ([1..3])
+  const bool staged = !mesh->on_device || !q->on_device;
+  unsigned long long* first = nullptr;
+  if (staged) {
+    CK(ctx->check.ensure(4 * sizeof(unsigned long long)), "input check");
+    first = static_cast<unsigned long long*>(ctx->check.p);
+    CK(cudaMemsetAsync(first, 0xff, 4 * sizeof(unsigned long long), ctx->stream), "input check");
+  }
+  auto check = [&](const double* x, int64_t n, int slot) -> cudaError_t {
+    const int64_t g = std::min<int64_t>((n + 255) / 256, int64_t(ctx->num_sms) * 8);
+    nonfinite_kernel<<<unsigned(std::max<int64_t>(g, 1)), 256, 0, ctx->stream>>>(x, n, first + slot);
+    return cudaGetLastError();
+  };
   if (mesh->on_device) {
     mv->tri = mesh->tri;
   } else {
-    for (int64_t i = 0; i < 18 * T; ++i)
-      if (!std::isfinite(mesh->tri[i]))
-        return fail(ctx, SPOLY_EINVAL, "mesh: non-finite value at row %lld, triangle %lld", (long long)(i / T),
-                    (long long)(i % T));
     CK(ctx->mesh.ensure(size_t(18 * T) * sizeof(double)), "mesh staging");
     CK(cudaMemcpyAsync(ctx->mesh.p, mesh->tri, size_t(18 * T) * sizeof(double), cudaMemcpyHostToDevice,
                        ctx->stream),
        "mesh copy");
     mv->tri = static_cast<const double*>(ctx->mesh.p);
+    CK(check(mv->tri, 18 * T, 0), "mesh check");
   }
   mv->n_tris = T;
   if (q->on_device) {
@@ -67,9 +86,6 @@ spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_qu
     qv->types = q->types;
     qv->k = q->k;
   } else {
-    for (int64_t i = 0; i < 3 * Q; ++i)
-      if (!std::isfinite(q->x_first[i]) || !std::isfinite(q->x_last[i]) || !std::isfinite(q->eta[i]))
-        return fail(ctx, SPOLY_EINVAL, "queries: non-finite value in query %lld", (long long)(i / 3));
     for (int64_t i = 0; i < Q; ++i) {
       if (q->k[i] < 1 || q->k[i] > 2) return fail(ctx, SPOLY_EINVAL, "queries: k[%lld] = %d", (long long)i, q->k[i]);
       if ((q->types[2 * i] != SPOLY_R && q->types[2 * i] != SPOLY_T))
@@ -91,8 +107,22 @@ spoly_status stage_inputs(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_qu
     qv->eta = static_cast<const double*>(ctx->eta.p);
     qv->types = static_cast<const int32_t*>(ctx->types.p);
     qv->k = static_cast<const int32_t*>(ctx->kk.p);
+    CK(check(qv->x_first, 3 * Q, 1), "query check");
+    CK(check(qv->x_last, 3 * Q, 2), "query check");
+    CK(check(qv->eta, 3 * Q, 3), "query check");
   }
   qv->n = Q;
+  if (staged) {
+    unsigned long long h[4];
+    CK(cudaMemcpyAsync(h, first, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "input check");
+    CK(cudaStreamSynchronize(ctx->stream), "input check");
+    if (h[0] != ~0ull)
+      return fail(ctx, SPOLY_EINVAL, "mesh: non-finite value at row %lld, triangle %lld", (long long)(h[0] / T),
+                  (long long)(h[0] % T));
+    for (int k = 1; k < 4; ++k)
+      if (h[k] != ~0ull)
+        return fail(ctx, SPOLY_EINVAL, "queries: non-finite value in query %lld", (long long)(h[k] / 3));
+  }
   return SPOLY_OK;
 }
 
@@ -234,7 +264,16 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
 
 extern "C" {
 
-const char* spoly_version(void) { return "spoly-gb300 0.1 (sm_103a)"; }
+const char* spoly_version(void) { return "spoly-gb300 0.2 (sm_103a)"; }
+
+spoly_status spoly_default_sqrt_table(double* dst, int32_t n) {
+  if (!dst || n < 1 + kSqrtPieces * 4) return SPOLY_EINVAL;
+  const SqrtTable t = default_sqrt_table();
+  for (int i = 0; i <= kSqrtPieces; ++i) dst[i] = t.breaks[i];
+  for (int k = 0; k < kSqrtPieces; ++k)
+    for (int j = 0; j < 3; ++j) dst[kSqrtPieces + 1 + 3 * k + j] = t.c[k][j];
+  return SPOLY_OK;
+}
 
 spoly_status spoly_ctx_create(int device, void* cuda_stream, spoly_ctx** out) {
   if (!out) return SPOLY_EINVAL;
@@ -259,13 +298,36 @@ spoly_status spoly_ctx_destroy(spoly_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf* b : {&ctx->mesh, &ctx->xf, &ctx->xl, &ctx->eta, &ctx->types, &ctx->kk, &ctx->boxes, &ctx->flag,
-                    &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries, &ctx->fp_boxes, &ctx->tt_pairs})
+                    &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries, &ctx->fp_boxes, &ctx->fp_mark,
+                    &ctx->tt_pairs, &ctx->check, &ctx->chain_stage, &ctx->chain_valid})
     b->release();
   delete ctx;
   return SPOLY_OK;
 }
 
 const char* spoly_last_error(const spoly_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+spoly_status spoly_upload(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, spoly_mesh* mesh_out,
+                          spoly_queries* q_out) {
+  if (!ctx) return SPOLY_EINVAL;
+  if (!mesh_out || !q_out) return fail(ctx, SPOLY_EINVAL, "upload: outputs are required");
+  CK(cudaSetDevice(ctx->device), "set device");
+  MeshView mv;
+  QueryView qv;
+  spoly_status st = stage_inputs(ctx, mesh, q, &mv, &qv);
+  if (st != SPOLY_OK) return st;
+  *mesh_out = *mesh;
+  mesh_out->tri = mv.tri;
+  mesh_out->on_device = 1;
+  *q_out = *q;
+  q_out->x_first = qv.x_first;
+  q_out->x_last = qv.x_last;
+  q_out->eta = qv.eta;
+  q_out->types = qv.types;
+  q_out->k = qv.k;
+  q_out->on_device = 1;
+  return SPOLY_OK;
+}
 
 spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
                                 const spoly_chain_opts* opts, spoly_chains** inout) {
@@ -298,6 +360,7 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
   };
   if (ch->counter.ensure(16) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain counter"));
   ch->n_k2 = 0;
+  ch->n_footprint = 0;
   ChainParams P{};
   P.mesh = mv;
   P.qv = qv;
@@ -323,12 +386,11 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     P.out = static_cast<int32_t*>(ch->buf.p);
     P.cap = n;
     const int32_t* src = opts->explicit_chains;
-    DevBuf tmp;
     if (!opts->explicit_on_device) {
-      if (tmp.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
-      e = cudaMemcpyAsync(tmp.p, src, size_t(n) * 12, cudaMemcpyHostToDevice, ctx->stream);
+      if (ctx->chain_stage.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
+      e = cudaMemcpyAsync(ctx->chain_stage.p, src, size_t(n) * 12, cudaMemcpyHostToDevice, ctx->stream);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain copy"));
-      src = static_cast<const int32_t*>(tmp.p);
+      src = static_cast<const int32_t*>(ctx->chain_stage.p);
     }
     e = launch_chains_explicit(P, src, n, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit"));
@@ -337,7 +399,6 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     e = cudaMemcpyAsync(&herr, P.error, 4, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hk2, P.count, 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    tmp.release();
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit sync"));
     if (herr) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain %d references a missing query or triangle", herr - 1));
     ch->n = n;
@@ -347,17 +408,16 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     const int64_t n = opts->n_explicit;
     if (!opts->explicit_chains || n <= 0) return bail(fail(ctx, SPOLY_EINVAL, "explicit chain list is empty"));
     if (!(opts->margin >= 0.0)) return bail(fail(ctx, SPOLY_EINVAL, "cone margin must be >= 0"));
-    DevBuf valid, tmp;
-    if (valid.ensure(size_t(n) * 12) != cudaSuccess || ctx->flag.ensure(16) != cudaSuccess)
+    if (ctx->chain_valid.ensure(size_t(n) * 12) != cudaSuccess || ctx->flag.ensure(16) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
     const int32_t* src = opts->explicit_chains;
     if (!opts->explicit_on_device) {
-      if (tmp.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
-      e = cudaMemcpyAsync(tmp.p, src, size_t(n) * 12, cudaMemcpyHostToDevice, ctx->stream);
+      if (ctx->chain_stage.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain staging"));
+      e = cudaMemcpyAsync(ctx->chain_stage.p, src, size_t(n) * 12, cudaMemcpyHostToDevice, ctx->stream);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain copy"));
-      src = static_cast<const int32_t*>(tmp.p);
+      src = static_cast<const int32_t*>(ctx->chain_stage.p);
     }
-    P.out = static_cast<int32_t*>(valid.p);
+    P.out = static_cast<int32_t*>(ctx->chain_valid.p);
     P.cap = n;
     e = launch_chains_explicit(P, src, n, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit"));
@@ -372,7 +432,8 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain counters"));
     if (ch->buf.ensure(size_t(n) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
     P.out = static_cast<int32_t*>(ch->buf.p);
-    e = launch_chains_explicit_cone(P, static_cast<const int32_t*>(valid.p), n, k2, ctx->num_sms, ctx->stream);
+    e = launch_chains_explicit_cone(P, static_cast<const int32_t*>(ctx->chain_valid.p), n, k2, ctx->num_sms,
+                                    ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chains_explicit_cone"));
     unsigned long long hn = 0, hk2 = 0;
     e = cudaMemcpyAsync(&hn, P.count, 8, cudaMemcpyDeviceToHost, ctx->stream);
@@ -469,7 +530,8 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
       e = cudaMemsetAsync(ch->counter.p, 0, 16, ctx->stream);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
     }
-  } else if (opts->mode == SPOLY_CHAINS_FOOTPRINT) {
+  } else if (opts->mode == SPOLY_CHAINS_FOOTPRINT || opts->mode == SPOLY_CHAINS_FOOTPRINT_UNIQUE) {
+    const bool unique = opts->mode == SPOLY_CHAINS_FOOTPRINT_UNIQUE;
     if (!opts->camera) return bail(fail(ctx, SPOLY_EINVAL, "footprint mode needs a camera"));
     const double* cam = opts->camera;
     if (int64_t(cam[14]) * int64_t(cam[15]) != qv.n || cam[14] < 1 || cam[15] < 1)
@@ -500,9 +562,39 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (ctx->fp_entries.ensure(size_t(std::max<int64_t>(n_entries, 1)) * 4) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "footprint grid entries"));
     const int* bounds_dev = static_cast<const int*>(ctx->bounds.p);
+    if (unique) {
+      // one chain per distinct candidate triangle, for query 0: every pixel
+      // must share its endpoints
+      bool shared = false;
+      if (ctx->flag.ensure(16) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
+      e = queries_shared(qv, static_cast<int32_t*>(ctx->flag.p), &shared, ctx->num_sms, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint queries"));
+      if (!shared)
+        return bail(fail(ctx, SPOLY_EINVAL, "distinct-triangle footprint: every query must share x_first, x_last, "
+                                            "eta, types and k"));
+      if (ctx->fp_mark.ensure(size_t(mv.n_tris)) != cudaSuccess)
+        return bail(fail(ctx, SPOLY_ENOMEM, "footprint marks"));
+      e = cudaMemsetAsync(ctx->fp_mark.p, 0, size_t(mv.n_tris), ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint marks"));
+    }
     e = fp_grid_fill_and_count(mv, boxes, g, ctx->fp_scratch.p, static_cast<int32_t*>(ctx->fp_entries.p), cam,
-                               bounds_dev, qv.n, &total, ctx->num_sms, ctx->stream);
+                               bounds_dev, qv.n, &total, ctx->num_sms, ctx->stream,
+                               unique ? static_cast<uint8_t*>(ctx->fp_mark.p) : nullptr);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint count"));
+    ch->n_footprint = total;
+    if (unique) {
+      if (ch->buf.ensure(size_t(mv.n_tris) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
+      int64_t nu = 0;
+      e = fp_unique_fill(static_cast<const uint8_t*>(ctx->fp_mark.p), mv.n_tris, 0,
+                         static_cast<unsigned long long*>(ch->counter.p), static_cast<int32_t*>(ch->buf.p), &nu,
+                         ctx->num_sms, ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint distinct triangles"));
+      ch->n = nu;
+      e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build_chains"));
+      *inout = ch;
+      return SPOLY_OK;
+    }
     if (ch->buf.ensure(size_t(std::max<int64_t>(total, 1)) * 12) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
     e = fp_fill(boxes, g, ctx->fp_scratch.p, static_cast<const int32_t*>(ctx->fp_entries.p), cam, bounds_dev, qv.n,
@@ -521,6 +613,12 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
 spoly_status spoly_chains_count(const spoly_chains* chains, int64_t* n) {
   if (!chains || !n) return SPOLY_EINVAL;
   *n = chains->n;
+  return SPOLY_OK;
+}
+
+spoly_status spoly_chains_footprint_pairs(const spoly_chains* chains, int64_t* n) {
+  if (!chains || !n) return SPOLY_EINVAL;
+  *n = chains->n_footprint;
   return SPOLY_OK;
 }
 
@@ -643,8 +741,11 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     P.pix.aspect = c[13];
     P.pix.w = int(c[14]);
     P.pix.h = int(c[15]);
+    P.pix.assign = (opts->flags & SPOLY_SOLVE_PIXEL_ASSIGN) ? 1 : 0;
     if (P.pix.w < 1 || P.pix.h < 1 || int64_t(P.pix.w) * P.pix.h != qv.n)
       return bail(fail(ctx, SPOLY_EINVAL, "pixel filter: width x height must equal n_queries"));
+  } else if (opts->flags & SPOLY_SOLVE_PIXEL_ASSIGN) {
+    return bail(fail(ctx, SPOLY_EINVAL, "SPOLY_SOLVE_PIXEL_ASSIGN needs a camera"));
   }
   P.chains = k1_list;
   P.chain_ids = k1_ids;
@@ -689,7 +790,8 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     key[12] = uint64_t(P.queue_cap);
     key[13] = uint64_t(P.side_cap);
     key[14] = uint64_t(P.path_cap);
-    key[15] = uint64_t(opts->precision) | (uint64_t(persistent) << 8) | (uint64_t(P.pix.on) << 9);
+    key[15] = uint64_t(opts->precision) | (uint64_t(persistent) << 8) | (uint64_t(P.pix.on) << 9) |
+              (uint64_t(P.pix.assign) << 10);
     key[16] = uint64_t(ctx->tune.block) | (uint64_t(ctx->tune.blocks_per_sm) << 16) | (uint64_t(ctx->tune.chunk) << 32);
     key[17] = uint64_t(mv.n_tris);
     key[18] = uint64_t(qv.n);

@@ -1,7 +1,7 @@
 // Candidate chain construction: ALL, EXPLICIT and the conservative CONE cull.
 //
 // The paper takes its triangle tuples from an external pruning step (Sec. 3.1
-// and Sec. 6 cite a path-space hierarchy with interval-arithmetic bounds).
+// and Sec. 5 cite a path-space hierarchy with interval-arithmetic bounds).
 // CONE stands in for it: a pair (query, triangle) survives only if the box of
 // outgoing unit directions over the triangle (reflected or refracted per the
 // query, by interval arithmetic over the triangle's bounding box and vertex

@@ -160,6 +160,7 @@ constexpr float kCert32Dip = 1e-3f;
 // phase (layout of spoly_chain_opts::camera).
 struct PixelFilter {
   int on;
+  int assign;  // 1: a path's query becomes the pixel its first vertex projects into
   int w, h;
   double o[3], f[3], r[3], u[3], th, aspect;
 };

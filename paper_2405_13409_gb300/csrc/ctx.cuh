@@ -39,8 +39,10 @@ struct spoly_ctx {
   int num_sms = 0;
   char err[512] = {0};
   spoly::DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
+  spoly::DevBuf check;                          // first non-finite index of staged inputs
+  spoly::DevBuf chain_stage, chain_valid;       // staged and validated explicit chain lists
   spoly::DevBuf boxes, flag;                    // cone cull scratch
-  spoly::DevBuf cam, bounds, fp_scratch, fp_entries, fp_boxes;  // footprint builder
+  spoly::DevBuf cam, bounds, fp_scratch, fp_entries, fp_boxes, fp_mark;  // footprint builder
   spoly::DevBuf tt_pairs;                // 2-bounce cone: receiver-independent pairs
   spoly::K1Launch tune;                  // persistent isolation launch shape (spoly_autotune)
 };
@@ -49,6 +51,7 @@ struct spoly_chains {
   spoly::DevBuf buf;        // [cap][3] int32
   int64_t n = 0;
   int64_t n_k2 = 0;         // chains with a second triangle (tri1 >= 0)
+  int64_t n_footprint = 0;  // FOOTPRINT modes: (pixel, triangle) candidate pairs
   spoly::DevBuf counter;    // unsigned long long + int32 error flag
 };
 

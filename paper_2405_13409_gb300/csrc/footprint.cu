@@ -207,17 +207,71 @@ SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const C
 
 // Count pass: candidates per pixel, the first kPixCand of them kept in
 // `cand` ([n_pixels][kPixCand]) so that the fill needs no second traversal.
+// With `mark` (distinct-triangle mode) nothing is kept: mark[t] = 1 for every
+// candidate triangle t of any pixel instead.
 __global__ void footprint_count_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
                                        const int* cell_count, const int64_t* cell_off, const int32_t* entries,
-                                       int64_t* pix_count, int32_t* cand) {
+                                       int64_t* pix_count, int32_t* cand, uint8_t* mark) {
   const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pixels; q += stride) {
-    int32_t* mine = cand + q * kPixCand;
-    pix_count[q] = pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
-                                    [&](int64_t k, int32_t t) {
-                                      if (k < kPixCand) mine[k] = t;
-                                    });
+    if (mark) {
+      pix_count[q] = pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
+                                      [&](int64_t, int32_t t) { mark[t] = 1; });
+    } else {
+      int32_t* mine = cand + q * kPixCand;
+      pix_count[q] = pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
+                                      [&](int64_t k, int32_t t) {
+                                        if (k < kPixCand) mine[k] = t;
+                                      });
+    }
+  }
+}
+
+// Distinct-triangle list: the marked triangles as chains (query, t, -1).
+// Each block compacts a chunk of 256 consecutive triangles in order and
+// takes its output range with one atomic, so the list is ordered by
+// triangle within chunks (chunks land in completion order).
+__global__ void __launch_bounds__(256) unique_fill_kernel(const uint8_t* __restrict__ mark, int64_t n_tris,
+                                                          int32_t query, unsigned long long* count, int32_t* out) {
+  __shared__ unsigned warp_n[8];
+  __shared__ unsigned long long base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t c0 = int64_t(blockIdx.x) * 256; c0 < n_tris; c0 += int64_t(gridDim.x) * 256) {
+    const int64_t t = c0 + threadIdx.x;
+    const bool on = t < n_tris && mark[t] != 0;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) warp_n[warp] = __popc(b);
+    __syncthreads();
+    unsigned before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      before += (w < warp) ? warp_n[w] : 0u;
+      total += warp_n[w];
+    }
+    if (threadIdx.x == 0) base = total ? atomicAdd(count, (unsigned long long)total) : 0ull;
+    __syncthreads();
+    if (on) {
+      const unsigned long long slot = base + before + __popc(b & ((1u << lane) - 1u));
+      out[3 * slot] = query;
+      out[3 * slot + 1] = int32_t(t);
+      out[3 * slot + 2] = -1;
+    }
+    __syncthreads();
+  }
+}
+
+// flag[0] = 1 when some query differs from query 0 in x_first, x_last, eta,
+// types or k (bitwise).
+__global__ void queries_shared_kernel(QueryView qv, int32_t* flag) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < qv.n; q += stride) {
+    bool same = qv.k[q] == qv.k[0] && qv.types[2 * q] == qv.types[0] && qv.types[2 * q + 1] == qv.types[1];
+    for (int c = 0; c < 3 && same; ++c)
+      same = __double_as_longlong(qv.x_first[3 * q + c]) == __double_as_longlong(qv.x_first[c]) &&
+             __double_as_longlong(qv.x_last[3 * q + c]) == __double_as_longlong(qv.x_last[c]) &&
+             __double_as_longlong(qv.eta[3 * q + c]) == __double_as_longlong(qv.eta[c]);
+    if (!same) flag[0] = 1;
   }
 }
 
@@ -381,9 +435,11 @@ cudaError_t fp_grid_count(const MeshView& M, const float4* boxes, const FpGrid& 
 }
 
 // Stage 2: fills the grid and counts candidates per pixel; returns the total.
+// With `mark` (cleared by the caller) the candidates are marked per triangle
+// instead of kept per pixel.
 cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch,
                                    int32_t* entries, const double* cam_host, const int* bounds_dev, int64_t n_pixels,
-                                   int64_t* total, int num_sms, cudaStream_t st) {
+                                   int64_t* total, int num_sms, cudaStream_t st, uint8_t* mark) {
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
@@ -391,9 +447,35 @@ cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const
   if (e != cudaSuccess) return e;
   grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, G, L.cell_count, L.cell_off, entries, 1);
   footprint_count_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels,
-                                                      L.cell_count, L.cell_off, entries, L.pix_count, L.pix_cand);
+                                                      L.cell_count, L.cell_off, entries, L.pix_count, L.pix_cand,
+                                                      mark);
   if ((e = exclusive_scan<int64_t>(L.pix_count, L.pix_off, n_pixels, L, st)) != cudaSuccess) return e;
   return read_total(L.pix_off, L.pix_count, true, n_pixels, total, st);
+}
+
+cudaError_t fp_unique_fill(const uint8_t* mark, int64_t n_tris, int32_t query, unsigned long long* count_dev,
+                           int32_t* out, int64_t* n_out, int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count_dev, 0, 8, st);
+  if (e != cudaSuccess) return e;
+  const int64_t g = std::min<int64_t>((n_tris + 255) / 256, int64_t(num_sms) * 8);
+  unique_fill_kernel<<<unsigned(g), 256, 0, st>>>(mark, n_tris, query, count_dev, out);
+  unsigned long long n = 0;
+  if ((e = cudaGetLastError()) == cudaSuccess) e = cudaMemcpyAsync(&n, count_dev, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *n_out = int64_t(n);
+  return e;
+}
+
+cudaError_t queries_shared(const QueryView& qv, int32_t* flag_dev, bool* shared, int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flag_dev, 0, 4, st);
+  if (e != cudaSuccess) return e;
+  const int64_t g = std::min<int64_t>((qv.n + 255) / 256, int64_t(num_sms) * 4);
+  queries_shared_kernel<<<unsigned(g), 256, 0, st>>>(qv, flag_dev);
+  int32_t f = 0;
+  if ((e = cudaGetLastError()) == cudaSuccess) e = cudaMemcpyAsync(&f, flag_dev, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *shared = (f == 0);
+  return e;
 }
 
 // Stage 3: writes the candidates ([total][3] int32, ordered by pixel).

@@ -92,7 +92,7 @@ SPOLY_D void add2(float a0, float a1, float b0, float b1, float& r0, float& r1) 
 constexpr int kGateRows = 128;                 // candidates per tile: the MMA's M, one per thread and TMEM lane
 constexpr uint32_t kGateTmemCols = kHid;       // one 128 x 64 FP32 accumulator, reused by the three layers
 constexpr uint32_t kGateIdesc = umma_idesc_bf16(kGateRows, kHid);
-constexpr long long kGateWaitCycles = 1ll << 31;  // about one second at the SM clock
+constexpr long long kGateWaitCycles = 1ll << 31;  // default wait limit: about one second at the SM clock
 constexpr int kGateMaxPerSm = 512 / kGateTmemCols;  // CTAs whose accumulators fit one SM's tensor memory
 static_assert(umma_off(kGateRows - 1, kHid - 1, kHid) == kGateRows * kHid * 2 - 2, "A tile layout");
 static_assert(umma_off(kHid - 1, kIn - 1, kIn) == 4 * kFragW1 - 2, "W1 tile layout");
@@ -114,8 +114,10 @@ SPOLY_D void gate_issue(uint32_t tmem, uint32_t a_s, uint32_t w_s, int K, uint32
 // output layer, the threshold, compaction.  Thread t owns row t of the tile:
 // it writes the row's features and hidden activations into the A tile and
 // reads the row's accumulator from TMEM lane t.  Every wait for the tensor
-// core is bounded; a wait that gives up sets *G.status, ends the CTA's loop,
-// and the CTA still frees its tensor memory.
+// core is bounded (G.wait_cycles per layer); a wait that gives up sets
+// *G.status and ends the CTA's loop, and the CTA then waits for the MMA
+// still in flight with the full default limit before it frees its tensor
+// memory.
 __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
   __shared__ __align__(1024) uint8_t sa[kGateRows * kHid * 2];  // A: 128 rows x K (32 or 64) BF16
   __shared__ __align__(1024) uint32_t sw[kPackWords];            // W1 W2 W3 (B tiles), then FP32 vectors
@@ -139,9 +141,10 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
   uint8_t* a_row64 = sa + (tid >> 3) * (kHid * 16) + (tid & 7) * 16;  // row tid of a K = 64 tile
   uint32_t parity = 0;
   bool bad = false;
+  const long long limit = G.wait_cycles > 0 ? G.wait_cycles : kGateWaitCycles;
   // completion of the layer just issued; warp-uniform result
   auto wait = [&]() {
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_s, parity, kGateWaitCycles));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_s, parity, limit));
     parity ^= 1u;
     tc_fence_after();
     return ok;
@@ -408,6 +411,12 @@ spoly_status spoly_mlp_free(spoly_mlp* m) {
   return SPOLY_OK;
 }
 
+spoly_status spoly_mlp_set_wait_limit(spoly_mlp* m, int64_t cycles) {
+  if (!m || cycles < 0) return SPOLY_EINVAL;
+  m->wait_cycles = (long long)cycles;
+  return SPOLY_OK;
+}
+
 spoly_status spoly_mlp_get_params(spoly_ctx* ctx, const spoly_mlp* m, float* dst) {
   if (!ctx) return SPOLY_EINVAL;
   if (!m || !dst) return fail(ctx, SPOLY_EINVAL, "mlp_get_params: NULL argument");
@@ -522,6 +531,7 @@ spoly_status spoly_mlp_forward(spoly_ctx* ctx, const spoly_mlp* m, const float* 
   G.packed = static_cast<const uint32_t*>(m->packed.p);
   G.logits = logits;
   G.status = static_cast<unsigned long long*>(m->status.p);
+  G.wait_cycles = m->wait_cycles;
   unsigned long long status = 0;
   CK(cudaMemsetAsync(m->status.p, 0, 8, ctx->stream), "mlp_forward status");
   CK(launch_gate(G, ctx->num_sms, ctx->stream), "mlp_forward");
@@ -594,6 +604,7 @@ spoly_status spoly_gate(spoly_ctx* ctx, const spoly_mlp* m, const spoly_mesh* me
   G.out_chains = static_cast<int32_t*>(ch->buf.p);
   G.out_n = static_cast<unsigned long long*>(ch->counter.p);
   G.status = G.out_n + 1;  // second word of the cleared counter
+  G.wait_cycles = m->wait_cycles;
   e = launch_gate(G, ctx->num_sms, ctx->stream);
   unsigned long long cnt[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, ch->counter.p, 16, cudaMemcpyDeviceToHost, ctx->stream);

@@ -3,7 +3,7 @@
 For a symmetric N x N Bezout matrix whose entry (i, j) is a polynomial of
 degree <= ED - i - j (zero when negative), the determinant is expanded by
 cofactors along each leading row, memoising the minors of the trailing rows
-over column subsets (Sec. 5.2 of the paper).  Minors that vanish
+over column subsets (Sec. 4.2 of the paper).  Minors that vanish
 structurally (no permutation through nonzero entries) are never formed.
 Every coefficient of every minor becomes one scalar, so the emitted code is
 straight-line and register-allocatable.

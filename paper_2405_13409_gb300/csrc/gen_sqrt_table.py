@@ -1,6 +1,6 @@
 """Generates sqrt_table.cuh: the library's default piecewise rational
 approximant of sqrt(x) on [0, 1] used by the refraction mapping of 2-bounce
-chains (Sec. 4.4: six pieces of (c0 + c1 x) / (d0 + d1 x), error below
+chains (Sec. 3.4: six pieces of (c0 + c1 x) / (d0 + d1 x), error below
 1e-3; the paper's own coefficients are in its supplement, which is not
 available).  Each piece is the minimax fit over Chebyshev nodes of the
 piece, by bisection on the error level with a linear feasibility program

@@ -95,7 +95,13 @@ cudaError_t fp_grid_count(const MeshView& M, const float4* boxes, const FpGrid& 
                           int64_t* n_entries, int num_sms, cudaStream_t st);
 cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch,
                                    int32_t* entries, const double* cam_host, const int* bounds_dev, int64_t n_pixels,
-                                   int64_t* total, int num_sms, cudaStream_t st);
+                                   int64_t* total, int num_sms, cudaStream_t st, uint8_t* mark = nullptr);
+// Distinct-triangle mode: the triangles with mark[t] != 0 as chains
+// (query, t, -1) into out (capacity n_tris); *n_out receives their number.
+cudaError_t fp_unique_fill(const uint8_t* mark, int64_t n_tris, int32_t query, unsigned long long* count_dev,
+                           int32_t* out, int64_t* n_out, int num_sms, cudaStream_t st);
+// *shared = every query equals query 0 bitwise (endpoints, IORs, types, k).
+cudaError_t queries_shared(const QueryView& qv, int32_t* flag_dev, bool* shared, int num_sms, cudaStream_t st);
 cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_host,
                     const int* bounds_dev, int64_t n_pixels, int32_t* out, int num_sms, cudaStream_t st);
 #endif

@@ -23,7 +23,7 @@ SPOLY_D void bezout_entry_rt(const BPd<2>& a, const BPd<DB>& b, int na, int nb, 
   }
 }
 
-// Memoised Laplace expansion with a runtime size n <= 6 (Sec. 5.2).
+// Memoised Laplace expansion with a runtime size n <= 6 (Sec. 4.2).
 template <int DB>
 SPOLY_D void laplace_rt(const double (&E)[6][6][DB + 2], int n, double (&r)[kRD + 1]) {
   constexpr int ED = DB + 1;

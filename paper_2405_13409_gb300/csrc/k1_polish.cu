@@ -1,4 +1,4 @@
-// FP64 polish kernel of the 1-bounce solve (path phase, Sec. 5.3), plus the
+// FP64 polish kernel of the 1-bounce solve (path phase, Sec. 4.3), plus the
 // host launchers of the 1-bounce kernels.
 #include <algorithm>
 

@@ -1,4 +1,4 @@
-// FP64 v-polish and path phase of the 1-bounce solve (Sec. 5.3).
+// FP64 v-polish and path phase of the 1-bounce solve (Sec. 4.3).
 #pragma once
 #include <type_traits>
 
@@ -216,7 +216,7 @@ SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigne
   it.flags = (v1 ? kRoot1Valid : 0u) | (v2 ? kRoot2Valid : 0u) | (f1 & 0xffu) | ((f2 & 0xffu) << 8);
 }
 
-// Path phase (Sec. 5.3) for one polished root z*: u from a(u, v*) = 0 (b if
+// Path phase (Sec. 4.3) for one polished root z*: u from a(u, v*) = 0 (b if
 // a(., v*) vanishes), Newton on (a, b), path-space check of Eq. eq_ch,
 // sidedness and the in-triangle test.  Appends up to 6 paths to `out`.
 template <int DB>
@@ -276,9 +276,12 @@ SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, d
     const double wmin = fmin(fmin(u, v), 1.0 - u - v);
     if (wmin < 0.0) continue;
     if (wmin < kEdgeEps) flags |= SPOLY_FLAG_EDGE;
+    int qout = q;
     if (pix.on) {
       int64_t pq;
-      if (!project_pixel(pix, x1.x, x1.y, x1.z, &pq) || pq != q) continue;
+      if (!project_pixel(pix, x1.x, x1.y, x1.z, &pq)) continue;
+      if (pix.assign) qout = int(pq);
+      else if (pq != q) continue;
     }
     bool dup = false;
     for (int k = 0; k < np; ++k)
@@ -288,7 +291,7 @@ SPOLY_D int k1_path_root(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, d
       }
     if (dup || np >= 6) continue;
     spoly_path& p = out[np++];
-    p.query = q;
+    p.query = qout;
     p.tri[0] = t;
     p.tri[1] = -1;
     p.chain = chain;

@@ -1,12 +1,12 @@
 // Per-candidate device code of the 1-bounce solve, shared by the isolation,
 // generic and polish kernels.
 //
-// Per candidate (query q, triangle t), following Sec. 5.3:
+// Per candidate (query q, triangle t), following Sec. 4.3:
 //   coefficient phase   a(u,v), b(u,v) in FP64 (Sec. 3.5 "R", "T")
 //   elimination phase   Bezout entries in FP64 (Eq. eq_bezout), converted to
 //                       T = float (mixed) or double (plain)
 //   univariate phase    r(z) = det by memoised Laplace expansion and
-//                       recursive-derivative isolation (Sec. 5.2) in T
+//                       recursive-derivative isolation (Sec. 4.2) in T
 //   path phase          FP64: bisection of the numeric determinant near the
 //                       bracket, u from a(u, v*) = 0, Newton on (a, b),
 //                       path-space check of Eq. eq_ch, in-triangle test.

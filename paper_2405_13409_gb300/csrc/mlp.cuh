@@ -12,6 +12,7 @@ struct spoly_mlp {
   spoly::DevBuf adam_v;  // Adam second moments [kParams]
   spoly::DevBuf packed;  // BF16 tensor-core operand tiles and FP32 vectors of inference [kPackWords]
   spoly::DevBuf status;  // inference status word (non-zero: a bounded wait gave up)
+  long long wait_cycles = 0;  // limit of the inference's tensor-core waits (0: the default)
   int64_t adam_step = 0;
   // Training scratch (grown on demand).
   spoly::DevBuf xb, yb, z1, z2, z3, dz1, dz2, dz3, grad, loss, lists, list_n, logits;
@@ -36,6 +37,7 @@ struct GateParams {
   int32_t* out_chains;
   unsigned long long* out_n;
   unsigned long long* status;
+  long long wait_cycles;  // limit of each per-layer completion wait in SM cycles (<= 0: the default)
 };
 
 cudaError_t launch_gate(const GateParams& G, int num_sms, cudaStream_t st);

@@ -13,6 +13,7 @@
 // start at zero and overwrites the queues, so two calls whose work overlaps
 // on the GPU (different streams, or different host threads without ordering)
 // race on it and corrupt each other's results.
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -33,6 +34,31 @@ static_assert(spoly::C_COUNT * sizeof(unsigned long long) <= kCounterBytes, "cou
 static_assert(kQueueBytes % 256 == 0, "queue keeps the side queue 256-byte aligned");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Offset, inside the counter block, of the validation slot: the smallest
+// (chain index << 8 | reason) over the caller's chains that fail the checks
+// below, or all ones when every chain passes.
+constexpr size_t kBadSlot = 248;
+static_assert(spoly::C_COUNT * sizeof(unsigned long long) <= kBadSlot, "validation slot after the counters");
+enum BadReason : unsigned { kBadQuery = 1, kBadTriangle = 2, kBadSecond = 3, kBadBounces = 4, kBadType = 5 };
+
+// One thread per chain: the query and triangle indices lie in range, the
+// chain has one bounce (tri1 < 0 and k[query] == 1) and a known type.  The
+// indices are checked before anything is read through them.
+__global__ void noalloc_validate_kernel(const int32_t* __restrict__ chains, int64_t n, int64_t n_queries,
+                                        int64_t n_tris, const int32_t* __restrict__ k,
+                                        const int32_t* __restrict__ types, unsigned long long* bad) {
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < n; c += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t q = chains[3 * c], t = chains[3 * c + 1], t2 = chains[3 * c + 2];
+    unsigned why = 0;
+    if (q < 0 || q >= n_queries) why = kBadQuery;
+    else if (t < 0 || t >= n_tris) why = kBadTriangle;
+    else if (t2 >= 0) why = kBadSecond;
+    else if (k[q] != 1) why = kBadBounces;
+    else if (types[2 * q] != SPOLY_R && types[2 * q] != SPOLY_T) why = kBadType;
+    if (why) atomicMin(bad, ((unsigned long long)c << 8) | why);
+  }
+}
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_lock;
@@ -111,9 +137,33 @@ extern "C" spoly_status spoly_solve_noalloc(int device, void* cuda_stream, const
   P.side_cap = kMaxChains;
   P.paths = paths;
   P.path_cap = path_capacity;
-  // The array keeps the previous call's contents: the counters must restart at zero.
-  if (cudaMemsetAsync(P.counters, 0, kCounterBytes, st) != cudaSuccess)
+  // The array keeps the previous call's contents: the counters must restart
+  // at zero, the validation slot at all ones.
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>(b + kBadSlot);
+  if (cudaMemsetAsync(P.counters, 0, kBadSlot, st) != cudaSuccess ||
+      cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), st) != cudaSuccess)
     return done(SPOLY_ECUDA, "spoly_solve_noalloc: memset failed");
+  if (n_chains > 0) {
+    // Validate the caller's list before any kernel reads through its indices.
+    const int64_t g = std::min<int64_t>((n_chains + 255) / 256, int64_t(num_sms) * 4);
+    noalloc_validate_kernel<<<int(g), 256, 0, st>>>(chains, n_chains, n_queries, n_tris, k, types, bad);
+    unsigned long long hbad = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return done(SPOLY_ECUDA, "spoly_solve_noalloc: validation failed to run");
+    if (hbad != ~0ull) {
+      static const char* what[] = {"", "query index out of range", "triangle index out of range",
+                                   "a second triangle (only 1-bounce chains are solved here)",
+                                   "a query with k != 1 (only 1-bounce chains are solved here)",
+                                   "a query whose type is neither SPOLY_R nor SPOLY_T"};
+      const unsigned why = unsigned(hbad & 0xffu);
+      char buf[200];
+      snprintf(buf, sizeof(buf), "spoly_solve_noalloc: chain %lld has %s", (long long)(hbad >> 8),
+               why < 6 ? what[why] : "an invalid entry");
+      return done(SPOLY_EINVAL, buf);
+    }
+  }
   if (n_chains > 0) {
     if (spoly::launch_k1_isolate(P, precision, num_sms, st) != cudaSuccess ||
         spoly::launch_k1_polish(P, num_sms, st) != cudaSuccess || spoly::launch_k1_paths(P, num_sms, st) != cudaSuccess)

@@ -152,7 +152,7 @@ SPOLY_D BPd<6> build_b_T(const Frame& f, d3 bvec, double eta0, double eta1) {
 }
 
 // Highest u-power with a non-negligible coefficient polynomial (Bezout size
-// rule "n is the degree", Sec. 5.1; negligible = max-abs <= kTrim * max-abs).
+// rule "n is the degree", Sec. 4.1; negligible = max-abs <= kTrim * max-abs).
 template <int D>
 SPOLY_D int deg_u(const BPd<D>& p) {
   long long m = 0;
@@ -367,7 +367,7 @@ SPOLY_D T horner_from(const T (&w)[DM + 1], int j, T x) {
   return s;
 }
 
-// Real roots of p on [lo, hi] by recursive-derivative isolation (Sec. 5.2):
+// Real roots of p on [lo, hi] by recursive-derivative isolation (Sec. 4.2):
 // the roots of the derivative of order j split [lo, hi] into monotone pieces
 // of the derivative of order j-1; each piece with a sign change holds one
 // root, found by bisection to width `tol`.  A root exactly at a piece end

@@ -1,6 +1,6 @@
 // 2-bounce refraction (TT) chains: FP64 construction of the bivariate system
-// of Sec. 4.4-4.5 in per-thread scratch, and the warp-cooperative Bezout
-// determinant sign of Sec. 5.2 (k >= 2 branch).
+// of Sec. 3.4-3.5 in per-thread scratch, and the warp-cooperative Bezout
+// determinant sign of Sec. 4.2 (k >= 2 branch).
 //
 // System (reading of the paper's TT row, Table tab_sum): with the scaled
 // refracted direction D at x1 (Eq. eq_refr_rational, sqrt(beta) replaced by
@@ -24,7 +24,7 @@ constexpr int kTTDmap = 8;            // u~, v~ (kappa: 7)
 constexpr int kTTMaxN = 32;           // largest Bezout size of the warp kernels
 constexpr int kSqrtPieces = 6;
 constexpr double kTTRootTol = 1e-10;  // FP64 polish width in v1
-constexpr int kTTPaperIters = 10;     // FP32 bisection iterations (Sec. 5.2)
+constexpr int kTTPaperIters = 10;     // FP32 bisection iterations (Sec. 4.2)
 constexpr int kTTNewtonIters = 8;
 constexpr double kTTIllCond = 1e-7;
 

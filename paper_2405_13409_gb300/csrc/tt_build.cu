@@ -1,5 +1,5 @@
 // TT chains, FP64 phase 1: piece enumeration and construction of the
-// bivariate system (Sec. 4.4-4.5) per (chain, sqrt piece), one warp per
+// bivariate system (Sec. 3.4-3.5) per (chain, sqrt piece), one warp per
 // system with its polynomials in shared memory.
 #include "tt_kernels.cuh"
 
@@ -255,7 +255,7 @@ SPOLY_D d3 rr_edge(const TriD& t1, const TriD& t2, d3 x3) {
   return (c1v < kSwitch && c2v > c1v) ? e2 : e1;
 }
 
-// Builds a, b, u~, v~, kappa of an RR system (Sec. 4.5, Eq. eq_rr1) in the
+// Builds a, b, u~, v~, kappa of an RR system (Sec. 3.5, Eq. eq_rr1) in the
 // warp's arena: the scaled reflected direction D = d0 |n1|^2 - 2 (d0.n1) n1
 // (Eq. eq_431_di) is a polynomial, so the mapping (Eq. eq_rct) is exact and
 // a chain is one system.  a = (D x (x3 - x1)) . M2 (degree 8) and

@@ -1,5 +1,5 @@
 // Group-cooperative sign of the Bezout determinant of a TT system at one
-// value of the hidden variable v1 (Sec. 5.2, k >= 2 branch).
+// value of the hidden variable v1 (Sec. 4.2, k >= 2 branch).
 //
 // A group of G aligned lanes evaluates one sample.  The matrix is padded to
 // a compile-time size N >= n with an identity block (the determinant is

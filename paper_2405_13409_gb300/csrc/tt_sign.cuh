@@ -1,6 +1,6 @@
 // TT chains, sign phase: the sign of the Bezout determinant at the
 // n_intervals + 1 uniform samples of v1 in [0, 1], bisection of every sign
-// change for the paper's 10 iterations (Sec. 5.2), the ill-conditioning
+// change for the paper's 10 iterations (Sec. 4.2), the ill-conditioning
 // flag, and the bracket queue.  One block per system; each sample is
 // evaluated by a group of G lanes (tt_group.cuh) with the matrix padded to N.
 // Instantiated for FP32 (mixed mode) in tt_sign_f32.cu and for FP64 (plain

@@ -5,7 +5,7 @@ lists that both the CUDA path and the FP64 oracle consume.  It holds none of
 the solver's arithmetic: no specular polynomial, resultant or root finding
 lives here, only heightfield geometry, analytic normals and endpoint grids.
 
-The scenes stand in for the paper's glint and caustic scenes (Sec. 6: brush,
+The scenes stand in for the paper's glint and caustic scenes (Sec. 5: brush,
 relief, Plane, Pool), which are not available; they reproduce their shape:
 curved triangles with interpolated vertex normals (Sec. 3.1, Eq. eq_xi and
 eq_ni), a point light, and a grid of receivers or a pinhole camera.

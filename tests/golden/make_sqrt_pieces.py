@@ -1,5 +1,5 @@
 """Writes tests/golden/sqrt_pieces.json: the oracle's fit of the six-piece
-rational approximant of sqrt(x) on [0, 1] (Sec. 4.4; the paper's own
+rational approximant of sqrt(x) on [0, 1] (Sec. 3.4; the paper's own
 coefficients are in its supplement, which is not available).  Calls only
 oracle/."""
 import json

@@ -143,3 +143,69 @@ def test_gate_passes_two_bounce_chains(bctx, batch):
     ctx.spoly_chains_free(gated)
     ctx.spoly_chains_free(cut)
     ctx.spoly_mlp_free(mlp)
+
+
+def test_batch_pipeline_matches_oracles(bctx):
+    """A batch shaped like the batched mixed workload (160 independent
+    queries, bounce count uniform in {1, 2}, candidate counts log-uniform in
+    1e2..2e4) through the workload's whole pipeline: the per-chain cone
+    test, the gate (its threshold below every logit, so every chain it
+    keeps is compared), the persistent isolation with the autotuner's launch
+    shape, and the 2-bounce pipeline with the library's default sqrt pieces.
+    Every 1-bounce chain of the explicit (unculled) list is solved by the
+    C++ oracle; a sample of 2-bounce chains (every culled chain with a GPU
+    path, culled chains at random and unculled chains at random) by the
+    numpy TT oracle with the same sqrt pieces.  Paths are paired at 1e-5."""
+    import oracle
+    from tests import oracle_pool
+    from .parity import assert_parity
+    from .test_gpu_tt import _compare
+    ctx, stream = bctx
+    s = scenes.batched_scene(seed=11, n_queries=160, c_min=1e2, c_max=2e4)
+    with torch.cuda.stream(stream):
+        d = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+             for a in (s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, s.chains)]
+    stream.synchronize()
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:6])
+    table = binding.spoly_default_sqrt_table()
+    cut = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT_CONE, margin=1e-3, explicit=d[6])
+    mlp = ctx.spoly_mlp_create(seed=9)
+    gated = ctx.spoly_gate(mlp, mesh, q, cut, -3e38)
+    kept = ctx.spoly_chains_copy(gated)
+    assert kept.shape[0] == ctx.spoly_chains_count(cut)
+    one = torch.from_numpy(np.ascontiguousarray(kept[kept[:, 2] < 0])).cuda()
+    ch1 = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=one)
+    ctx.spoly_autotune(mesh, q, ch1, binding.MIXED)
+    ctx.spoly_chains_free(ch1)
+    sol = ctx.spoly_solve(mesh, q, gated, precision=binding.MIXED, flags=binding.SOLVE_PERSISTENT,
+                          sqrt_table=table)
+    paths = ctx.spoly_paths(sol)
+    stats = ctx.spoly_stats(sol)
+    for h in (gated, cut):
+        ctx.spoly_chains_free(h)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_mlp_free(mlp)
+    # 1 bounce: every chain of the unculled list
+    ex1 = np.ascontiguousarray(s.chains[s.chains[:, 2] < 0])
+    ref1, _ = oracle.solve(s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, ex1)
+    g1 = paths[paths["tri"][:, 1] < 0]
+    assert ref1.size > 10
+    assert_parity(g1, ref1, ex1.shape[0])
+    # 2 bounces: a sample
+    rng = np.random.default_rng(12)
+    k2kept = kept[kept[:, 2] >= 0]
+    ex2 = s.chains[s.chains[:, 2] >= 0]
+    g2 = paths[paths["tri"][:, 1] >= 0]
+    with_path = {(int(a), int(b), int(c)) for a, b, c in zip(g2["query"], g2["tri"][:, 0], g2["tri"][:, 1])}
+    rows = set(with_path)
+    rows |= {tuple(r) for r in k2kept[rng.choice(k2kept.shape[0], min(200, k2kept.shape[0]), replace=False)].tolist()}
+    rows |= {tuple(r) for r in ex2[rng.choice(ex2.shape[0], 100, replace=False)].tolist()}
+    sample = np.array(sorted(rows), np.int32)
+    ref2, _ = oracle_pool.tt_solve(s.tri, s.x_first, s.x_last, s.eta, sample, table[1])
+    mine = g2[[(int(a), int(b), int(c)) in rows for a, b, c in zip(g2["query"], g2["tri"][:, 0], g2["tri"][:, 1])]]
+    matched, un, worst = _compare(mine, ref2)
+    bad = [u for u in un if not (u[3] & (binding.FLAG_ILL_COND | binding.FLAG_EDGE))]
+    assert not bad, (bad, stats)
+    assert len(un) <= max(1, 1e-4 * sample.shape[0]), (un, stats)
+    assert matched >= 5 and worst <= 1e-5
+    assert stats["k2_systems"] > 0 and stats["unsolved"] == 0

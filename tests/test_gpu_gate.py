@@ -123,6 +123,38 @@ def test_forward_matches_oracle(ctx):
     assert err.max() < 2e-2 * scale, err.max()
 
 
+def test_bounded_wait_gives_up_and_context_recovers(ctx):
+    """The inference kernel's tensor-core waits are bounded.  With a limit of
+    one SM cycle the first wait on a single 128-row tile gives up before the
+    product completes: the call returns SPOLY_ETIMEOUT (the kernel still
+    waits for the product in flight with the default limit before freeing
+    its tensor memory).  The context stays usable: with the default limit
+    restored the same call returns the oracle's logits."""
+    rng = np.random.default_rng(17)
+    n = 128
+    f = (rng.normal(size=(n, 24)) * 0.7).astype(np.float32)
+    mlp = ctx.spoly_mlp_create(seed=5)
+    try:
+        th = _random_theta(18)
+        ctx.spoly_mlp_set_params(mlp, th)
+        z = torch.empty(n, dtype=torch.float32, device="cuda")
+        ft = torch.from_numpy(f).cuda()
+        ctx.spoly_mlp_set_wait_limit(mlp, 1)
+        with pytest.raises(binding.SpolyError) as e:
+            ctx.spoly_mlp_forward(mlp, ft, z)
+        assert e.value.status == binding.SPOLY_ETIMEOUT
+        ctx.spoly_mlp_set_wait_limit(mlp, 0)
+        ctx.spoly_mlp_forward(mlp, ft, z)
+        got = z.cpu().numpy().astype(np.float64)
+        with pytest.raises(binding.SpolyError):
+            ctx.spoly_mlp_set_wait_limit(mlp, -1)
+    finally:
+        ctx.spoly_mlp_free(mlp)
+    want, _ = G.forward(th.astype(np.float64), f.astype(np.float64))
+    scale = 1.0 + np.abs(want).mean()
+    assert np.median(np.abs(got - want)) < 1e-4 * scale
+
+
 def test_gradient_matches_oracle(ctx):
     rng = np.random.default_rng(13)
     n = 3000

@@ -70,6 +70,18 @@ def test_graph_replays_match_and_recapture(sctx):
         sol = ctx.spoly_solve(mesh, q, ch, precision=binding.MIXED, flags=binding.SOLVE_GRAPH | binding.SOLVE_PERSISTENT,
                               reuse=sol)
         assert _keys(ctx.spoly_paths(sol)) == want
+    # the replayed solve against the FP64 oracle's exhaustive solve of 96
+    # sampled receivers (every triangle)
+    import oracle
+    from .parity import assert_parity
+    rng = np.random.default_rng(8)
+    qs = np.sort(rng.choice(s.n_queries, 96, replace=False)).astype(np.int32)
+    every = np.stack([np.repeat(qs, s.n_tris), np.tile(np.arange(s.n_tris, dtype=np.int32), qs.size),
+                      -np.ones(qs.size * s.n_tris, np.int32)], -1).astype(np.int32)
+    ref, _ = oracle.solve(s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, every)
+    got = ctx.spoly_paths(sol)
+    assert ref.size > 10
+    assert_parity(got[np.isin(got["query"], qs)], ref, every.shape[0])
     # a different chain list (a triangle range) is captured again
     ch2 = ctx.spoly_build_chains(mesh, q, binding.CHAINS_CONE, margin=1e-3, tri_range=(0, s.n_tris // 2))
     ref2 = ctx.spoly_solve(mesh, q, ch2, precision=binding.MIXED)

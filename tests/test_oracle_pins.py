@@ -1,8 +1,8 @@
 """Pins of the FP64 oracle against facts outside the oracle itself.
 
-* Eq. eq_bezout + Sec. 5.2 Laplace: det of the Bezout matrix equals the
+* Eq. eq_bezout + Sec. 4.2 Laplace: det of the Bezout matrix equals the
   Sylvester resultant (sympy) up to sign and the leading-coefficient power.
-* Sec. 5.2 root isolation: exact Sturm counts (sympy) and planted roots.
+* Sec. 4.2 root isolation: exact Sturm counts (sympy) and planted roots.
 * Table tab_sum / tab_equ: polynomial degrees for curved and face-normal input.
 * Closed forms: a flat triangle with a constant normal has exactly the
   mirror-image point (R) or the unique Fermat/Snell point (T).
@@ -106,7 +106,7 @@ def test_bezout_det_equals_sylvester_resultant(da, db):
         assert ok_pos or ok_neg, (da, db, ec, got)
 
 
-# ------------------------------------------------ root isolation (Sec. 5.2)
+# ------------------------------------------------ root isolation (Sec. 4.2)
 def test_isolation_matches_exact_sturm_counts():
     x = sympy.symbols("x")
     rng = np.random.default_rng(7)

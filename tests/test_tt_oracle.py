@@ -20,7 +20,7 @@ def _table():
 
 
 def test_sqrt_pieces_error_bound():
-    """Sec. 4.4: the six-piece approximant stays within 1e-3 of sqrt on [0, 1]."""
+    """Sec. 3.4: the six-piece approximant stays within 1e-3 of sqrt on [0, 1]."""
     x = np.linspace(0.0, 1.0, 1_000_001)
     err = np.abs(tt.sqrt_approx(x, _table()) - np.sqrt(x))
     assert err.max() < 1e-3, err.max()
@@ -33,7 +33,7 @@ def _refl_dir(d, n):
 
 def test_mapping_matches_ray_plane_intersection():
     """Eq. eq_rct with an exactly rational direction (the scaled reflected
-    direction of Sec. 4.4) reproduces the textbook ray-plane intersection."""
+    direction of Sec. 3.4) reproduces the textbook ray-plane intersection."""
     rng = np.random.default_rng(0)
     for _ in range(50):
         P1 = rng.normal(size=(3, 3))
@@ -299,7 +299,7 @@ def test_brute_force_tiny_slab():
     """2x2-cell surfaces, all (T1, T2) pairs for a receiver that a traced
     path reaches: every path the method returns is an exact solution, and
     its recall of the exact set is reported (the rational sqrt and the
-    finite bisection make the method approximate, Sec. 7).  1024 initial
+    finite bisection make the method approximate, Sec. 6).  1024 initial
     intervals here to bound the test's time."""
     from paper_2405_13409_gb300 import scenes
     s = scenes.slab_scene(seed=0, n_cells=2, n_recv=2)
