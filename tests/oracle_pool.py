@@ -26,15 +26,15 @@ def pool():
 
 
 def _tt_part(args):
-    tri, xf, xl, eta, chains, coeffs, n_intervals = args
+    tri, xf, xl, eta, chains, coeffs, n_intervals, v_solver = args
     from oracle import tt
-    return tt.solve(tri, xf, xl, eta, chains, coeffs, n_intervals)
+    return tt.solve(tri, xf, xl, eta, chains, coeffs, n_intervals, v_solver=v_solver)
 
 
 def _rr_part(args):
-    tri, xf, xl, chains, n_intervals = args
+    tri, xf, xl, chains, n_intervals, v_solver = args
     from oracle import rr
-    return rr.solve(tri, xf, xl, chains, n_intervals), None
+    return rr.solve(tri, xf, xl, chains, n_intervals, v_solver=v_solver), None
 
 
 def _run(fn, parts_args, offsets):
@@ -58,13 +58,36 @@ def _split(chains, n_parts):
     return [(chains[a:b], a) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
 
 
-def tt_solve(tri, xf, xl, eta, chains, coeffs, n_intervals=4096):
+def tt_solve(tri, xf, xl, eta, chains, coeffs, n_intervals=4096, v_solver="bisect"):
     """oracle.tt.solve over the chains, in parallel.  Returns (paths, unrefined uv)."""
     parts = _split(np.asarray(chains, np.int32), 4 * _workers())
-    return _run(_tt_part, [(tri, xf, xl, eta, c, coeffs, n_intervals) for c, _ in parts], [o for _, o in parts])
+    return _run(_tt_part, [(tri, xf, xl, eta, c, coeffs, n_intervals, v_solver) for c, _ in parts],
+                [o for _, o in parts])
 
 
-def rr_solve(tri, xf, xl, chains, n_intervals=4096):
+def rr_solve(tri, xf, xl, chains, n_intervals=4096, v_solver="bisect"):
     """oracle.rr.solve over the chains, in parallel."""
     parts = _split(np.asarray(chains, np.int32), 4 * _workers())
-    return _run(_rr_part, [(tri, xf, xl, c, n_intervals) for c, _ in parts], [o for _, o in parts])[0]
+    return _run(_rr_part, [(tri, xf, xl, c, n_intervals, v_solver) for c, _ in parts], [o for _, o in parts])[0]
+
+
+def _bf_part(args):
+    tri, xf, xl, eta, chains, grid = args
+    from tests.test_tt_oracle import _brute_force
+    T = np.asarray(tri, float)
+    out = []
+    for q, t1, t2 in chains:
+        P1, N1 = T[0:9, t1].reshape(3, 3), T[9:18, t1].reshape(3, 3)
+        P2, N2 = T[0:9, t2].reshape(3, 3), T[9:18, t2].reshape(3, 3)
+        for w in _brute_force(xf[q], xl[q], eta[q], P1, N1, P2, N2, grid=grid):
+            out.append((int(q), int(t1), int(t2), np.asarray(w, float)))
+    return out
+
+
+def tt_brute_force(tri, xf, xl, eta, chains, grid=6):
+    """The exact TT path set of each chain by the polynomial-free 4D Newton
+    brute force of the TT oracle pins, in parallel.  Returns
+    [(query, tri0, tri1, (u1, v1, u2, v2))]."""
+    parts = _split(np.asarray(chains, np.int32), 4 * _workers())
+    res = pool().map(_bf_part, [(tri, xf, xl, eta, c, grid) for c, _ in parts], chunksize=1)
+    return [r for part in res for r in part]
