@@ -623,6 +623,23 @@ def main():
     n_paths = rec[-1]["paths"]
     got_paths = ctx.spoly_paths(pipe.sol)
 
+    # the path phase's last steps on the final step's paths (outside the
+    # metric's step): visibility, contributions and the glint image
+    render = None
+    if camera is not None and n_paths > 0:
+        ra, rb, rc = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        img = torch.zeros(s.n_queries, dtype=torch.float64, device=dev)
+        ra.record(stream)
+        n_vis = ctx.spoly_visibility(mesh, q, pipe.sol)
+        rb.record(stream)
+        ctx.spoly_contributions(mesh, q, pipe.sol, 1.0, image=img)
+        rc.record(stream)
+        rc.synchronize()
+        render = {"visible_paths": n_vis, "occluded_paths": n_paths - n_vis, "visibility_ms": ra.elapsed_time(rb),
+                  "contributions_ms": rb.elapsed_time(rc), "lit_pixels": int((img > 0).sum().item()),
+                  "image_sum": float(img.sum().item())}
+        got_paths = ctx.spoly_paths(pipe.sol)
+
     # plain FP64 path on the same candidates: no gate, every step in FP64
     plain = None
     if (camera is not None or batched) and not args.no_plain and precision == binding.MIXED:
@@ -742,6 +759,7 @@ def main():
         "solved_per_step": n_solved, "paths_per_step": n_paths, "counters": stats,
         "phase_ms": ph,
         "plain_fp64": plain,
+        "render": render,
         "gate": gate_info,
         "autotune": tune,
         "roofline": roofline,

@@ -63,6 +63,7 @@ typedef int32_t spoly_status;
 #define SPOLY_FLAG_NEWTON 8u        /* refined by path-space Newton (k = 2) */
 #define SPOLY_FLAG_SQRT_SPLIT 16u   /* rational sqrt piece split (k = 2, T) */
 #define SPOLY_FLAG_TANGENT 32u      /* root found at a critical point of r */
+#define SPOLY_FLAG_OCCLUDED 64u     /* a segment of the path is blocked (spoly_visibility) */
 
 typedef struct spoly_ctx spoly_ctx;
 typedef struct spoly_chains spoly_chains;
@@ -309,6 +310,37 @@ spoly_status spoly_paths(spoly_ctx* ctx, const spoly_solution_set* set, spoly_pa
 
 /* Counters of the last solve into `set` (synchronises the context stream). */
 spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_counters* out);
+
+/* Visibility test of the path phase (Sec. 4.3: a path is rejected when the
+ * segment from a vertex to the next is blocked): every path of `set` whose
+ * segments x0 -> x1 (-> x2) -> x_last meet a triangle of `mesh` strictly
+ * inside (ray parameter in (1e-9, 1 - 1e-9); each segment's own end
+ * triangles excluded) gets SPOLY_FLAG_OCCLUDED, in place; *n_visible (host)
+ * receives the number of the others.  mesh and q must be the solve's (with
+ * SPOLY_SOLVE_PIXEL_ASSIGN every pixel shares the endpoints, which the test
+ * takes from the path's query).  Builds a uniform xy grid over the mesh
+ * (library scratch, FP64 triangle tests).  Synchronises.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+spoly_status spoly_visibility(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q, spoly_solution_set* set,
+                              int64_t* n_visible);
+
+/* Contribution of every path of `set` (Sec. 4.3; the paper cites the
+ * generalised geometric term of specular chains without printing it, so the
+ * library states its own reading): the irradiance at the camera point
+ * x_first of a point light of intensity `intensity` at x_last carried
+ * through the chain, f = I / (|x1 - x_first|^2 |det J|), where J is the
+ * 2 x 2 derivative (central differences in FP64) of where a ray leaving the
+ * light toward the last vertex, traced back through the planes of the
+ * chain's triangles with their interpolated normals, passes the camera, per
+ * unit solid angle of emission.  Occluded paths (SPOLY_FLAG_OCCLUDED)
+ * contribute 0.  per_path (device FP64 [number of paths], may be NULL)
+ * receives f in the set's path order; image (device FP64 [image_size], may
+ * be NULL) is accumulated: image[query] += f (a pixel, with
+ * SPOLY_SOLVE_PIXEL_ASSIGN).  Synchronises.  Errors: EINVAL (intensity < 0,
+ * image_size <= 0 with an image), ECUDA. */
+spoly_status spoly_contributions(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_queries* q,
+                                 const spoly_solution_set* set, double intensity, double* per_path, double* image,
+                                 int64_t image_size);
 
 /* Device time of the last solve's phases, measured with CUDA events on the
  * context stream when the solve set SPOLY_SOLVE_TIMING: ms[0] = isolation

@@ -34,6 +34,7 @@ FLAG_BACKFACE = 4
 FLAG_NEWTON = 8
 FLAG_SQRT_SPLIT = 16
 FLAG_TANGENT = 32
+FLAG_OCCLUDED = 64
 
 CHAINS_ALL = 0
 CHAINS_CONE = 1
@@ -134,6 +135,10 @@ def load():
         "spoly_build_chains": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries),
                                 ctypes.POINTER(spoly_chain_opts), ctypes.POINTER(P)], c_int32),
         "spoly_default_sqrt_table": ([P, c_int32], c_int32),
+        "spoly_visibility": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P, ctypes.POINTER(c_int64)],
+                             c_int32),
+        "spoly_contributions": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), P, ctypes.c_double, P, P,
+                                 c_int64], c_int32),
         "spoly_upload": ([P, ctypes.POINTER(spoly_mesh), ctypes.POINTER(spoly_queries), ctypes.POINTER(spoly_mesh),
                           ctypes.POINTER(spoly_queries)], c_int32),
         "spoly_chains_count": ([P, ctypes.POINTER(c_int64)], c_int32),
@@ -230,6 +235,23 @@ class Context:
     def queries(x_first, x_last, eta, types, k) -> spoly_queries:
         return spoly_queries(_ptr(x_first), _ptr(x_last), _ptr(eta), _ptr(types), _ptr(k),
                              int(x_first.shape[0]), _on_device(x_first), 0)
+
+    def spoly_visibility(self, mesh: spoly_mesh, q: spoly_queries, sol) -> int:
+        """Marks occluded paths of the solution set in place; returns the
+        number of visible paths."""
+        n = c_int64()
+        self.check(self.lib.spoly_visibility(self.h, ctypes.byref(mesh), ctypes.byref(q), sol, ctypes.byref(n)),
+                   "spoly_visibility")
+        return int(n.value)
+
+    def spoly_contributions(self, mesh: spoly_mesh, q: spoly_queries, sol, intensity: float = 1.0, per_path=None,
+                            image=None):
+        """per_path / image: device FP64 tensors (or None)."""
+        self.check(self.lib.spoly_contributions(self.h, ctypes.byref(mesh), ctypes.byref(q), sol, float(intensity),
+                                                c_void_p(_ptr(per_path)) if per_path is not None else None,
+                                                c_void_p(_ptr(image)) if image is not None else None,
+                                                int(image.numel()) if image is not None else 0),
+                   "spoly_contributions")
 
     def spoly_upload(self, mesh: spoly_mesh, q: spoly_queries):
         """Host inputs staged into the context's device buffers; returns

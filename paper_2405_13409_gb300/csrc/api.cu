@@ -299,7 +299,8 @@ spoly_status spoly_ctx_destroy(spoly_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf* b : {&ctx->mesh, &ctx->xf, &ctx->xl, &ctx->eta, &ctx->types, &ctx->kk, &ctx->boxes, &ctx->flag,
                     &ctx->cam, &ctx->bounds, &ctx->fp_scratch, &ctx->fp_entries, &ctx->fp_boxes, &ctx->fp_mark,
-                    &ctx->tt_pairs, &ctx->check, &ctx->chain_stage, &ctx->chain_valid})
+                    &ctx->tt_pairs, &ctx->check, &ctx->chain_stage, &ctx->chain_valid,
+                    &ctx->vis_grid, &ctx->vis_entries})
     b->release();
   delete ctx;
   return SPOLY_OK;

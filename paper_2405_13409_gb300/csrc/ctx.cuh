@@ -41,6 +41,7 @@ struct spoly_ctx {
   spoly::DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs
   spoly::DevBuf check;                          // first non-finite index of staged inputs
   spoly::DevBuf chain_stage, chain_valid;       // staged and validated explicit chain lists
+  spoly::DevBuf vis_grid, vis_entries;          // visibility grid (cells, offsets, z ranges) and entries
   spoly::DevBuf boxes, flag;                    // cone cull scratch
   spoly::DevBuf cam, bounds, fp_scratch, fp_entries, fp_boxes, fp_mark;  // footprint builder
   spoly::DevBuf tt_pairs;                // 2-bounce cone: receiver-independent pairs

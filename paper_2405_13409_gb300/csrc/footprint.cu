@@ -14,12 +14,13 @@
 #include <cstring>
 
 #include "k1.cuh"
+#include "scan.cuh"
 
 namespace spoly {
 
 namespace {
 
-constexpr int kScanBlock = 1024;
+using scan::kScanBlock;
 
 // Ordered-int encoding of floats for atomicMin / atomicMax.
 SPOLY_D int f2o(float f) {
@@ -313,41 +314,6 @@ __global__ void footprint_overflow_kernel(const float4* boxes, GridGeom G, const
   }
 }
 
-// Exclusive scan of int64 (or int32 widened) values, in blocks of kScanBlock.
-template <typename In>
-__global__ void scan_block_kernel(const In* in, int64_t* out, int64_t* block_sums, int64_t n) {
-  __shared__ int64_t s[kScanBlock / 32];
-  const int64_t i = int64_t(blockIdx.x) * kScanBlock + threadIdx.x;
-  const int64_t v = i < n ? int64_t(in[i]) : 0;
-  int64_t x = v;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int64_t w = s[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    s[lane] = w;
-  }
-  __syncthreads();
-  const int64_t incl = x + (warp ? s[warp - 1] : 0);
-  if (i < n) out[i] = incl - v;
-  if (threadIdx.x == kScanBlock - 1) block_sums[blockIdx.x] = incl;
-}
-
-__global__ void scan_add_kernel(int64_t* out, const int64_t* block_off, int64_t n) {
-  const int64_t i = int64_t(blockIdx.x) * kScanBlock + threadIdx.x;
-  if (i < n) out[i] += block_off[blockIdx.x];
-}
-
 }  // namespace
 
 // Scratch layout of the footprint builder (bytes, library-owned).
@@ -390,22 +356,9 @@ static FpLayout fp_layout(void* scratch, int64_t n_cells, int64_t n_pixels) {
   return L;
 }
 
-// Exclusive scan with up to three levels of block sums (n <= 2^30).
 template <typename In>
 static cudaError_t exclusive_scan(const In* in, int64_t* out, int64_t n, const FpLayout& L, cudaStream_t st) {
-  const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-  scan_block_kernel<In><<<unsigned(nb), kScanBlock, 0, st>>>(in, out, L.sums1, n);
-  if (nb > 1) {
-    const int64_t nb2 = (nb + kScanBlock - 1) / kScanBlock;
-    scan_block_kernel<int64_t><<<unsigned(nb2), kScanBlock, 0, st>>>(L.sums1, L.sums1_off, L.sums2, nb);
-    if (nb2 > 1) {
-      int64_t* s2off = L.sums2 + kScanBlock;
-      scan_block_kernel<int64_t><<<1, kScanBlock, 0, st>>>(L.sums2, s2off, L.sums2 + 2 * kScanBlock, nb2);
-      scan_add_kernel<<<unsigned(nb2), kScanBlock, 0, st>>>(L.sums1_off, s2off, nb);
-    }
-    scan_add_kernel<<<unsigned(nb), kScanBlock, 0, st>>>(out, L.sums1_off, n);
-  }
-  return cudaGetLastError();
+  return scan::exclusive_scan<In>(in, out, n, L.sums1, L.sums1_off, L.sums2, st);
 }
 
 static cudaError_t read_total(const int64_t* off, const void* count, bool count64, int64_t n, int64_t* total,
