@@ -538,6 +538,39 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (int64_t(cam[14]) * int64_t(cam[15]) != qv.n || cam[14] < 1 || cam[15] < 1)
       return bail(fail(ctx, SPOLY_EINVAL, "footprint: width x height (%g x %g) must equal n_queries (%lld)", cam[14],
                        cam[15], (long long)qv.n));
+    if (unique) {
+      // one chain per distinct candidate triangle, for query 0 (every pixel
+      // must share its endpoints); one read-back, a second pass only when the
+      // grid outgrew its capacity
+      const int g = int(std::min(8192.0, std::max(1.0, std::ceil(std::sqrt(double(mv.n_tris) / 2.0)))));
+      const int64_t n_cells = int64_t(g) * g;
+      if (ctx->bounds.ensure(64) != cudaSuccess || ctx->flag.ensure(fp_unique_info_bytes()) != cudaSuccess ||
+          ctx->fp_boxes.ensure(size_t(mv.n_tris) * sizeof(float4)) != cudaSuccess ||
+          ctx->fp_mark.ensure(size_t(mv.n_tris)) != cudaSuccess ||
+          ctx->fp_scratch.ensure(footprint_scratch_bytes(n_cells, qv.n)) != cudaSuccess ||
+          ch->buf.ensure(size_t(mv.n_tris) * 12) != cudaSuccess)
+        return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
+      int64_t cap = std::max<int64_t>(int64_t(ctx->fp_entries.bytes / 4), 4 * mv.n_tris);
+      FpUniqueCounts cnt{};
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        if (ctx->fp_entries.ensure(size_t(cap) * 4) != cudaSuccess)
+          return bail(fail(ctx, SPOLY_ENOMEM, "footprint grid entries"));
+        e = fp_unique_build(mv, qv, static_cast<float4*>(ctx->fp_boxes.p), static_cast<int*>(ctx->bounds.p), g,
+                            ctx->fp_scratch.p, qv.n, static_cast<int32_t*>(ctx->fp_entries.p), cap, cam,
+                            static_cast<uint8_t*>(ctx->fp_mark.p), static_cast<int32_t*>(ch->buf.p), ctx->flag.p,
+                            &cnt, ctx->num_sms, ctx->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint distinct triangles"));
+        if (cnt.n_entries <= cap) break;
+        cap = cnt.n_entries;
+      }
+      if (!cnt.shared)
+        return bail(fail(ctx, SPOLY_EINVAL, "distinct-triangle footprint: every query must share x_first, x_last, "
+                                            "eta, types and k"));
+      ch->n = cnt.n_unique;
+      ch->n_footprint = cnt.pairs;
+      *inout = ch;
+      return SPOLY_OK;
+    }
     if (ctx->bounds.ensure(64) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
     if (ctx->fp_boxes.ensure(size_t(mv.n_tris) * sizeof(float4)) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "footprint triangle boxes"));
@@ -563,39 +596,10 @@ spoly_status spoly_build_chains(spoly_ctx* ctx, const spoly_mesh* mesh, const sp
     if (ctx->fp_entries.ensure(size_t(std::max<int64_t>(n_entries, 1)) * 4) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "footprint grid entries"));
     const int* bounds_dev = static_cast<const int*>(ctx->bounds.p);
-    if (unique) {
-      // one chain per distinct candidate triangle, for query 0: every pixel
-      // must share its endpoints
-      bool shared = false;
-      if (ctx->flag.ensure(16) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "footprint scratch"));
-      e = queries_shared(qv, static_cast<int32_t*>(ctx->flag.p), &shared, ctx->num_sms, ctx->stream);
-      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint queries"));
-      if (!shared)
-        return bail(fail(ctx, SPOLY_EINVAL, "distinct-triangle footprint: every query must share x_first, x_last, "
-                                            "eta, types and k"));
-      if (ctx->fp_mark.ensure(size_t(mv.n_tris)) != cudaSuccess)
-        return bail(fail(ctx, SPOLY_ENOMEM, "footprint marks"));
-      e = cudaMemsetAsync(ctx->fp_mark.p, 0, size_t(mv.n_tris), ctx->stream);
-      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint marks"));
-    }
     e = fp_grid_fill_and_count(mv, boxes, g, ctx->fp_scratch.p, static_cast<int32_t*>(ctx->fp_entries.p), cam,
-                               bounds_dev, qv.n, &total, ctx->num_sms, ctx->stream,
-                               unique ? static_cast<uint8_t*>(ctx->fp_mark.p) : nullptr);
+                               bounds_dev, qv.n, &total, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint count"));
     ch->n_footprint = total;
-    if (unique) {
-      if (ch->buf.ensure(size_t(mv.n_tris) * 12) != cudaSuccess) return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
-      int64_t nu = 0;
-      e = fp_unique_fill(static_cast<const uint8_t*>(ctx->fp_mark.p), mv.n_tris, 0,
-                         static_cast<unsigned long long*>(ch->counter.p), static_cast<int32_t*>(ch->buf.p), &nu,
-                         ctx->num_sms, ctx->stream);
-      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "footprint distinct triangles"));
-      ch->n = nu;
-      e = cudaStreamSynchronize(ctx->stream);
-      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build_chains"));
-      *inout = ch;
-      return SPOLY_OK;
-    }
     if (ch->buf.ensure(size_t(std::max<int64_t>(total, 1)) * 12) != cudaSuccess)
       return bail(fail(ctx, SPOLY_ENOMEM, "chain list"));
     e = fp_fill(boxes, g, ctx->fp_scratch.p, static_cast<const int32_t*>(ctx->fp_entries.p), cam, bounds_dev, qv.n,

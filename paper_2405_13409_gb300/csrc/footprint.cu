@@ -181,7 +181,7 @@ constexpr int kPixCand = 128;  // candidates per pixel kept by the count pass fo
 template <typename Emit>
 SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const CamF& C, float zlo, float zhi,
                                  int64_t q, const int* cell_count, const int64_t* cell_off, const int32_t* entries,
-                                 Emit emit) {
+                                 Emit emit, int64_t cap = INT64_MAX) {
   float xl, xh, yl, yh;
   int64_t n = 0;
   if (!pixel_footprint(C, q, zlo, zhi, xl, xh, yl, yh)) return 0;
@@ -190,7 +190,7 @@ SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const C
   for (int cy = fy0; cy <= fy1; ++cy)
     for (int cx = fx0; cx <= fx1; ++cx) {
       const int64_t cell = int64_t(cy) * G.gx + cx;
-      const int64_t b = cell_off[cell], e = b + cell_count[cell];
+      const int64_t b = cell_off[cell], e = min(b + cell_count[cell], cap);
       for (int64_t k = b; k < e; ++k) {
         const int32_t t = entries[k];
         float txl, txh, tyl, tyh;
@@ -208,24 +208,79 @@ SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const C
 
 // Count pass: candidates per pixel, the first kPixCand of them kept in
 // `cand` ([n_pixels][kPixCand]) so that the fill needs no second traversal.
-// With `mark` (distinct-triangle mode) nothing is kept: mark[t] = 1 for every
-// candidate triangle t of any pixel instead.
 __global__ void footprint_count_kernel(const float4* boxes, GridGeom G, const int* bounds, CamF C, int64_t n_pixels,
                                        const int* cell_count, const int64_t* cell_off, const int32_t* entries,
-                                       int64_t* pix_count, int32_t* cand, uint8_t* mark) {
+                                       int64_t* pix_count, int32_t* cand) {
   const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pixels; q += stride) {
-    if (mark) {
-      pix_count[q] = pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
-                                      [&](int64_t, int32_t t) { mark[t] = 1; });
-    } else {
-      int32_t* mine = cand + q * kPixCand;
-      pix_count[q] = pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
-                                      [&](int64_t k, int32_t t) {
-                                        if (k < kPixCand) mine[k] = t;
-                                      });
-    }
+    int32_t* mine = cand + q * kPixCand;
+    pix_count[q] = pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
+                                    [&](int64_t k, int32_t t) {
+                                      if (k < kPixCand) mine[k] = t;
+                                    });
+  }
+}
+
+// ---- distinct-triangle mode without host round trips: the grid geometry
+// is derived on the device from the mesh bounds, the grid fill checks its
+// capacity, and the counts the host needs land in one record read once.
+struct FpUniqueDev {
+  GridGeom G;
+  unsigned long long n_entries, pairs, n_unique;
+  int32_t differ;  // some query differs from query 0
+  int32_t pad;
+};
+
+// Square cells over the bounds' larger extent, g x g of them.
+__global__ void grid_setup_kernel(const int* bounds, int g, FpUniqueDev* info) {
+  const float xl = o2f(bounds[0]), yl = o2f(bounds[1]), xh = o2f(bounds[3]), yh = o2f(bounds[4]);
+  const float w = fmaxf(fmaxf(xh - xl, yh - yl), 1e-20f) * (1.0f + 1e-5f);
+  info->G.x0 = xl;
+  info->G.y0 = yl;
+  info->G.inv = float(g) / w;
+  info->G.gx = g;
+  info->G.gy = g;
+}
+
+// pass 0: count entries per cell; pass 1: fill, writing only below cap.
+__global__ void grid_insert_dev_kernel(MeshView M, const float4* boxes, const FpUniqueDev* info, int* cell_count,
+                                       const int64_t* cell_off, int32_t* entries, int64_t cap, int pass) {
+  const GridGeom G = info->G;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < M.n_tris; t += stride) {
+    float xl, xh, yl, yh;
+    tri_bbox(boxes, t, xl, xh, yl, yh);
+    int cx0, cx1, cy0, cy1;
+    cell_range(G, xl, xh, yl, yh, cx0, cx1, cy0, cy1);
+    for (int cy = cy0; cy <= cy1; ++cy)
+      for (int cx = cx0; cx <= cx1; ++cx) {
+        const int64_t cell = int64_t(cy) * G.gx + cx;
+        const int slot = atomicAdd(cell_count + cell, 1);
+        if (pass == 1 && cell_off[cell] + slot < cap) entries[cell_off[cell] + slot] = int32_t(t);
+      }
+  }
+}
+
+__global__ void grid_total_kernel(const int* cell_count, const int64_t* cell_off, int64_t n_cells, FpUniqueDev* info) {
+  info->n_entries = (unsigned long long)(cell_off[n_cells - 1] + cell_count[n_cells - 1]);
+}
+
+// Marks the candidate triangles of every pixel and sums the (pixel,
+// triangle) pairs (one atomic per warp).
+__global__ void footprint_mark_kernel(const float4* boxes, FpUniqueDev* info, const int* bounds, CamF C,
+                                      int64_t n_pixels, const int* cell_count, const int64_t* cell_off,
+                                      const int32_t* entries, int64_t cap, uint8_t* mark) {
+  const GridGeom G = info->G;
+  const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q0 = int64_t(blockIdx.x) * blockDim.x; q0 < n_pixels; q0 += stride) {
+    const int64_t q = q0 + threadIdx.x;
+    unsigned n = 0;
+    if (q < n_pixels)
+      n = unsigned(pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
+                                    [&](int64_t, int32_t t) { mark[t] = 1; }, cap));
+    warp_count(&info->pairs, n);
   }
 }
 
@@ -388,11 +443,9 @@ cudaError_t fp_grid_count(const MeshView& M, const float4* boxes, const FpGrid& 
 }
 
 // Stage 2: fills the grid and counts candidates per pixel; returns the total.
-// With `mark` (cleared by the caller) the candidates are marked per triangle
-// instead of kept per pixel.
 cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch,
                                    int32_t* entries, const double* cam_host, const int* bounds_dev, int64_t n_pixels,
-                                   int64_t* total, int num_sms, cudaStream_t st, uint8_t* mark) {
+                                   int64_t* total, int num_sms, cudaStream_t st) {
   const int64_t n_cells = int64_t(g.gx) * g.gy;
   FpLayout L = fp_layout(scratch, n_cells, n_pixels);
   GridGeom G{float(g.x0), float(g.y0), float(1.0 / g.cell), g.gx, g.gy};
@@ -400,36 +453,48 @@ cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const
   if (e != cudaSuccess) return e;
   grid_insert_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, G, L.cell_count, L.cell_off, entries, 1);
   footprint_count_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, G, bounds_dev, make_cam(cam_host), n_pixels,
-                                                      L.cell_count, L.cell_off, entries, L.pix_count, L.pix_cand,
-                                                      mark);
+                                                      L.cell_count, L.cell_off, entries, L.pix_count, L.pix_cand);
   if ((e = exclusive_scan<int64_t>(L.pix_count, L.pix_off, n_pixels, L, st)) != cudaSuccess) return e;
   return read_total(L.pix_off, L.pix_count, true, n_pixels, total, st);
 }
 
-cudaError_t fp_unique_fill(const uint8_t* mark, int64_t n_tris, int32_t query, unsigned long long* count_dev,
-                           int32_t* out, int64_t* n_out, int num_sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(count_dev, 0, 8, st);
+cudaError_t fp_unique_build(const MeshView& M, const QueryView& qv, float4* boxes, int* bounds_dev, int g,
+                            void* scratch, int64_t n_pixels, int32_t* entries, int64_t entries_cap,
+                            const double* cam_host, uint8_t* mark, int32_t* out, void* info_dev,
+                            FpUniqueCounts* counts, int num_sms, cudaStream_t st) {
+  const int64_t n_cells = int64_t(g) * g;
+  FpLayout L = fp_layout(scratch, n_cells, n_pixels);
+  FpUniqueDev* info = static_cast<FpUniqueDev*>(info_dev);
+  cudaError_t e = cudaMemsetAsync(info, 0, sizeof(FpUniqueDev), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.cell_count, 0, size_t(n_cells) * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mark, 0, size_t(M.n_tris), st);
   if (e != cudaSuccess) return e;
-  const int64_t g = std::min<int64_t>((n_tris + 255) / 256, int64_t(num_sms) * 8);
-  unique_fill_kernel<<<unsigned(g), 256, 0, st>>>(mark, n_tris, query, count_dev, out);
-  unsigned long long n = 0;
-  if ((e = cudaGetLastError()) == cudaSuccess) e = cudaMemcpyAsync(&n, count_dev, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  *n_out = int64_t(n);
-  return e;
+  init_bounds_kernel<<<1, 32, 0, st>>>(bounds_dev);
+  mesh_bounds_kernel<<<num_sms * 4, 256, 0, st>>>(M, bounds_dev, boxes);
+  grid_setup_kernel<<<1, 1, 0, st>>>(bounds_dev, g, info);
+  grid_insert_dev_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, info, L.cell_count, L.cell_off, entries, entries_cap, 0);
+  if ((e = exclusive_scan<int>(L.cell_count, L.cell_off, n_cells, L, st)) != cudaSuccess) return e;
+  grid_total_kernel<<<1, 1, 0, st>>>(L.cell_count, L.cell_off, n_cells, info);
+  if ((e = cudaMemsetAsync(L.cell_count, 0, size_t(n_cells) * 4, st)) != cudaSuccess) return e;
+  grid_insert_dev_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, info, L.cell_count, L.cell_off, entries, entries_cap, 1);
+  footprint_mark_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, info, bounds_dev, make_cam(cam_host), n_pixels,
+                                                     L.cell_count, L.cell_off, entries, entries_cap, mark);
+  const int64_t gq = std::min<int64_t>((qv.n + 255) / 256, int64_t(num_sms) * 4);
+  queries_shared_kernel<<<unsigned(gq), 256, 0, st>>>(qv, &info->differ);
+  const int64_t gu = std::min<int64_t>((M.n_tris + 255) / 256, int64_t(num_sms) * 8);
+  unique_fill_kernel<<<unsigned(gu), 256, 0, st>>>(mark, M.n_tris, 0, &info->n_unique, out);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  FpUniqueDev h;
+  if ((e = cudaMemcpyAsync(&h, info, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  counts->n_entries = int64_t(h.n_entries);
+  counts->pairs = int64_t(h.pairs);
+  counts->n_unique = int64_t(h.n_unique);
+  counts->shared = h.differ == 0;
+  return cudaSuccess;
 }
 
-cudaError_t queries_shared(const QueryView& qv, int32_t* flag_dev, bool* shared, int num_sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(flag_dev, 0, 4, st);
-  if (e != cudaSuccess) return e;
-  const int64_t g = std::min<int64_t>((qv.n + 255) / 256, int64_t(num_sms) * 4);
-  queries_shared_kernel<<<unsigned(g), 256, 0, st>>>(qv, flag_dev);
-  int32_t f = 0;
-  if ((e = cudaGetLastError()) == cudaSuccess) e = cudaMemcpyAsync(&f, flag_dev, 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  *shared = (f == 0);
-  return e;
-}
+size_t fp_unique_info_bytes() { return sizeof(FpUniqueDev); }
 
 // Stage 3: writes the candidates ([total][3] int32, ordered by pixel).
 cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_host,

@@ -95,13 +95,22 @@ cudaError_t fp_grid_count(const MeshView& M, const float4* boxes, const FpGrid& 
                           int64_t* n_entries, int num_sms, cudaStream_t st);
 cudaError_t fp_grid_fill_and_count(const MeshView& M, const float4* boxes, const FpGrid& g, void* scratch,
                                    int32_t* entries, const double* cam_host, const int* bounds_dev, int64_t n_pixels,
-                                   int64_t* total, int num_sms, cudaStream_t st, uint8_t* mark = nullptr);
-// Distinct-triangle mode: the triangles with mark[t] != 0 as chains
-// (query, t, -1) into out (capacity n_tris); *n_out receives their number.
-cudaError_t fp_unique_fill(const uint8_t* mark, int64_t n_tris, int32_t query, unsigned long long* count_dev,
-                           int32_t* out, int64_t* n_out, int num_sms, cudaStream_t st);
-// *shared = every query equals query 0 bitwise (endpoints, IORs, types, k).
-cudaError_t queries_shared(const QueryView& qv, int32_t* flag_dev, bool* shared, int num_sms, cudaStream_t st);
+                                   int64_t* total, int num_sms, cudaStream_t st);
+// Distinct-triangle footprint in one pass with one read-back: mesh bounds,
+// a g x g grid derived on the device, the grid fill (capacity entries_cap;
+// counts->n_entries > entries_cap means it must be run again with more),
+// the marks of every pixel's candidates, the equality of the queries and the
+// distinct triangles as chains (0, t, -1) into out (capacity n_tris).
+struct FpUniqueCounts {
+  int64_t n_entries, pairs, n_unique;
+  bool shared;
+};
+size_t fp_unique_info_bytes();
+cudaError_t fp_unique_build(const MeshView& M, const QueryView& qv, float4* boxes, int* bounds_dev, int g,
+                            void* scratch, int64_t n_pixels, int32_t* entries, int64_t entries_cap,
+                            const double* cam_host, uint8_t* mark, int32_t* out, void* info_dev,
+                            FpUniqueCounts* counts, int num_sms, cudaStream_t st);
+
 cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const int32_t* entries, const double* cam_host,
                     const int* bounds_dev, int64_t n_pixels, int32_t* out, int num_sms, cudaStream_t st);
 #endif

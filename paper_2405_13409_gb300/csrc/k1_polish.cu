@@ -94,16 +94,20 @@ cudaError_t launch_partition(const int32_t* chains, int64_t n, int32_t* k1, int3
   return cudaGetLastError();
 }
 
-cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, cudaStream_t st);
-cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, cudaStream_t st);
+cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, int block, cudaStream_t st);
+cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, int block, cudaStream_t st);
 cudaError_t launch_k1_generic(const K1Params& P, int num_sms, cudaStream_t st);
 
 cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st) {
-  int64_t g = (P.n_chains + 127) / 128;
+  // lists too short to give every SM two blocks of 128 run in one-warp
+  // blocks, so that their warps spread over all SMs (each chain is one
+  // thread's long serial solve)
+  const int block = (P.n_chains < int64_t(num_sms) * 256) ? 32 : 128;
+  int64_t g = (P.n_chains + block - 1) / block;
   if (g < 1) g = 1;
-  if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
-  cudaError_t e = (precision == SPOLY_PLAIN_FP64) ? launch_k1_isolate_f64(P, int(g), st)
-                                                  : launch_k1_isolate_f32(P, int(g), st);
+  if (g > int64_t(num_sms) * 16 * (128 / block)) g = int64_t(num_sms) * 16 * (128 / block);
+  cudaError_t e = (precision == SPOLY_PLAIN_FP64) ? launch_k1_isolate_f64(P, int(g), block, st)
+                                                  : launch_k1_isolate_f32(P, int(g), block, st);
   if (e != cudaSuccess) return e;
   return launch_k1_generic(P, num_sms, st);
 }

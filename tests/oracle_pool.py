@@ -12,16 +12,35 @@ import os
 import numpy as np
 
 _POOL = None
+_BLAS_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
 def _workers():
-    return max(1, min(32, os.cpu_count() or 1))
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return max(1, min(32, n))
 
 
 def pool():
+    """The worker pool.  Each worker runs numpy single-threaded (the
+    environment variables are inherited by the spawned children before they
+    import numpy), so that the workers do not oversubscribe the cores with
+    BLAS threads."""
     global _POOL
     if _POOL is None:
-        _POOL = mp.get_context("spawn").Pool(_workers())
+        saved = {k: os.environ.get(k) for k in _BLAS_VARS}
+        for k in _BLAS_VARS:
+            os.environ[k] = "1"
+        try:
+            _POOL = mp.get_context("spawn").Pool(_workers())
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     return _POOL
 
 
