@@ -527,7 +527,9 @@ def main():
     torch.cuda.set_device(local)
     __graft_entry__.build_library()
     dev = torch.device(f"cuda:{local}")
-    stream = torch.cuda.current_stream()
+    # a non-default stream, current for torch and the library (graph capture needs one)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     ctx = binding.Context(local, stream.cuda_stream)
     s, mode, kind, desc, camera = workload(args.workload, args.slab_receivers, args.batch_queries, args.corridor_receivers)
     precision = binding.MIXED if args.precision == "mixed" else binding.PLAIN_FP64
@@ -591,8 +593,11 @@ def main():
         del one
     footprint = mode in (binding.CHAINS_FOOTPRINT, binding.CHAINS_FOOTPRINT_UNIQUE)
     assign = binding.SOLVE_PIXEL_ASSIGN if mode == binding.CHAINS_FOOTPRINT_UNIQUE else 0
+    # the batched solve (both bounce depths) is captured once into a CUDA graph
+    # and replayed every step
     pipe = Pipeline(ctx, mode, precision, camera, mlp, tau, ranges, explicit,
-                    (binding.SOLVE_PERSISTENT if batched else 0) | assign, n_intervals=args.intervals)
+                    ((binding.SOLVE_PERSISTENT | binding.SOLVE_GRAPH) if batched else 0) | assign,
+                    n_intervals=args.intervals)
     for _ in range(args.warmup):
         pipe.step(mesh, q)
     torch.cuda.synchronize()

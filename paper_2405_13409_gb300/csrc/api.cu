@@ -260,6 +260,95 @@ spoly_status solve_tt(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& m
   return SPOLY_OK;
 }
 
+// The 2-bounce chains of a solve without a host read-back, so that the whole
+// solve can be captured into one CUDA graph: the system offsets come from a
+// device scan, every system runs in one pass (scratch sized for the bound of
+// kSqrtPieces systems per chain), the FP64 re-sampling pass always runs and
+// finds its systems on the device.  Counters stay on the device; the caller
+// reads them after the work completes.  Returns ENOMEM when the bound's
+// scratch exceeds kDeviceDrivenBytes (the caller then uses the staged solve).
+constexpr size_t kDeviceDrivenBytes = size_t(48) << 30;
+
+size_t tt_device_bytes(int64_t n2) {
+  const int64_t nb = n2 * kSqrtPieces;
+  return size_t(nb) * (sizeof(TTSys) + kTTKeep * sizeof(double) + kTT32 * sizeof(float) + 128 * sizeof(RootItem)) +
+         tt_offsets_scratch_bytes(n2) + size_t(n2) * 13;
+}
+
+spoly_status solve_tt_device(spoly_ctx* ctx, spoly_solution_set* set, const MeshView& mv, const QueryView& qv,
+                             const int32_t* k2, const int32_t* k2_ids, int64_t n2, const spoly_solve_opts* opts,
+                             unsigned long long* path_counter, spoly_path* paths, int64_t path_cap,
+                             bool enqueue = true) {
+  cudaStream_t st = ctx->stream;
+  if (tt_device_bytes(n2) > kDeviceDrivenBytes) return SPOLY_ENOMEM;
+  TTParams T{};
+  T.mesh = mv;
+  T.qv = qv;
+  T.chains = k2;
+  T.chain_ids = k2_ids;
+  T.n_chains = n2;
+  if (opts->sqrt_table) {
+    const double* t = opts->sqrt_table;
+    for (int i = 0; i <= kSqrtPieces; ++i) T.sqrt_tab.breaks[i] = t[i];
+    for (int k = 0; k < kSqrtPieces; ++k)
+      for (int j = 0; j < 3; ++j) T.sqrt_tab.c[k][j] = t[kSqrtPieces + 1 + 3 * k + j];
+  } else {
+    T.sqrt_tab = default_sqrt_table();
+  }
+  T.n_intervals = opts->n_intervals > 0 ? opts->n_intervals : 4096;
+  T.precision = opts->precision;
+  T.paths = paths;
+  T.path_cap = path_cap;
+  T.path_counter = path_counter;
+  const int64_t bound = n2 * kSqrtPieces;
+  CK(set->tt_counters.ensure(16 * sizeof(unsigned long long)), "tt counters");
+  CK(set->tt_chain_sys.ensure(size_t(n2) * 2 * sizeof(int32_t)), "tt chain systems");
+  CK(set->tt_masks.ensure(size_t(n2)), "tt masks");
+  CK(set->tt_active.ensure(8 + size_t(n2) * sizeof(int32_t)), "tt active chains");
+  CK(set->tt_offsets.ensure(tt_offsets_scratch_bytes(n2)), "tt offsets");
+  CK(set->tt_sys.ensure(size_t(bound) * sizeof(TTSys)), "tt systems");
+  CK(set->tt_scratch.ensure(size_t(bound) * kTTKeep * sizeof(double)), "tt scratch");
+  CK(set->tt_coef32.ensure(size_t(bound) * kTT32 * sizeof(float)), "tt scratch");
+  CK(set->tt_queue.ensure(size_t(bound) * 128 * sizeof(RootItem)), "tt queue");
+  constexpr int64_t kNoisy = 1024;
+  CK(set->tt_noisy.ensure(size_t(kNoisy) * (kTTSampleSlots * (sizeof(int8_t) + sizeof(float)) + 3 * sizeof(int32_t))),
+     "tt noisy");
+  T.counters = static_cast<unsigned long long*>(set->tt_counters.p);
+  T.active_n = static_cast<unsigned long long*>(set->tt_active.p);
+  T.active = reinterpret_cast<int32_t*>(static_cast<char*>(set->tt_active.p) + 8);
+  T.chain_sys = static_cast<int32_t*>(set->tt_chain_sys.p);
+  T.sys = static_cast<TTSys*>(set->tt_sys.p);
+  T.sys_cap = bound;
+  T.n_sys = bound;
+  T.sys_offset = 0;
+  T.n_sys_dev = T.counters + TT_SYSTEMS;
+  T.scratch = static_cast<double*>(set->tt_scratch.p);
+  T.coef32 = static_cast<float*>(set->tt_coef32.p);
+  T.queue = static_cast<RootItem*>(set->tt_queue.p);
+  T.queue_cap = bound * 128;
+  T.noisy_lg = static_cast<float*>(set->tt_noisy.p);
+  T.noisy_span = reinterpret_cast<int32_t*>(T.noisy_lg + kNoisy * kTTSampleSlots);
+  T.noisy_sgn = reinterpret_cast<int8_t*>(T.noisy_span + 3 * kNoisy);
+  T.noisy_cap = kNoisy;
+  set->n_k2 = n2;
+  set->tt_device = true;
+  if (!enqueue) return SPOLY_OK;  // the buffers are sized (outside a capture)
+  CK(cudaMemsetAsync(T.counters, 0, 16 * sizeof(unsigned long long), st), "tt counters");
+  CK(launch_tt_count(T, static_cast<uint8_t*>(set->tt_masks.p), ctx->num_sms, st), "tt count");
+  CK(launch_tt_offsets(T, set->tt_offsets.p, ctx->num_sms, st), "tt offsets");
+  CK(launch_tt_fill(T, static_cast<const uint8_t*>(set->tt_masks.p), ctx->num_sms, st), "tt fill");
+  CK(launch_tt_build(T, ctx->num_sms, st), "tt build");
+  CK(launch_tt_sign(T, ctx->num_sms, st), "tt sign");
+  T.resample_only = 1;
+  CK(launch_tt_sign(T, ctx->num_sms, st), "tt sign (FP64 resample)");
+  T.resample_only = 0;
+  CK(launch_tt_polish(T, ctx->num_sms, st), "tt polish");
+  CK(launch_tt_paths(T, 0, n2, ctx->num_sms, st), "tt paths");
+  set->n_k2 = n2;
+  set->tt_device = true;
+  return SPOLY_OK;
+}
+
 }  // namespace spoly
 
 extern "C" {
@@ -718,18 +807,22 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     int32_t* i1 = base + 3 * n1;
     int32_t* a2 = i1 + n1;
     int32_t* i2 = a2 + 3 * n2;
-    {
-      cudaError_t e0 = cudaMemsetAsync(set->part_n.p, 0, 16, ctx->stream);
-      if (e0 == cudaSuccess)
-        e0 = launch_partition(k1_list, nc, a1, i1, a2, i2, static_cast<unsigned long long*>(set->part_n.p),
-                              ctx->num_sms, ctx->stream);
-      if (e0 != cudaSuccess) return bail(cuda_fail(ctx, e0, "chain partition"));
-    }
     k1_list = a1;
     k1_ids = i1;
     k2_list = a2;
     k2_ids = i2;
   }
+  // the split of a mixed list into its 1- and 2-bounce parts (enqueued by
+  // the staged solve below, or inside the captured graph)
+  auto partition = [&]() -> cudaError_t {
+    if (n2 == 0) return cudaSuccess;
+    cudaError_t e0 = cudaMemsetAsync(set->part_n.p, 0, 16, ctx->stream);
+    if (e0 == cudaSuccess)
+      e0 = launch_partition(static_cast<const int32_t*>(chains->buf.p), nc, const_cast<int32_t*>(k1_list),
+                            const_cast<int32_t*>(k1_ids), const_cast<int32_t*>(k2_list), const_cast<int32_t*>(k2_ids),
+                            static_cast<unsigned long long*>(set->part_n.p), ctx->num_sms, ctx->stream);
+    return e0;
+  };
   K1Params P{};
   P.mesh = mv;
   P.qv = qv;
@@ -782,12 +875,33 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     return persistent ? launch_k1_isolate_persistent(P, opts->precision, ctx->num_sms, ctx->tune, ctx->stream)
                       : launch_k1_isolate(P, opts->precision, ctx->num_sms, ctx->stream);
   };
-  // Graph mode (1-bounce lists): replay the captured launch sequence when
-  // everything it baked in is unchanged; otherwise capture it again.
-  if ((opts->flags & SPOLY_SOLVE_GRAPH) && n2 == 0 && n1 > 0) {
+  // Graph mode: replay the captured launch sequence when everything it baked
+  // in is unchanged; otherwise capture it again.  A list with 2-bounce chains
+  // takes the device-driven 2-bounce pass (no host read-back), whose scratch
+  // is prepared before the capture.
+  const bool tt_graph = n2 > 0 && tt_device_bytes(n2) <= kDeviceDrivenBytes;
+  if ((opts->flags & SPOLY_SOLVE_GRAPH) && (n2 == 0 || tt_graph) && nc > 0) {
     if (!ctx->stream) return bail(fail(ctx, SPOLY_EINVAL, "graph mode needs a non-default stream"));
     bind();
-    uint64_t key[24] = {0};
+    auto run_tt_device = [&](bool enqueue) -> spoly_status {
+      return solve_tt_device(ctx, set, mv, qv, k2_list, k2_ids, n2, opts,
+                             static_cast<unsigned long long*>(set->counters.p) + C_ADMISSIBLE,
+                             static_cast<spoly_path*>(set->paths.p), set->path_cap, enqueue);
+    };
+    if (n2 > 0) {
+      // sizes the 2-bounce scratch (and checks the options) outside the capture
+      if (opts->sqrt_table) {
+        const double* t = opts->sqrt_table;
+        if (t[0] != 0.0 || t[kSqrtPieces] != 1.0) return bail(fail(ctx, SPOLY_EINVAL, "sqrt_table: breaks must run from 0 to 1"));
+        for (int i = 0; i < kSqrtPieces; ++i)
+          if (!(t[i + 1] > t[i])) return bail(fail(ctx, SPOLY_EINVAL, "sqrt_table: breaks must increase"));
+      }
+      if ((opts->n_intervals > 0 ? opts->n_intervals : 4096) > 8192)
+        return bail(fail(ctx, SPOLY_EINVAL, "n_intervals %d exceeds 8192", opts->n_intervals));
+      st = run_tt_device(false);
+      if (st != SPOLY_OK) return bail(st);
+    }
+    uint64_t key[48] = {0};
     const void* ptrs[] = {P.chains, P.queue, P.side, P.paths, P.counters, mv.tri, qv.x_first, qv.x_last, qv.eta,
                           qv.types, qv.k};
     for (int i = 0; i < 11; ++i) key[i] = uint64_t(reinterpret_cast<uintptr_t>(ptrs[i]));
@@ -803,6 +917,21 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     std::memcpy(&key[19], &P.pix.th, sizeof(double));
     std::memcpy(&key[20], &P.pix.o[0], sizeof(double));
     key[21] = uint64_t(reinterpret_cast<uintptr_t>(ctx->stream));
+    key[22] = uint64_t(n2);
+    if (n2 > 0) {
+      const void* tptr[] = {set->part.p, set->tt_counters.p, set->tt_sys.p, set->tt_scratch.p, set->tt_coef32.p,
+                            set->tt_queue.p, set->tt_noisy.p, set->tt_active.p, set->tt_offsets.p, set->tt_chain_sys.p,
+                            set->tt_masks.p};
+      for (int i = 0; i < 11; ++i) key[23 + i] = uint64_t(reinterpret_cast<uintptr_t>(tptr[i]));
+      key[34] = uint64_t(opts->n_intervals);
+      for (int i = 0; i < 13 && opts->sqrt_table; ++i) {
+        double a = opts->sqrt_table[2 * i], b = (2 * i + 1 < 25) ? opts->sqrt_table[2 * i + 1] : 0.0;
+        uint64_t ua, ub;
+        std::memcpy(&ua, &a, 8);
+        std::memcpy(&ub, &b, 8);
+        key[35 + i] = ua ^ (ub * 0x9e3779b97f4a7c15ull);
+      }
+    }
     if (!set->gexec || std::memcmp(key, set->gkey, sizeof(key)) != 0) {
       if (set->gexec) cudaGraphExecDestroy(set->gexec);
       set->gexec = nullptr;
@@ -810,10 +939,17 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
       e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "graph capture"));
       cudaError_t ec = cudaMemsetAsync(set->counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
-      if (ec == cudaSuccess) ec = isolate();
-      if (ec == cudaSuccess) ec = launch_k1_polish(P, ctx->num_sms, ctx->stream);
-      if (ec == cudaSuccess) ec = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+      if (ec == cudaSuccess) ec = partition();
+      if (ec == cudaSuccess && n1 > 0) ec = isolate();
+      if (ec == cudaSuccess && n1 > 0) ec = launch_k1_polish(P, ctx->num_sms, ctx->stream);
+      if (ec == cudaSuccess && n1 > 0) ec = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+      spoly_status tst = SPOLY_OK;
+      if (ec == cudaSuccess && n2 > 0) tst = run_tt_device(true);
       e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (tst != SPOLY_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return bail(tst);
+      }
       if (ec != cudaSuccess) e = ec;
       if (e == cudaSuccess) e = cudaGraphInstantiate(&set->gexec, graph, 0);
       if (graph) cudaGraphDestroy(graph);
@@ -836,6 +972,10 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
       return SPOLY_OK;
     }
     e = read_counters();
+    if (e == cudaSuccess && n2 > 0) {
+      e = cudaMemcpyAsync(set->tt_host, set->tt_counters.p, sizeof(set->tt_host), cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "graph solve"));
     if (int64_t(set->host[C_QUEUED]) <= set->queue_cap && int64_t(set->host[C_SIDE]) <= set->side_cap &&
         int64_t(set->host[C_ADMISSIBLE]) <= set->path_cap) {
@@ -843,9 +983,13 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
       *inout = set;
       return SPOLY_OK;
     }
+    set->tt_device = false;
     // a queue or the path buffer overflowed: the staged solve below grows them
     // (and the next graph call captures again)
   }
+  set->tt_device = false;
+  e = partition();
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain partition"));
   // Stage 1: isolation.  Re-run (only in synchronous mode) until the bracket
   // queue and the side queue hold every item; each re-run grows them to the
   // exact counts, so two passes suffice.
@@ -944,8 +1088,13 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
   out->admissible = int64_t(h[C_ADMISSIBLE]);
   out->flagged = int64_t(h[C_FLAGGED]);
   out->fallback = int64_t(h[C_SIDE]);
+  unsigned long long tdev[16];
+  if (set->n_k2 > 0 && set->tt_device) {  // device-driven pass: its counters are on the device
+    CK(cudaMemcpyAsync(tdev, set->tt_counters.p, sizeof(tdev), cudaMemcpyDeviceToHost, ctx->stream), "stats");
+    CK(cudaStreamSynchronize(ctx->stream), "stats sync");
+  }
   if (set->n_k2 > 0) {  // 2-bounce chains of the same solve (their paths are already in admissible)
-    const unsigned long long* t = set->tt_host;
+    const unsigned long long* t = set->tt_device ? tdev : set->tt_host;
     out->candidates += set->n_k2;
     out->degenerate += int64_t(t[TT_DEGENERATE]);
     out->v_roots += int64_t(t[TT_BRACKETS]);
@@ -1100,7 +1249,8 @@ spoly_status spoly_solution_free(spoly_solution_set* set) {
   set->paths.release();
   set->counters.release();
   for (DevBuf* b : {&set->part, &set->part_n, &set->tt_counters, &set->tt_chain_sys, &set->tt_masks, &set->tt_sys,
-                    &set->tt_scratch, &set->tt_coef32, &set->tt_queue, &set->tt_noisy, &set->tt_active})
+                    &set->tt_scratch, &set->tt_coef32, &set->tt_queue, &set->tt_noisy, &set->tt_active,
+                    &set->tt_offsets})
     b->release();
   if (set->gexec) cudaGraphExecDestroy(set->gexec);
   delete set;

@@ -72,12 +72,13 @@ struct spoly_solution_set {
   bool timed = false;
   // 2-bounce chains: partitioned lists, systems, per-batch scratch
   spoly::DevBuf part, part_n, tt_counters, tt_chain_sys, tt_masks, tt_sys, tt_scratch, tt_coef32, tt_queue, tt_noisy,
-      tt_active;
+      tt_active, tt_offsets;
   unsigned long long tt_host[16] = {0};  // TT_COUNT <= 16
+  bool tt_device = false;  // the last 2-bounce pass ran device-driven: tt_host is read from the device
   int64_t n_k2 = 0;
   // captured 1-bounce solve (SPOLY_SOLVE_GRAPH) and the inputs it was captured for
   cudaGraphExec_t gexec = nullptr;
-  uint64_t gkey[24] = {0};
+  uint64_t gkey[48] = {0};
 };
 
 namespace spoly {

@@ -1,6 +1,7 @@
 // TT chains, FP64 phase 1: piece enumeration and construction of the
 // bivariate system (Sec. 3.4-3.5) per (chain, sqrt piece), one warp per
 // system with its polynomials in shared memory.
+#include "scan.cuh"
 #include "tt_kernels.cuh"
 
 namespace spoly {
@@ -472,7 +473,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) tt_build_kernel(TTParams P) 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* arena = build_smem + int64_t(warp) * kArena;
   const int64_t nw = int64_t(gridDim.x) * kBuildWarps;
-  for (int64_t i = int64_t(blockIdx.x) * kBuildWarps + warp; i < P.n_sys; i += nw) {
+  const int64_t n_sys = tt_n_sys(P);
+  for (int64_t i = int64_t(blockIdx.x) * kBuildWarps + warp; i < n_sys; i += nw) {
     TTSys sy = P.sys[P.sys_offset + i];
     const int64_t c = sy.chain;
     const int q = P.chains[3 * c], t1 = P.chains[3 * c + 1], t2 = P.chains[3 * c + 2];
@@ -511,6 +513,40 @@ cudaError_t launch_tt_fill(const TTParams& P, const uint8_t* masks, int num_sms,
   if (P.n_chains <= 0) return cudaSuccess;
   const int64_t g = std::min<int64_t>((P.n_chains + 127) / 128, int64_t(num_sms) * 8);
   tt_fill_kernel<<<int(g), 128, 0, st>>>(P, masks);
+  return cudaGetLastError();
+}
+
+__global__ void tt_counts_kernel(const int32_t* chain_sys, int64_t n, int32_t* cnt) {
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < n; c += int64_t(gridDim.x) * blockDim.x)
+    cnt[c] = chain_sys[2 * c + 1];
+}
+
+__global__ void tt_offsets_kernel(int32_t* chain_sys, int64_t n, const int32_t* cnt, const int64_t* off,
+                                  unsigned long long* n_sys) {
+  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < n; c += int64_t(gridDim.x) * blockDim.x) {
+    chain_sys[2 * c] = int32_t(off[c]);
+    if (c == n - 1) *n_sys = (unsigned long long)(off[c] + cnt[c]);
+  }
+}
+
+size_t tt_offsets_scratch_bytes(int64_t n_chains) {
+  const int64_t nb = n_chains / scan::kScanBlock + 2;
+  return size_t(n_chains) * 12 + 256 + size_t(2 * nb + 3 * scan::kScanBlock) * 8;
+}
+
+cudaError_t launch_tt_offsets(const TTParams& P, void* tmp, int num_sms, cudaStream_t st) {
+  const int64_t n = P.n_chains;
+  if (n <= 0) return cudaSuccess;
+  char* b = static_cast<char*>(tmp);
+  int32_t* cnt = reinterpret_cast<int32_t*>(b);
+  int64_t* off = reinterpret_cast<int64_t*>(b + ((size_t(n) * 4 + 255) & ~size_t(255)));
+  int64_t* sums = off + n;
+  const int64_t nb = n / scan::kScanBlock + 2;
+  const int64_t g = std::min<int64_t>((n + 255) / 256, int64_t(num_sms) * 8);
+  tt_counts_kernel<<<int(g), 256, 0, st>>>(P.chain_sys, n, cnt);
+  cudaError_t e = scan::exclusive_scan<int32_t>(cnt, off, n, sums, sums + nb, sums + 2 * nb, st);
+  if (e != cudaSuccess) return e;
+  tt_offsets_kernel<<<int(g), 256, 0, st>>>(P.chain_sys, n, cnt, off, P.counters + TT_SYSTEMS);
   return cudaGetLastError();
 }
 

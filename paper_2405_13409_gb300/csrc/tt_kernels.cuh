@@ -57,8 +57,11 @@ struct TTParams {
   int32_t* chain_sys;      // [n_chains][2] first system, count
   TTSys* sys;
   int64_t sys_cap;
-  int64_t n_sys;           // systems of this batch (build, sign)
+  int64_t n_sys;           // systems of this batch (build, sign); with n_sys_dev, their bound
   int64_t sys_offset;      // first system of this batch
+  // device-driven pass (no host read-backs): the system count on the device
+  // (counters[TT_SYSTEMS], written by launch_tt_offsets), else NULL
+  const unsigned long long* n_sys_dev;
   double* scratch;         // [n_sys][kTTKeep] FP64: a, b, u~, v~, kappa (batch-local)
   float* coef32;           // [n_sys][kTT32] FP32: scaled, normalised a and b (batch-local)
   RootItem* queue;         // brackets: zlo = zhi = v1 after the polish; chain = system (global index)
@@ -77,10 +80,25 @@ struct TTParams {
   unsigned long long* path_counter;  // shared with the 1-bounce paths
 };
 
+#ifndef SPOLY_HOST_BUILD
+// Systems of the current pass: the host's count, or (device-driven) the
+// device's count capped by the host's bound.
+SPOLY_D int64_t tt_n_sys(const TTParams& P) {
+  if (!P.n_sys_dev) return P.n_sys;
+  const unsigned long long n = *(volatile const unsigned long long*)P.n_sys_dev;
+  return n < (unsigned long long)P.n_sys ? int64_t(n) : P.n_sys;
+}
+#endif
+
 // Systems: counts per chain into chain_sys[2c + 1] and piece masks; then,
 // with chain_sys[2c] set to the exclusive prefix of the counts, the records.
 cudaError_t launch_tt_count(const TTParams& P, uint8_t* masks, int num_sms, cudaStream_t st);
 cudaError_t launch_tt_fill(const TTParams& P, const uint8_t* masks, int num_sms, cudaStream_t st);
+// Device-driven replacement of the host prefix sum: chain_sys[2c] = the
+// exclusive prefix of the counts and counters[TT_SYSTEMS] = their total
+// (scan scratch: tmp holds n_chains int32 + n_chains int64 + block sums).
+size_t tt_offsets_scratch_bytes(int64_t n_chains);
+cudaError_t launch_tt_offsets(const TTParams& P, void* tmp, int num_sms, cudaStream_t st);
 // Per batch of systems [sys_offset, sys_offset + n_sys):
 cudaError_t launch_tt_build(const TTParams& P, int num_sms, cudaStream_t st);
 cudaError_t launch_tt_sign(const TTParams& P, int num_sms, cudaStream_t st);

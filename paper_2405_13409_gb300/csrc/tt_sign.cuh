@@ -271,7 +271,8 @@ template <typename T, int N, int G>
 __global__ void __launch_bounds__(kSignThreads) tt_sign_kernel(TTParams P, int n_lo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SignSmem<T>& S = *reinterpret_cast<SignSmem<T>*>(smem_raw);
-  for (int64_t i = blockIdx.x; i < P.n_sys; i += gridDim.x) {
+  const int64_t n_sys = tt_n_sys(P);
+  for (int64_t i = blockIdx.x; i < n_sys; i += gridDim.x) {
     TTSys sy = P.sys[P.sys_offset + i];
     if (P.resample_only) {
       if (!(sy.flags & kTTResample)) continue;

@@ -151,7 +151,8 @@ def test_batch_pipeline_matches_oracles(bctx):
     1e2..2e4) through the workload's whole pipeline: the per-chain cone
     test, the gate (its threshold below every logit, so every chain it
     keeps is compared), the persistent isolation with the autotuner's launch
-    shape, and the 2-bounce pipeline with the library's default sqrt pieces.
+    shape, and the 2-bounce pipeline with the library's default sqrt pieces;
+    then the same solve captured into one CUDA graph and replayed.
     Every 1-bounce chain of the explicit (unculled) list is solved by the
     C++ oracle; a sample of 2-bounce chains (every culled chain with a GPU
     path, culled chains at random and unculled chains at random) by the
@@ -200,9 +201,21 @@ def test_batch_pipeline_matches_oracles(bctx):
                           sqrt_table=table)
     paths = ctx.spoly_paths(sol)
     stats = ctx.spoly_stats(sol)
+    ctx.spoly_solution_free(sol)
+    # the same list captured once into a CUDA graph (1- and 2-bounce parts,
+    # the 2-bounce pass without host read-backs) and replayed: the paths of
+    # the staged solve, on both calls
+    gsol = None
+    for _ in range(2):
+        gsol = ctx.spoly_solve(mesh, q, gated, precision=binding.MIXED,
+                               flags=binding.SOLVE_PERSISTENT | binding.SOLVE_GRAPH, sqrt_table=table, reuse=gsol)
+        gp = ctx.spoly_paths(gsol)
+        assert _keys(gp) == _keys(paths)
+    gstats = ctx.spoly_stats(gsol)
+    assert gstats["k2_systems"] == stats["k2_systems"] and gstats["admissible"] == stats["admissible"]
+    ctx.spoly_solution_free(gsol)
     for h in (gated, cut):
         ctx.spoly_chains_free(h)
-    ctx.spoly_solution_free(sol)
     ctx.spoly_mlp_free(mlp)
     # 1 bounce: every chain of the unculled list
     ex1 = np.ascontiguousarray(s.chains[s.chains[:, 2] < 0])
