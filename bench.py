@@ -744,8 +744,10 @@ def main():
                      "traffic": traffic("gate_kernel", args.workload), "flops_per_candidate": GATE_FLOPS}
         # the dominant phase of the step carries the headline roofline
         if not (batched and roofline.get("pipe") == "fp32"):
-            roofline = roof_gate if ph["gate"] >= iso else roof_iso
-            roofline = dict(roofline, other={"isolation": roof_iso if roofline is roof_gate else roof_gate})
+            if ph["gate"] >= iso:
+                roofline = dict(roof_gate, other={"isolation": roof_iso})
+            else:
+                roofline = dict(roof_iso, other={"gate": roof_gate})
         else:
             roofline = dict(roofline, other={"gate": roof_gate, "isolation": roof_iso})
     line = {

@@ -229,12 +229,19 @@ class Context:
 
     @staticmethod
     def mesh(tri) -> spoly_mesh:
-        return spoly_mesh(_ptr(tri), int(tri.shape[1]), _on_device(tri), 0)
+        """A view of a [18, n_tris] FP64 array; the view holds a reference
+        to the array, so the memory stays valid while the view lives."""
+        m = spoly_mesh(_ptr(tri), int(tri.shape[1]), _on_device(tri), 0)
+        m._owner = (tri,)
+        return m
 
     @staticmethod
     def queries(x_first, x_last, eta, types, k) -> spoly_queries:
-        return spoly_queries(_ptr(x_first), _ptr(x_last), _ptr(eta), _ptr(types), _ptr(k),
-                             int(x_first.shape[0]), _on_device(x_first), 0)
+        """A view of the query arrays; like mesh(), it keeps them alive."""
+        q = spoly_queries(_ptr(x_first), _ptr(x_last), _ptr(eta), _ptr(types), _ptr(k),
+                          int(x_first.shape[0]), _on_device(x_first), 0)
+        q._owner = (x_first, x_last, eta, types, k)
+        return q
 
     def spoly_visibility(self, mesh: spoly_mesh, q: spoly_queries, sol) -> int:
         """Marks occluded paths of the solution set in place; returns the

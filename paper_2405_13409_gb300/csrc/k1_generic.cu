@@ -14,8 +14,15 @@ __global__ void __launch_bounds__(64) k1_side_kernel(K1Params P) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const unsigned long long ns = *(volatile unsigned long long*)(P.counters + C_SIDE);
   const int64_t n_side = int64_t(ns < (unsigned long long)P.side_cap ? ns : P.side_cap);
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n_side; base += stride) {
-    const int64_t i = base + lane;
+  // A short side queue (no more chains than the grid has warps) takes one
+  // chain per warp: its lanes would otherwise run the chains' different
+  // Bezout sizes and root counts one after another.
+  const int64_t n_warps = stride >> 5;
+  const bool per_warp = n_side <= n_warps;
+  const int64_t first = per_warp ? (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5
+                                 : int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
+  for (int64_t base = first; base < n_side; base += per_warp ? n_warps : stride) {
+    const int64_t i = per_warp ? (lane == 0 ? base : n_side) : base + lane;
     RootItem items[kRD + 1];
     int nq = 0;
     unsigned n_v = 0, n_pref = 0, n_deg = 0;

@@ -74,3 +74,26 @@ def test_ctx_create_reports_missing_device(lib):
     h = ctypes.c_void_p()
     assert lib.spoly_ctx_create(0, None, ctypes.byref(h)) == binding.SPOLY_ECUDA
     assert not h.value
+
+
+def test_views_keep_their_arrays_alive():
+    """A mesh or query view built from temporaries must not dangle: the view
+    holds the arrays its pointers name."""
+    import gc
+    import weakref
+
+    import numpy as np
+
+    def make():
+        tri = np.zeros((18, 4))
+        xs = [np.zeros((2, 3)), np.zeros((2, 3)), np.ones((2, 3)), np.zeros((2, 2), np.int32), np.ones(2, np.int32)]
+        refs = [weakref.ref(a) for a in [tri] + xs]
+        return binding.Context.mesh(tri), binding.Context.queries(*xs), refs
+
+    m, q, refs = make()
+    gc.collect()
+    assert all(r() is not None for r in refs)
+    assert m.tri == refs[0]().ctypes.data and q.x_first == refs[1]().ctypes.data
+    del m, q
+    gc.collect()
+    assert all(r() is None for r in refs)
