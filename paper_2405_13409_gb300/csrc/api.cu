@@ -374,7 +374,14 @@ spoly_status spoly_ctx_create(int device, void* cuda_stream, spoly_ctx** out) {
   if (!ctx) return SPOLY_ENOMEM;
   ctx->device = device;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
-  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+  int lo = 0, hi = 0;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->side_stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     delete ctx;
     return SPOLY_ECUDA;
   }
@@ -391,6 +398,10 @@ spoly_status spoly_ctx_destroy(spoly_ctx* ctx) {
                     &ctx->tt_pairs, &ctx->check, &ctx->chain_stage, &ctx->chain_valid,
                     &ctx->vis_grid, &ctx->vis_entries})
     b->release();
+  cudaStreamSynchronize(ctx->side_stream);
+  cudaStreamDestroy(ctx->side_stream);
+  cudaEventDestroy(ctx->fork_ev);
+  cudaEventDestroy(ctx->join_ev);
   delete ctx;
   return SPOLY_OK;
 }
@@ -871,6 +882,11 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     return r;
   };
   const bool persistent = (opts->flags & SPOLY_SOLVE_PERSISTENT) != 0;
+  // the side chains' FP64 solve runs on the context's second stream,
+  // overlapping the polish of the bracket queue
+  auto finish = [&]() -> cudaError_t {
+    return launch_k1_finish(P, ctx->num_sms, ctx->stream, ctx->side_stream, ctx->fork_ev, ctx->join_ev);
+  };
   auto isolate = [&]() -> cudaError_t {
     return persistent ? launch_k1_isolate_persistent(P, opts->precision, ctx->num_sms, ctx->tune, ctx->stream)
                       : launch_k1_isolate(P, opts->precision, ctx->num_sms, ctx->stream);
@@ -941,8 +957,7 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
       cudaError_t ec = cudaMemsetAsync(set->counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
       if (ec == cudaSuccess) ec = partition();
       if (ec == cudaSuccess && n1 > 0) ec = isolate();
-      if (ec == cudaSuccess && n1 > 0) ec = launch_k1_polish(P, ctx->num_sms, ctx->stream);
-      if (ec == cudaSuccess && n1 > 0) ec = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+      if (ec == cudaSuccess && n1 > 0) ec = finish();
       spoly_status tst = SPOLY_OK;
       if (ec == cudaSuccess && n2 > 0) tst = run_tt_device(true);
       e = cudaStreamEndCapture(ctx->stream, &graph);
@@ -1025,10 +1040,8 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   // path phase is re-run if the path buffer overflowed: it reads the polished
   // queue and is idempotent once its counters are reset.
   if (n1 > 0) {
-    e = launch_k1_polish(P, ctx->num_sms, ctx->stream);
+    e = finish();
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
-    e = launch_k1_paths(P, ctx->num_sms, ctx->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_paths"));
   }
   if (timing) cudaEventRecord(set->ev[2], ctx->stream);
   auto run_tt = [&]() -> spoly_status {
@@ -1055,7 +1068,9 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
       }
       if (n1 > 0) {
-        e = launch_k1_paths(P, ctx->num_sms, ctx->stream);
+        P.rerun = 1;
+        e = finish();
+        P.rerun = 0;
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_paths"));
       }
       st = run_tt();
@@ -1081,7 +1096,7 @@ spoly_status spoly_stats(spoly_ctx* ctx, const spoly_solution_set* set, spoly_co
   out->candidates = int64_t(h[C_CANDIDATES]);
   out->degenerate = int64_t(h[C_DEGENERATE]);
   out->v_roots = int64_t(h[C_VROOTS]);
-  out->queued = int64_t(h[C_QUEUED]);
+  out->queued = int64_t(h[C_QUEUED]) + int64_t(h[C_SIDE_QUEUED]);
   out->prefiltered = int64_t(h[C_PREFILTERED]);
   out->polish_lost = int64_t(h[C_POLISH_LOST]);
   out->u_roots = int64_t(h[C_UROOTS]);

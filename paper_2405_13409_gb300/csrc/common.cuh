@@ -203,6 +203,7 @@ enum Counter {
   C_QUEUE_OVERFLOW,
   C_SIDE,         // chains sent to the generic-size kernel
   C_TICKET,       // work-queue ticket of the persistent isolation kernel
+  C_SIDE_QUEUED,  // brackets of the side chains (polished in the side kernel)
   C_COUNT
 };
 

@@ -36,6 +36,8 @@ struct DevBuf {
 struct spoly_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side_stream = nullptr;  // the library's own: the side chains' FP64 solve
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int num_sms = 0;
   char err[512] = {0};
   spoly::DevBuf mesh, xf, xl, eta, types, kk;  // staged host inputs

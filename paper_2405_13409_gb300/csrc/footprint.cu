@@ -191,16 +191,25 @@ SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const C
     for (int cx = fx0; cx <= fx1; ++cx) {
       const int64_t cell = int64_t(cy) * G.gx + cx;
       const int64_t b = cell_off[cell], e = min(b + cell_count[cell], cap);
-      for (int64_t k = b; k < e; ++k) {
-        const int32_t t = entries[k];
-        float txl, txh, tyl, tyh;
-        tri_bbox(boxes, t, txl, txh, tyl, tyh);
-        if (txh < xl || txl > xh || tyh < yl || tyl > yh) continue;
-        int tx0, tx1, ty0, ty1;
-        cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
-        if (cx != max(tx0, fx0) || cy != max(ty0, fy0)) continue;  // emitted from its first shared cell
-        emit(n, t);
-        ++n;
+      // four entries at a time: their index loads, then their box gathers,
+      // are independent, so each group waits for two memory round trips
+      for (int64_t k0 = b; k0 < e; k0 += 4) {
+        int32_t t[4];
+        float4 bx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = (k0 + u < e) ? __ldg(entries + k0 + u) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bx[u] = (t[u] >= 0) ? __ldg(boxes + t[u]) : make_float4(1.f, -1.f, 1.f, -1.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float txl = bx[u].x, txh = bx[u].y, tyl = bx[u].z, tyh = bx[u].w;
+          if (t[u] < 0 || txh < xl || txl > xh || tyh < yl || tyl > yh) continue;
+          int tx0, tx1, ty0, ty1;
+          cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
+          if (cx != max(tx0, fx0) || cy != max(ty0, fy0)) continue;  // emitted from its first shared cell
+          emit(n, t[u]);
+          ++n;
+        }
       }
     }
   return n;

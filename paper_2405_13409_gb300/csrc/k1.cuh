@@ -18,6 +18,7 @@ struct K1Params {
   spoly_path* paths;
   int64_t path_cap;
   PixelFilter pix;  // optional: keep a path of query q only if x1 projects into pixel q
+  int32_t rerun;    // 1: path phase again after a path-buffer overflow (no polish, no isolation counters)
 };
 
 #ifndef SPOLY_HOST_BUILD
@@ -36,8 +37,12 @@ struct K1Launch {
 };
 cudaError_t launch_k1_isolate_persistent(const K1Params& P, int precision, int num_sms, const K1Launch& cfg,
                                          cudaStream_t st);
-cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st);
-cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st);
+// After the isolation: the FP64 solve of the side chains (isolation, polish
+// and paths in one thread each) and the FP64 polish and path phase of the
+// bracket queue.  With side_st, the side chains run on side_st concurrently
+// (fork and join through the two events); otherwise both run on st.
+cudaError_t launch_k1_finish(const K1Params& P, int num_sms, cudaStream_t st, cudaStream_t side_st, cudaEvent_t fork,
+                             cudaEvent_t join);
 
 // Candidate construction.
 struct ChainParams {

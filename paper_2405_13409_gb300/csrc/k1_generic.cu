@@ -4,10 +4,26 @@
 // of the sizes the unrolled kernels are instantiated for (flat or degenerate
 // triangles, index-matched refraction), which run the same algorithm with
 // runtime loops, and candidates whose FP32 isolation was not certified, which
-// re-run the unrolled expansion and the isolation in FP64.
-#include "k1_generic.cuh"
+// re-run the unrolled expansion and the isolation in FP64.  Each chain's
+// polish and path phase follow in the same thread.
+#include "k1_polish.cuh"
 
 namespace spoly {
+
+// One side chain per thread: FP64 isolation, polish and path phase, so the
+// kernel needs nothing from the bracket queue and can run beside the queue's
+// polish.  A path re-run (P.rerun) repeats the solve but counts only paths.
+template <int DB, typename Emit>
+SPOLY_D int side_solve(const TriD& tr, const QueryD& qd, int c, int q, int t, const PixelFilter& pix, unsigned& n_v,
+                       unsigned& n_pref, unsigned& lost, unsigned& n_u, Emit&& emit) {
+  K1Sys<DB> s;
+  if (!k1_system<DB>(tr, qd, s)) return -1;
+  RootItem items[kRD + 1];
+  int r = k1_isolate_dispatch<double, DB>(s, items, c, n_v, n_pref);
+  if (r == -2) r = k1_generic_one<DB>(s, items, c, n_v, n_pref);
+  if (r > 0) k1_chain_solve<DB>(s, true, tr, qd, items, r, q, t, pix, lost, n_u, emit);
+  return r;
+}
 
 __global__ void __launch_bounds__(64) k1_side_kernel(K1Params P) {
   const int lane = threadIdx.x & 31;
@@ -23,48 +39,47 @@ __global__ void __launch_bounds__(64) k1_side_kernel(K1Params P) {
                                  : int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
   for (int64_t base = first; base < n_side; base += per_warp ? n_warps : stride) {
     const int64_t i = per_warp ? (lane == 0 ? base : n_side) : base + lane;
-    RootItem items[kRD + 1];
-    int nq = 0;
-    unsigned n_v = 0, n_pref = 0, n_deg = 0;
+    unsigned n_v = 0, n_pref = 0, n_deg = 0, n_q = 0, lost = 0, n_u = 0, n_flag = 0;
+    spoly_path out[6];
+    int np = 0;
     if (i < n_side) {
       const int c = P.side[i];
       const int q = __ldg(P.chains + 3 * int64_t(c));
       const int t = __ldg(P.chains + 3 * int64_t(c) + 1);
       const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
       const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
-      int r = 0;
-      if (qd.type == SPOLY_R) {
-        K1Sys<4> s;
-        if (!k1_system<4>(tr, qd, s)) {
-          r = -1;
+      auto emit = [&](const spoly_path& p) {
+        if (np < 6) {
+          out[np++] = p;
+          if (p.flags & SPOLY_FLAG_ILL_COND) ++n_flag;
         } else {
-          r = k1_isolate_dispatch<double, 4>(s, items, c, n_v, n_pref);
-          if (r == -2) r = k1_generic_one<4>(s, items, c, n_v, n_pref);
+          append_path(P, p);
         }
-      } else {
-        K1Sys<6> s;
-        if (!k1_system<6>(tr, qd, s)) {
-          r = -1;
-        } else {
-          r = k1_isolate_dispatch<double, 6>(s, items, c, n_v, n_pref);
-          if (r == -2) r = k1_generic_one<6>(s, items, c, n_v, n_pref);
-        }
-      }
+      };
+      const int r = (qd.type == SPOLY_R) ? side_solve<4>(tr, qd, c, q, t, P.pix, n_v, n_pref, lost, n_u, emit)
+                                         : side_solve<6>(tr, qd, c, q, t, P.pix, n_v, n_pref, lost, n_u, emit);
       n_deg = (r < 0) ? 1u : 0u;
-      nq = r > 0 ? r : 0;
+      n_q = r > 0 ? unsigned(r) : 0u;
     }
-    warp_count(P.counters + C_DEGENERATE, n_deg);
-    warp_count(P.counters + C_VROOTS, n_v);
-    warp_count(P.counters + C_PREFILTERED, n_pref);
-    const unsigned long long slot = warp_append(P.counters + C_QUEUED, unsigned(nq));
-    for (int k = 0; k < nq; ++k) {
+    if (!P.rerun) {
+      warp_count(P.counters + C_DEGENERATE, n_deg);
+      warp_count(P.counters + C_VROOTS, n_v);
+      warp_count(P.counters + C_PREFILTERED, n_pref);
+      warp_count(P.counters + C_SIDE_QUEUED, n_q);
+      warp_count(P.counters + C_POLISH_LOST, lost);
+    }
+    warp_count(P.counters + C_UROOTS, n_u);
+    warp_count(P.counters + C_FLAGGED, n_flag);
+    const unsigned long long slot = warp_append(P.counters + C_ADMISSIBLE, unsigned(np));
+    for (int k = 0; k < np; ++k) {
       const unsigned long long idx = slot + k;
-      if (idx < (unsigned long long)P.queue_cap) P.queue[idx] = items[k];
+      if (P.chain_ids) out[k].chain = __ldg(P.chain_ids + out[k].chain);
+      if (idx < (unsigned long long)P.path_cap) P.paths[idx] = out[k];
     }
   }
 }
 
-cudaError_t launch_k1_generic(const K1Params& P, int num_sms, cudaStream_t st) {
+cudaError_t launch_k1_side(const K1Params& P, int num_sms, cudaStream_t st) {
   k1_side_kernel<<<num_sms * 4, 64, 0, st>>>(P);
   return cudaGetLastError();
 }

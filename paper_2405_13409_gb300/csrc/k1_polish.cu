@@ -11,33 +11,12 @@ SPOLY_D int64_t queue_items(const K1Params& P) {
   return int64_t(queued < (unsigned long long)P.queue_cap ? queued : P.queue_cap);
 }
 
-// FP64 v-polish of every queued bracket, in place.
-__global__ void __launch_bounds__(32) k1_polish_kernel(K1Params P) {
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  const int64_t n_items = queue_items(P);
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n_items; base += stride) {
-    const int64_t i = base + lane;
-    unsigned lost = 0;
-    if (i < n_items) {
-      RootItem it = P.queue[i];
-      const int q = __ldg(P.chains + 3 * int64_t(it.chain));
-      const int t = __ldg(P.chains + 3 * int64_t(it.chain) + 1);
-      const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
-      const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
-      if (qd.type == SPOLY_R)
-        k1_polish_v<4>(tr, qd, it, lost);
-      else
-        k1_polish_v<6>(tr, qd, it, lost);
-      P.queue[i] = it;
-    }
-    warp_count(P.counters + C_POLISH_LOST, lost);
-  }
-}
-
-// Path phase of every polished bracket; admissible paths appended with one
-// atomic per warp.
-__global__ void __launch_bounds__(32) k1_path_kernel(K1Params P) {
+// FP64 polish and path phase of every queued candidate.  The items of one
+// candidate are contiguous in the queue; the lane on the first item of a run
+// polishes the run in place (once: a path re-run finds it polished) and runs
+// its path phase, so the candidate's system is built once for both.
+// Admissible paths are appended with one atomic per warp.
+__global__ void __launch_bounds__(32) k1_finish_kernel(K1Params P) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t n_items = queue_items(P);
   const int lane = threadIdx.x & 31;
@@ -45,19 +24,34 @@ __global__ void __launch_bounds__(32) k1_path_kernel(K1Params P) {
     const int64_t i = base + lane;
     spoly_path out[6];
     int np = 0;
-    unsigned n_u = 0, n_flag = 0;
-    if (i < n_items) {
+    unsigned lost = 0, n_u = 0, n_flag = 0;
+    if (i < n_items && (i == 0 || P.queue[i - 1].chain != P.queue[i].chain)) {
       const int chain = P.queue[i].chain;
+      int64_t end = i + 1;
+      while (end < n_items && P.queue[end].chain == chain) ++end;
       const int q = __ldg(P.chains + 3 * int64_t(chain));
       const int t = __ldg(P.chains + 3 * int64_t(chain) + 1);
       const QueryD qd = load_query(P.qv.x_first, P.qv.x_last, P.qv.eta, P.qv.types, q);
       const TriD tr = load_tri(P.mesh.tri, P.mesh.n_tris, t);
-      if (qd.type == SPOLY_R)
-        np = k1_path_item<4>(tr, qd, P.queue, i, q, t, out, n_u, P.pix);
-      else
-        np = k1_path_item<6>(tr, qd, P.queue, i, q, t, out, n_u, P.pix);
-      for (int k = 0; k < np; ++k) n_flag += (out[k].flags & SPOLY_FLAG_ILL_COND) ? 1u : 0u;
+      auto emit = [&](const spoly_path& p) {
+        if (np < 6) {
+          out[np++] = p;
+          if (p.flags & SPOLY_FLAG_ILL_COND) ++n_flag;
+        } else {
+          append_path(P, p);
+        }
+      };
+      if (qd.type == SPOLY_R) {
+        K1Sys<4> s;
+        const bool ok = k1_system<4>(tr, qd, s);
+        k1_chain_solve<4>(s, ok, tr, qd, P.queue + i, int(end - i), q, t, P.pix, lost, n_u, emit);
+      } else {
+        K1Sys<6> s;
+        const bool ok = k1_system<6>(tr, qd, s);
+        k1_chain_solve<6>(s, ok, tr, qd, P.queue + i, int(end - i), q, t, P.pix, lost, n_u, emit);
+      }
     }
+    warp_count(P.counters + C_POLISH_LOST, lost);
     warp_count(P.counters + C_UROOTS, n_u);
     warp_count(P.counters + C_FLAGGED, n_flag);
     const unsigned long long slot = warp_append(P.counters + C_ADMISSIBLE, unsigned(np));
@@ -96,7 +90,7 @@ cudaError_t launch_partition(const int32_t* chains, int64_t n, int32_t* k1, int3
 
 cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, int block, cudaStream_t st);
 cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, int block, cudaStream_t st);
-cudaError_t launch_k1_generic(const K1Params& P, int num_sms, cudaStream_t st);
+cudaError_t launch_k1_side(const K1Params& P, int num_sms, cudaStream_t st);
 
 cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st) {
   // lists too short to give every SM two blocks of 128 run in one-warp
@@ -106,10 +100,8 @@ cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cud
   int64_t g = (P.n_chains + block - 1) / block;
   if (g < 1) g = 1;
   if (g > int64_t(num_sms) * 16 * (128 / block)) g = int64_t(num_sms) * 16 * (128 / block);
-  cudaError_t e = (precision == SPOLY_PLAIN_FP64) ? launch_k1_isolate_f64(P, int(g), block, st)
-                                                  : launch_k1_isolate_f32(P, int(g), block, st);
-  if (e != cudaSuccess) return e;
-  return launch_k1_generic(P, num_sms, st);
+  return (precision == SPOLY_PLAIN_FP64) ? launch_k1_isolate_f64(P, int(g), block, st)
+                                         : launch_k1_isolate_f32(P, int(g), block, st);
 }
 
 cudaError_t launch_k1_isolate_persistent_f32(const K1Params& P, int grid, int block, int chunk, cudaStream_t st);
@@ -123,22 +115,29 @@ cudaError_t launch_k1_isolate_persistent(const K1Params& P, int precision, int n
   const int occ = f64 ? k1_isolate_persistent_f64_blocks_per_sm(cfg.block) : k1_isolate_persistent_f32_blocks_per_sm(cfg.block);
   const int bps = std::max(1, std::min(cfg.blocks_per_sm, occ));
   const int grid = num_sms * bps;
-  cudaError_t e = f64 ? launch_k1_isolate_persistent_f64(P, grid, cfg.block, cfg.chunk, st)
-                      : launch_k1_isolate_persistent_f32(P, grid, cfg.block, cfg.chunk, st);
-  if (e != cudaSuccess) return e;
-  return launch_k1_generic(P, num_sms, st);
+  return f64 ? launch_k1_isolate_persistent_f64(P, grid, cfg.block, cfg.chunk, st)
+             : launch_k1_isolate_persistent_f32(P, grid, cfg.block, cfg.chunk, st);
 }
 
-cudaError_t launch_k1_polish(const K1Params& P, int num_sms, cudaStream_t st) {
-  // one-warp blocks: the few thousand brackets of a step spread evenly over
-  // the SMs (the kernel is FP64-bound per SM)
-  k1_polish_kernel<<<num_sms * 32, 32, 0, st>>>(P);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_k1_paths(const K1Params& P, int num_sms, cudaStream_t st) {
-  k1_path_kernel<<<num_sms * 32, 32, 0, st>>>(P);
-  return cudaGetLastError();
+cudaError_t launch_k1_finish(const K1Params& P, int num_sms, cudaStream_t st, cudaStream_t side_st, cudaEvent_t fork,
+                             cudaEvent_t join) {
+  cudaError_t e;
+  if (side_st) {
+    // the side chains' FP64 solve (one warp each, a long serial chain of FP64
+    // instructions) overlaps the polish of the main queue
+    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side_st, fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_k1_side(P, num_sms, side_st)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(join, side_st)) != cudaSuccess) return e;
+  } else if ((e = launch_k1_side(P, num_sms, st)) != cudaSuccess) {
+    return e;
+  }
+  // one-warp blocks: the few thousand candidates of a step spread evenly over
+  // the SMs (each lane runs a long serial chain of FP64 instructions)
+  k1_finish_kernel<<<num_sms * 32, 32, 0, st>>>(P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (side_st && (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 }  // namespace spoly

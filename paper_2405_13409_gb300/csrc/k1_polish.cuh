@@ -10,6 +10,7 @@ namespace spoly {
 // in bits 0-7, root 2 in zhi with public flags in bits 8-15.
 constexpr uint32_t kRoot1Valid = 1u << 30;
 constexpr uint32_t kRoot2Valid = 1u << 31;
+constexpr uint32_t kPolished = 1u << 29;  // the item's roots are final (a path re-run skips the polish)
 
 // Generic-size FP64 resultant (runtime n), kept out of line so its large
 // local arrays do not shape the register allocation of the common path.
@@ -103,8 +104,42 @@ SPOLY_D double dhorner64(const double (&r)[kRD + 1], int deg, double z) {
   return f;
 }
 
-// FP64 bisection of r on [zl, zh] (signs differ) to width kPolishTol in v.
+// r and r' at z by one Horner pass.
+SPOLY_D void horner64_d(const double (&r)[kRD + 1], int deg, double z, double* f, double* df) {
+  double a = 0.0, d = 0.0;
+#pragma unroll
+  for (int c = kRD; c >= 0; --c)
+    if (c <= deg) {
+      d = fma(d, z, a);
+      a = fma(a, z, r[c]);
+    }
+  *f = a;
+  *df = d;
+}
+
+// Root of r in [zl, zh] (signs differ) to width kPolishTol in v: Newton
+// steps from the midpoint while they stay inside the shrinking bracket (a
+// step below tol / 4 ends the search), then bisection.  Every FP64
+// instruction costs about 64 cycles of an SM sub-partition on this part, so
+// the few Newton steps replace the ~20 bisection steps from an FP32 bracket.
 SPOLY_D double bisect64(const double (&r)[kRD + 1], int deg, double zl, double zh, double fl, double tol) {
+  double x = 0.5 * (zl + zh);
+  for (int it = 0; it < 6 && zh - zl > tol; ++it) {
+    double f, df;
+    horner64_d(r, deg, x, &f, &df);
+    if (f == 0.0) return x;
+    if ((f < 0.0) == (fl < 0.0)) {
+      zl = x;
+      fl = f;
+    } else {
+      zh = x;
+    }
+    const double st = f / df;
+    const double xn = x - st;
+    if (!(xn > zl && xn < zh)) break;
+    if (fabs(st) <= 0.25 * tol) return xn;
+    x = xn;
+  }
   while (zh - zl > tol) {
     const double zm = 0.5 * (zl + zh);
     if (!(zm > zl && zm < zh)) break;
@@ -146,32 +181,63 @@ SPOLY_D bool side_root64(const double (&r)[kRD + 1], int deg, double t, double c
   return false;
 }
 
+// Root next to c found by Newton from c (within `reach` of c and inside
+// [zmin, zmax]), confirmed by a sign change of r across [x - tol, x + tol].
+// A displaced FP32 root is a simple root a little outside its bracket, which
+// this finds in a few steps.
+SPOLY_D bool newton_root64(const double (&r)[kRD + 1], int deg, double c, double zmin, double zmax, double reach,
+                           double tol, double* root) {
+  double x = c;
+  for (int it = 0; it < 10; ++it) {
+    double f, df;
+    horner64_d(r, deg, x, &f, &df);
+    if (f == 0.0) {
+      *root = x;
+      return true;
+    }
+    if (!(fabs(df) > 0.0)) return false;
+    const double st = f / df;
+    x -= st;
+    if (!(x >= zmin && x <= zmax) || !(fabs(x - c) <= reach)) return false;
+    if (fabs(st) <= 0.25 * tol) {
+      const double fl = horner64(r, deg, x - tol), fh = horner64(r, deg, x + tol);
+      if (fl == 0.0 || fh == 0.0 || (fl < 0.0) != (fh < 0.0)) {
+        *root = x;
+        return true;
+      }
+      return false;
+    }
+  }
+  return false;
+}
+
 // ILL_COND when |r'(v*)| / sum_i |r_i| < kIllCond (v-domain coefficients:
 // r(v) = p(v / t), so r_i = p_i t^-i and r'(v) = p'(z) / t).
 SPOLY_D uint32_t ill_flag64(const double (&r)[kRD + 1], int deg, double t, double z) {
   double S = 0.0, ti = 1.0;
+  const double it = 1.0 / t;  // t is a power of two: exact
 #pragma unroll
   for (int c = 0; c <= kRD; ++c) {
     if (c <= deg) S += fabs(r[c]) * ti;
-    ti /= t;
+    ti *= it;
   }
   return (fabs(dhorner64(r, deg, z)) / t < kIllCond * S) ? SPOLY_FLAG_ILL_COND : 0u;
 }
 
-// v-polish of one bracket in FP64 (root polishing by bisection near the
-// final interval) on the FP64 resultant.  A sign-change bracket from the
-// isolation is bisected to width 1e-12 in v.  A bracket whose FP64 signs agree
-// (the FP32 root is displaced) and a tangent bracket (critical point of the
-// isolated polynomial) are resolved into the nearest FP64 roots on either
-// side, within kSideReach.  Writes the roots back into `it`.
+// v-polish of one bracket in FP64 on the FP64 resultant of the candidate's
+// system s (ok: k1_system succeeded).  A sign-change bracket from the
+// isolation is refined to width 1e-12 in v.  A bracket whose FP64 signs agree
+// (the FP32 root is displaced) takes the Newton root next to its centre;
+// failing that, and for a tangent bracket (critical point of the isolated
+// polynomial), the nearest FP64 roots on either side within kSideReach.
+// Writes the roots back into `it`.
 template <int DB>
-SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigned& lost) {
-  K1Sys<DB> s;
+SPOLY_D void k1_polish_v(const K1Sys<DB>& s, bool ok, RootItem& it, unsigned& lost) {
   const uint32_t in_flags = it.flags & 0xffu;
   it.flags = 0u;
   double r[kRD + 1];
   int deg = -1;
-  if (k1_system<DB>(tr, qd, s)) deg = k1_r64<DB>(s, r);
+  if (ok) deg = k1_r64<DB>(s, r);
   if (deg < 1) {
     ++lost;
     return;
@@ -201,6 +267,8 @@ SPOLY_D void k1_polish_v(const TriD& tr, const QueryD& qd, RootItem& it, unsigne
     v1 = true;
   } else if ((flo < 0.0) != (fhi < 0.0)) {
     r1 = bisect64(r, deg, zlo, zhi, flo, tol);
+    v1 = true;
+  } else if (newton_root64(r, deg, 0.5 * (zlo + zhi), zmin, zmax, kSideReach / t, tol, &r1)) {
     v1 = true;
   } else {
     v1 = side_root64(r, deg, t, zlo, flo, -1, zmin, zmax, &r1);
@@ -333,37 +401,54 @@ SPOLY_D int k1_item_paths(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, 
   return np;
 }
 
-// Path phase of queue item i.  The items of one candidate are contiguous in
-// the queue.  Roots equal within 1e-9 in v to a root of an earlier item of
-// the candidate, or to the item's other root, are skipped; so is a path
-// within 1e-9 in (u, v) of a path of an earlier item (two brackets around a
-// near-double root of r(v) whose Newton refinements meet), so that each
-// candidate reports a solution once, like the oracle's merge rule.
-template <int DB>
-SPOLY_D int k1_path_item(const TriD& tr, const QueryD& qd, const RootItem* queue, int64_t i, int q, int t,
-                         spoly_path (&out)[6], unsigned& n_u, const PixelFilter& pix) {
-  const RootItem it = queue[i];
-  K1Sys<DB> s;
-  if (!k1_system<DB>(tr, qd, s)) return 0;
-  int64_t first = i;
-  while (first > 0 && queue[first - 1].chain == it.chain) --first;
-  int np = k1_item_paths<DB>(s, tr, qd, it, q, t, out, 0, n_u, pix, queue + first, i - first);
-  // paths of the earlier items, recomputed (rare: candidates with several brackets)
-  for (int64_t j = first; j < i && np > 0; ++j) {
-    spoly_path prev[6];
-    unsigned n_u_prev = 0;
-    const int npv = k1_item_paths<DB>(s, tr, qd, queue[j], q, t, prev, 0, n_u_prev, pix, queue + first, j - first);
-    int keep = 0;
-    for (int k = 0; k < np; ++k) {
-      bool dup = false;
-      for (int m = 0; m < npv; ++m)
-        if (fabs(prev[m].uv[0][0] - out[k].uv[0][0]) <= 1e-9 && fabs(prev[m].uv[0][1] - out[k].uv[0][1]) <= 1e-9)
-          dup = true;
-      if (!dup) out[keep++] = out[k];
+// FP64 polish (once per item) and path phase of the n items of one
+// candidate, in their isolation order.  A root equal within 1e-9 in v to a
+// root of an earlier item, or to the item's other root, is skipped; so is a
+// path within 1e-9 in (u, v) of a path of an earlier item (two brackets
+// around a near-double root of r(v) whose Newton refinements meet), so that
+// each candidate reports a solution once, like the oracle's merge rule.
+// Every path goes to emit(path).
+constexpr int kChainHist = 24;  // earlier-item paths kept for the duplicate test
+template <int DB, typename Emit>
+SPOLY_D void k1_chain_solve(const K1Sys<DB>& s, bool ok, const TriD& tr, const QueryD& qd, RootItem* items, int n,
+                            int q, int t, const PixelFilter& pix, unsigned& lost, unsigned& n_u, Emit&& emit) {
+  for (int k = 0; k < n; ++k) {
+    RootItem it = items[k];
+    if (!(it.flags & kPolished)) {
+      k1_polish_v<DB>(s, ok, it, lost);
+      it.flags |= kPolished;
+      items[k] = it;
     }
-    np = keep;
   }
-  return np;
+  if (!ok) return;
+  double hu[kChainHist], hv[kChainHist];
+  int nh = 0;
+  for (int k = 0; k < n; ++k) {
+    spoly_path cur[6];
+    const int np = k1_item_paths<DB>(s, tr, qd, items[k], q, t, cur, 0, n_u, pix, items, k);
+    for (int m = 0; m < np; ++m) {
+      bool dup = false;
+      for (int h = 0; h < nh; ++h)
+        if (fabs(hu[h] - cur[m].uv[0][0]) <= 1e-9 && fabs(hv[h] - cur[m].uv[0][1]) <= 1e-9) dup = true;
+      if (!dup) emit(cur[m]);
+    }
+    for (int m = 0; m < np && nh < kChainHist; ++m) {
+      hu[nh] = cur[m].uv[0][0];
+      hv[nh] = cur[m].uv[0][1];
+      ++nh;
+    }
+  }
 }
+
+#ifndef SPOLY_HOST_BUILD
+// Appends one path outside the warp-aggregated append (a candidate with more
+// paths than a lane keeps).
+SPOLY_D void append_path(const K1Params& P, spoly_path p) {
+  const unsigned long long idx = atomicAdd(P.counters + C_ADMISSIBLE, 1ull);
+  if (p.flags & SPOLY_FLAG_ILL_COND) atomicAdd(P.counters + C_FLAGGED, 1ull);
+  if (P.chain_ids) p.chain = __ldg(P.chain_ids + p.chain);
+  if (idx < (unsigned long long)P.path_cap) P.paths[idx] = p;
+}
+#endif
 
 }  // namespace spoly

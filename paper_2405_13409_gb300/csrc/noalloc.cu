@@ -166,7 +166,7 @@ extern "C" spoly_status spoly_solve_noalloc(int device, void* cuda_stream, const
   }
   if (n_chains > 0) {
     if (spoly::launch_k1_isolate(P, precision, num_sms, st) != cudaSuccess ||
-        spoly::launch_k1_polish(P, num_sms, st) != cudaSuccess || spoly::launch_k1_paths(P, num_sms, st) != cudaSuccess)
+        spoly::launch_k1_finish(P, num_sms, st, nullptr, nullptr, nullptr) != cudaSuccess)
       return done(SPOLY_ECUDA, "spoly_solve_noalloc: kernel launch failed");
   }
   unsigned long long count = 0;

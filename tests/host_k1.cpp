@@ -37,18 +37,16 @@ int run(const TriD& tr, const QueryD& qd, int precision, double* out, int cap, i
   for (int i = 0; i < nq; ++i) ntang += (items[i].flags & SPOLY_FLAG_TANGENT) ? 1 : 0;
   status[4] = ntang;
   int total = 0;
-  for (int i = 0; i < nq; ++i) k1_polish_v<DB>(tr, qd, items[i], lost);
-  status[3] = int(lost);
-  for (int i = 0; i < nq; ++i) {
-    spoly_path paths[6];
-    PixelFilter nofilter{};
-    const int np = k1_path_item<DB>(tr, qd, items, i, 0, 0, paths, nu, nofilter);
-    for (int k = 0; k < np && total < cap; ++k, ++total) {
-      out[3 * total] = paths[k].uv[0][0];
-      out[3 * total + 1] = paths[k].uv[0][1];
-      out[3 * total + 2] = double(paths[k].flags);
+  PixelFilter nofilter{};
+  k1_chain_solve<DB>(s, true, tr, qd, items, nq, 0, 0, nofilter, lost, nu, [&](const spoly_path& p) {
+    if (total < cap) {
+      out[3 * total] = p.uv[0][0];
+      out[3 * total + 1] = p.uv[0][1];
+      out[3 * total + 2] = double(p.flags);
+      ++total;
     }
-  }
+  });
+  status[3] = int(lost);
   return total;
 }
 
