@@ -194,11 +194,12 @@ SPOLY_D bool flat_shaded(const TriD& tr) {
 }
 
 #ifndef SPOLY_HOST_BUILD
-// Isolation of the 32 chains [base, base + 32) by one warp: per-chain
-// numerics, then warp-aggregated counters and appends.  All lanes call it.
+// Isolation of the chains [base, base + width) by one warp (lane l < width
+// takes chain base + l): per-chain numerics, then warp-aggregated counters
+// and appends.  All lanes call it.
 template <typename T>
-SPOLY_D void isolate_warp(const K1Params& P, int64_t base, int lane) {
-  const int64_t c = base + lane;
+SPOLY_D void isolate_warp(const K1Params& P, int64_t base, int lane, int width = 32) {
+  const int64_t c = lane < width ? base + lane : P.n_chains;
   RootItem items[kRD + 1];
   int nq = 0;
   unsigned n_v = 0, n_pref = 0, n_deg = 0, n_cand = 0, n_side = 0;
@@ -239,12 +240,18 @@ SPOLY_D void isolate_warp(const K1Params& P, int64_t base, int lane) {
   }
 }
 
+// `width` chains per warp (a power of two up to 32).  A short list uses fewer
+// lanes per warp and more warps: the chains' different Bezout sizes and loop
+// counts then diverge within fewer lanes, and every FP64 warp instruction
+// costs the same whatever its active lanes (one warp per SM sub-partition
+// keeps the FP64 units busy either way).
 template <typename T>
-__global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P) {
+__global__ void __launch_bounds__(128) k1_isolate_kernel(K1Params P, int width) {
   const int lane = threadIdx.x & 31;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < P.n_chains; base += stride)
-    isolate_warp<T>(P, base, lane);
+  const int64_t n_warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * width; base < P.n_chains;
+       base += n_warps * width)
+    isolate_warp<T>(P, base, lane, width);
 }
 
 // Persistent variant: a fixed grid whose warps take `chunk` chains at a time

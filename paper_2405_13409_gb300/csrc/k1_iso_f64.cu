@@ -3,8 +3,8 @@
 
 namespace spoly {
 
-cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, int block, cudaStream_t st) {
-  k1_isolate_kernel<double><<<grid, block, 0, st>>>(P);
+cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, int block, int width, cudaStream_t st) {
+  k1_isolate_kernel<double><<<grid, block, 0, st>>>(P, width);
   return cudaGetLastError();
 }
 

@@ -16,12 +16,19 @@ SPOLY_D int64_t queue_items(const K1Params& P) {
 // polishes the run in place (once: a path re-run finds it polished) and runs
 // its path phase, so the candidate's system is built once for both.
 // Admissible paths are appended with one atomic per warp.
-__global__ void __launch_bounds__(32) k1_finish_kernel(K1Params P) {
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+__global__ void __launch_bounds__(32) k1_finish_kernel(K1Params P, int num_sms) {
   const int64_t n_items = queue_items(P);
   const int lane = threadIdx.x & 31;
-  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n_items; base += stride) {
-    const int64_t i = base + lane;
+  // lanes per warp: enough warps for one per SM sub-partition (a short queue
+  // diverges within fewer lanes; FP64 warp instructions cost the same
+  // whatever their active lanes)
+  const int64_t per = (n_items + 4 * int64_t(num_sms) - 1) / (4 * int64_t(num_sms));
+  int width = 1;
+  while (width < 32 && width < per) width <<= 1;
+  const int64_t n_warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * width; base < n_items;
+       base += n_warps * width) {
+    const int64_t i = lane < width ? base + lane : n_items;
     spoly_path out[6];
     int np = 0;
     unsigned lost = 0, n_u = 0, n_flag = 0;
@@ -88,8 +95,17 @@ cudaError_t launch_partition(const int32_t* chains, int64_t n, int32_t* k1, int3
   return cudaGetLastError();
 }
 
-cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, int block, cudaStream_t st);
-cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, int block, cudaStream_t st);
+cudaError_t launch_k1_isolate_f32(const K1Params& P, int grid, int block, int width, cudaStream_t st);
+cudaError_t launch_k1_isolate_f64(const K1Params& P, int grid, int block, int width, cudaStream_t st);
+
+// Lanes per warp for n work items: enough warps to give every SM
+// sub-partition one (4 per SM), at most 32 lanes.
+static int lanes_for(int64_t n, int num_sms) {
+  const int64_t per = (n + 4 * int64_t(num_sms) - 1) / (4 * int64_t(num_sms));
+  int w = 1;
+  while (w < 32 && w < per) w <<= 1;
+  return w;
+}
 cudaError_t launch_k1_side(const K1Params& P, int num_sms, cudaStream_t st);
 
 cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cudaStream_t st) {
@@ -97,11 +113,12 @@ cudaError_t launch_k1_isolate(const K1Params& P, int precision, int num_sms, cud
   // blocks, so that their warps spread over all SMs (each chain is one
   // thread's long serial solve)
   const int block = (P.n_chains < int64_t(num_sms) * 256) ? 32 : 128;
-  int64_t g = (P.n_chains + block - 1) / block;
+  const int width = (block == 32) ? lanes_for(P.n_chains, num_sms) : 32;
+  int64_t g = (P.n_chains + int64_t(width) * (block / 32) - 1) / (int64_t(width) * (block / 32));
   if (g < 1) g = 1;
   if (g > int64_t(num_sms) * 16 * (128 / block)) g = int64_t(num_sms) * 16 * (128 / block);
-  return (precision == SPOLY_PLAIN_FP64) ? launch_k1_isolate_f64(P, int(g), block, st)
-                                         : launch_k1_isolate_f32(P, int(g), block, st);
+  return (precision == SPOLY_PLAIN_FP64) ? launch_k1_isolate_f64(P, int(g), block, width, st)
+                                         : launch_k1_isolate_f32(P, int(g), block, width, st);
 }
 
 cudaError_t launch_k1_isolate_persistent_f32(const K1Params& P, int grid, int block, int chunk, cudaStream_t st);
@@ -134,7 +151,7 @@ cudaError_t launch_k1_finish(const K1Params& P, int num_sms, cudaStream_t st, cu
   }
   // one-warp blocks: the few thousand candidates of a step spread evenly over
   // the SMs (each lane runs a long serial chain of FP64 instructions)
-  k1_finish_kernel<<<num_sms * 32, 32, 0, st>>>(P);
+  k1_finish_kernel<<<num_sms * 32, 32, 0, st>>>(P, num_sms);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (side_st && (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) return e;
   return cudaSuccess;

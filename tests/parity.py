@@ -94,17 +94,19 @@ def project_pixels(cam, x):
     return np.where(ok, pix, -1)
 
 
-def footprint_numpy(s, cam):
-    """Brute force: triangles whose xy bbox meets each pixel's footprint box."""
+def footprint_boxes(s, cam, qs):
+    """Footprint box (xl, xh, yl, yh) of each pixel in qs: the xy box of its
+    four corner rays between the mesh's z bounds (FP32-rounded, as the
+    library takes them), with a 1e-5 relative margin; None where a corner
+    ray never descends."""
     T = s.tri
-    xs, ys, zs = T[[0, 3, 6]], T[[1, 4, 7]], T[[2, 5, 8]]
-    txl, txh, tyl, tyh = xs.min(0), xs.max(0), ys.min(0), ys.max(0)
+    zs = T[[2, 5, 8]]
     zlo, zhi = float(np.float32(zs.min())), float(np.float32(zs.max()))
     o, f, r, u = cam[0:3], cam[3:6], cam[6:9], cam[9:12]
     th, asp, w, h = cam[12], cam[13], int(cam[14]), int(cam[15])
-    out = set()
-    for q in range(w * h):
-        ix, iy = q % w, q // w
+    out = []
+    for q in qs:
+        ix, iy = int(q) % w, int(q) // w
         pts = []
         for k in range(4):
             sx = -1 + 2 * (ix + (k & 1)) / w
@@ -117,11 +119,25 @@ def footprint_numpy(s, cam):
                 t = (z - o[2]) / d[2]
                 pts.append(o + t * d)
         if pts is None:
+            out.append(None)
             continue
         pts = np.array(pts)
         m = 1e-5 * (1 + max(abs(pts[:, 0].min()), abs(pts[:, 1].max())))
-        xl, xh = pts[:, 0].min() - m, pts[:, 0].max() + m
-        yl, yh = pts[:, 1].min() - m, pts[:, 1].max() + m
+        out.append((pts[:, 0].min() - m, pts[:, 0].max() + m, pts[:, 1].min() - m, pts[:, 1].max() + m))
+    return out
+
+
+def footprint_numpy(s, cam):
+    """Brute force: triangles whose xy bbox meets each pixel's footprint box."""
+    T = s.tri
+    xs, ys = T[[0, 3, 6]], T[[1, 4, 7]]
+    txl, txh, tyl, tyh = xs.min(0), xs.max(0), ys.min(0), ys.max(0)
+    w, h = int(cam[14]), int(cam[15])
+    out = set()
+    for q, b in enumerate(footprint_boxes(s, cam, range(w * h))):
+        if b is None:
+            continue
+        xl, xh, yl, yh = b
         hit = np.where(~((txh < xl) | (txl > xh) | (tyh < yl) | (tyl > yh)))[0]
         out.update((q, int(t)) for t in hit)
     return out

@@ -57,6 +57,27 @@ def _pair(gpu_rows, ref_rows, tol=1e-5):
     return len(d_all), un_f, un_u, float(d.max()), float(np.quantile(d, 0.99))
 
 
+def _block_footprint(s, cam, origins, side=16):
+    """(pixel, triangle, -1) candidates of the 16x16-pixel blocks at the given
+    origins: the triangles whose xy box meets the pixel's footprint box (its
+    four corner rays between the mesh's z bounds)."""
+    from tests.parity import footprint_boxes
+    T = s.tri
+    xs, ys = T[[0, 3, 6]], T[[1, 4, 7]]
+    txl, txh, tyl, tyh = xs.min(0), xs.max(0), ys.min(0), ys.max(0)
+    w = int(cam[14])
+    rows = []
+    for x0, y0 in origins:
+        qs = np.array([iy * w + ix for iy in range(y0, y0 + side) for ix in range(x0, x0 + side)])
+        for q, b in zip(qs, footprint_boxes(s, cam, qs)):
+            if b is None:
+                continue
+            bx0, bx1, by0, by1 = b
+            t = np.where(~((txh < bx0) | (txl > bx1) | (tyh < by0) | (tyl > by1)))[0]
+            rows.append(np.stack([np.full(t.size, q), t, -np.ones(t.size, np.int64)], -1))
+    return np.ascontiguousarray(np.unique(np.concatenate(rows), axis=0).astype(np.int32))
+
+
 def _rows1(paths, gpu):
     if gpu:
         return [((int(p["query"]), int(p["tri"][0])), p["uv"][:2], p["flags"]) for p in paths]
@@ -129,19 +150,25 @@ def main():
     mine = p[[(int(a), int(b), int(c)) in rows for a, b, c in zip(p["query"], p["tri"][:, 0], p["tri"][:, 1])]]
     out.append(("TT slab 16x16+16x16 cells x 64x64 receivers (culled chains with paths + 300 seeded)",
                 sample.shape[0], mine.size, ref.size, *_pair(_rows2(mine, True), _rows2(ref, False))))
-    # glints: distinct triangles + pixel assignment; oracle on seeded blocks
-    import bench
+    # glints: distinct triangles + pixel assignment; the oracle solves every
+    # footprint candidate of 16x16-pixel blocks, 6 around seeded lit pixels
+    # of the GPU image and 2 at seeded positions
     s = scenes.glint_scene()
     cam = s.meta["camera"].as_array()
     p, _ = solve(s, binding.CHAINS_FOOTPRINT_UNIQUE, camera=cam, flags=binding.SOLVE_PIXEL_ASSIGN)
-    fp, nb = bench.footprint_sample(s, cam, 2048, 11)
+    w, h = int(cam[14]), int(cam[15])
+    rng = np.random.default_rng(11)
+    lit = rng.choice(np.unique(p["query"]), 6, replace=False)
+    origins = [(int(min(max(q % w - 8, 0), w - 16)), int(min(max(q // w - 8, 0), h - 16))) for q in lit]
+    origins += [(int(rng.integers(0, w - 15)), int(rng.integers(0, h - 15))) for _ in range(2)]
+    fp = _block_footprint(s, cam, origins)
     ref, _ = oracle.solve(s.tri, s.x_first, s.x_last, s.eta, s.types, s.k, fp)
     from tests.parity import project_pixels
     ref = ref[project_pixels(cam, ref["x"][:, :3]) == ref["query"]]
     pix = np.unique(fp[:, 0])
     mine = p[np.isin(p["query"], pix)]
-    out.append((f"glints 1024x1024 cells, 512x512 px ({nb} seeded 16x16-pixel blocks)", fp.shape[0], mine.size,
-                ref.size, *_pair(_rows1(mine, True), _rows1(ref, False))))
+    out.append((f"glints 1024x1024 cells, 512x512 px (8 16x16-pixel blocks: 6 around lit pixels, 2 seeded)",
+                fp.shape[0], mine.size, ref.size, *_pair(_rows1(mine, True), _rows1(ref, False))))
     # batched mixed workload at its full size (4096 queries); the oracle
     # solves every chain of 24 seeded 1-bounce queries and a sample of the
     # culled 2-bounce chains

@@ -102,6 +102,40 @@ def test_corridor_candidate_sample_matches_oracle(ctx, corridor):
     assert stats["candidates"] == chains.shape[0]
 
 
+def test_corridor_large_sample_reaches_fp64_resampling(ctx, corridor):
+    """About 1,300 (floor, ceiling) pairs around 16 planted paths and random
+    pairs in mixed precision, against the RR oracle (in parallel): unflagged
+    paths agree one to one, flagged disagreements stay within 1e-4 of the
+    candidates, and the FP64 re-sampling of noisy systems runs."""
+    from tests import oracle_pool
+    cases = planted_corridor_cases(32, 16)
+    half = corridor.n_tris // 2
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    rng = np.random.default_rng(5)
+    rows = []
+    for i, c in enumerate(cases):
+        for d1 in (-2, -1, 0, 1, 2):
+            for d2 in (-34, -2, 0, 2, 32):
+                a, b = c[2] + d1, c[3] + d2
+                if 0 <= a < half and half <= b < corridor.n_tris:
+                    rows.append([i, a, b])
+        for _ in range(60):
+            rows.append([i, int(rng.integers(0, half)), int(rng.integers(half, corridor.n_tris))])
+    chains = np.array(rows, np.int32)
+    paths, stats = _solve(ctx, corridor.tri, x0s, x3s, chains, *_rr(len(cases)))
+    ref = oracle_pool.rr_solve(corridor.tri, x0s, x3s, chains)
+    matched, un, worst = _compare(paths, ref)
+    bad = [u for u in un if not (u[3] & ALLOWED)]
+    assert not bad, (bad, stats)
+    assert len(un) <= max(1, 1e-4 * chains.shape[0]), (un, stats)
+    assert worst < 1e-9
+    assert stats["k2_fp64_samples"] > 0, stats
+    for i, c in enumerate(cases):
+        got = paths[paths["query"] == i]
+        assert any(np.max(np.abs(p["uv"].ravel() - c[4])) < 1e-9 for p in got), (i, c[4], got["uv"])
+
+
 def test_rr_and_one_bounce_chains_in_one_list(ctx, corridor):
     """One explicit list with RR chains and 1-bounce reflection chains on
     the floor: each part equals its own oracle (RR oracle, C oracle)."""

@@ -142,6 +142,59 @@ def test_candidate_sample_matches_oracle(ctx):
     assert stats["candidates"] == chains.shape[0]
 
 
+@pytest.mark.parametrize("table_kind", ["oracle", "library default"])
+def test_large_sample_reaches_fp64_resampling_and_split_pieces(ctx, table_kind):
+    """About 4,000 (top, bottom) pairs around 48 planted paths in mixed
+    precision, half of them seen from a grazing light so that the sqrt
+    argument over the top triangle spans two pieces (SQRT_SPLIT): against
+    the TT oracle with the same sqrt table (the oracle's fitted pieces, or
+    the library's default pieces fed to the oracle).  Unflagged paths agree
+    one to one, flagged disagreements stay within 1e-4 of the candidates,
+    the FP64 re-sampling of noisy systems runs, and split paths are found."""
+    from tests import oracle_pool
+    s = scenes.slab_scene(seed=0, n_cells=16, n_recv=4)
+    half = s.n_tris // 2
+    cases = planted_slab_cases(12, 24) + planted_slab_cases(21, 24, x0=[-2.2, 0.0, 1.0], x_range=(-0.45, -0.1))
+    x0s = np.array([c[0] for c in cases])
+    x3s = np.array([c[1] for c in cases])
+    rng = np.random.default_rng(3)
+    rows = []
+    for i, c in enumerate(cases):
+        t1, t2 = c[2], c[3]
+        for d1 in (-2, -1, 0, 1, 2):
+            for d2 in (-34, -2, 0, 2, 32):
+                a, b = t1 + d1, t2 + d2
+                if 0 <= a < half and half <= b < s.n_tris:
+                    rows.append([i, a, b])
+        for _ in range(58):
+            rows.append([i, int(rng.integers(0, half)), int(rng.integers(half, s.n_tris))])
+    chains = np.array(rows, np.int32)
+    table = _table() if table_kind == "oracle" else binding.spoly_default_sqrt_table()
+    n = x0s.shape[0]
+    eta = np.tile([1.0, 1.5, 1.0], (n, 1))
+    types = np.full((n, 2), binding.SPOLY_T, np.int32)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (s.tri, x0s, x3s, eta, types, np.full(n, 2, np.int32))]
+    mesh, q = ctx.mesh(d[0]), ctx.queries(*d[1:])
+    ch = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=chains)
+    sol = ctx.spoly_solve(mesh, q, ch, precision=binding.MIXED, sqrt_table=table)
+    paths, stats = ctx.spoly_paths(sol), ctx.spoly_stats(sol)
+    ctx.spoly_solution_free(sol)
+    ctx.spoly_chains_free(ch)
+    ref, _ = oracle_pool.tt_solve(s.tri, x0s, x3s, eta, chains, table[1])
+    matched, un, worst = _compare(paths, ref)
+    bad = [u for u in un if not (u[3] & ALLOWED)]
+    assert not bad, (bad, stats)
+    assert len(un) <= max(1, 1e-4 * chains.shape[0]), (un, stats)
+    assert worst < 1e-9
+    assert stats["k2_fp64_samples"] > 0, stats
+    split = paths[(paths["flags"] & binding.FLAG_SQRT_SPLIT) != 0]
+    assert split.size >= 8, (split.size, stats)
+    assert np.sum((ref["flags"] & binding.FLAG_SQRT_SPLIT) != 0) == split.size
+    for i, c in enumerate(cases):
+        got = paths[paths["query"] == i]
+        assert any(np.max(np.abs(p["uv"].ravel() - c[4])) < 1e-9 for p in got), (i, c[4], got["uv"])
+
+
 def test_flat_slab_fermat(ctx):
     rng = np.random.default_rng(4)
     P1 = np.array([[-1.0, -1.0, 0.0], [1.5, -1.0, 0.0], [-1.0, 1.5, 0.0]])

@@ -181,19 +181,22 @@ def _ray_tri(o, d, P):
     return u, (d @ qv) / det, (e2 @ qv) / det
 
 
-def planted_slab_cases(seed, n, n_cells=16):
+def planted_slab_cases(seed, n, n_cells=16, x0=None, x_range=None):
     """Exact TT paths traced through the slab generator's surfaces: a point
     of a top triangle, Snell refraction into the slab, the bottom triangle
-    it hits, Snell refraction out, and the receiver on z = -1."""
+    it hits, Snell refraction out, and the receiver on z = -1.  x0 defaults
+    to the scene's light; x_range limits the top triangles to those whose
+    first vertex has x in [lo, hi]."""
     from paper_2405_13409_gb300 import scenes
     s = scenes.slab_scene(seed=0, n_cells=n_cells, n_recv=4)
     T = s.tri
     half = T.shape[1] // 2
     rng = np.random.default_rng(seed)
-    x0 = s.x_first[0]
+    x0 = s.x_first[0] if x0 is None else np.asarray(x0, float)
+    tops = np.arange(half) if x_range is None else np.where((T[0, :half] >= x_range[0]) & (T[0, :half] <= x_range[1]))[0]
     out = []
     while len(out) < n:
-        t1 = int(rng.integers(0, half))
+        t1 = int(tops[rng.integers(0, tops.size)])
         u, v = rng.random(2)
         if u + v > 1:
             u, v = 1 - u, 1 - v
