@@ -92,8 +92,8 @@ def launches_per_step(workload, use_gate, stats):
 # value the capture was taken on.
 TRAFFIC = {
     "gate_kernel": {"workload": "glints", "sources": ["gate.cu", "gate.cuh", "mlp.cuh", "common.cuh", "umma.cuh"],
-                    "sources_sha256": "12e06fa080a9888be0bafdef5767136f9bd98e0e68857223e1088dd16943a9be",
-                    "bytes_per_launch": 395362048 + 3331328},
+                    "sources_sha256": "30b7222bc639f60a214b9d45fdb1bd9c887c3655e4830313d6aadba3ddc10379",
+                    "bytes_per_launch": 288524544 + 3619840},
     "k1_isolate_kernel": {"workload": "refract",
                           "sources": ["common.cuh", "polys.cuh", "laplace_gen.cuh", "k1_sys.cuh", "k1_iso.cuh",
                                       "k1_iso_f32.cu"], "sources_sha256": None, "bytes_per_launch": None},

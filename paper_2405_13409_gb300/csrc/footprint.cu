@@ -40,6 +40,7 @@ float o2f_host(int i) {
 // grid and footprint passes read instead of the six FP64 coordinates.
 __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
   float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  float wx = 0.0f, wy = 0.0f;  // largest box width and height
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < M.n_tris; t += stride) {
     float tl[3] = {3e38f, 3e38f, 3e38f}, th[3] = {-3e38f, -3e38f, -3e38f};
@@ -54,6 +55,16 @@ __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
       lo[c] = fminf(lo[c], tl[c]);
       hi[c] = fmaxf(hi[c], th[c]);
     }
+    wx = fmaxf(wx, th[0] - tl[0]);
+    wy = fmaxf(wy, th[1] - tl[1]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    wx = fmaxf(wx, __shfl_xor_sync(0xffffffffu, wx, o));
+    wy = fmaxf(wy, __shfl_xor_sync(0xffffffffu, wy, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(bounds + 6, f2o(wx));
+    atomicMax(bounds + 7, f2o(wy));
   }
   for (int c = 0; c < 3; ++c) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -70,6 +81,7 @@ __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
 __global__ void init_bounds_kernel(int* bounds) {
   if (threadIdx.x < 3) bounds[threadIdx.x] = f2o(3e38f);
   else if (threadIdx.x < 6) bounds[threadIdx.x] = f2o(-3e38f);
+  else if (threadIdx.x < 8) bounds[threadIdx.x] = f2o(0.0f);
 }
 
 struct GridGeom {
@@ -178,17 +190,23 @@ constexpr int kPixCand = 128;  // candidates per pixel kept by the count pass fo
 
 // Candidates of pixel q in emission order: each one goes to emit(t); returns
 // their number.
+// ext < 0: every triangle sits in every cell its box meets, and a triangle
+// is emitted from the first cell it shares with the footprint.  ext >= 0
+// (single-cell grid): every triangle sits in its box's lower-corner cell
+// only, and the traversal starts ext cells lower in x and y.
 template <typename Emit>
 SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const CamF& C, float zlo, float zhi,
                                  int64_t q, const int* cell_count, const int64_t* cell_off, const int32_t* entries,
-                                 Emit emit, int64_t cap = INT64_MAX) {
+                                 Emit emit, int64_t cap = INT64_MAX, int ext = -1) {
   float xl, xh, yl, yh;
   int64_t n = 0;
   if (!pixel_footprint(C, q, zlo, zhi, xl, xh, yl, yh)) return 0;
   int fx0, fx1, fy0, fy1;
   cell_range(G, xl, xh, yl, yh, fx0, fx1, fy0, fy1);
-  for (int cy = fy0; cy <= fy1; ++cy)
-    for (int cx = fx0; cx <= fx1; ++cx) {
+  const bool single = ext >= 0;
+  const int sx0 = single ? max(0, fx0 - ext) : fx0, sy0 = single ? max(0, fy0 - ext) : fy0;
+  for (int cy = sy0; cy <= fy1; ++cy)
+    for (int cx = sx0; cx <= fx1; ++cx) {
       const int64_t cell = int64_t(cy) * G.gx + cx;
       const int64_t b = cell_off[cell], e = min(b + cell_count[cell], cap);
       // four entries at a time: their index loads, then their box gathers,
@@ -204,9 +222,11 @@ SPOLY_D int64_t pixel_candidates(const float4* boxes, const GridGeom& G, const C
         for (int u = 0; u < 4; ++u) {
           const float txl = bx[u].x, txh = bx[u].y, tyl = bx[u].z, tyh = bx[u].w;
           if (t[u] < 0 || txh < xl || txl > xh || tyh < yl || tyl > yh) continue;
-          int tx0, tx1, ty0, ty1;
-          cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
-          if (cx != max(tx0, fx0) || cy != max(ty0, fy0)) continue;  // emitted from its first shared cell
+          if (!single) {
+            int tx0, tx1, ty0, ty1;
+            cell_range(G, txl, txh, tyl, tyh, tx0, tx1, ty0, ty1);
+            if (cx != max(tx0, fx0) || cy != max(ty0, fy0)) continue;  // emitted from its first shared cell
+          }
           emit(n, t[u]);
           ++n;
         }
@@ -238,8 +258,16 @@ struct FpUniqueDev {
   GridGeom G;
   unsigned long long n_entries, pairs, n_unique;
   int32_t differ;  // some query differs from query 0
+  int32_t single;  // 1: each triangle sits in the cell of its box's lower corner only
+  int32_t ext;     // single: the most cells a box spans beyond its lower corner's (set by pass 0)
   int32_t pad;
 };
+
+// Single-cell insertion is used while the widest triangle box is narrower
+// than kSingleCellSpan cells: a pixel's traversal then reaches `ext` cells
+// further down in x and y (ext = the largest span of a box beyond its lower
+// corner's cell), and no triangle is met twice.
+constexpr float kSingleCellSpan = 2.0f;
 
 // Square cells over the bounds' larger extent, g x g of them.
 __global__ void grid_setup_kernel(const int* bounds, int g, FpUniqueDev* info) {
@@ -250,24 +278,39 @@ __global__ void grid_setup_kernel(const int* bounds, int g, FpUniqueDev* info) {
   info->G.inv = float(g) / w;
   info->G.gx = g;
   info->G.gy = g;
+  const float span = fmaxf(o2f(bounds[6]), o2f(bounds[7])) * info->G.inv;
+  info->single = (span < kSingleCellSpan) ? 1 : 0;
+  info->ext = 0;
 }
 
-// pass 0: count entries per cell; pass 1: fill, writing only below cap.
-__global__ void grid_insert_dev_kernel(MeshView M, const float4* boxes, const FpUniqueDev* info, int* cell_count,
+// pass 0: count entries per cell (single-cell mode: also the largest span
+// beyond the lower corner's cell); pass 1: fill, writing only below cap.
+__global__ void grid_insert_dev_kernel(MeshView M, const float4* boxes, FpUniqueDev* info, int* cell_count,
                                        const int64_t* cell_off, int32_t* entries, int64_t cap, int pass) {
   const GridGeom G = info->G;
+  const bool single = info->single != 0;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int span = 0;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < M.n_tris; t += stride) {
     float xl, xh, yl, yh;
     tri_bbox(boxes, t, xl, xh, yl, yh);
     int cx0, cx1, cy0, cy1;
     cell_range(G, xl, xh, yl, yh, cx0, cx1, cy0, cy1);
+    if (single) {
+      span = max(span, max(cx1 - cx0, cy1 - cy0));
+      cx1 = cx0;
+      cy1 = cy0;
+    }
     for (int cy = cy0; cy <= cy1; ++cy)
       for (int cx = cx0; cx <= cx1; ++cx) {
         const int64_t cell = int64_t(cy) * G.gx + cx;
         const int slot = atomicAdd(cell_count + cell, 1);
         if (pass == 1 && cell_off[cell] + slot < cap) entries[cell_off[cell] + slot] = int32_t(t);
       }
+  }
+  if (single && pass == 0) {
+    span = __reduce_max_sync(0xffffffffu, span);
+    if ((threadIdx.x & 31) == 0 && span > 0) atomicMax(&info->ext, span);
   }
 }
 
@@ -281,6 +324,7 @@ __global__ void footprint_mark_kernel(const float4* boxes, FpUniqueDev* info, co
                                       int64_t n_pixels, const int* cell_count, const int64_t* cell_off,
                                       const int32_t* entries, int64_t cap, uint8_t* mark) {
   const GridGeom G = info->G;
+  const int ext = info->single ? info->ext : -1;
   const float zlo = o2f(bounds[2]), zhi = o2f(bounds[5]);
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q0 = int64_t(blockIdx.x) * blockDim.x; q0 < n_pixels; q0 += stride) {
@@ -288,7 +332,7 @@ __global__ void footprint_mark_kernel(const float4* boxes, FpUniqueDev* info, co
     unsigned n = 0;
     if (q < n_pixels)
       n = unsigned(pixel_candidates(boxes, G, C, zlo, zhi, q, cell_count, cell_off, entries,
-                                    [&](int64_t, int32_t t) { mark[t] = 1; }, cap));
+                                    [&](int64_t, int32_t t) { mark[t] = 1; }, cap, ext));
     warp_count(&info->pairs, n);
   }
 }

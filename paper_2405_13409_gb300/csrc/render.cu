@@ -111,6 +111,7 @@ struct VisView {
   const int32_t* entries;
   const int* zlo;
   const int* zhi;
+  double zmin, zmax;  // the mesh's z range, padded: a segment outside it meets no triangle
 };
 
 // Segment a -> b against triangle t (FP64 Moller-Trumbore): a hit strictly
@@ -152,7 +153,9 @@ SPOLY_D bool segment_blocked(const VisView& V, d3 a, d3 b, int ea, int eb) {
     t1 = fmin(t1, tb);
     return t0 <= t1;
   };
-  if (!clip(a.x, d.x, X0, X1) || !clip(a.y, d.y, Y0, Y1)) return false;
+  // and to the mesh's z slab: from a camera or a light above a heightfield,
+  // only the segment's end near the surface needs the walk
+  if (!clip(a.x, d.x, X0, X1) || !clip(a.y, d.y, Y0, Y1) || !clip(a.z, d.z, V.zmin, V.zmax)) return false;
   // 2D DDA from the entry cell
   const double px = a.x + t0 * d.x, py = a.y + t0 * d.y;
   int cx = max(0, min(G.gx - 1, int(floor((px - G.x0) * G.inv))));
@@ -385,7 +388,9 @@ spoly_status spoly_visibility(spoly_ctx* ctx, const spoly_mesh* mesh, const spol
   CK(ctx->vis_entries.ensure(size_t(std::max<int64_t>(n_entries, 1)) * 4), "visibility grid entries");
   vis_grid_kernel<<<g, 256, 0, s>>>(mv, G, count, zlo, zhi, off, cursor, static_cast<int32_t*>(ctx->vis_entries.p), 1);
   CK(cudaGetLastError(), "visibility grid");
-  VisView V{mv, G, count, off, static_cast<const int32_t*>(ctx->vis_entries.p), zlo, zhi};
+  const double zpad = 1e-5 * (1.0 + std::max(std::fabs(bh[2]), std::fabs(bh[5])));
+  VisView V{mv, G, count, off, static_cast<const int32_t*>(ctx->vis_entries.p), zlo, zhi, double(bh[2]) - zpad,
+            double(bh[5]) + zpad};
   CK(ctx->flag.ensure(16), "visibility count");
   unsigned long long* nv = static_cast<unsigned long long*>(ctx->flag.p);
   CK(cudaMemsetAsync(nv, 0, 8, s), "visibility count");
