@@ -67,7 +67,7 @@ BF16_PEAK_TFLOPS = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["b
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
 # Kernel launches per step, counted from the committed ncu launch list of
 # each workload.
-LAUNCHES_PER_STEP = {("refract", False): 6, ("reflect", False): 3, ("glints", False): 15, ("glints", True): 16}
+LAUNCHES_PER_STEP = {("refract", False): 7, ("reflect", False): 4, ("glints", False): 15, ("glints", True): 16}
 # 2-bounce solve: systems count + fill, then per batch of <= 16,384 systems the
 # build, six FP32 sign classes, five FP64 re-sampling chunk classes and five
 # re-sampling scan classes, five polish classes, the active-chain list and the
@@ -84,8 +84,10 @@ def launches_per_step(workload, use_gate, stats):
         tt = TT_FIXED + TT_PER_BATCH * batches
         if workload in ("slab", "corridor"):
             return 5 + 1 + tt  # cone cull (flag, shared check, forward boxes, pairs, chains), partition
-        # explicit validation + cone test, gate, partition, persistent isolation, side solve, finish
-        return 2 + (1 if use_gate else 0) + 1 + 3 + tt
+        # explicit validation + cone test, gate, then the graph: partition, persistent isolation, side
+        # solve, finish, and the device-driven 2-bounce pass (its 31 launches plus 3 of its scan),
+        # counted from the committed launch list
+        return 2 + (1 if use_gate else 0) + 4 + 31
     return LAUNCHES_PER_STEP.get((workload, use_gate), 7)
 # DRAM bytes (read + write) per launch from an ncu capture of the kernel on
 # the workload named, reported only while the kernel's sources hash to the
