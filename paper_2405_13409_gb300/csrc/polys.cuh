@@ -410,6 +410,69 @@ SPOLY_D void refine_root(const T (&w)[DM + 1], int j, T& a, T& b, T fa, T tol) {
       }
     }
   } else {
+    // FP32 first: safeguarded Newton on the FP32-rounded coefficients to
+    // FP32 accuracy, then at most three FP64 Newton steps from there and the
+    // FP64 sign test of a bracket of width tol around the result.  Each FP32
+    // instruction costs a fraction of an FP64 one on this part; any failure
+    // falls through to the FP64 search below, from the original bracket.
+    {
+      float wf[DM + 1];
+#pragma unroll
+      for (int i = 0; i <= DM; ++i) wf[i] = (i >= j) ? float(w[i]) : 0.0f;
+      float af = float(a), bf = float(b), faf = float(fa);
+      float x = 0.5f * (af + bf);
+      float dxo = bf - af;
+      for (int it = 0; it < 40; ++it) {
+        float f, df;
+        horner_from_d<float, DM>(wf, j, x, &f, &df);
+        if (f == 0.0f) break;
+        if ((f < 0.0f) == (faf < 0.0f)) {
+          af = x;
+          faf = f;
+        } else {
+          bf = x;
+        }
+        const float xn = x - f / df;
+        float xs;
+        if (!(xn > af && xn < bf) || fabsf(2.0f * f) > fabsf(dxo * df)) {
+          xs = 0.5f * (af + bf);
+        } else {
+          xs = xn;
+        }
+        dxo = fabsf(xs - x);
+        if (!(xs > af && xs < bf) || xs == x) break;
+        x = xs;
+      }
+      double xd = double(x);
+      bool conv = false;
+      for (int it = 0; it < 3 && xd > a && xd < b; ++it) {
+        double f, df;
+        horner_from_d<double, DM>(w, j, xd, &f, &df);
+        if (f == 0.0) {
+          a = b = xd;
+          return;
+        }
+        const double st = f / df;
+        xd -= st;
+        if (fabs(st) <= 0.25 * tol) {
+          conv = true;
+          break;
+        }
+      }
+      if (conv && xd > a && xd < b) {
+        const double l = fmax(a, xd - 0.5 * tol), h = fmin(b, xd + 0.5 * tol);
+        const double fl = horner_from<double, DM>(w, j, l), fh = horner_from<double, DM>(w, j, h);
+        if (fl == 0.0 || fh == 0.0) {
+          a = b = (fl == 0.0) ? l : h;
+          return;
+        }
+        if ((fl < 0.0) == (fa < 0.0) && (fh < 0.0) != (fa < 0.0)) {
+          a = l;
+          b = h;
+          return;
+        }
+      }
+    }
     T x = T(0.5) * (a + b), dx = b - a, dxold = b - a;
     for (int it = 0; it < 96; ++it) {
       T f, df;
