@@ -13,15 +13,46 @@ namespace spoly {
 // One side chain per thread: FP64 isolation, polish and path phase, so the
 // kernel needs nothing from the bracket queue and can run beside the queue's
 // polish.  A path re-run (P.rerun) repeats the solve but counts only paths.
+// The isolation kernels' post-Laplace steps on the FP64 resultant, at the
+// degree bound of the candidate's Bezout size (so that the FP64 loops run over
+// that many coefficients, not kRD).
+template <int RD, int DB>
+SPOLY_D int finish_rd(const K1Sys<DB>& s, const double (&r64)[kRD + 1], RootItem (&items)[kRD + 1], int c,
+                      unsigned& n_v, unsigned& n_pref) {
+  double r[RD + 1];
+#pragma unroll
+  for (int k = 0; k <= RD; ++k) r[k] = r64[k];
+  return k1_finish<double, RD, DB>(s, r, r, items, c, n_v, n_pref);
+}
+
+template <int DB>
+SPOLY_D int finish_sized(const K1Sys<DB>& s, const double (&r64)[kRD + 1], RootItem (&items)[kRD + 1], int c,
+                         unsigned& n_v, unsigned& n_pref) {
+  constexpr int ED = DB + 1;  // entry degree bound of the Bezout matrix (a has total degree 2)
+  if constexpr (DB == 4) {
+    if (s.n == 4 || s.n == 2) return finish_rd<4 * (ED - 4 + 1), DB>(s, r64, items, c, n_v, n_pref);
+    if (s.n == 3) return finish_rd<3 * (ED - 3 + 1), DB>(s, r64, items, c, n_v, n_pref);
+  } else {
+    if (s.n == 6 || s.n == 2) return finish_rd<6 * (ED - 6 + 1), DB>(s, r64, items, c, n_v, n_pref);
+    if (s.n == 5 || s.n == 3) return finish_rd<5 * (ED - 5 + 1), DB>(s, r64, items, c, n_v, n_pref);
+    if (s.n == 4) return finish_rd<4 * (ED - 4 + 1), DB>(s, r64, items, c, n_v, n_pref);
+  }
+  return finish_rd<kRD, DB>(s, r64, items, c, n_v, n_pref);
+}
+
 template <int DB, typename Emit>
 SPOLY_D int side_solve(const TriD& tr, const QueryD& qd, int c, int q, int t, const PixelFilter& pix, unsigned& n_v,
                        unsigned& n_pref, unsigned& lost, unsigned& n_u, Emit&& emit) {
   K1Sys<DB> s;
   if (!k1_system<DB>(tr, qd, s)) return -1;
+  // the FP64 resultant once, for the isolation (the isolation kernels'
+  // post-Laplace steps on it; it is already normalised and trimmed, which
+  // they repeat exactly) and for the polish
+  double r64[kRD + 1];
+  const int deg64 = k1_r64<DB>(s, r64);
   RootItem items[kRD + 1];
-  int r = k1_isolate_dispatch<double, DB>(s, items, c, n_v, n_pref);
-  if (r == -2) r = k1_generic_one<DB>(s, items, c, n_v, n_pref);
-  if (r > 0) k1_chain_solve<DB>(s, true, tr, qd, items, r, q, t, pix, lost, n_u, emit);
+  const int r = finish_sized<DB>(s, r64, items, c, n_v, n_pref);
+  if (r > 0) k1_chain_solve<DB>(s, true, tr, qd, items, r, q, t, pix, lost, n_u, emit, r64, deg64);
   return r;
 }
 

@@ -29,9 +29,11 @@ SPOLY_NOINLINE void k1_r64_generic(const K1Sys<DB>& s, double (&r)[kRD + 1]) {
 
 // FP64 resultant r(z) of a candidate's scaled system (the same Bezout entries
 // and Laplace expansion as the isolation, in FP64), normalised by a power of
-// two and trimmed like the isolation's.  Returns its degree (< 1: none).
+// two and trimmed like the isolation's.  Returns its degree (< 1: none; -1
+// when r vanishes).  Out of line: a kernel that calls it from several places
+// holds one copy of the expansions.
 template <int DB>
-SPOLY_D int k1_r64(const K1Sys<DB>& s, double (&r)[kRD + 1]) {
+SPOLY_NOINLINE int k1_r64(const K1Sys<DB>& s, double (&r)[kRD + 1]) {
   constexpr int ED = DB + 1;
 #pragma unroll
   for (int c = 0; c <= kRD; ++c) r[c] = 0.0;
@@ -231,13 +233,22 @@ SPOLY_D uint32_t ill_flag64(const double (&r)[kRD + 1], int deg, double t, doubl
 // failing that, and for a tangent bracket (critical point of the isolated
 // polynomial), the nearest FP64 roots on either side within kSideReach.
 // Writes the roots back into `it`.
+// r64 / deg64: the candidate's FP64 resultant when the caller has it
+// (nullptr: formed here).
 template <int DB>
-SPOLY_D void k1_polish_v(const K1Sys<DB>& s, bool ok, RootItem& it, unsigned& lost) {
+SPOLY_D void k1_polish_v(const K1Sys<DB>& s, bool ok, RootItem& it, unsigned& lost, const double* r64 = nullptr,
+                         int deg64 = -1) {
   const uint32_t in_flags = it.flags & 0xffu;
   it.flags = 0u;
   double r[kRD + 1];
   int deg = -1;
-  if (ok) deg = k1_r64<DB>(s, r);
+  if (ok && r64) {
+#pragma unroll
+    for (int c = 0; c <= kRD; ++c) r[c] = r64[c];
+    deg = deg64;
+  } else if (ok) {
+    deg = k1_r64<DB>(s, r);
+  }
   if (deg < 1) {
     ++lost;
     return;
@@ -411,11 +422,12 @@ SPOLY_D int k1_item_paths(const K1Sys<DB>& s, const TriD& tr, const QueryD& qd, 
 constexpr int kChainHist = 24;  // earlier-item paths kept for the duplicate test
 template <int DB, typename Emit>
 SPOLY_D void k1_chain_solve(const K1Sys<DB>& s, bool ok, const TriD& tr, const QueryD& qd, RootItem* items, int n,
-                            int q, int t, const PixelFilter& pix, unsigned& lost, unsigned& n_u, Emit&& emit) {
+                            int q, int t, const PixelFilter& pix, unsigned& lost, unsigned& n_u, Emit&& emit,
+                            const double* r64 = nullptr, int deg64 = -1) {
   for (int k = 0; k < n; ++k) {
     RootItem it = items[k];
     if (!(it.flags & kPolished)) {
-      k1_polish_v<DB>(s, ok, it, lost);
+      k1_polish_v<DB>(s, ok, it, lost, r64, deg64);
       it.flags |= kPolished;
       items[k] = it;
     }
