@@ -11,6 +11,7 @@
 // keeps each pixel's first candidates, so the fill copies them instead of
 // traversing the grid again (pixels with more candidates traverse it again).
 #include <algorithm>
+#include <climits>
 #include <cstring>
 
 #include "k1.cuh"
@@ -38,25 +39,40 @@ float o2f_host(int i) {
 // Mesh bounds ([0..2] min xyz, [3..5] max xyz as ordered ints; slack added
 // by the caller) and every triangle's FP32 xy box (xl, xh, yl, yh), which the
 // grid and footprint passes read instead of the six FP64 coordinates.
+// Ordered-int64 keys of doubles: integer min / max on them order the values,
+// so the FP64 comparisons of the box run on the integer pipe (the FP64 pipe
+// takes about 64 cycles per warp instruction on this part).
+SPOLY_D long long d2o(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : b ^ 0x7fffffffffffffffll;
+}
+SPOLY_D double o2d(long long o) { return __longlong_as_double(o >= 0 ? o : o ^ 0x7fffffffffffffffll); }
+
 __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
   float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
-  float wx = 0.0f, wy = 0.0f;  // largest box width and height
+  long long zlo = LLONG_MAX, zhi = LLONG_MIN;  // z range, as keys (converted once per thread)
+  float wx = 0.0f, wy = 0.0f;                  // largest box width and height
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < M.n_tris; t += stride) {
-    float tl[3] = {3e38f, 3e38f, 3e38f}, th[3] = {-3e38f, -3e38f, -3e38f};
-    for (int v = 0; v < 3; ++v)
-      for (int c = 0; c < 3; ++c) {
-        const float x = float(M.tri[int64_t(3 * v + c) * M.n_tris + t]);
-        tl[c] = fminf(tl[c], x);
-        th[c] = fmaxf(th[c], x);
-      }
-    boxes[t] = make_float4(tl[0], th[0], tl[1], th[1]);
-    for (int c = 0; c < 3; ++c) {
-      lo[c] = fminf(lo[c], tl[c]);
-      hi[c] = fmaxf(hi[c], th[c]);
-    }
-    wx = fmaxf(wx, th[0] - tl[0]);
-    wy = fmaxf(wy, th[1] - tl[1]);
+    long long k[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) k[i] = d2o(__ldg(M.tri + int64_t(i) * M.n_tris + t));
+    // float(min) = min(float): rounding to nearest is monotone
+    const float xl = float(o2d(min(k[0], min(k[3], k[6])))), xh = float(o2d(max(k[0], max(k[3], k[6]))));
+    const float yl = float(o2d(min(k[1], min(k[4], k[7])))), yh = float(o2d(max(k[1], max(k[4], k[7]))));
+    zlo = min(zlo, min(k[2], min(k[5], k[8])));
+    zhi = max(zhi, max(k[2], max(k[5], k[8])));
+    boxes[t] = make_float4(xl, xh, yl, yh);
+    lo[0] = fminf(lo[0], xl);
+    hi[0] = fmaxf(hi[0], xh);
+    lo[1] = fminf(lo[1], yl);
+    hi[1] = fmaxf(hi[1], yh);
+    wx = fmaxf(wx, xh - xl);
+    wy = fmaxf(wy, yh - yl);
+  }
+  if (zlo <= zhi) {
+    lo[2] = float(o2d(zlo));
+    hi[2] = float(o2d(zhi));
   }
   for (int o = 16; o > 0; o >>= 1) {
     wx = fmaxf(wx, __shfl_xor_sync(0xffffffffu, wx, o));
