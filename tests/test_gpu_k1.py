@@ -171,6 +171,40 @@ def test_curved_planted_cases(ctx, type_, precision):
         assert stats["fallback"] > 0
 
 
+@pytest.mark.parametrize("stream_kind", ["default", "own"])
+def test_path_buffer_overflow_reruns_only_the_path_phase(ctx, stream_kind):
+    """Curved refraction cases with FP64 side chains, solved into an 8-path
+    buffer: the solve grows the buffer and re-runs the path phase (the
+    finish kernel skips the polished brackets, the side kernel repeats its
+    chains without counting their isolation again).  The paths and the
+    isolation counters equal those of a solve with room to spare, on the
+    default stream and on a context with its own stream."""
+    from tests.test_oracle_pins import _planted_cases
+    tri, x0, x2 = _planted_cases(71, 600, 1)
+    s = _single_triangle_scene(tri, x0, x2, 1)
+    st = torch.cuda.Stream()
+    c = ctx if stream_kind == "default" else binding.Context(0, st.cuda_stream)
+    tri_d, xf, xl, eta, ty, k = _gpu_arrays(s)
+    torch.cuda.synchronize()
+    mesh, q = c.mesh(tri_d), c.queries(xf, xl, eta, ty, k)
+    chains = c.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=_dev(s.chains))
+    out = []
+    for cap in (0, 8):
+        sol = c.spoly_solve(mesh, q, chains, precision=binding.MIXED, path_capacity=cap)
+        out.append((c.spoly_paths(sol), c.spoly_stats(sol)))
+        c.spoly_solution_free(sol)
+    c.spoly_chains_free(chains)
+    (a, sa), (b, sb) = out
+    assert sa["fallback"] > 0 and a.size > 8
+    ka = sorted(zip(a["query"].tolist(), a["uv"][:, 0].round(12).tolist(), a["uv"][:, 1].round(12).tolist()))
+    kb = sorted(zip(b["query"].tolist(), b["uv"][:, 0].round(12).tolist(), b["uv"][:, 1].round(12).tolist()))
+    assert ka == kb
+    for key in ("candidates", "v_roots", "queued", "prefiltered", "polish_lost", "admissible", "fallback", "u_roots"):
+        assert sa[key] == sb[key], (key, sa[key], sb[key])
+    if c is not ctx:
+        c.close()
+
+
 def test_host_and_device_inputs_agree(ctx):
     s = scenes.reflect_scene(seed=2, n_cells=8, n_recv=12)
     a, _, _ = _run(ctx, s, binding.CHAINS_ALL, binding.MIXED, host=True)
