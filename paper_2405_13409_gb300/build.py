@@ -60,8 +60,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        logs = list(ex.map(compile_one, srcs, objs))
+    # every core, the translation units with the unrolled expansions first
+    # (they take the longest), so the build takes about as long as its slowest
+    heavy = ("k1_iso", "k1_polish", "k1_generic", "tt_sign", "noalloc")
+    order = sorted(range(len(srcs)), key=lambda i: not os.path.basename(srcs[i]).startswith(heavy))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
+        done = dict(zip(order, ex.map(compile_one, [srcs[i] for i in order], [objs[i] for i in order])))
+    logs = [done[i] for i in range(len(srcs))]
     if verbose:
         for s, log in zip(srcs, logs):
             if log:
