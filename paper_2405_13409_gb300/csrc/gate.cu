@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
       }
     }
   };
+  QueryF qc;  // the last query's FP32 data, reused while the chains share it
   for (int64_t base = int64_t(blockIdx.x) * kGateRows; base < G.n; base += int64_t(gridDim.x) * kGateRows) {
     const int64_t row = base + tid;
     const bool valid = row < G.n;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(128, 4) gate_kernel(GateParams G) {
         f[4 * j + 3] = v.w;
       }
     } else if (valid) {
-      chain_features(G.mesh, G.qv, G.chains, row, f);
+      chain_features(G.mesh, G.qv, G.chains, row, f, qc);
     } else {
 #pragma unroll
       for (int j = 0; j < kFeat; ++j) f[j] = 0.0f;

@@ -151,9 +151,29 @@ SPOLY_D void gate_features(f3 x0, f3 x2, float e0, float e1, int type, const f3 
   f[23] = type == SPOLY_T ? 1.0f : 0.0f;
 }
 
+// A query's endpoints, IORs and type in FP32, kept by a thread across the
+// chains it takes (consecutive chains usually share their query: every chain
+// of the distinct-triangle glint list does).
+struct QueryF {
+  int q = -1;
+  f3 x0, x2;
+  float e0, e1;
+  int type;
+};
+
+SPOLY_D void load_query_f(const QueryView& qv, int q, QueryF& c) {
+  if (q == c.q) return;
+  c.q = q;
+  c.x0 = {d2f(qv.x_first[3 * q]), d2f(qv.x_first[3 * q + 1]), d2f(qv.x_first[3 * q + 2])};
+  c.x2 = {d2f(qv.x_last[3 * q]), d2f(qv.x_last[3 * q + 1]), d2f(qv.x_last[3 * q + 2])};
+  c.e0 = d2f(qv.eta[3 * q]);
+  c.e1 = d2f(qv.eta[3 * q + 1]);
+  c.type = qv.types[2 * q];
+}
+
 // Features of chain `i` = (query, tri0, tri1) of a 1-bounce problem.
 SPOLY_D void chain_features(const MeshView& mesh, const QueryView& qv, const int32_t* chains, int64_t i,
-                             float (&f)[kFeat]) {
+                             float (&f)[kFeat], QueryF& qc) {
   const int q = chains[3 * i];
   const int64_t t = chains[3 * i + 1];
   const int64_t T = mesh.n_tris;
@@ -163,9 +183,14 @@ SPOLY_D void chain_features(const MeshView& mesh, const QueryView& qv, const int
     P[v] = ld3(mesh.tri, T, 3 * v, t);
     N[v] = ld3(mesh.tri, T, 9 + 3 * v, t);
   }
-  const f3 x0 = {d2f(qv.x_first[3 * q]), d2f(qv.x_first[3 * q + 1]), d2f(qv.x_first[3 * q + 2])};
-  const f3 x2 = {d2f(qv.x_last[3 * q]), d2f(qv.x_last[3 * q + 1]), d2f(qv.x_last[3 * q + 2])};
-  gate_features(x0, x2, d2f(qv.eta[3 * q]), d2f(qv.eta[3 * q + 1]), qv.types[2 * q], P, N, f);
+  load_query_f(qv, q, qc);
+  gate_features(qc.x0, qc.x2, qc.e0, qc.e1, qc.type, P, N, f);
+}
+
+SPOLY_D void chain_features(const MeshView& mesh, const QueryView& qv, const int32_t* chains, int64_t i,
+                             float (&f)[kFeat]) {
+  QueryF qc;
+  chain_features(mesh, qv, chains, i, f, qc);
 }
 
 }  // namespace spoly
