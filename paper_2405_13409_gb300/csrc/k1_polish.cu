@@ -1,5 +1,5 @@
-// FP64 polish kernel of the 1-bounce solve (path phase, Sec. 4.3), plus the
-// host launchers of the 1-bounce kernels.
+// FP64 polish and path phase kernel of the 1-bounce solve (Sec. 4.3), plus
+// the host launchers of the 1-bounce kernels.
 #include <algorithm>
 
 #include "k1_polish.cuh"

@@ -1,5 +1,5 @@
 // Per-candidate device code of the 1-bounce solve, shared by the isolation,
-// generic and polish kernels.
+// side and finish kernels.
 //
 // Per candidate (query q, triangle t), following Sec. 4.3:
 //   coefficient phase   a(u,v), b(u,v) in FP64 (Sec. 3.5 "R", "T")
@@ -7,8 +7,9 @@
 //                       T = float (mixed) or double (plain)
 //   univariate phase    r(z) = det by memoised Laplace expansion and
 //                       recursive-derivative isolation (Sec. 4.2) in T
-//   path phase          FP64: bisection of the numeric determinant near the
-//                       bracket, u from a(u, v*) = 0, Newton on (a, b),
+//   polish              FP64: the same resultant in FP64, each bracket's root
+//                       by Newton steps inside it (then bisection)
+//   path phase          FP64: u from a(u, v*) = 0, Newton on (a, b),
 //                       path-space check of Eq. eq_ch, in-triangle test.
 #pragma once
 #include "k1.cuh"
