@@ -115,7 +115,8 @@ SPOLY_D bool vertex_check(d3 xprev, d3 x, d3 xnext, d3 n, int type, double eta_i
 }
 
 // Newton on the scaled system (a, b)(w, z) = 0; accepted when the move in
-// (u, v) stays within kNewtonMove.
+// (u, v) stays within kNewtonMove.  A step below 1e-16 in (u, v) ends it
+// (the next one would move the root by less than its last bit).
 template <int DB>
 SPOLY_D void newton_ab(const K1Sys<DB>& s, double& w, double& z) {
   double ww = w, zz = z;
@@ -130,6 +131,7 @@ SPOLY_D void newton_ab(const K1Sys<DB>& s, double& w, double& z) {
     if (!isfinite(dw) || !isfinite(dz)) break;
     ww -= dw;
     zz -= dz;
+    if (fabs(dw) * s.sc.s <= 1e-16 && fabs(dz) * s.sc.t <= 1e-16) break;
   }
   if (fabs(ww - w) * s.sc.s <= kNewtonMove && fabs(zz - z) * s.sc.t <= kNewtonMove) {
     w = ww;
