@@ -1005,9 +1005,16 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   set->tt_device = false;
   e = partition();
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "chain partition"));
-  // Stage 1: isolation.  Re-run (only in synchronous mode) until the bracket
-  // queue and the side queue hold every item; each re-run grows them to the
-  // exact counts, so two passes suffice.
+  // Stage 1: isolation, and Stage 2: FP64 v-polish (in place, once) and the
+  // path phase.  In synchronous mode the isolation is re-run until the
+  // bracket queue and the side queue hold every item; each re-run grows them
+  // to the exact counts, so two passes suffice.  A synchronous solve of
+  // 1-bounce chains reads the counters once, after the finish (the finish
+  // kernels take the item counts from the device and stop at the capacities,
+  // and an overflowed pass is solved again from the start); with 2-bounce
+  // chains they are read between the stages.
+  const bool check_after_finish = !async && n2 == 0;
+  bool finished = false, have_counters = false;
   for (int attempt = 0; attempt < 3; ++attempt) {
     bind();
     e = cudaMemsetAsync(set->counters.p, 0, C_COUNT * sizeof(unsigned long long), ctx->stream);
@@ -1019,11 +1026,21 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
     }
     if (timing) cudaEventRecord(set->ev[1], ctx->stream);
     if (async && n2 == 0) break;
+    if (check_after_finish) {
+      if (n1 > 0) {
+        e = finish();
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
+      }
+      if (timing) cudaEventRecord(set->ev[2], ctx->stream);
+      finished = true;
+    }
     e = read_counters();
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "isolation"));
+    have_counters = finished;
     const int64_t queued = int64_t(set->host[C_QUEUED]);
     const int64_t side = int64_t(set->host[C_SIDE]);
     if (queued <= set->queue_cap && side <= set->side_cap) break;
+    finished = have_counters = false;
     if (attempt == 2) return bail(fail(ctx, SPOLY_ECAPACITY, "bracket queue did not converge"));
     if (side > set->side_cap) {
       if (set->side.ensure(size_t(side) * sizeof(int32_t)) != cudaSuccess)
@@ -1036,14 +1053,15 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
       set->queue_cap = queued;
     }
   }
-  // Stage 2: FP64 v-polish (in place, once) and the path phase.  Only the
-  // path phase is re-run if the path buffer overflowed: it reads the polished
-  // queue and is idempotent once its counters are reset.
-  if (n1 > 0) {
-    e = finish();
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
+  // Only the path phase is re-run if the path buffer overflowed: it reads the
+  // polished queue and is idempotent once its counters are reset.
+  if (!finished) {
+    if (n1 > 0) {
+      e = finish();
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "k1_polish"));
+    }
+    if (timing) cudaEventRecord(set->ev[2], ctx->stream);
   }
-  if (timing) cudaEventRecord(set->ev[2], ctx->stream);
   auto run_tt = [&]() -> spoly_status {
     if (n2 == 0) return SPOLY_OK;
     return solve_tt(ctx, set, mv, qv, k2_list, k2_ids, n2, opts,
@@ -1054,8 +1072,10 @@ spoly_status spoly_solve(spoly_ctx* ctx, const spoly_mesh* mesh, const spoly_que
   if (st != SPOLY_OK) return bail(st);
   if (timing) cudaEventRecord(set->ev[3], ctx->stream);
   if (!async || n2 > 0) {
-    e = read_counters();
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
+    if (!have_counters) {
+      e = read_counters();
+      if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "solve"));
+    }
     const int64_t paths = int64_t(set->host[C_ADMISSIBLE]);
     if (paths > set->path_cap) {
       if (set->paths.ensure(size_t(paths) * sizeof(spoly_path)) != cudaSuccess)

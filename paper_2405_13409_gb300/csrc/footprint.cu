@@ -48,6 +48,25 @@ SPOLY_D long long d2o(double x) {
 }
 SPOLY_D double o2d(long long o) { return __longlong_as_double(o >= 0 ? o : o ^ 0x7fffffffffffffffll); }
 
+// FP64 -> FP32, round to nearest even, with integer instructions where the
+// result is a normal float or zero (the conversion instruction runs on the
+// narrow FP64 pipe of this part); other cases take the instruction.  The
+// 29 dropped mantissa bits decide the rounding; a carry out of the mantissa
+// steps the exponent (up to infinity, as the rounding rule says).
+SPOLY_D float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+  const int e = int((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e >= 1 && e <= 254) {
+    unsigned f = (hi & 0x80000000u) | (unsigned(e) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned drop = lo & 0x1fffffffu;
+    f += (drop > 0x10000000u || (drop == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+  }
+  if ((b << 1) == 0ull) return __uint_as_float(hi & 0x80000000u);
+  return float(x);
+}
+
 __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
   float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
   long long zlo = LLONG_MAX, zhi = LLONG_MIN;  // z range, as keys (converted once per thread)
@@ -58,8 +77,8 @@ __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) k[i] = d2o(__ldg(M.tri + int64_t(i) * M.n_tris + t));
     // float(min) = min(float): rounding to nearest is monotone
-    const float xl = float(o2d(min(k[0], min(k[3], k[6])))), xh = float(o2d(max(k[0], max(k[3], k[6]))));
-    const float yl = float(o2d(min(k[1], min(k[4], k[7])))), yh = float(o2d(max(k[1], max(k[4], k[7]))));
+    const float xl = f32_rn(o2d(min(k[0], min(k[3], k[6])))), xh = f32_rn(o2d(max(k[0], max(k[3], k[6]))));
+    const float yl = f32_rn(o2d(min(k[1], min(k[4], k[7])))), yh = f32_rn(o2d(max(k[1], max(k[4], k[7]))));
     zlo = min(zlo, min(k[2], min(k[5], k[8])));
     zhi = max(zhi, max(k[2], max(k[5], k[8])));
     boxes[t] = make_float4(xl, xh, yl, yh);
@@ -71,8 +90,8 @@ __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
     wy = fmaxf(wy, yh - yl);
   }
   if (zlo <= zhi) {
-    lo[2] = float(o2d(zlo));
-    hi[2] = float(o2d(zhi));
+    lo[2] = f32_rn(o2d(zlo));
+    hi[2] = f32_rn(o2d(zhi));
   }
   for (int o = 16; o > 0; o >>= 1) {
     wx = fmaxf(wx, __shfl_xor_sync(0xffffffffu, wx, o));
@@ -92,6 +111,23 @@ __global__ void mesh_bounds_kernel(MeshView M, int* bounds, float4* boxes) {
       atomicMax(bounds + 3 + c, f2o(hi[c]));
     }
   }
+}
+
+// One wave of a grid-stride kernel of `Block` threads per block: every
+// resident block on every SM, so no block starts late and leaves a tail.  The
+// count is taken once per kernel.
+template <auto Kernel, int Block>
+int resident_grid(int num_sms) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, Kernel, Block, 0) != cudaSuccess || b < 1) {
+      (void)cudaGetLastError();
+      b = 4;
+    }
+    per_sm = b;
+  }
+  return num_sms * per_sm;
 }
 
 __global__ void init_bounds_kernel(int* bounds) {
@@ -391,11 +427,13 @@ __global__ void __launch_bounds__(256) unique_fill_kernel(const uint8_t* __restr
 __global__ void queries_shared_kernel(QueryView qv, int32_t* flag) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < qv.n; q += stride) {
-    bool same = qv.k[q] == qv.k[0] && qv.types[2 * q] == qv.types[0] && qv.types[2 * q + 1] == qv.types[1];
-    for (int c = 0; c < 3 && same; ++c)
-      same = __double_as_longlong(qv.x_first[3 * q + c]) == __double_as_longlong(qv.x_first[c]) &&
-             __double_as_longlong(qv.x_last[3 * q + c]) == __double_as_longlong(qv.x_last[c]) &&
-             __double_as_longlong(qv.eta[3 * q + c]) == __double_as_longlong(qv.eta[c]);
+    // every field compared without short-circuit, so all loads issue at once
+    bool same = (qv.k[q] == qv.k[0]) & (qv.types[2 * q] == qv.types[0]) & (qv.types[2 * q + 1] == qv.types[1]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      same &= (__double_as_longlong(qv.x_first[3 * q + c]) == __double_as_longlong(qv.x_first[c])) &
+              (__double_as_longlong(qv.x_last[3 * q + c]) == __double_as_longlong(qv.x_last[c])) &
+              (__double_as_longlong(qv.eta[3 * q + c]) == __double_as_longlong(qv.eta[c]));
     if (!same) flag[0] = 1;
   }
 }
@@ -539,16 +577,20 @@ cudaError_t fp_unique_build(const MeshView& M, const QueryView& qv, float4* boxe
   if (e == cudaSuccess) e = cudaMemsetAsync(mark, 0, size_t(M.n_tris), st);
   if (e != cudaSuccess) return e;
   init_bounds_kernel<<<1, 32, 0, st>>>(bounds_dev);
-  mesh_bounds_kernel<<<num_sms * 4, 256, 0, st>>>(M, bounds_dev, boxes);
+  mesh_bounds_kernel<<<resident_grid<mesh_bounds_kernel, 256>(num_sms), 256, 0, st>>>(M, bounds_dev, boxes);
   grid_setup_kernel<<<1, 1, 0, st>>>(bounds_dev, g, info);
-  grid_insert_dev_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, info, L.cell_count, L.cell_off, entries, entries_cap, 0);
+  const int gi = resident_grid<grid_insert_dev_kernel, 256>(num_sms);
+  grid_insert_dev_kernel<<<gi, 256, 0, st>>>(M, boxes, info, L.cell_count, L.cell_off, entries, entries_cap, 0);
   if ((e = exclusive_scan<int>(L.cell_count, L.cell_off, n_cells, L, st)) != cudaSuccess) return e;
   grid_total_kernel<<<1, 1, 0, st>>>(L.cell_count, L.cell_off, n_cells, info);
   if ((e = cudaMemsetAsync(L.cell_count, 0, size_t(n_cells) * 4, st)) != cudaSuccess) return e;
-  grid_insert_dev_kernel<<<num_sms * 8, 256, 0, st>>>(M, boxes, info, L.cell_count, L.cell_off, entries, entries_cap, 1);
-  footprint_mark_kernel<<<num_sms * 8, 128, 0, st>>>(boxes, info, bounds_dev, make_cam(cam_host), n_pixels,
-                                                     L.cell_count, L.cell_off, entries, entries_cap, mark);
-  const int64_t gq = std::min<int64_t>((qv.n + 255) / 256, int64_t(num_sms) * 4);
+  grid_insert_dev_kernel<<<gi, 256, 0, st>>>(M, boxes, info, L.cell_count, L.cell_off, entries, entries_cap, 1);
+  // One block of 128 pixels each (up to 64 per SM): footprints differ in
+  // size, and the block scheduler balances them better than a fixed share.
+  const int64_t gm = std::max<int64_t>(1, std::min<int64_t>((n_pixels + 127) / 128, int64_t(num_sms) * 64));
+  footprint_mark_kernel<<<unsigned(gm), 128, 0, st>>>(boxes, info, bounds_dev, make_cam(cam_host), n_pixels,
+                                                      L.cell_count, L.cell_off, entries, entries_cap, mark);
+  const int64_t gq = std::max<int64_t>(1, std::min<int64_t>((qv.n + 255) / 256, int64_t(num_sms) * 16));
   queries_shared_kernel<<<unsigned(gq), 256, 0, st>>>(qv, &info->differ);
   const int64_t gu = std::min<int64_t>((M.n_tris + 255) / 256, int64_t(num_sms) * 8);
   unique_fill_kernel<<<unsigned(gu), 256, 0, st>>>(mark, M.n_tris, 0, &info->n_unique, out);
@@ -581,7 +623,7 @@ cudaError_t fp_fill(const float4* boxes, const FpGrid& g, void* scratch, const i
 cudaError_t compute_mesh_bounds(const MeshView& M, int* bounds_dev, float* bounds_host, float4* boxes, int num_sms,
                                 cudaStream_t st) {
   init_bounds_kernel<<<1, 32, 0, st>>>(bounds_dev);
-  mesh_bounds_kernel<<<num_sms * 4, 256, 0, st>>>(M, bounds_dev, boxes);
+  mesh_bounds_kernel<<<resident_grid<mesh_bounds_kernel, 256>(num_sms), 256, 0, st>>>(M, bounds_dev, boxes);
   int b[6];
   cudaError_t e = cudaMemcpyAsync(b, bounds_dev, sizeof(b), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

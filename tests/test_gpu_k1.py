@@ -205,6 +205,40 @@ def test_path_buffer_overflow_reruns_only_the_path_phase(ctx, stream_kind):
         c.close()
 
 
+@pytest.mark.parametrize("precision", [binding.PLAIN_FP64, binding.MIXED])
+def test_queue_overflow_solves_again_with_grown_queues(ctx, precision):
+    """The curved refraction cases repeated 40 times in one chain list: more
+    brackets than a fresh solution's first bracket queue holds (a quarter of
+    the chain count plus 4,096), so the first pass overflows and the solve
+    runs again with grown queues.  The paths are 40 copies of those of one
+    solve of the cases, and every counter is 40 times theirs."""
+    from tests.test_oracle_pins import _planted_cases
+    tri, x0, x2 = _planted_cases(71, 600, 1)
+    s = _single_triangle_scene(tri, x0, x2, 1)
+    tri_d, xf, xl, eta, ty, k = _gpu_arrays(s)
+    torch.cuda.synchronize()
+    mesh, q = ctx.mesh(tri_d), ctx.queries(xf, xl, eta, ty, k)
+    reps = 40
+    out = []
+    for ch in (s.chains, np.tile(s.chains, (reps, 1))):
+        chains = ctx.spoly_build_chains(mesh, q, binding.CHAINS_EXPLICIT, explicit=_dev(ch))
+        sol = ctx.spoly_solve(mesh, q, chains, precision=precision)
+        out.append((ctx.spoly_paths(sol), ctx.spoly_stats(sol)))
+        ctx.spoly_solution_free(sol)
+        ctx.spoly_chains_free(chains)
+    (a, sa), (b, sb) = out
+    n = reps * s.chains.shape[0]
+    assert reps * sa["queued"] > n // 4 + 4096 and a.size > 0
+
+    def key(p):
+        return sorted(zip(p["query"].tolist(), p["uv"][:, 0].round(12).tolist(), p["uv"][:, 1].round(12).tolist()))
+
+    assert key(b) == sorted(key(a) * reps)
+    for name in ("candidates", "v_roots", "queued", "prefiltered", "polish_lost", "admissible", "fallback",
+                 "u_roots", "flagged"):
+        assert sb[name] == reps * sa[name], (name, sa[name], sb[name])
+
+
 def test_host_and_device_inputs_agree(ctx):
     s = scenes.reflect_scene(seed=2, n_cells=8, n_recv=12)
     a, _, _ = _run(ctx, s, binding.CHAINS_ALL, binding.MIXED, host=True)
